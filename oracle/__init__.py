@@ -1,0 +1,140 @@
+"""CPU FP64 oracle for P1 quadrature element integration -- TEST INFRASTRUCTURE.
+
+Only the test suite, ``__graft_entry__.smoke()`` and the benchmark's CPU-baseline
+leg may import this package. The product path (the CUDA library and its binding)
+never does. The arithmetic lives in ``fem_oracle.c`` (plain C, FP64, one cell at a
+time); this module compiles it with gcc and calls it through ctypes.
+
+Functions take numpy arrays in the layouts documented in ``fem_oracle.c`` and
+return new float64 arrays.
+"""
+
+from __future__ import annotations
+
+import ctypes
+import os
+import platform
+import subprocess
+import tempfile
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "fem_oracle.c")
+_LIB = None
+
+
+def lib_path() -> str:
+    return os.path.join(_HERE, f"liboracle_{platform.machine()}.so")
+
+
+def build(force: bool = False) -> str:
+    """Compile fem_oracle.c into a shared library (OpenMP if the compiler has it)."""
+    out = lib_path()
+    if not force and os.path.exists(out) and os.path.getmtime(out) >= os.path.getmtime(_SRC):
+        return out
+    base = ["gcc", "-O2", "-ffp-contract=off", "-fPIC", "-shared", "-std=c11", _SRC, "-lm"]
+    fd, tmp = tempfile.mkstemp(suffix=".so", dir=_HERE)
+    os.close(fd)
+    try:
+        r = subprocess.run(base[:1] + ["-fopenmp"] + base[1:] + ["-o", tmp], capture_output=True, text=True)
+        if r.returncode != 0:
+            r = subprocess.run(base + ["-o", tmp], capture_output=True, text=True)
+        if r.returncode != 0:
+            raise RuntimeError(f"oracle build failed:\n{r.stderr}")
+        os.replace(tmp, out)
+    finally:
+        if os.path.exists(tmp):
+            os.unlink(tmp)
+    return out
+
+
+def _lib():
+    global _LIB
+    if _LIB is None:
+        lib = ctypes.CDLL(build())
+        P = ctypes.c_void_p
+        i64 = ctypes.c_int64
+        ci = ctypes.c_int
+        lib.oracle_laplacian.argtypes = [ci, i64, i64, P, P, P, P, ci, P, P, P]
+        lib.oracle_elasticity.argtypes = [ci, i64, i64, P, P, P, P, P, ci, P, P, P]
+        lib.oracle_adjoint_laplacian.argtypes = [ci, i64, i64, P, P, P, P, ci, P, P, P, P, P]
+        for f in (lib.oracle_laplacian, lib.oracle_elasticity, lib.oracle_adjoint_laplacian):
+            f.restype = ci
+        lib.oracle_num_threads.restype = ci
+        _LIB = lib
+    return _LIB
+
+
+def _f64(a):
+    return np.ascontiguousarray(a, dtype=np.float64)
+
+
+def _ptr(a):
+    return a.ctypes.data_as(ctypes.c_void_p) if a is not None else None
+
+
+class OracleError(RuntimeError):
+    pass
+
+
+def _check(st):
+    if st != 0:
+        raise OracleError({-1: "bad argument", -5: "bad mesh"}.get(st, f"status {st}"))
+
+
+def num_threads() -> int:
+    return int(_lib().oracle_num_threads())
+
+
+def laplacian(coords, conn, u, K, qpts, qw) -> np.ndarray:
+    coords, u, K, qpts, qw = map(_f64, (coords, u, K, qpts, qw))
+    conn = np.ascontiguousarray(conn, dtype=np.int32)
+    dim, V = coords.shape
+    C = conn.shape[1]
+    nq = qw.shape[0]
+    out = np.zeros((dim + 1, C), dtype=np.float64)
+    _check(_lib().oracle_laplacian(dim, C, V, _ptr(coords), _ptr(conn), _ptr(u), _ptr(K), nq,
+                                   _ptr(qpts), _ptr(qw), _ptr(out)))
+    return out
+
+
+def elasticity(coords, conn, u, lam, mu, qpts, qw) -> np.ndarray:
+    coords, u, lam, mu, qpts, qw = map(_f64, (coords, u, lam, mu, qpts, qw))
+    conn = np.ascontiguousarray(conn, dtype=np.int32)
+    dim, V = coords.shape
+    C = conn.shape[1]
+    nq = qw.shape[0]
+    out = np.zeros(((dim + 1) * dim, C), dtype=np.float64)
+    _check(_lib().oracle_elasticity(dim, C, V, _ptr(coords), _ptr(conn), _ptr(u), _ptr(lam), _ptr(mu),
+                                    nq, _ptr(qpts), _ptr(qw), _ptr(out)))
+    return out
+
+
+def adjoint_laplacian(coords, conn, u, K, qpts, qw, lam_adj):
+    """Returns (dK [n_q][C], du [V]) for J = sum lambda . r."""
+    coords, u, K, qpts, qw, lam_adj = map(_f64, (coords, u, K, qpts, qw, lam_adj))
+    conn = np.ascontiguousarray(conn, dtype=np.int32)
+    dim, V = coords.shape
+    C = conn.shape[1]
+    nq = qw.shape[0]
+    dK = np.zeros((nq, C), dtype=np.float64)
+    du = np.zeros(V, dtype=np.float64)
+    _check(_lib().oracle_adjoint_laplacian(dim, C, V, _ptr(coords), _ptr(conn), _ptr(u), _ptr(K), nq,
+                                           _ptr(qpts), _ptr(qw), _ptr(lam_adj), _ptr(dK), _ptr(du)))
+    return dK, du
+
+
+# convenience wrappers over a workloads.Case (the oracle does not import workloads;
+# it reads the attributes by name)
+def residual_for(case) -> np.ndarray:
+    m, r = case.mesh, case.rule
+    if case.physics == "laplacian":
+        return laplacian(m.coords, m.conn, case.u, case.K, r.points, r.weights)
+    return elasticity(m.coords, m.conn, case.u, case.lam, case.mu, r.points, r.weights)
+
+
+def adjoint_for(case, lam_adj=None):
+    m, r = case.mesh, case.rule
+    return adjoint_laplacian(m.coords, m.conn, case.u, case.K, r.points, r.weights,
+                             case.adj if lam_adj is None else lam_adj)
