@@ -1,0 +1,560 @@
+#!/usr/bin/env python
+"""Benchmark: batched P1 quadrature element integration on GB300.
+
+Headline workload: the 3D P1 Laplacian with variable coefficient on the unit cube as
+64^3 hexes x 6 = 1,572,864 jittered tets (interior jitter +-0.15h), 4-point degree-2
+rule, K ~ lognormal(0,1) per quadrature point, nodal u ~ U[-1,1]. One step = one
+element-residual evaluation of the whole mesh (gather, geometry, quadrature phase,
+basis phase) in the FP32-mixed form; the float64 form is timed beside it.
+
+Timing: W warm-up steps, then K steps, each launched after an L2 flush (a read of a
+512 MiB buffer, more than the 129 MB L2), each bracketed by CUDA events on the
+launching stream; barrier + synchronize around the timed loop; max over ranks.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+                    [--rows all|none] [--no-cpu-baseline]
+
+Rank 0 prints one JSON line. With N > 1 (torchrun), every rank integrates its own
+copy of the workload (independent problems, no data-path collective): weak scaling.
+"""
+
+from __future__ import annotations
+
+import argparse
+import datetime as _dt
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import workloads  # noqa: E402
+from paper_1607_04245_gb300 import perfmodel  # noqa: E402
+
+METRIC = "cells/s and HBM GB/s (% of GB300 peak), FP32 vs FP64 at stated error; served p99"
+WORKLOAD = "3D P1 Laplacian, variable coefficient: 64^3 hexes x 6 = 1,572,864 jittered tets, 4-pt degree-2 rule"
+HEADLINE_CELLS = 1572864
+FLUSH_BYTES = 512 << 20
+TOL = {"fp64": 1e-12, "mixed": 2e-5, "fp32": 1e-3}
+
+
+# ----------------------------------------------------------------------------- helpers
+
+
+def algorithmic_bytes(physics, dim, prec, C, V, nq):
+    """Compulsory HBM bytes of one residual launch: every cell-indexed array once,
+    every vertex once."""
+    s = 8 if prec == "fp64" else 4
+    ncomp = 1 if physics == "laplacian" else dim
+    ncoef = 1 if physics == "laplacian" else 2
+    return ((dim + 1) * 4 * C + ncoef * nq * s * C + (dim + 1) * ncomp * s * C + dim * 8 * V + ncomp * s * V)
+
+
+def adjoint_bytes(dim, prec, C, V, nq):
+    """Element kernel (conn, K, lambda, coords, u in; dK, per-element dJ/du out) plus the
+    vertex gather (lists and per-element values in, dJ/du out)."""
+    s = 8 if prec == "fp64" else 4
+    nb = dim + 1
+    elem = nb * 4 * C + nq * s * C + nb * s * C + dim * 8 * V + s * V + nq * s * C + nb * s * C
+    gather = (V + 1) * 4 + nb * C * 4 + nb * s * C + s * V
+    return elem + gather
+
+
+def load_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(p) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+def src_hash():
+    h = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_1607_04245_gb300", "csrc")
+    for f in sorted(os.listdir(csrc)):
+        with open(os.path.join(csrc, f), "rb") as fh:
+            h.update(f.encode() + fh.read())
+    with open(os.path.join(ROOT, "include", "fem.h"), "rb") as fh:
+        h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def recorded_traffic(kernel_key):
+    """DRAM bytes per launch from a committed ncu summary, if it was taken on the current
+    kernel sources (profiles/dram_traffic.txt: 'key src=<hash> bytes=<n>' lines)."""
+    p = os.path.join(ROOT, "profiles", "dram_traffic.txt")
+    if not os.path.exists(p):
+        return None
+    cur = src_hash()
+    for line in open(p):
+        parts = line.split()
+        if len(parts) >= 3 and parts[0] == kernel_key:
+            kv = dict(x.split("=", 1) for x in parts[1:] if "=" in x)
+            if kv.get("src") == cur:
+                return float(kv["bytes"])
+    return None
+
+
+class ClockSampler:
+    """nvidia-smi samples (100 ms) of SM clock, power and throttle reasons."""
+
+    FIELDS = ("timestamp,uuid,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, uuid=None):
+        self.uuid = uuid
+        self.proc = None
+        self.file = None
+
+    def start(self):
+        try:
+            self.file = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+            self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                                          "-lms", "100"], stdout=self.file, stderr=subprocess.DEVNULL)
+            time.sleep(0.6)  # nvidia-smi start-up
+        except Exception:
+            self.proc = None
+        return self
+
+    def stop(self, t_begin, t_end):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.file.flush()
+        rows = []
+        with open(self.file.name) as f:
+            for line in f:
+                p = [x.strip() for x in line.split(",")]
+                if len(p) < 9:
+                    continue
+                try:
+                    ts = _dt.datetime.strptime(p[0], "%Y/%m/%d %H:%M:%S.%f").timestamp()
+                except ValueError:
+                    continue
+                if self.uuid and p[1] != self.uuid:
+                    continue
+                rows.append((ts, p))
+        os.unlink(self.file.name)
+        inside = [p for ts, p in rows if t_begin - 0.05 <= ts <= t_end + 0.05] or [p for _, p in rows[-3:]]
+        if not inside:
+            return None
+
+        def num(x):
+            try:
+                return float(x)
+            except ValueError:
+                return None
+
+        sm = [num(p[2]) for p in inside if num(p[2]) is not None]
+        reasons = set()
+        for p in inside:
+            for name, v in zip(("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"), p[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(name)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": num(inside[0][3]),
+                "power_w_max": max((num(p[4]) or 0.0) for p in inside), "samples": len(inside),
+                "reasons": sorted(reasons)}
+
+
+# ----------------------------------------------------------------------------- distributed
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    return int(os.environ.get("RANK", "0")), int(os.environ.get("LOCAL_RANK", "0")), ws
+
+
+def dist_init(ws, backend):
+    import torch.distributed as dist
+
+    if ws > 1 and not dist.is_initialized():
+        dist.init_process_group(backend=backend)
+    return dist
+
+
+def barrier(dist, ws):
+    if ws > 1:
+        dist.barrier()
+
+
+def max_over_ranks(dist, ws, x, device):
+    if ws == 1:
+        return x
+    import torch
+
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+# ----------------------------------------------------------------------------- timing
+
+
+def timed_steps(step_fn, steps, warmup, stream, flush, dist=None, ws=1, sampler=None):
+    """Per-step device time (ms) of step_fn with an L2 flush before every step."""
+    import torch
+
+    for _ in range(warmup):
+        flush()
+        step_fn()
+    torch.cuda.synchronize()
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+    if sampler:
+        sampler.start()
+    barrier(dist, ws)
+    torch.cuda.synchronize()
+    t0 = time.time()
+    for a, b in evs:
+        flush()
+        a.record(stream)
+        step_fn()
+        b.record(stream)
+    torch.cuda.synchronize()
+    barrier(dist, ws)
+    t1 = time.time()
+    clocks = sampler.stop(t0, t1) if sampler else None
+    ms = [a.elapsed_time(b) for a, b in evs]
+    return ms, t1 - t0, clocks
+
+
+def make_flush(device):
+    import torch
+
+    buf = torch.ones(FLUSH_BYTES // 4, dtype=torch.float32, device=device)
+    sink = torch.empty((), dtype=torch.float32, device=device)
+
+    def flush():
+        torch.sum(buf, out=sink)  # a full read of the buffer evicts the working set from L2
+
+    return flush
+
+
+# ----------------------------------------------------------------------------- rows
+
+
+def device_case(case, prec, device):
+    import torch
+
+    import paper_1607_04245_gb300 as fem
+
+    c = case if prec == "fp64" else case.rounded_to_f32()
+    dt = fem.value_dtype(prec)
+    f = lambda a: torch.from_numpy(np.ascontiguousarray(a)).to(device=device, dtype=dt)
+    d = {"coords": torch.from_numpy(c.mesh.coords).to(device), "conn": torch.from_numpy(c.mesh.conn).to(device),
+         "u": f(c.u)}
+    for k in ("K", "lam", "mu", "adj"):
+        if getattr(c, k) is not None:
+            d[k] = f(getattr(c, k))
+    return c, d
+
+
+def residual_fn(c, d, prec, stream):
+    import paper_1607_04245_gb300 as fem
+
+    q = c.rule
+    C = c.n_cells
+    dt = fem.value_dtype(prec)
+    import torch
+
+    out = torch.empty(((c.dim + 1) * c.n_comp, C), dtype=dt, device=d["coords"].device)
+    if c.physics == "laplacian":
+        return out, lambda: fem.fem_integrate_laplacian(d["coords"], d["conn"], d["u"], d["K"], q.points, q.weights,
+                                                        out=out, prec=prec, stream=stream)
+    return out, lambda: fem.fem_integrate_elasticity(d["coords"], d["conn"], d["u"], d["lam"], d["mu"], q.points,
+                                                     q.weights, out=out, prec=prec, stream=stream)
+
+
+def rel_err(gpu, ref):
+    g = gpu.double().cpu().numpy()
+    return float(np.abs(g - ref).max() / np.abs(ref).max())
+
+
+def measure_residual(case, prec, device, stream, flush, steps, warmup, peak, oracle_mod=None, dist=None, ws=1,
+                     sampler=None):
+    import torch
+
+    c, d = device_case(case, prec, device)
+    out, fn = residual_fn(c, d, prec, stream)
+    with torch.cuda.stream(stream):
+        ms, wall, clocks = timed_steps(fn, steps, warmup, stream, flush, dist, ws, sampler)
+    t = statistics.mean(ms) * 1e-3
+    nbytes = algorithmic_bytes(c.physics, c.dim, prec, c.n_cells, c.n_verts, c.rule.n_q)
+    row = {"physics": c.physics, "dim": c.dim, "prec": prec, "cells": c.n_cells, "verts": c.n_verts,
+           "ms_per_launch": round(statistics.mean(ms), 6), "ms_median": round(statistics.median(ms), 6),
+           "cells_per_s": c.n_cells / t, "alg_bytes_per_launch": nbytes, "alg_gbs": nbytes / t / 1e9,
+           "hbm_frac_of_measured": nbytes / t / 1e9 / peak,
+           "paper_model_gflops": perfmodel.flops_per_cell(c.dim, c.rule.n_q, c.n_comp) * c.n_cells / t / 1e9}
+    if oracle_mod is not None:
+        torch.cuda.synchronize()
+        row["rel_maxnorm_err_vs_oracle"] = rel_err(out, oracle_mod.residual_for(c))
+        row["tolerance"] = TOL[prec]
+    return row, ms, wall, clocks
+
+
+def measure_adjoint(case, prec, device, stream, flush, steps, warmup, peak, oracle_mod=None):
+    import torch
+
+    import paper_1607_04245_gb300 as fem
+
+    c, d = device_case(case, prec, device)
+    q = c.rule
+    with torch.cuda.stream(stream):
+        ptr, idx = fem.fem_build_node2cell(d["conn"], c.n_verts, stream=stream)
+        dt = fem.value_dtype(prec)
+        dK = torch.empty((q.n_q, c.n_cells), dtype=dt, device=device)
+        du = torch.empty(c.n_verts, dtype=dt, device=device)
+        scratch = torch.empty((c.dim + 1, c.n_cells), dtype=dt, device=device)
+        fn = lambda: fem.fem_adjoint_laplacian(d["coords"], d["conn"], d["u"], d["K"], q.points, q.weights, d["adj"],
+                                               ptr, idx, dK=dK, du=du, scratch=scratch, prec=prec, stream=stream)
+        ms, _, _ = timed_steps(fn, steps, warmup, stream, flush)
+    t = statistics.mean(ms) * 1e-3
+    nbytes = adjoint_bytes(c.dim, prec, c.n_cells, c.n_verts, q.n_q)
+    row = {"physics": "laplacian_adjoint", "dim": c.dim, "prec": prec, "cells": c.n_cells,
+           "ms_per_step": round(statistics.mean(ms), 6), "cells_per_s": c.n_cells / t,
+           "alg_bytes_per_step": nbytes, "alg_gbs": nbytes / t / 1e9, "hbm_frac_of_measured": nbytes / t / 1e9 / peak,
+           "kernels_per_step": 2}
+    if oracle_mod is not None:
+        torch.cuda.synchronize()
+        rK, ru = oracle_mod.adjoint_for(c)
+        row["rel_err_dK"] = rel_err(dK, rK)
+        row["rel_err_du"] = rel_err(du, ru)
+        row["tolerance"] = TOL[prec]
+    return row
+
+
+def measure_e2e(case, prec, device, steps, warmup):
+    """Same metric through the host-buffer API: H2D of all inputs, kernel, D2H of the result."""
+    import torch
+
+    from paper_1607_04245_gb300.host import HostIntegrator
+
+    c = case if prec == "fp64" else case.rounded_to_f32()
+    import paper_1607_04245_gb300 as fem
+
+    dt = fem.value_dtype(prec)
+    hi = HostIntegrator(device)
+    coords_h = hi.pinned("coords", c.mesh.coords, torch.float64)
+    conn_h = hi.pinned("conn", c.mesh.conn, torch.int32)
+    u_h = hi.pinned("u", c.u, dt)
+    K_h = hi.pinned("K", c.K, dt)
+    step = lambda: hi.laplacian(coords_h, conn_h, u_h, K_h, c.rule.points, c.rule.weights, prec=prec)
+    for _ in range(warmup):
+        step()
+    torch.cuda.synchronize()
+    hi.h2d_bytes = hi.d2h_bytes = 0
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record(hi.stream)
+    for _ in range(steps):
+        step()
+    b.record(hi.stream)
+    b.synchronize()
+    t = a.elapsed_time(b) * 1e-3 / steps
+    return {"value": c.n_cells / t, "unit": "cells/s", "h2d_bytes_per_step": hi.h2d_bytes // steps,
+            "d2h_bytes_per_step": hi.d2h_bytes // steps, "ms_per_step": t * 1e3}
+
+
+def cpu_baseline(case, min_seconds=10.0, max_reps=200):
+    import oracle
+
+    oracle.build()
+    reps, t0 = 0, time.perf_counter()
+    while reps < max_reps:
+        oracle.residual_for(case)
+        reps += 1
+        if time.perf_counter() - t0 >= min_seconds:
+            break
+    dt = time.perf_counter() - t0
+    return {"value": case.n_cells * reps / dt, "unit": "cells/s", "cores": oracle.num_threads(), "kind": "oracle",
+            "sample": f"the full {case.n_cells}-cell workload x {reps} repetitions ({dt:.1f} s, float64, "
+                      f"OpenMP over cells)"}
+
+
+# ----------------------------------------------------------------------------- arms
+
+
+def run_reference(args):
+    """The CPU oracle timed as it stands on the host cores (rank 0 only)."""
+    rank, _, ws = dist_env()
+    if rank != 0:
+        return 0
+    import oracle
+
+    oracle.build()
+    case = workloads.laplacian_cube_case(HEADLINE_CELLS).rounded_to_f32()
+    m = case.mesh
+    # calibrate, then size each step so the whole run stays around a minute
+    t0 = time.perf_counter()
+    oracle.residual_for(case)
+    rate = case.n_cells / (time.perf_counter() - t0)
+    budget = 60.0 / max(1, args.steps + args.warmup)
+    S = int(min(case.n_cells, max(4096, rate * budget)))
+    S -= S % 4
+    nslices = max(1, min(8, case.n_cells // S))
+    slices = []
+    for i in range(nslices):
+        a = i * S
+        conn = np.ascontiguousarray(m.conn[:, a:a + S])
+        K = np.ascontiguousarray(case.K[:, a:a + S])
+        slices.append((conn, K))
+    q = case.rule
+
+    def step(i):
+        conn, K = slices[i % nslices]
+        oracle.laplacian(m.coords, conn, case.u, K, q.points, q.weights)
+
+    for i in range(args.warmup):
+        step(i)
+    t0 = time.perf_counter()
+    for i in range(args.steps):
+        step(i)
+    dt = time.perf_counter() - t0
+    value = S * args.steps / dt
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "cells/s", "n_gpus": ws,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt / args.steps * 1e3,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "cells": HEADLINE_CELLS, "sample_cells_per_step": S,
+                       "form": "float64 CPU oracle on float32-rounded inputs"},
+            "cpu_baseline": {"value": value, "unit": "cells/s", "cores": oracle.num_threads(), "kind": "oracle",
+                             "sample": f"{S} cells per step (slices of the {HEADLINE_CELLS}-cell workload)"},
+            "e2e": {"value": value, "unit": "cells/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+            "gpu_launches": 0}
+    print(json.dumps(line))
+    return 0
+
+
+def run_ours(args):
+    import torch
+
+    import paper_1607_04245_gb300 as fem
+
+    rank, local_rank, ws = dist_env()
+    if ws != args.gpus:
+        ws = max(ws, 1)
+    torch.cuda.set_device(local_rank)
+    device = torch.device("cuda", local_rank)
+    dist = dist_init(ws, "nccl")
+    fem.lib()
+    peak, peak_kind = load_peaks()
+    import oracle
+
+    oracle.build()
+    stream = torch.cuda.Stream(device=device)
+    flush = make_flush(device)
+    uuid = None
+    try:
+        uuid = "GPU-" + str(torch.cuda.get_device_properties(device).uuid)
+    except Exception:
+        pass
+
+    case = workloads.laplacian_cube_case(HEADLINE_CELLS)
+
+    # headline: FP32-mixed residual
+    row, ms, wall, clocks = measure_residual(case, "mixed", device, stream, flush, args.steps, args.warmup, peak,
+                                             oracle if rank == 0 else None, dist, ws, ClockSampler(uuid))
+    t_max = max_over_ranks(dist, ws, sum(ms) * 1e-3, device)
+    ms_per_step = t_max / args.steps * 1e3
+    value = ws * case.n_cells * args.steps / t_max
+
+    fp64_steps = max(3, args.steps // 20)
+    row64, _, _, _ = measure_residual(case, "fp64", device, stream, flush, fp64_steps, args.warmup, peak,
+                                      oracle if rank == 0 else None)
+
+    if rank != 0:
+        barrier(dist, ws)
+        return 0
+
+    nbytes = row["alg_bytes_per_launch"]
+    achieved = nbytes / (row["ms_per_launch"] * 1e-3) / 1e9
+    traffic = recorded_traffic("lap3d_mixed")
+    roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                "traffic": traffic, "peak_kind": f"{peak_kind} copy bandwidth (MEASURED_PEAKS.json hbm_gbs)"
+                if peak_kind == "measured" else "fallback 6800 GB/s",
+                "kernel": "lap_kernel<3, FP32_MIXED, 4 cells/thread>",
+                "alg_bytes_per_launch": nbytes,
+                "alg_bytes_per_cell": "conn 16 + K 16 + out 16 + (V/C)(coords 24 + u 4)"}
+
+    rows = {"fp64": row64}
+    if args.rows == "all":
+        rsteps = max(3, args.steps // 50)
+        rows["fp32_ablation"] = measure_residual(case, "fp32", device, stream, flush, rsteps, args.warmup, peak,
+                                                 oracle)[0]
+        rows["lap2d_8192_fp64"] = measure_residual(workloads.laplacian_square_case(), "fp64", device, stream, flush,
+                                                   rsteps, args.warmup, peak, oracle)[0]
+        for dim in (2, 3):
+            el = workloads.elasticity_case(dim)
+            for prec in ("mixed", "fp64"):
+                rows[f"elast{dim}d_{prec}"] = measure_residual(el, prec, device, stream, flush, rsteps, args.warmup,
+                                                               peak, oracle)[0]
+        adj = workloads.adjoint_case(HEADLINE_CELLS)
+        for prec in ("mixed", "fp64"):
+            rows[f"adjoint3d_{prec}"] = measure_adjoint(adj, prec, device, stream, flush, rsteps, args.warmup, peak,
+                                                        oracle)
+        sweep = {}
+        for e in range(16, 24):
+            sc = workloads.laplacian_cube_case(1 << e)
+            r = measure_residual(sc, "mixed", device, stream, flush, max(3, rsteps // 2), args.warmup, peak)[0]
+            sweep[str(1 << e)] = {"cells_per_s": r["cells_per_s"], "alg_gbs": r["alg_gbs"],
+                                  "hbm_frac_of_measured": r["hbm_frac_of_measured"], "ms": r["ms_per_launch"]}
+        rows["sweep_lap3d_mixed"] = sweep
+
+    e2e = measure_e2e(case, "mixed", device, max(3, args.steps // 100), 3)
+
+    line = {"metric": METRIC, "value": value, "unit": "cells/s", "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "cells": case.n_cells, "verts": case.n_verts,
+                       "form": "fp32_mixed (float32 values, float64 coordinates split to float32 pairs, "
+                               "compensated quadrature sum, float64 fallback for badly shaped cells)",
+                       "l2": "flushed before every timed step (read of a 512 MiB buffer)",
+                       "parallelism": f"replicas x{ws}"},
+            "hbm_gbs": row["alg_gbs"], "hbm_frac_of_measured_peak": row["hbm_frac_of_measured"],
+            "hbm_frac_of_nominal_8tbs": row["alg_gbs"] / 8000.0,
+            "paper_model_gflops": row["paper_model_gflops"],
+            "rel_maxnorm_err_vs_oracle": row.get("rel_maxnorm_err_vs_oracle"),
+            "fp64": {"cells_per_s": row64["cells_per_s"], "ms_per_launch": row64["ms_per_launch"],
+                     "alg_gbs": row64["alg_gbs"], "hbm_frac_of_measured": row64["hbm_frac_of_measured"],
+                     "rel_maxnorm_err_vs_oracle": row64.get("rel_maxnorm_err_vs_oracle")},
+            "speedup_fp32_mixed_over_fp64": row["cells_per_s"] / row64["cells_per_s"],
+            "roofline": roofline,
+            "cpu_baseline": cpu_baseline(case) if (ws == 1 and not args.no_cpu_baseline) else None,
+            "e2e": e2e, "gpu_launches": args.steps,
+            "clocks": clocks, "rows": rows}
+    print(json.dumps(line))
+    barrier(dist, ws)
+    return 0
+
+
+def main(argv=None):
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10000)
+    ap.add_argument("--warmup", type=int, default=20)
+    ap.add_argument("--impl", choices=("ours", "reference"), default="ours")
+    ap.add_argument("--rows", choices=("all", "none"), default="all")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args(argv)
+    if args.warmup < 3:
+        ap.error("--warmup must be >= 3")
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,205 @@
+/*
+ * fem.h -- C ABI of libfem: batched quadrature-based P1 element integration on GB300.
+ *
+ * Method: Knepley, Rupp, Terrel, "Finite Element Integration with Quadrature on the
+ * GPU". For every cell of a simplex mesh the library evaluates the bracket of Eq. 2
+ * with f0 = 0,
+ *
+ *     r_{e,b} = sum_q w_q |det J_e| (J_e^{-T} grad_ref phi_b(xi_q)) . f1(u, grad u)(x_q),
+ *
+ * producing unassembled per-cell element vectors. The pointwise functions are the
+ * two of Sec. 6: the variable-coefficient Laplacian f1 = K grad u (Sec. 2) and linear
+ * elasticity, generalised from the paper's symmetric-gradient listing to the Lame
+ * stress f1 = lambda tr(eps) I + 2 mu eps, eps = (grad u + grad u^T)/2.
+ * The affine Jacobian J = [x_1 - x_0 | ... | x_d - x_0], its determinant and its
+ * inverse are computed in-kernel from the vertex coordinates (the paper loads them
+ * precomputed, Sec. 3 and Appendix).
+ *
+ * Conventions shared by every entry point:
+ *  - All array arguments are DEVICE pointers owned by the caller, except qpts and qw,
+ *    which are small HOST tables copied into the launch. No entry point allocates
+ *    device memory or synchronises the stream: work is enqueued on `stream`
+ *    (0 = the legacy default stream) and the call returns after the launch.
+ *  - Layouts are structure-of-arrays with the cell (or vertex) index fastest:
+ *        coords [dim][n_verts]        always float64
+ *        conn   [dim+1][n_cells]      int32 vertex ids in [0, n_verts)
+ *        u      [n_verts] (Laplacian) or [dim][n_verts] (elasticity)
+ *        K, lam, mu [n_q][n_cells]    one coefficient per quadrature point
+ *        out    [(dim+1)*n_comp][n_cells], row b*n_comp + k (n_comp = 1 or dim)
+ *    Value arrays (u, K, lam, mu, out, lambda, dK, du, scratch) are float64 for
+ *    FEM_FP64 and float32 for FEM_FP32_MIXED and FEM_FP32.
+ *  - Reference simplex: vertices 0, e_1, ..., e_d. qpts [n_q][dim] are reference
+ *    coordinates and qw [n_q] the weights (they sum to 1/d! for an exact rule).
+ *    The P1 reference gradients are constant, so only the weights enter the
+ *    arithmetic; qpts may be NULL and, when given, must lie in the reference simplex.
+ *  - Errors are returned synchronously (argument checks, launch failures); an error
+ *    leaves the outputs untouched or partially written. fem_last_error() gives a
+ *    thread-local message for the most recent failing call. No exception crosses
+ *    the ABI. n_cells = 0 is a valid no-op.
+ *  - Vertex ids are clamped into [0, n_verts) in-kernel, so malformed connectivity
+ *    cannot make a kernel read out of bounds; it gives meaningless values instead.
+ *    fem_check_mesh() detects such input.
+ *  - Vectorised (128-bit) loads are used when every cell-indexed row is 16-byte
+ *    aligned (n_cells a multiple of 4 and 16-byte aligned base pointers); other
+ *    inputs run the same kernels with scalar loads, still on the GPU.
+ */
+#ifndef FEM_H
+#define FEM_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct CUstream_st *fem_stream; /* identical to cudaStream_t */
+
+typedef enum {
+    FEM_OK = 0,
+    FEM_ERR_ARG = -1,       /* bad scalar argument or NULL pointer */
+    FEM_ERR_SHAPE = -2,     /* sizes out of the supported range */
+    FEM_ERR_CUDA = -3,      /* a CUDA launch or runtime call failed */
+    FEM_ERR_OOM = -4,       /* a caller-provided buffer is too small */
+    FEM_ERR_BADMESH = -5,   /* reported by fem_check_mesh */
+    FEM_ERR_TIMEOUT = -6,   /* a bounded device-side wait gave up */
+    FEM_ERR_UNSUPPORTED = -7
+} fem_status;
+
+typedef enum {
+    /* every value and every operation in float64 */
+    FEM_FP64 = 0,
+    /* values stored in float32; coordinates read as float64 and split into float32
+     * (hi, lo) pairs so the Jacobian columns are exact to float32 rounding; geometry
+     * and physics in float32; the quadrature sum of the element vector compensated
+     * (TwoSum/TwoProduct); cells failing the shape test |det J| >= tau prod_j |J e_j|
+     * (Hadamard ratio) or giving a non-finite result are recomputed in float64 */
+    FEM_FP32_MIXED = 1,
+    /* ablation: float32 values, coordinates rounded to float32 before the Jacobian,
+     * plain float32 sums, no float64 fallback */
+    FEM_FP32 = 2
+} fem_precision;
+
+#define FEM_MAX_QPTS 32
+
+/* ---------------------------------------------------------------------------------
+ * fem_integrate_laplacian -- element residuals of the variable-coefficient Laplacian
+ * (Eq. 2 with f0 = 0, f1 = K grad u; Sec. 2 and the Sec. 6 Laplacian listing).
+ *   dim        2 (triangles) or 3 (tetrahedra)
+ *   n_cells    C >= 0, n_verts V >= 1 (when C > 0); (dim+1)*C and V below 2^31
+ *   coords     [dim][V] float64
+ *   conn       [dim+1][C] int32
+ *   u          [V] nodal values
+ *   K          [n_q][C] coefficient at each quadrature point of each cell
+ *   n_q        1..FEM_MAX_QPTS; qpts [n_q][dim] (host, may be NULL), qw [n_q] (host)
+ *   elem_out   [dim+1][C] element vectors (written)
+ * Returns FEM_OK, FEM_ERR_ARG, FEM_ERR_SHAPE or FEM_ERR_CUDA.
+ * ------------------------------------------------------------------------------- */
+fem_status fem_integrate_laplacian(int dim, int64_t n_cells, int64_t n_verts, const double *coords,
+                                   const int32_t *conn, const void *u, const void *K, int n_q,
+                                   const double *qpts, const double *qw, void *elem_out,
+                                   fem_precision prec, fem_stream stream);
+
+/* ---------------------------------------------------------------------------------
+ * fem_integrate_elasticity -- element residuals of linear elasticity (Eq. 2 with f0 = 0
+ * and the vector form of Eq. 1: f1 = lambda tr(eps) I + 2 mu eps; with lambda = 0,
+ * mu = 1/2 this is the Sec. 6 elasticity listing).
+ *   u          [dim][V] nodal displacement components
+ *   lam, mu    [n_q][C] Lame parameters at each quadrature point
+ *   elem_out   [(dim+1)*dim][C], row b*dim + k = component k of basis function b
+ * Other arguments and returns as fem_integrate_laplacian.
+ * ------------------------------------------------------------------------------- */
+fem_status fem_integrate_elasticity(int dim, int64_t n_cells, int64_t n_verts, const double *coords,
+                                    const int32_t *conn, const void *u, const void *lam, const void *mu,
+                                    int n_q, const double *qpts, const double *qw, void *elem_out,
+                                    fem_precision prec, fem_stream stream);
+
+/* ---------------------------------------------------------------------------------
+ * fem_set_mixed_threshold / fem_get_mixed_threshold -- the shape-test threshold tau of
+ * FEM_FP32_MIXED (default 0.05). tau = 0 sends no cell to the float64 path, tau > 1
+ * sends every cell. Process-wide; set it between calls, not during them.
+ * ------------------------------------------------------------------------------- */
+fem_status fem_set_mixed_threshold(double tau);
+double fem_get_mixed_threshold(void);
+
+/* ---------------------------------------------------------------------------------
+ * fem_check_mesh -- validation pass (not on the hot path). Writes into the DEVICE
+ * array counts[4] (int64, overwritten):
+ *   counts[0] = number of connectivity entries outside [0, V)
+ *   counts[1] = number of cells with det J <= 0 (or non-finite) in float64
+ *   counts[2] = number of cells FEM_FP32_MIXED sends to its float64 path
+ *   counts[3] = number of cells with det J < 0
+ * Read counts after synchronising the stream.
+ * ------------------------------------------------------------------------------- */
+fem_status fem_check_mesh(int dim, int64_t n_cells, int64_t n_verts, const double *coords,
+                          const int32_t *conn, int64_t *counts, fem_stream stream);
+
+/* ---------------------------------------------------------------------------------
+ * fem_adjoint_laplacian -- gradient of the scalar J(u, K) = sum_e sum_b lambda_{e,b} r_{e,b}
+ * with r the Laplacian element residual above (not in the paper):
+ *   dK[q][e] = dJ/dK_{e,q} = w_q |det J_e| (sum_b lambda_{e,b} G_b) . grad u_e
+ *   du[n]    = dJ/du_n = sum over (e, a) with conn[a][e] = n of
+ *              (sum_q w_q |det J_e| K_{e,q}) G_a . (sum_b lambda_{e,b} G_b)
+ * where G_b = J_e^{-T} grad_ref phi_b. The per-element part of du equals the
+ * Laplacian element residual of the field lambda_e (the element operator is
+ * symmetric); it is written to `scratch` and then summed per vertex through the
+ * vertex-to-cell lists of fem_build_node2cell, in a fixed order (bitwise
+ * reproducible, no atomics).
+ *   lambda     [dim+1][C]            adjoint weights per element dof
+ *   dK         [n_q][C]              written
+ *   du         [V]                   written
+ *   node_ptr   [V+1], node_idx [(dim+1)*C]  from fem_build_node2cell for this conn
+ *   scratch    [dim+1][C] value type, caller-owned workspace (contents overwritten)
+ * Other arguments as fem_integrate_laplacian.
+ * ------------------------------------------------------------------------------- */
+fem_status fem_adjoint_laplacian(int dim, int64_t n_cells, int64_t n_verts, const double *coords,
+                                 const int32_t *conn, const void *u, const void *K, int n_q,
+                                 const double *qpts, const double *qw, const void *lambda, void *dK,
+                                 void *du, const int32_t *node_ptr, const int32_t *node_idx,
+                                 void *scratch, fem_precision prec, fem_stream stream);
+
+/* ---------------------------------------------------------------------------------
+ * fem_build_node2cell -- vertex-to-(cell, local vertex) lists: the transpose of conn,
+ * i.e. the assembly operator E_e of Eq. 2 stored as lists. Built on the device,
+ * deterministically:
+ *   node_ptr [V+1]            node_ptr[n] .. node_ptr[n+1] delimit vertex n's entries
+ *   node_idx [(dim+1)*C]      entries e*(dim+1) + a (cell e, local vertex a), sorted
+ *                             ascending within each vertex, i.e. in cell order
+ *   work     int32 workspace of fem_node2cell_work_size(V) entries
+ * All three are caller-owned device arrays. conn must be valid (see fem_check_mesh).
+ * ------------------------------------------------------------------------------- */
+int64_t fem_node2cell_work_size(int64_t n_verts);
+fem_status fem_build_node2cell(int dim, int64_t n_cells, int64_t n_verts, const int32_t *conn,
+                               int32_t *node_ptr, int32_t *node_idx, int32_t *work, fem_stream stream);
+
+/* ---------------------------------------------------------------------------------
+ * fem_gather_nodes -- the assembly sum E^T of Eq. 2 for element vectors:
+ *   out[k][n] = sum over the entries e*(dim+1) + a of vertex n (in list order) of
+ *               elem[(a*n_comp + k)*C + e]
+ * elem is [(dim+1)*n_comp][C] (the layout of the integrate outputs), out is
+ * [n_comp][V]; both of the value type of prec. Fixed summation order, no atomics.
+ * ------------------------------------------------------------------------------- */
+fem_status fem_gather_nodes(int dim, int n_comp, int64_t n_cells, int64_t n_verts, const void *elem,
+                            const int32_t *node_ptr, const int32_t *node_idx, void *out,
+                            fem_precision prec, fem_stream stream);
+
+/* ---------------------------------------------------------------------------------
+ * Throughput probes for the roofline (not part of the method): each thread runs
+ * `iters` iterations of 8 independent dependent chains of the chosen operation and
+ * writes one value to out[thread] (float64 or float32 as the kind's type).
+ *   kind 0: float64 FMA   kind 1: float32 FMA   kind 2: float64 -> float32 conversion
+ *   kind 3: 32-bit integer add/logic (LOP3 + IADD pairs)
+ * n_threads > 0, multiple of 256.
+ * ------------------------------------------------------------------------------- */
+fem_status fem_probe(int kind, int64_t n_threads, int iters, void *out, fem_stream stream);
+
+/* status text and the thread-local message of the last failing call */
+const char *fem_status_string(fem_status st);
+const char *fem_last_error(void);
+/* library version string */
+const char *fem_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* FEM_H */

@@ -1,0 +1,267 @@
+"""Thin Python binding of libfem's C ABI (include/fem.h).
+
+Every function here has the name of the C entry point it calls and does argument
+marshalling only: it checks tensor devices, dtypes, shapes and contiguity, derives
+the sizes, allocates outputs with torch when the caller passes none, and hands raw
+pointers and the current CUDA stream to the library. All arithmetic runs in the
+library's CUDA kernels. There is no fallback: if libfem.so is missing or the call
+fails, a RuntimeError is raised.
+"""
+
+from __future__ import annotations
+
+import ctypes
+import os
+from typing import Optional, Tuple, Union
+
+import numpy as np
+import torch
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "libfem.so")
+
+FEM_FP64, FEM_FP32_MIXED, FEM_FP32 = 0, 1, 2
+_PREC_NAMES = {"fp64": FEM_FP64, "mixed": FEM_FP32_MIXED, "fp32_mixed": FEM_FP32_MIXED, "fp32": FEM_FP32}
+FEM_MAX_QPTS = 32
+
+_lib = None
+
+
+class FemError(RuntimeError):
+    def __init__(self, fn: str, status: int, message: str):
+        super().__init__(f"{fn} failed with status {status}: {message}")
+        self.status = status
+
+
+def lib():
+    """The loaded libfem (raises if it has not been built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"libfem.so not found at {LIB_PATH}: build it with __graft_entry__.build() "
+                               "or python -m paper_1607_04245_gb300.build")
+        L = ctypes.CDLL(LIB_PATH)
+        P, i64, ci, cd = ctypes.c_void_p, ctypes.c_int64, ctypes.c_int, ctypes.c_double
+        sig = {
+            "fem_integrate_laplacian": [ci, i64, i64, P, P, P, P, ci, P, P, P, ci, P],
+            "fem_integrate_elasticity": [ci, i64, i64, P, P, P, P, P, ci, P, P, P, ci, P],
+            "fem_adjoint_laplacian": [ci, i64, i64, P, P, P, P, ci, P, P, P, P, P, P, P, P, ci, P],
+            "fem_build_node2cell": [ci, i64, i64, P, P, P, P, P],
+            "fem_gather_nodes": [ci, ci, i64, i64, P, P, P, P, ci, P],
+            "fem_check_mesh": [ci, i64, i64, P, P, P, P],
+            "fem_probe": [ci, i64, ci, P, P],
+            "fem_set_mixed_threshold": [cd],
+        }
+        for name, args in sig.items():
+            f = getattr(L, name)
+            f.argtypes = args
+            f.restype = ci
+        L.fem_get_mixed_threshold.argtypes = []
+        L.fem_get_mixed_threshold.restype = cd
+        L.fem_node2cell_work_size.argtypes = [i64]
+        L.fem_node2cell_work_size.restype = i64
+        for name in ("fem_last_error", "fem_version"):
+            getattr(L, name).restype = ctypes.c_char_p
+        L.fem_status_string.argtypes = [ci]
+        L.fem_status_string.restype = ctypes.c_char_p
+        _lib = L
+    return _lib
+
+
+def _check(fn: str, st: int):
+    if st != 0:
+        raise FemError(fn, st, lib().fem_last_error().decode())
+
+
+def precision(p: Union[int, str]) -> int:
+    if isinstance(p, str):
+        return _PREC_NAMES[p.lower()]
+    if p not in (FEM_FP64, FEM_FP32_MIXED, FEM_FP32):
+        raise ValueError(f"unknown precision {p}")
+    return int(p)
+
+
+def value_dtype(prec) -> torch.dtype:
+    return torch.float64 if precision(prec) == FEM_FP64 else torch.float32
+
+
+def _stream(stream) -> int:
+    if stream is None:
+        return torch.cuda.current_stream().cuda_stream
+    if isinstance(stream, torch.cuda.Stream):
+        return stream.cuda_stream
+    return int(stream)
+
+
+def _dev(t: Optional[torch.Tensor], name: str, dtype: torch.dtype, shape=None, device=None) -> int:
+    if t is None:
+        raise ValueError(f"{name} is required")
+    if not t.is_cuda:
+        raise ValueError(f"{name} must be a CUDA tensor")
+    if device is not None and t.device != device:
+        raise ValueError(f"{name} is on {t.device}, expected {device}")
+    if t.dtype != dtype:
+        raise ValueError(f"{name} must be {dtype}, got {t.dtype}")
+    if not t.is_contiguous():
+        raise ValueError(f"{name} must be contiguous")
+    if shape is not None and tuple(t.shape) != tuple(shape):
+        raise ValueError(f"{name} has shape {tuple(t.shape)}, expected {tuple(shape)}")
+    return t.data_ptr() if t.numel() else 0
+
+
+class _HostTable:
+    """A float64 host table kept alive for the duration of a call."""
+
+    def __init__(self, a, shape=None, name="table"):
+        if a is None:
+            self.arr, self.ptr = None, None
+            return
+        if isinstance(a, torch.Tensor):
+            a = a.detach().cpu().numpy()
+        self.arr = np.ascontiguousarray(a, dtype=np.float64)
+        if shape is not None and self.arr.shape != tuple(shape):
+            raise ValueError(f"{name} has shape {self.arr.shape}, expected {tuple(shape)}")
+        self.ptr = self.arr.ctypes.data
+
+
+def _mesh_sizes(coords: torch.Tensor, conn: torch.Tensor):
+    if coords.dim() != 2 or conn.dim() != 2:
+        raise ValueError("coords must be (dim, V) and conn (dim+1, C)")
+    dim, V = coords.shape
+    if conn.shape[0] != dim + 1:
+        raise ValueError(f"conn must have dim+1 = {dim + 1} rows")
+    return int(dim), int(V), int(conn.shape[1])
+
+
+def fem_integrate_laplacian(coords, conn, u, K, qpts, qw, out=None, prec="mixed", stream=None) -> torch.Tensor:
+    """Element residuals [dim+1][C] of the variable-coefficient Laplacian."""
+    p = precision(prec)
+    dt = value_dtype(p)
+    dim, V, C = _mesh_sizes(coords, conn)
+    nq = int(np.asarray(qw).shape[0]) if not isinstance(qw, torch.Tensor) else int(qw.shape[0])
+    dev = coords.device
+    if out is None:
+        out = torch.empty((dim + 1, C), dtype=dt, device=dev)
+    qp, w = _HostTable(qpts, (nq, dim), "qpts"), _HostTable(qw, (nq,), "qw")
+    st = lib().fem_integrate_laplacian(
+        dim, C, V, _dev(coords, "coords", torch.float64, device=dev), _dev(conn, "conn", torch.int32, device=dev),
+        _dev(u, "u", dt, (V,), dev), _dev(K, "K", dt, (nq, C), dev), nq, qp.ptr, w.ptr,
+        _dev(out, "out", dt, (dim + 1, C), dev), p, _stream(stream))
+    _check("fem_integrate_laplacian", st)
+    return out
+
+
+def fem_integrate_elasticity(coords, conn, u, lam, mu, qpts, qw, out=None, prec="mixed", stream=None) -> torch.Tensor:
+    """Element residuals [(dim+1)*dim][C] of linear elasticity (row b*dim + k)."""
+    p = precision(prec)
+    dt = value_dtype(p)
+    dim, V, C = _mesh_sizes(coords, conn)
+    nq = int(np.asarray(qw).shape[0]) if not isinstance(qw, torch.Tensor) else int(qw.shape[0])
+    dev = coords.device
+    if out is None:
+        out = torch.empty(((dim + 1) * dim, C), dtype=dt, device=dev)
+    qp, w = _HostTable(qpts, (nq, dim), "qpts"), _HostTable(qw, (nq,), "qw")
+    st = lib().fem_integrate_elasticity(
+        dim, C, V, _dev(coords, "coords", torch.float64, device=dev), _dev(conn, "conn", torch.int32, device=dev),
+        _dev(u, "u", dt, (dim, V), dev), _dev(lam, "lam", dt, (nq, C), dev), _dev(mu, "mu", dt, (nq, C), dev),
+        nq, qp.ptr, w.ptr, _dev(out, "out", dt, ((dim + 1) * dim, C), dev), p, _stream(stream))
+    _check("fem_integrate_elasticity", st)
+    return out
+
+
+def fem_build_node2cell(conn, n_verts: int, node_ptr=None, node_idx=None, work=None, stream=None):
+    """Vertex-to-(cell, local vertex) lists: (node_ptr [V+1], node_idx [(dim+1)*C])."""
+    dim = int(conn.shape[0]) - 1
+    C = int(conn.shape[1])
+    dev = conn.device
+    if node_ptr is None:
+        node_ptr = torch.empty(n_verts + 1, dtype=torch.int32, device=dev)
+    if node_idx is None:
+        node_idx = torch.empty((dim + 1) * C, dtype=torch.int32, device=dev)
+    if work is None:
+        work = torch.empty(max(1, lib().fem_node2cell_work_size(n_verts)), dtype=torch.int32, device=dev)
+    if work.numel() < lib().fem_node2cell_work_size(n_verts):
+        raise ValueError("work is too small")
+    st = lib().fem_build_node2cell(dim, C, n_verts, _dev(conn, "conn", torch.int32, device=dev),
+                                   _dev(node_ptr, "node_ptr", torch.int32, (n_verts + 1,), dev),
+                                   _dev(node_idx, "node_idx", torch.int32, ((dim + 1) * C,), dev),
+                                   _dev(work, "work", torch.int32, None, dev), _stream(stream))
+    _check("fem_build_node2cell", st)
+    return node_ptr, node_idx
+
+
+def fem_adjoint_laplacian(coords, conn, u, K, qpts, qw, lam_adj, node_ptr, node_idx, dK=None, du=None,
+                          scratch=None, prec="mixed", stream=None) -> Tuple[torch.Tensor, torch.Tensor]:
+    """Gradient of J = sum lambda . r: returns (dK [n_q][C], du [V])."""
+    p = precision(prec)
+    dt = value_dtype(p)
+    dim, V, C = _mesh_sizes(coords, conn)
+    nq = int(np.asarray(qw).shape[0]) if not isinstance(qw, torch.Tensor) else int(qw.shape[0])
+    dev = coords.device
+    dK = torch.empty((nq, C), dtype=dt, device=dev) if dK is None else dK
+    du = torch.empty(V, dtype=dt, device=dev) if du is None else du
+    scratch = torch.empty((dim + 1, C), dtype=dt, device=dev) if scratch is None else scratch
+    qp, w = _HostTable(qpts, (nq, dim), "qpts"), _HostTable(qw, (nq,), "qw")
+    st = lib().fem_adjoint_laplacian(
+        dim, C, V, _dev(coords, "coords", torch.float64, device=dev), _dev(conn, "conn", torch.int32, device=dev),
+        _dev(u, "u", dt, (V,), dev), _dev(K, "K", dt, (nq, C), dev), nq, qp.ptr, w.ptr,
+        _dev(lam_adj, "lambda", dt, (dim + 1, C), dev), _dev(dK, "dK", dt, (nq, C), dev),
+        _dev(du, "du", dt, (V,), dev), _dev(node_ptr, "node_ptr", torch.int32, (V + 1,), dev),
+        _dev(node_idx, "node_idx", torch.int32, ((dim + 1) * C,), dev),
+        _dev(scratch, "scratch", dt, (dim + 1, C), dev), p, _stream(stream))
+    _check("fem_adjoint_laplacian", st)
+    return dK, du
+
+
+def fem_gather_nodes(elem, node_ptr, node_idx, n_verts: int, dim: int, out=None, prec="mixed", stream=None):
+    """Assembly E^T of element vectors [(dim+1)*n_comp][C] into nodal values [n_comp][V]."""
+    p = precision(prec)
+    dt = value_dtype(p)
+    rows, C = int(elem.shape[0]), int(elem.shape[1])
+    n_comp = rows // (dim + 1)
+    if n_comp * (dim + 1) != rows:
+        raise ValueError("elem rows must be a multiple of dim+1")
+    dev = elem.device
+    out = torch.empty((n_comp, n_verts), dtype=dt, device=dev) if out is None else out
+    st = lib().fem_gather_nodes(dim, n_comp, C, n_verts, _dev(elem, "elem", dt, None, dev),
+                                _dev(node_ptr, "node_ptr", torch.int32, (n_verts + 1,), dev),
+                                _dev(node_idx, "node_idx", torch.int32, ((dim + 1) * C,), dev),
+                                _dev(out, "out", dt, (n_comp, n_verts), dev), p, _stream(stream))
+    _check("fem_gather_nodes", st)
+    return out
+
+
+def fem_check_mesh(coords, conn, counts=None, stream=None) -> torch.Tensor:
+    """Device int64[4]: bad vertex ids, degenerate cells, mixed-form fallback cells, inverted cells."""
+    dim, V, C = _mesh_sizes(coords, conn)
+    dev = coords.device
+    counts = torch.empty(4, dtype=torch.int64, device=dev) if counts is None else counts
+    st = lib().fem_check_mesh(dim, C, V, _dev(coords, "coords", torch.float64, device=dev),
+                              _dev(conn, "conn", torch.int32, device=dev),
+                              _dev(counts, "counts", torch.int64, (4,), dev), _stream(stream))
+    _check("fem_check_mesh", st)
+    return counts
+
+
+def fem_probe(kind: int, n_threads: int, iters: int, out=None, stream=None) -> torch.Tensor:
+    dt = torch.float64 if kind == 0 else torch.float32
+    out = torch.empty(n_threads, dtype=dt, device="cuda") if out is None else out
+    st = lib().fem_probe(kind, n_threads, iters, _dev(out, "out", dt, (n_threads,)), _stream(stream))
+    _check("fem_probe", st)
+    return out
+
+
+def fem_set_mixed_threshold(tau: float) -> None:
+    _check("fem_set_mixed_threshold", lib().fem_set_mixed_threshold(float(tau)))
+
+
+def fem_get_mixed_threshold() -> float:
+    return float(lib().fem_get_mixed_threshold())
+
+
+def fem_version() -> str:
+    return lib().fem_version().decode()
+
+
+def fem_status_string(st: int) -> str:
+    return lib().fem_status_string(int(st)).decode()

@@ -1,0 +1,203 @@
+// fem_cell.cuh -- per-cell device arithmetic shared by the integration kernels.
+//
+// Geometry of a P1 simplex (reference vertices 0, e_1, ..., e_d):
+//   columns of the Jacobian   e_j = x_j - x_0                  (j = 1..d)
+//   adjugate rows             n_j = det(J) * (row j of J^{-1})
+//       2D: n_1 = (e_2y, -e_2x), n_2 = (-e_1y, e_1x)
+//       3D: n_1 = e_2 x e_3, n_2 = e_3 x e_1, n_3 = e_1 x e_2
+//   determinant               det J = e_1 . n_1
+// so the physical basis gradients are G_j = J^{-T} grad_ref phi_j = n_j / det J for
+// j >= 1 and G_0 = -(G_1 + ... + G_d). All kernels work with n_j and det J and divide
+// once per cell.
+#pragma once
+
+#include <cfloat>
+#include <type_traits>
+
+#include "fem_internal.cuh"
+
+namespace fem {
+
+template <int P>
+using val_t = typename std::conditional<P == FEM_FP64, double, float>::type;
+
+// ------------------------------------------------------------------ row access (cell-indexed arrays)
+
+template <int CPT>
+__device__ __forceinline__ void load_row(const int32_t *p, int32_t (&v)[CPT]) {
+    if constexpr (CPT == 4) {
+        int4 t = ld_stream(reinterpret_cast<const int4 *>(p));
+        v[0] = t.x, v[1] = t.y, v[2] = t.z, v[3] = t.w;
+    } else {
+#pragma unroll
+        for (int i = 0; i < CPT; ++i) v[i] = ld_stream(p + i);
+    }
+}
+
+template <int CPT>
+__device__ __forceinline__ void load_row(const float *p, float (&v)[CPT]) {
+    if constexpr (CPT == 4) {
+        float4 t = ld_stream(reinterpret_cast<const float4 *>(p));
+        v[0] = t.x, v[1] = t.y, v[2] = t.z, v[3] = t.w;
+    } else {
+#pragma unroll
+        for (int i = 0; i < CPT; ++i) v[i] = ld_stream(p + i);
+    }
+}
+
+template <int CPT>
+__device__ __forceinline__ void load_row(const double *p, double (&v)[CPT]) {
+    if constexpr (CPT == 4) {
+        double2 a = ld_stream(reinterpret_cast<const double2 *>(p));
+        double2 b = ld_stream(reinterpret_cast<const double2 *>(p) + 1);
+        v[0] = a.x, v[1] = a.y, v[2] = b.x, v[3] = b.y;
+    } else {
+#pragma unroll
+        for (int i = 0; i < CPT; ++i) v[i] = ld_stream(p + i);
+    }
+}
+
+template <int CPT>
+__device__ __forceinline__ void store_row(float *p, const float (&v)[CPT]) {
+    if constexpr (CPT == 4) {
+        __stcs(reinterpret_cast<float4 *>(p), make_float4(v[0], v[1], v[2], v[3]));
+    } else {
+#pragma unroll
+        for (int i = 0; i < CPT; ++i) __stcs(p + i, v[i]);
+    }
+}
+
+template <int CPT>
+__device__ __forceinline__ void store_row(double *p, const double (&v)[CPT]) {
+    if constexpr (CPT == 4) {
+        __stcs(reinterpret_cast<double2 *>(p), make_double2(v[0], v[1]));
+        __stcs(reinterpret_cast<double2 *>(p) + 1, make_double2(v[2], v[3]));
+    } else {
+#pragma unroll
+        for (int i = 0; i < CPT; ++i) __stcs(p + i, v[i]);
+    }
+}
+
+// ------------------------------------------------------------------ geometry
+
+template <int DIM, class T>
+__device__ __forceinline__ T adjugate_rows(const T (&e)[DIM][DIM], T (&n)[DIM][DIM]) {
+    if constexpr (DIM == 2) {
+        n[0][0] = e[1][1], n[0][1] = -e[1][0];
+        n[1][0] = -e[0][1], n[1][1] = e[0][0];
+        return e[0][0] * e[1][1] - e[0][1] * e[1][0];
+    } else {
+#pragma unroll
+        for (int j = 0; j < 3; ++j) {
+            const T *a = e[(j + 1) % 3], *b = e[(j + 2) % 3];
+            n[j][0] = a[1] * b[2] - a[2] * b[1];
+            n[j][1] = a[2] * b[0] - a[0] * b[2];
+            n[j][2] = a[0] * b[1] - a[1] * b[0];
+        }
+        return e[0][0] * n[0][0] + e[0][1] * n[0][1] + e[0][2] * n[0][2];
+    }
+}
+
+template <int DIM, class T>
+__device__ __forceinline__ T dotv(const T *a, const T *b) {
+    T s = a[0] * b[0];
+#pragma unroll
+    for (int i = 1; i < DIM; ++i) s += a[i] * b[i];
+    return s;
+}
+
+// Float64 Jacobian columns of a cell from the coordinate arrays.
+template <int DIM>
+__device__ __forceinline__ void columns_f64(const double *const (&X)[DIM], const uint32_t (&v)[DIM + 1],
+                                            double (&e)[DIM][DIM]) {
+    double x0[DIM];
+#pragma unroll
+    for (int k = 0; k < DIM; ++k) x0[k] = ld_gather(X[k] + v[0]);
+#pragma unroll
+    for (int j = 0; j < DIM; ++j)
+#pragma unroll
+        for (int k = 0; k < DIM; ++k) e[j][k] = ld_gather(X[k] + v[j + 1]) - x0[k];
+}
+
+// Float32 Jacobian columns from float64 coordinates split into (hi, lo) pairs:
+// e_jk = (hi_jk - hi_0k) + (lo_jk - lo_0k); exact up to float32 rounding of the result.
+template <int DIM>
+__device__ __forceinline__ void columns_mixed(const double *const (&X)[DIM], const uint32_t (&v)[DIM + 1],
+                                              float (&e)[DIM][DIM]) {
+    float hi[DIM + 1][DIM], lo[DIM + 1][DIM];
+#pragma unroll
+    for (int b = 0; b <= DIM; ++b)
+#pragma unroll
+        for (int k = 0; k < DIM; ++k) {
+            double x = ld_gather(X[k] + v[b]);
+            split_f64(static_cast<uint32_t>(__double2loint(x)), static_cast<uint32_t>(__double2hiint(x)),
+                      hi[b][k], lo[b][k]);
+        }
+#pragma unroll
+    for (int j = 0; j < DIM; ++j)
+#pragma unroll
+        for (int k = 0; k < DIM; ++k) e[j][k] = fmaf(lo[j + 1][k] - lo[0][k], 0x1p-23f, hi[j + 1][k] - hi[0][k]);
+}
+
+// Float32 Jacobian columns from coordinates rounded to float32 (FP32 ablation).
+template <int DIM>
+__device__ __forceinline__ void columns_f32(const double *const (&X)[DIM], const uint32_t (&v)[DIM + 1],
+                                            float (&e)[DIM][DIM]) {
+    float x[DIM + 1][DIM];
+#pragma unroll
+    for (int b = 0; b <= DIM; ++b)
+#pragma unroll
+        for (int k = 0; k < DIM; ++k) {
+            double d = ld_gather(X[k] + v[b]);
+            x[b][k] = round_f64_to_f32(static_cast<uint32_t>(__double2loint(d)),
+                                       static_cast<uint32_t>(__double2hiint(d)));
+        }
+#pragma unroll
+    for (int j = 0; j < DIM; ++j)
+#pragma unroll
+        for (int k = 0; k < DIM; ++k) e[j][k] = x[j + 1][k] - x[0][k];
+}
+
+// Shape test of the mixed form: det^2 >= tau^2 prod_j |e_j|^2 (Hadamard ratio >= tau),
+// with det^2 inside float32's normal range; failing cells take the float64 path.
+template <int DIM>
+__device__ __forceinline__ bool shape_ok(const float (&e)[DIM][DIM], float det, float tau2) {
+    float p = dotv<DIM>(e[0], e[0]);
+#pragma unroll
+    for (int j = 1; j < DIM; ++j) p *= dotv<DIM>(e[j], e[j]);
+    float d2 = det * det;
+    return d2 >= fmaxf(tau2 * p, FLT_MIN) && d2 <= FLT_MAX;
+}
+
+// ------------------------------------------------------------------ quadrature sums
+
+// sum_q w_q c_q, plain (FMA chain) -- float64 form and float32 ablation
+template <class T>
+struct PlainSum {
+    T s;
+    __device__ __forceinline__ void first(T w, T c) { s = w * c; }
+    __device__ __forceinline__ void add(T w, T c) { s = fma(w, c, s); }
+    __device__ __forceinline__ T value() const { return s; }
+    __device__ __forceinline__ double value_f64() const { return static_cast<double>(s); }
+};
+
+// sum_q w_q c_q compensated: Dot2 (Ogita, Rump, Oishi 2005) with TwoProduct and TwoSum;
+// the result is as accurate as if computed in twice the working precision.
+struct Dot2Sum {
+    float s, c;
+    __device__ __forceinline__ void first(float w, float x) { two_prod(w, x, s, c); }
+    __device__ __forceinline__ void add(float w, float x) {
+        float p, pe, se;
+        two_prod(w, x, p, pe);
+        two_sum(s, p, s, se);
+        c += pe + se;
+    }
+    __device__ __forceinline__ float value() const { return s + c; }
+    __device__ __forceinline__ double value_f64() const { return static_cast<double>(s) + static_cast<double>(c); }
+};
+
+template <int P>
+using qsum_t = typename std::conditional<P == FEM_FP64, PlainSum<double>,
+                                         typename std::conditional<P == FEM_FP32_MIXED, Dot2Sum, PlainSum<float>>::type>::type;
+
+}  // namespace fem

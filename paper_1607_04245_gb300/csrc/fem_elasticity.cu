@@ -1,0 +1,216 @@
+// fem_elasticity.cu -- element residual of P1 linear elasticity.
+//
+// Eq. 2 with f0 = 0 in its vector form (Sec. 2: f1 becomes a tensor) and the Lame
+// stress f1 = lambda tr(eps) I + 2 mu eps, eps = (grad u + grad u^T)/2. For P1 the
+// displacement gradient is constant on the cell: grad u = H / det J with
+//     H[k][i] = sum_{j>=1} (u_{j,k} - u_{0,k}) n_j[i]
+// (n_j the adjugate rows, fem_cell.cuh). The quadrature sum of the stress is
+//     sum_q w_q sigma_q = T / det J,   T = Lbar tr(H) I + Mbar (H + H^T),
+//     Lbar = sum_q w_q lambda_q,  Mbar = sum_q w_q mu_q,
+// and the basis phase gives, for every basis function b and component k,
+//     r_{b,k} = sum_q w_q |det J| sum_i sigma_q[k][i] G_b[i] = (T n_b)_k / |det J|,
+// with r_0 = -(r_1 + ... + r_d) per component.
+#include "fem_cell.cuh"
+
+namespace fem {
+
+struct ElArgs {
+    const double *X[3];
+    const int32_t *conn;
+    const void *u;  // [dim][V]
+    const void *lam;
+    const void *mu;
+    void *out;  // [(dim+1)*dim][C]
+    int64_t C;
+    uint32_t V;
+    float tau2;
+    QuadW w;
+};
+
+template <int DIM, class T>
+__device__ __forceinline__ void el_element(const T (&n)[DIM][DIM], T det, const T (&uu)[DIM + 1][DIM], T lbar,
+                                           T mbar, T (&r)[DIM + 1][DIM]) {
+    T H[DIM][DIM];
+#pragma unroll
+    for (int k = 0; k < DIM; ++k)
+#pragma unroll
+        for (int i = 0; i < DIM; ++i) H[k][i] = T(0);
+#pragma unroll
+    for (int j = 0; j < DIM; ++j)
+#pragma unroll
+        for (int k = 0; k < DIM; ++k) {
+            T du = uu[j + 1][k] - uu[0][k];
+#pragma unroll
+            for (int i = 0; i < DIM; ++i) H[k][i] = fma(du, n[j][i], H[k][i]);
+        }
+    T tr = H[0][0];
+#pragma unroll
+    for (int k = 1; k < DIM; ++k) tr += H[k][k];
+    T s;
+    if constexpr (std::is_same<T, double>::value) s = T(1) / fabs(det);
+    else s = __fdividef(1.0f, fabsf(det));
+    const T ltr = lbar * tr;
+    T Tm[DIM][DIM];
+#pragma unroll
+    for (int k = 0; k < DIM; ++k)
+#pragma unroll
+        for (int i = 0; i < DIM; ++i) Tm[k][i] = s * (mbar * (H[k][i] + H[i][k]) + (k == i ? ltr : T(0)));
+#pragma unroll
+    for (int k = 0; k < DIM; ++k) r[0][k] = T(0);
+#pragma unroll
+    for (int b = 1; b <= DIM; ++b)
+#pragma unroll
+        for (int k = 0; k < DIM; ++k) {
+            r[b][k] = dotv<DIM>(Tm[k], n[b - 1]);
+            r[0][k] -= r[b][k];
+        }
+}
+
+template <int P>
+__device__ __forceinline__ val_t<P> el_weight(const QuadW &w, int q) {
+    if constexpr (P == FEM_FP64) return w.wd[q];
+    else return w.wf[q];
+}
+
+template <int DIM, int P, int CPT>
+__global__ void __launch_bounds__(kBlock) el_kernel(const __grid_constant__ ElArgs a) {
+    constexpr int NB = DIM + 1;
+    using T = val_t<P>;
+    const int64_t C = a.C;
+    const T *__restrict__ u = static_cast<const T *>(a.u);
+    const T *__restrict__ lam = static_cast<const T *>(a.lam);
+    const T *__restrict__ mu = static_cast<const T *>(a.mu);
+    T *__restrict__ out = static_cast<T *>(a.out);
+    const double *X[DIM];
+#pragma unroll
+    for (int k = 0; k < DIM; ++k) X[k] = a.X[k];
+    const int64_t V = a.V;
+
+    const int64_t ngroups = (C + CPT - 1) / CPT;
+    const int64_t stride = int64_t(gridDim.x) * blockDim.x;
+    for (int64_t g = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; g < ngroups; g += stride) {
+        const int64_t c0 = g * CPT;
+        int32_t vid[NB][CPT];
+#pragma unroll
+        for (int b = 0; b < NB; ++b) load_row<CPT>(a.conn + b * C + c0, vid[b]);
+
+        qsum_t<P> ls[CPT], ms[CPT];
+        {
+            T lq[CPT], mq[CPT];
+            load_row<CPT>(lam + c0, lq);
+            load_row<CPT>(mu + c0, mq);
+            const T w0 = el_weight<P>(a.w, 0);
+#pragma unroll
+            for (int i = 0; i < CPT; ++i) ls[i].first(w0, lq[i]), ms[i].first(w0, mq[i]);
+        }
+        for (int q = 1; q < a.w.nq; ++q) {
+            T lq[CPT], mq[CPT];
+            load_row<CPT>(lam + q * C + c0, lq);
+            load_row<CPT>(mu + q * C + c0, mq);
+            const T wq = el_weight<P>(a.w, q);
+#pragma unroll
+            for (int i = 0; i < CPT; ++i) ls[i].add(wq, lq[i]), ms[i].add(wq, mq[i]);
+        }
+
+        T r[NB * DIM][CPT];
+#pragma unroll
+        for (int i = 0; i < CPT; ++i) {
+            uint32_t v[NB];
+            T uu[NB][DIM];
+#pragma unroll
+            for (int b = 0; b < NB; ++b) {
+                v[b] = clamp_vid(vid[b][i], a.V);
+#pragma unroll
+                for (int k = 0; k < DIM; ++k) uu[b][k] = ld_gather(u + k * V + v[b]);
+            }
+            T rr[NB][DIM];
+            if constexpr (P == FEM_FP64) {
+                double e[DIM][DIM], n[DIM][DIM];
+                columns_f64<DIM>(X, v, e);
+                double det = adjugate_rows<DIM>(e, n);
+                el_element<DIM>(n, det, uu, ls[i].value(), ms[i].value(), rr);
+            } else {
+                float e[DIM][DIM], n[DIM][DIM];
+                if constexpr (P == FEM_FP32_MIXED) columns_mixed<DIM>(X, v, e);
+                else columns_f32<DIM>(X, v, e);
+                float det = adjugate_rows<DIM>(e, n);
+                bool ok = true;
+                if constexpr (P == FEM_FP32_MIXED) ok = shape_ok<DIM>(e, det, a.tau2);
+                if (ok) {
+                    el_element<DIM>(n, det, uu, ls[i].value(), ms[i].value(), rr);
+                } else {
+                    double e64[DIM][DIM], n64[DIM][DIM], u64[NB][DIM], r64[NB][DIM];
+                    columns_f64<DIM>(X, v, e64);
+                    double det64 = adjugate_rows<DIM>(e64, n64);
+#pragma unroll
+                    for (int b = 0; b < NB; ++b)
+#pragma unroll
+                        for (int k = 0; k < DIM; ++k) u64[b][k] = uu[b][k];
+                    el_element<DIM>(n64, det64, u64, ls[i].value_f64(), ms[i].value_f64(), r64);
+#pragma unroll
+                    for (int b = 0; b < NB; ++b)
+#pragma unroll
+                        for (int k = 0; k < DIM; ++k) rr[b][k] = static_cast<float>(r64[b][k]);
+                }
+            }
+#pragma unroll
+            for (int b = 0; b < NB; ++b)
+#pragma unroll
+                for (int k = 0; k < DIM; ++k) r[b * DIM + k][i] = rr[b][k];
+        }
+#pragma unroll
+        for (int row = 0; row < NB * DIM; ++row) store_row<CPT>(out + row * C + c0, r[row]);
+    }
+}
+
+template <int DIM, int P>
+static fem_status launch_el(const ElArgs &a, bool vec, cudaStream_t s) {
+    if (vec) {
+        auto k = el_kernel<DIM, P, 4>;
+        k<<<grid_for((a.C + 3) / 4, kBlock, reinterpret_cast<const void *>(k)), kBlock, 0, s>>>(a);
+    } else {
+        auto k = el_kernel<DIM, P, 1>;
+        k<<<grid_for(a.C, kBlock, reinterpret_cast<const void *>(k)), kBlock, 0, s>>>(a);
+    }
+    return check_launch("fem_integrate_elasticity");
+}
+
+}  // namespace fem
+
+using namespace fem;
+
+extern "C" fem_status fem_integrate_elasticity(int dim, int64_t n_cells, int64_t n_verts, const double *coords,
+                                               const int32_t *conn, const void *u, const void *lam, const void *mu,
+                                               int n_q, const double *qpts, const double *qw, void *elem_out,
+                                               fem_precision prec, fem_stream stream) {
+    fem_status st = check_common(dim, n_cells, n_verts, coords, conn);
+    if (st != FEM_OK) return st;
+    if (prec != FEM_FP64 && prec != FEM_FP32_MIXED && prec != FEM_FP32)
+        return fail(FEM_ERR_ARG, "unknown precision %d", static_cast<int>(prec));
+    if (int64_t(dim) * n_verts >= (int64_t(1) << 31)) return fail(FEM_ERR_SHAPE, "too many vertices");
+    ElArgs a;
+    if ((st = load_quadrature(dim, n_q, qpts, qw, a.w)) != FEM_OK) return st;
+    if (n_cells == 0) return FEM_OK;
+    if (!u || !lam || !mu || !elem_out) return fail(FEM_ERR_ARG, "u, lam, mu or elem_out is NULL");
+    for (int k = 0; k < 3; ++k) a.X[k] = coords + (k < dim ? k : 0) * n_verts;
+    a.conn = conn;
+    a.u = u;
+    a.lam = lam;
+    a.mu = mu;
+    a.out = elem_out;
+    a.C = n_cells;
+    a.V = static_cast<uint32_t>(n_verts);
+    const float tau = mixed_tau();
+    a.tau2 = tau * tau;
+    const bool vec = n_cells % 4 == 0 && aligned16(conn) && aligned16(lam) && aligned16(mu) && aligned16(elem_out);
+    const int key = dim * 10 + static_cast<int>(prec);
+    switch (key) {
+        case 20: return launch_el<2, FEM_FP64>(a, vec, stream);
+        case 21: return launch_el<2, FEM_FP32_MIXED>(a, vec, stream);
+        case 22: return launch_el<2, FEM_FP32>(a, vec, stream);
+        case 30: return launch_el<3, FEM_FP64>(a, vec, stream);
+        case 31: return launch_el<3, FEM_FP32_MIXED>(a, vec, stream);
+        case 32: return launch_el<3, FEM_FP32>(a, vec, stream);
+    }
+    return fail(FEM_ERR_ARG, "unsupported dim/precision");
+}

@@ -1,0 +1,108 @@
+"""The C-ABI library loads, exports every function include/fem.h declares, and its
+host-side argument checks return the documented statuses. No kernel is launched:
+every call here fails validation (or is a no-op) before touching a GPU."""
+
+import ctypes
+import os
+import re
+
+import numpy as np
+import pytest
+
+from paper_1607_04245_gb300 import build as fem_build
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    fem_build.build()
+    from paper_1607_04245_gb300 import binding
+
+    return binding.lib()
+
+
+def declared_functions():
+    names = set()
+    for f in os.listdir(os.path.join(ROOT, "include")):
+        if f.endswith(".h"):
+            text = open(os.path.join(ROOT, "include", f)).read()
+            text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+            names |= set(re.findall(r"\b(fem_\w+)\s*\(", text))
+    return sorted(names)
+
+
+def test_header_declares_the_boundary():
+    names = declared_functions()
+    for required in ("fem_integrate_laplacian", "fem_integrate_elasticity", "fem_adjoint_laplacian",
+                     "fem_build_node2cell", "fem_status_string", "fem_last_error"):
+        assert required in names
+
+
+def test_every_declared_symbol_is_exported(lib):
+    missing = [n for n in declared_functions() if not hasattr(lib, n)]
+    assert not missing, missing
+
+
+def test_status_strings(lib):
+    for st in (0, -1, -2, -3, -4, -5, -6, -7):
+        assert lib.fem_status_string(st)
+    assert b"sm_103a" in lib.fem_version()
+
+
+def _qw(n):
+    return np.full(n, 1.0 / (2 * n))
+
+
+def test_host_validation(lib):
+    P = ctypes.c_void_p
+    qw = _qw(3)
+    qwp = qw.ctypes.data_as(P)
+    fake = P(0x1000)  # never dereferenced: validation fails or the call is a no-op first
+    # dim outside {2, 3}
+    assert lib.fem_integrate_laplacian(4, 10, 10, fake, fake, fake, fake, 3, None, qwp, fake, 0, None) == -1
+    # negative size
+    assert lib.fem_integrate_laplacian(2, -1, 10, fake, fake, fake, fake, 3, None, qwp, fake, 0, None) == -1
+    # n_q out of range
+    assert lib.fem_integrate_laplacian(2, 10, 10, fake, fake, fake, fake, 0, None, qwp, fake, 0, None) == -2
+    assert lib.fem_integrate_laplacian(2, 10, 10, fake, fake, fake, fake, 33, None, qwp, fake, 0, None) == -2
+    # NULL weights
+    assert lib.fem_integrate_laplacian(2, 10, 10, fake, fake, fake, fake, 3, None, None, fake, 0, None) == -1
+    # quadrature point outside the reference triangle
+    bad = np.array([[0.5, 0.6], [0.1, 0.1], [0.2, 0.2]])
+    assert lib.fem_integrate_laplacian(2, 10, 10, fake, fake, fake, fake, 3, bad.ctypes.data_as(P), qwp, fake, 0,
+                                       None) == -1
+    # unknown precision
+    assert lib.fem_integrate_laplacian(2, 10, 10, fake, fake, fake, fake, 3, None, qwp, fake, 7, None) == -1
+    # too large for int32 indexing
+    assert lib.fem_integrate_laplacian(3, 1 << 30, 10, fake, fake, fake, fake, 3, None, qwp, fake, 0, None) == -2
+    assert b"int32" in lib.fem_last_error()
+    # NULL output
+    assert lib.fem_integrate_elasticity(2, 10, 10, fake, fake, fake, fake, fake, 3, None, qwp, None, 0, None) == -1
+    # n_cells = 0 is a valid no-op (no launch)
+    assert lib.fem_integrate_laplacian(2, 0, 0, None, None, None, None, 3, None, qwp, None, 1, None) == 0
+    assert lib.fem_integrate_elasticity(3, 0, 0, None, None, None, None, None, 3, None, qwp, None, 1, None) == 0
+
+
+def test_mixed_threshold(lib):
+    old = lib.fem_get_mixed_threshold()
+    assert old == pytest.approx(0.05)
+    assert lib.fem_set_mixed_threshold(ctypes.c_double(-1.0)) == -1
+    assert lib.fem_set_mixed_threshold(ctypes.c_double(0.2)) == 0
+    assert lib.fem_get_mixed_threshold() == pytest.approx(0.2)
+    assert lib.fem_set_mixed_threshold(ctypes.c_double(old)) == 0
+
+
+def test_node2cell_work_size(lib):
+    assert lib.fem_node2cell_work_size(0) == 1
+    assert lib.fem_node2cell_work_size(4096) == 4096 + 1 + 1
+    assert lib.fem_node2cell_work_size(4097) == 4097 + 2 + 1
+
+
+def test_binding_fails_loudly_without_library(monkeypatch, tmp_path):
+    from paper_1607_04245_gb300 import binding
+
+    monkeypatch.setattr(binding, "_lib", None)
+    monkeypatch.setattr(binding, "LIB_PATH", str(tmp_path / "missing.so"))
+    with pytest.raises(RuntimeError, match="libfem.so not found"):
+        binding.lib()
