@@ -79,24 +79,30 @@ def load_peaks():
         return 6800.0, "fallback"
 
 
-def src_hash():
+KERNEL_SOURCES = {
+    "lap": ("fem_internal.cuh", "fem_cell.cuh", "fem_laplacian.cu"),
+    "el": ("fem_internal.cuh", "fem_cell.cuh", "fem_elasticity.cu"),
+}
+
+
+def src_hash(files):
+    """Hash of the sources that define a kernel (a recorded ncu figure is only reused
+    while they are unchanged)."""
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_1607_04245_gb300", "csrc")
-    for f in sorted(os.listdir(csrc)):
+    for f in files:
         with open(os.path.join(csrc, f), "rb") as fh:
             h.update(f.encode() + fh.read())
-    with open(os.path.join(ROOT, "include", "fem.h"), "rb") as fh:
-        h.update(fh.read())
     return h.hexdigest()[:16]
 
 
-def recorded_traffic(kernel_key):
+def recorded_traffic(kernel_key, family="lap"):
     """DRAM bytes per launch from a committed ncu summary, if it was taken on the current
-    kernel sources (profiles/dram_traffic.txt: 'key src=<hash> bytes=<n>' lines)."""
+    kernel sources (profiles/dram_traffic.txt: '<key> src=<hash> bytes=<n> ...' lines)."""
     p = os.path.join(ROOT, "profiles", "dram_traffic.txt")
     if not os.path.exists(p):
         return None
-    cur = src_hash()
+    cur = src_hash(KERNEL_SOURCES[family])
     for line in open(p):
         parts = line.split()
         if len(parts) >= 3 and parts[0] == kernel_key:
@@ -240,7 +246,7 @@ def make_flush(device):
     sink = torch.empty((), dtype=torch.float32, device=device)
 
     def flush():
-        torch.sum(buf, out=sink)  # a full read of the buffer evicts the working set from L2
+        torch.sum(buf, dim=(0,), out=sink)  # a full read of the buffer evicts the working set from L2
 
     return flush
 
@@ -369,6 +375,46 @@ def measure_e2e(case, prec, device, steps, warmup):
             "d2h_bytes_per_step": hi.d2h_bytes // steps, "ms_per_step": t * 1e3}
 
 
+def measure_serving(device, n_requests, seed=0):
+    """Serving stream: n requests (residual or adjoint, 2D/3D Laplacian and elasticity,
+    log-uniform 1e3..1e6 cells, fresh seeded meshes), FP32-mixed. First all requests at
+    t = 0 (saturation: the service capacity in requests/s), then Poisson arrivals at
+    85% of that capacity; p50/p99 latency from arrival to observed completion."""
+    from paper_1607_04245_gb300.serving import GpuExecutor, Scheduler, make_request, poisson_arrivals
+
+    t_gen = time.time()
+    specs = workloads.cases.serving_specs(n_requests, seed=seed)
+    reqs = [make_request(sp["rid"], workloads.cases.serving_case(sp), sp["kind"], "mixed") for sp in specs]
+    t_gen = time.time() - t_gen
+    ex = GpuExecutor(device, capacity=2 << 30, n_slots=16)
+
+    def reset(arrivals):
+        for r, a in zip(reqs, arrivals):
+            r.arrival, r.status = float(a), "pending"
+
+    warm = reqs[:8]
+    reset([0.0] * len(reqs))
+    Scheduler(ex).run(warm)
+    reset([0.0] * len(reqs))
+    sat = Scheduler(ex).run(reqs)
+    rate = 0.85 * sat.req_per_s
+    reset(poisson_arrivals(len(reqs), rate, seed=seed + 1))
+    ex.launches = 0
+    st = Scheduler(ex).run(reqs, arrival_rate=rate)
+    kinds = {}
+    for sp in specs:
+        k = f"{sp['physics']}{sp['dim']}d_{sp['kind']}"
+        kinds[k] = kinds.get(k, 0) + 1
+    return {"requests": n_requests, "generation_s": round(t_gen, 2), "mix": kinds,
+            "arena_bytes": ex.arena.capacity, "slots": ex.n_slots,
+            "saturation": {"req_per_s": sat.req_per_s, "cells_per_s": sat.cells_per_s, "p50_ms": sat.p50_ms,
+                           "p99_ms": sat.p99_ms, "makespan_s": sat.makespan_s},
+            "poisson": {"arrival_rate_req_per_s": rate, "req_per_s": st.req_per_s, "cells_per_s": st.cells_per_s,
+                        "p50_ms": st.p50_ms, "p99_ms": st.p99_ms, "mean_ms": st.mean_ms,
+                        "max_inflight": st.max_inflight, "rejected": st.n_rejected, "makespan_s": st.makespan_s,
+                        "cells": st.cells}}
+
+
 def cpu_baseline(case, min_seconds=10.0, max_reps=200):
     import oracle
 
@@ -449,7 +495,9 @@ def run_ours(args):
     torch.cuda.set_device(local_rank)
     device = torch.device("cuda", local_rank)
     dist = dist_init(ws, "nccl")
-    fem.lib()
+    from paper_1607_04245_gb300 import binding
+
+    binding.lib()
     peak, peak_kind = load_peaks()
     import oracle
 
@@ -512,6 +560,8 @@ def run_ours(args):
             sweep[str(1 << e)] = {"cells_per_s": r["cells_per_s"], "alg_gbs": r["alg_gbs"],
                                   "hbm_frac_of_measured": r["hbm_frac_of_measured"], "ms": r["ms_per_launch"]}
         rows["sweep_lap3d_mixed"] = sweep
+        if args.serving_requests > 0:
+            rows["serving"] = measure_serving(device, args.serving_requests)
 
     e2e = measure_e2e(case, "mixed", device, max(3, args.steps // 100), 3)
 
@@ -534,7 +584,8 @@ def run_ours(args):
             "roofline": roofline,
             "cpu_baseline": cpu_baseline(case) if (ws == 1 and not args.no_cpu_baseline) else None,
             "e2e": e2e, "gpu_launches": args.steps,
-            "clocks": clocks, "rows": rows}
+            "clocks": clocks, "rows": rows,
+            "served_p99_ms": rows.get("serving", {}).get("poisson", {}).get("p99_ms")}
     print(json.dumps(line))
     barrier(dist, ws)
     return 0
@@ -548,6 +599,7 @@ def main(argv=None):
     ap.add_argument("--impl", choices=("ours", "reference"), default="ours")
     ap.add_argument("--rows", choices=("all", "none"), default="all")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--serving-requests", type=int, default=500)
     args = ap.parse_args(argv)
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")

@@ -125,9 +125,9 @@ double fem_get_mixed_threshold(void);
  * fem_check_mesh -- validation pass (not on the hot path). Writes into the DEVICE
  * array counts[4] (int64, overwritten):
  *   counts[0] = number of connectivity entries outside [0, V)
- *   counts[1] = number of cells with det J <= 0 (or non-finite) in float64
+ *   counts[1] = number of degenerate cells: |det J| <= 16 eps_64 prod_j |J e_j| or non-finite
  *   counts[2] = number of cells FEM_FP32_MIXED sends to its float64 path
- *   counts[3] = number of cells with det J < 0
+ *   counts[3] = number of non-degenerate cells with det J < 0 (inverted; allowed, |det J| is used)
  * Read counts after synchronising the stream.
  * ------------------------------------------------------------------------------- */
 fem_status fem_check_mesh(int dim, int64_t n_cells, int64_t n_verts, const double *coords,
@@ -181,6 +181,24 @@ fem_status fem_build_node2cell(int dim, int64_t n_cells, int64_t n_verts, const 
 fem_status fem_gather_nodes(int dim, int n_comp, int64_t n_cells, int64_t n_verts, const void *elem,
                             const int32_t *node_ptr, const int32_t *node_idx, void *out,
                             fem_precision prec, fem_stream stream);
+
+/* ---------------------------------------------------------------------------------
+ * Device-memory arena for the serving loop (not in the paper). A host-side first-fit
+ * sub-allocator of offsets into ONE caller-owned device buffer of `capacity` bytes;
+ * it makes no CUDA call and never touches the buffer. Offsets are multiples of
+ * `alignment` (a power of two); sizes are rounded up to it. Released ranges merge
+ * with free neighbours. Thread-safe.
+ *   fem_arena_alloc  FEM_ERR_OOM when no free range holds `bytes`
+ *   fem_arena_free   FEM_ERR_ARG when `offset` was not returned by fem_arena_alloc
+ * ------------------------------------------------------------------------------- */
+typedef struct fem_arena fem_arena;
+fem_status fem_arena_create(int64_t capacity, int64_t alignment, fem_arena **out);
+void fem_arena_destroy(fem_arena *arena);
+fem_status fem_arena_alloc(fem_arena *arena, int64_t bytes, int64_t *offset);
+fem_status fem_arena_free(fem_arena *arena, int64_t offset);
+int64_t fem_arena_free_bytes(fem_arena *arena);
+int64_t fem_arena_largest_free(fem_arena *arena);
+int64_t fem_arena_capacity(fem_arena *arena);
 
 /* ---------------------------------------------------------------------------------
  * Throughput probes for the roofline (not part of the method): each thread runs

@@ -22,7 +22,7 @@ OUT = os.path.join(PKG, "libfem.so")
 BUILD = os.path.join(PKG, "_build")
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-SOURCES = ["fem_core.cu", "fem_laplacian.cu", "fem_elasticity.cu", "fem_mesh.cu"]
+SOURCES = ["fem_core.cu", "fem_laplacian.cu", "fem_elasticity.cu", "fem_mesh.cu", "fem_arena.cpp"]
 
 
 def nvcc() -> str:
@@ -47,7 +47,7 @@ def build(force: bool = False, verbose_ptxas: bool = False) -> str:
         flags += ["-Xptxas", "-v"]
 
     def compile_one(src):
-        obj = os.path.join(BUILD, src.replace(".cu", ".o"))
+        obj = os.path.join(BUILD, os.path.splitext(src)[0] + ".o")
         cmd = [cc] + flags + ["-c", os.path.join(CSRC, src), "-o", obj]
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode != 0:

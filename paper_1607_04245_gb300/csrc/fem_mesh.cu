@@ -240,8 +240,14 @@ __global__ void check_mesh_kernel(const double *X0, int64_t C, uint32_t V, const
         double e[DIM][DIM], n[DIM][DIM];
         columns_f64<DIM>(X, v, e);
         double det = adjugate_rows<DIM>(e, n);
-        if (!(det != 0.0) || !isfinite(det)) ++c_degen;
-        if (det < 0.0) ++c_neg;
+        // degenerate to rounding: |det J| <= 16 eps_64 prod_j |e_j| (FMA contraction can
+        // leave a rounding residue instead of an exact zero for repeated vertices)
+        double pn = 1.0;
+#pragma unroll
+        for (int j = 0; j < DIM; ++j) pn *= sqrt(dotv<DIM>(e[j], e[j]));
+        const bool degenerate = !(fabs(det) > 16.0 * DBL_EPSILON * pn) || !isfinite(det);
+        if (degenerate) ++c_degen;
+        else if (det < 0.0) ++c_neg;
         float ef[DIM][DIM], nf[DIM][DIM];
         columns_mixed<DIM>(X, v, ef);
         float detf = adjugate_rows<DIM>(ef, nf);

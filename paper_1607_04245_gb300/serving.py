@@ -1,0 +1,376 @@
+"""Continuous-batching server for residual and adjoint evaluations (not in the paper).
+
+Requests (a mesh, its field and coefficients, and the kind of evaluation) arrive over
+time. The scheduler admits them as soon as an execution slot is free and the device
+arena can hold their footprint; admitted requests run on per-slot CUDA streams, so
+uploads, kernels and downloads of different requests overlap on the device while
+new ones keep arriving. Latency is measured from arrival to the moment the host sees
+the request's completion event.
+
+Pieces:
+  Arena           ctypes wrapper of libfem's host-side first-fit arena (fem_arena_*)
+  Request         one evaluation with pinned host inputs and pinned host results
+  footprint()     device bytes a request needs (every array rounded to 256 B)
+  GpuExecutor     carves a request's arrays out of one device buffer, launches the
+                  libfem kernels on the slot's stream, polls completion events
+  Scheduler       the real-time admission loop (FIFO, optional backfill); it talks to
+                  the executor through try_admit / launch / poll only
+"""
+
+from __future__ import annotations
+
+import collections
+import ctypes
+import dataclasses
+import math
+import statistics
+import time
+from typing import Dict, List, Optional
+
+import numpy as np
+import torch
+
+from . import binding
+from .binding import (fem_adjoint_laplacian, fem_build_node2cell, fem_integrate_elasticity, fem_integrate_laplacian,
+                      value_dtype)
+
+ALIGN = 256
+
+
+# ----------------------------------------------------------------------------- arena
+
+
+class Arena:
+    """Offsets into one device buffer, managed by libfem's native first-fit allocator."""
+
+    def __init__(self, capacity: int, alignment: int = ALIGN):
+        L = binding.lib()
+        P = ctypes.c_void_p
+        for name, args, res in (("fem_arena_create", [ctypes.c_int64, ctypes.c_int64, ctypes.POINTER(P)], ctypes.c_int),
+                                ("fem_arena_destroy", [P], None),
+                                ("fem_arena_alloc", [P, ctypes.c_int64, ctypes.POINTER(ctypes.c_int64)], ctypes.c_int),
+                                ("fem_arena_free", [P, ctypes.c_int64], ctypes.c_int),
+                                ("fem_arena_free_bytes", [P], ctypes.c_int64),
+                                ("fem_arena_largest_free", [P], ctypes.c_int64),
+                                ("fem_arena_capacity", [P], ctypes.c_int64)):
+            f = getattr(L, name)
+            f.argtypes = args
+            f.restype = res
+        self._L = L
+        self._h = P()
+        st = L.fem_arena_create(int(capacity), int(alignment), ctypes.byref(self._h))
+        if st != 0:
+            raise binding.FemError("fem_arena_create", st, L.fem_last_error().decode())
+
+    def alloc(self, nbytes: int) -> Optional[int]:
+        off = ctypes.c_int64()
+        st = self._L.fem_arena_alloc(self._h, int(nbytes), ctypes.byref(off))
+        if st == -4:
+            return None
+        if st != 0:
+            raise binding.FemError("fem_arena_alloc", st, self._L.fem_last_error().decode())
+        return int(off.value)
+
+    def free(self, offset: int) -> None:
+        st = self._L.fem_arena_free(self._h, int(offset))
+        if st != 0:
+            raise binding.FemError("fem_arena_free", st, self._L.fem_last_error().decode())
+
+    @property
+    def free_bytes(self) -> int:
+        return int(self._L.fem_arena_free_bytes(self._h))
+
+    @property
+    def largest_free(self) -> int:
+        return int(self._L.fem_arena_largest_free(self._h))
+
+    @property
+    def capacity(self) -> int:
+        return int(self._L.fem_arena_capacity(self._h))
+
+    def __del__(self):
+        try:
+            if self._h:
+                self._L.fem_arena_destroy(self._h)
+                self._h = ctypes.c_void_p()
+        except Exception:
+            pass
+
+
+# ----------------------------------------------------------------------------- requests
+
+
+@dataclasses.dataclass
+class Request:
+    rid: int
+    kind: str  # "residual" or "adjoint" (adjoint: Laplacian only)
+    physics: str  # "laplacian" or "elasticity"
+    dim: int
+    n_cells: int
+    n_verts: int
+    qpts: np.ndarray
+    qw: np.ndarray
+    host: Dict[str, torch.Tensor]  # pinned inputs: coords, conn, u, K | lam, mu, adj
+    prec: str = "mixed"
+    arrival: float = 0.0  # seconds after the start of the stream
+    status: str = "pending"
+    t_arrive: float = math.nan
+    t_admit: float = math.nan
+    t_done: float = math.nan
+    result: Dict[str, torch.Tensor] = dataclasses.field(default_factory=dict)
+    error: str = ""
+
+    @property
+    def n_comp(self) -> int:
+        return 1 if self.physics == "laplacian" else self.dim
+
+    @property
+    def latency(self) -> float:
+        return self.t_done - self.t_arrive
+
+    def device_arrays(self):
+        """(name, shape, dtype) of every device array the request needs."""
+        d, C, V, nq = self.dim, self.n_cells, self.n_verts, int(self.qw.shape[0])
+        dt = value_dtype(self.prec)
+        arrs = [("coords", (d, V), torch.float64), ("conn", (d + 1, C), torch.int32),
+                ("u", (V,) if self.physics == "laplacian" else (d, V), dt)]
+        if self.physics == "laplacian":
+            arrs.append(("K", (nq, C), dt))
+        else:
+            arrs += [("lam", (nq, C), dt), ("mu", (nq, C), dt)]
+        if self.kind == "residual":
+            arrs.append(("out", ((d + 1) * self.n_comp, C), dt))
+        else:
+            arrs += [("adj", (d + 1, C), dt), ("dK", (nq, C), dt), ("du", (V,), dt), ("scratch", (d + 1, C), dt),
+                     ("node_ptr", (V + 1,), torch.int32), ("node_idx", ((d + 1) * C,), torch.int32),
+                     ("work", (max(1, binding.lib().fem_node2cell_work_size(V)),), torch.int32)]
+        return arrs
+
+    def alloc_results(self):
+        dt = value_dtype(self.prec)
+        d, C, V, nq = self.dim, self.n_cells, self.n_verts, int(self.qw.shape[0])
+        if self.kind == "residual":
+            self.result = {"out": torch.empty(((d + 1) * self.n_comp, C), dtype=dt, pin_memory=True)}
+        else:
+            self.result = {"dK": torch.empty((nq, C), dtype=dt, pin_memory=True),
+                           "du": torch.empty(V, dtype=dt, pin_memory=True)}
+
+
+def _nbytes(shape, dtype) -> int:
+    n = 1
+    for s in shape:
+        n *= int(s)
+    return n * torch.empty((), dtype=dtype).element_size()
+
+
+def footprint(req: Request) -> int:
+    """Device bytes of a request: every array rounded up to the 256-byte alignment."""
+    return sum((_nbytes(s, t) + ALIGN - 1) // ALIGN * ALIGN for _, s, t in req.device_arrays())
+
+
+def make_request(rid, case, kind, prec="mixed", arrival=0.0, adj=None) -> Request:
+    """A request from a workloads.Case (values rounded to the precision's storage type)."""
+    dt = value_dtype(prec)
+    c = case if prec == "fp64" else case.rounded_to_f32()
+    pin = lambda a, t: torch.from_numpy(np.ascontiguousarray(a)).to(t).pin_memory()
+    host = {"coords": pin(c.mesh.coords, torch.float64), "conn": pin(c.mesh.conn, torch.int32), "u": pin(c.u, dt)}
+    if c.physics == "laplacian":
+        host["K"] = pin(c.K, dt)
+    else:
+        host["lam"], host["mu"] = pin(c.lam, dt), pin(c.mu, dt)
+    if kind == "adjoint":
+        if c.physics != "laplacian":
+            raise ValueError("adjoint requests are Laplacian only")
+        a = c.adj if adj is None else adj
+        host["adj"] = pin(a if prec == "fp64" else np.asarray(a, dtype=np.float32), dt)
+    r = Request(rid, kind, c.physics, c.dim, c.n_cells, c.n_verts, np.ascontiguousarray(c.rule.points),
+                np.ascontiguousarray(c.rule.weights), host, prec=prec, arrival=arrival)
+    r.alloc_results()
+    return r
+
+
+# ----------------------------------------------------------------------------- executor
+
+
+class GpuExecutor:
+    """Runs admitted requests: one CUDA stream per slot, device arrays carved from one
+    preallocated buffer through the arena. Nothing is allocated per request."""
+
+    def __init__(self, device="cuda", capacity: int = 4 << 30, n_slots: int = 8):
+        self.device = torch.device(device)
+        self.pool = torch.empty(int(capacity), dtype=torch.uint8, device=self.device)
+        self.arena = Arena(capacity)
+        self.streams = [torch.cuda.Stream(device=self.device) for _ in range(n_slots)]
+        self.free_slots = list(range(n_slots))
+        self.inflight: Dict[int, tuple] = {}  # rid -> (req, slot, offsets, event)
+        self.launches = 0
+
+    @property
+    def n_slots(self) -> int:
+        return len(self.streams)
+
+    def fits_ever(self, req: Request) -> bool:
+        return footprint(req) <= self.arena.capacity
+
+    def try_admit(self, req: Request):
+        if not self.free_slots:
+            return None
+        offs = []
+        views = {}
+        for name, shape, dt in req.device_arrays():
+            nb = _nbytes(shape, dt)
+            off = self.arena.alloc(nb)
+            if off is None:
+                for o in offs:
+                    self.arena.free(o)
+                return None
+            offs.append(off)
+            views[name] = self.pool[off:off + nb].view(dt).view(shape) if nb else torch.empty(shape, dtype=dt,
+                                                                                                device=self.device)
+        slot = self.free_slots.pop()
+        return slot, offs, views
+
+    def launch(self, req: Request, admitted) -> None:
+        slot, offs, v = admitted
+        s = self.streams[slot]
+        with torch.cuda.stream(s):
+            for name, t in req.host.items():
+                v[name].copy_(t, non_blocking=True)
+            if req.kind == "residual":
+                if req.physics == "laplacian":
+                    fem_integrate_laplacian(v["coords"], v["conn"], v["u"], v["K"], req.qpts, req.qw, out=v["out"],
+                                            prec=req.prec, stream=s)
+                else:
+                    fem_integrate_elasticity(v["coords"], v["conn"], v["u"], v["lam"], v["mu"], req.qpts, req.qw,
+                                             out=v["out"], prec=req.prec, stream=s)
+                req.result["out"].copy_(v["out"], non_blocking=True)
+                self.launches += 1
+            else:
+                fem_build_node2cell(v["conn"], req.n_verts, node_ptr=v["node_ptr"], node_idx=v["node_idx"],
+                                    work=v["work"], stream=s)
+                fem_adjoint_laplacian(v["coords"], v["conn"], v["u"], v["K"], req.qpts, req.qw, v["adj"],
+                                      v["node_ptr"], v["node_idx"], dK=v["dK"], du=v["du"], scratch=v["scratch"],
+                                      prec=req.prec, stream=s)
+                req.result["dK"].copy_(v["dK"], non_blocking=True)
+                req.result["du"].copy_(v["du"], non_blocking=True)
+                self.launches += 9  # list build (count, 3 scan passes, copy, fill, sort) + element + gather
+            ev = torch.cuda.Event()
+            ev.record(s)
+        self.inflight[req.rid] = (req, slot, offs, ev)
+
+    def poll(self) -> List[Request]:
+        done = []
+        for rid in list(self.inflight):
+            req, slot, offs, ev = self.inflight[rid]
+            if ev.query():
+                for o in offs:
+                    self.arena.free(o)
+                self.free_slots.append(slot)
+                del self.inflight[rid]
+                done.append(req)
+        return done
+
+    def busy(self) -> bool:
+        return bool(self.inflight)
+
+
+# ----------------------------------------------------------------------------- scheduler
+
+
+@dataclasses.dataclass
+class ServeStats:
+    n: int
+    n_done: int
+    n_rejected: int
+    makespan_s: float
+    cells: int
+    cells_per_s: float
+    req_per_s: float
+    p50_ms: float
+    p99_ms: float
+    mean_ms: float
+    max_inflight: int
+    arrival_rate: float
+
+    def as_dict(self):
+        return dataclasses.asdict(self)
+
+
+class Scheduler:
+    """Real-time continuous batching: requests join a FIFO queue when their arrival time
+    passes and are admitted whenever a slot and enough arena memory are free; with
+    backfill, a later request that fits may overtake a head that does not."""
+
+    def __init__(self, executor, backfill: bool = True, clock=time.perf_counter, idle_sleep: float = 20e-6):
+        self.ex = executor
+        self.backfill = backfill
+        self.clock = clock
+        self.idle_sleep = idle_sleep
+
+    def run(self, requests: List[Request], arrival_rate: float = math.nan) -> ServeStats:
+        pending = collections.deque(sorted(requests, key=lambda r: r.arrival))
+        queue: collections.deque = collections.deque()
+        n, finished, max_inflight = len(requests), 0, 0
+        t0 = self.clock()
+        while finished < n:
+            now = self.clock()
+            while pending and pending[0].arrival <= now - t0:
+                r = pending.popleft()
+                r.t_arrive = t0 + r.arrival
+                r.status = "queued"
+                queue.append(r)
+            progressed = False
+            i = 0
+            while i < len(queue):
+                r = queue[i]
+                if not self.ex.fits_ever(r):
+                    r.status, r.error = "rejected", "footprint exceeds the device arena"
+                    r.t_done = self.clock()
+                    del queue[i]
+                    finished += 1
+                    continue
+                adm = self.ex.try_admit(r)
+                if adm is not None:
+                    del queue[i]
+                    r.t_admit = self.clock()
+                    r.status = "running"
+                    self.ex.launch(r, adm)
+                    progressed = True
+                    continue
+                if not self.backfill:
+                    break
+                i += 1
+            max_inflight = max(max_inflight, len(getattr(self.ex, "inflight", ())))
+            for r in self.ex.poll():
+                r.t_done = self.clock()
+                r.status = "done"
+                finished += 1
+                progressed = True
+            if not progressed:
+                if pending and not queue and not self.ex.busy():
+                    wait = pending[0].arrival - (self.clock() - t0)
+                    if wait > 0:
+                        time.sleep(min(wait, 1e-3))
+                else:
+                    time.sleep(self.idle_sleep)
+        t1 = self.clock()
+        done = [r for r in requests if r.status == "done"]
+        lat = sorted(r.latency * 1e3 for r in done) or [math.nan]
+        cells = sum(r.n_cells for r in done)
+        span = t1 - t0
+
+        def pct(p):
+            k = max(0, min(len(lat) - 1, int(math.ceil(p / 100.0 * len(lat))) - 1))
+            return lat[k]
+
+        return ServeStats(n=n, n_done=len(done), n_rejected=sum(r.status == "rejected" for r in requests),
+                          makespan_s=span, cells=cells, cells_per_s=cells / span if span > 0 else math.nan,
+                          req_per_s=len(done) / span if span > 0 else math.nan, p50_ms=pct(50), p99_ms=pct(99),
+                          mean_ms=statistics.mean(lat) if done else math.nan, max_inflight=max_inflight,
+                          arrival_rate=arrival_rate)
+
+
+def poisson_arrivals(n: int, rate: float, seed: int = 0) -> np.ndarray:
+    """Arrival times (s) of a Poisson process: cumulative exponential gaps of mean 1/rate."""
+    rng = np.random.Generator(np.random.Philox(seed))
+    return np.cumsum(rng.exponential(1.0 / rate, size=n)) if rate > 0 else np.zeros(n)

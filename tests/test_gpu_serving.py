@@ -1,0 +1,67 @@
+"""The serving loop on the GPU: every request's result is bitwise the same alone and in
+the concurrent mix, matches the oracle within the FP32-mixed tolerance, requests too
+large for the arena are rejected, and Poisson arrivals produce latency statistics."""
+
+import numpy as np
+import pytest
+import torch
+
+import oracle
+import workloads
+from gpu_util import TOL, rel_err
+from paper_1607_04245_gb300.serving import GpuExecutor, Scheduler, footprint, make_request, poisson_arrivals
+
+pytestmark = pytest.mark.gpu
+
+
+def _stream(n, seed, max_cells, prec="mixed"):
+    specs = workloads.cases.serving_specs(n, seed=seed, min_cells=1000, max_cells=max_cells)
+    cases = [workloads.cases.serving_case(s) for s in specs]
+    return cases, [make_request(s["rid"], c, s["kind"], prec) for s, c in zip(specs, cases)]
+
+
+def test_mix_equals_alone_and_matches_oracle():
+    cases, mix = _stream(48, seed=11, max_cells=60000)
+    biggest = max(footprint(r) for r in mix)
+    ex = GpuExecutor(capacity=3 * biggest, n_slots=6)  # memory, not slots, limits admission
+    st = Scheduler(ex).run(mix)
+    assert st.n_done == len(mix) and st.n_rejected == 0
+    assert st.max_inflight >= 2  # work really overlapped
+    _, alone = _stream(48, seed=11, max_cells=60000)
+    ex1 = GpuExecutor(capacity=2 * biggest, n_slots=1)
+    for r in alone:
+        Scheduler(ex1).run([r])
+    for a, b in zip(mix, alone):
+        assert a.result.keys() == b.result.keys()
+        for k in a.result:
+            assert torch.equal(a.result[k], b.result[k]), (a.rid, k)
+    for c, r in zip(cases, mix):
+        c32 = c.rounded_to_f32()
+        if r.kind == "residual":
+            assert rel_err(r.result["out"], oracle.residual_for(c32)) <= TOL["mixed"]
+        else:
+            rK, ru = oracle.adjoint_for(c32)
+            assert rel_err(r.result["dK"], rK) <= TOL["mixed"] and rel_err(r.result["du"], ru) <= TOL["mixed"]
+
+
+def test_too_large_request_is_rejected():
+    cases, reqs = _stream(6, seed=5, max_cells=20000)
+    small = min(footprint(r) for r in reqs)
+    ex = GpuExecutor(capacity=small + 4096, n_slots=2)
+    st = Scheduler(ex).run(reqs)
+    assert st.n_rejected >= 1
+    assert st.n_done + st.n_rejected == len(reqs)
+    assert all(r.status in ("done", "rejected") for r in reqs)
+
+
+def test_poisson_arrivals_latency():
+    cases, reqs = _stream(60, seed=3, max_cells=100000)
+    t = poisson_arrivals(len(reqs), rate=400.0, seed=9)
+    for r, a in zip(reqs, t):
+        r.arrival = float(a)
+    ex = GpuExecutor(capacity=1 << 30, n_slots=8)
+    st = Scheduler(ex).run(reqs, arrival_rate=400.0)
+    assert st.n_done == len(reqs)
+    assert 0 < st.p50_ms <= st.p99_ms
+    assert st.makespan_s >= t[-1]
+    assert all(r.t_done > r.t_arrive for r in reqs)

@@ -155,3 +155,42 @@ def adjoint_case(n_cells: int = 1572864, jitter: float = 0.15, seed: int = 0) ->
 def adjoint_weights(case: Case, seed: int = 7919) -> np.ndarray:
     s_adj, = _streams(seed, 1)
     return s_adj.uniform(-1.0, 1.0, size=(case.n_comp * (case.dim + 1), case.n_cells))
+
+
+SERVING_PHYSICS = (("laplacian", 2), ("laplacian", 3), ("elasticity", 2), ("elasticity", 3))
+
+
+def serving_specs(n: int = 500, seed: int = 0, min_cells: int = 1000, max_cells: int = 1_000_000):
+    """Request mix of the serving stream: physics uniform over {2D, 3D} x {Laplacian,
+    elasticity}; Laplacian requests are a residual or an adjoint evaluation with equal
+    probability (elasticity: residual); cell counts log-uniform in [min_cells, max_cells];
+    a fresh seed per request."""
+    rng = np.random.Generator(np.random.Philox(np.random.SeedSequence(seed).spawn(1)[0]))
+    specs = []
+    for i in range(n):
+        physics, dim = SERVING_PHYSICS[int(rng.integers(0, 4))]
+        kind = "adjoint" if physics == "laplacian" and rng.random() < 0.5 else "residual"
+        C = int(round(np.exp(rng.uniform(np.log(min_cells), np.log(max_cells)))))
+        specs.append({"rid": i, "physics": physics, "dim": dim, "kind": kind, "n_cells": C,
+                      "seed": int(seed) * 1_000_003 + i + 1})
+    return specs
+
+
+def serving_case(spec) -> Case:
+    """The case of one serving request: the first C cells of the smallest grid mesh that
+    holds them (jitter, coefficients and fields as in the other workloads)."""
+    C, dim, s = spec["n_cells"], spec["dim"], spec["seed"]
+    if spec["physics"] == "elasticity":
+        case = elasticity_case(dim, C, seed=s)
+    elif dim == 2:
+        m = smallest_square_for(C)
+        base = laplacian_square_case(m, seed=s)
+        mesh = first_cells(base.mesh, C) if base.n_cells != C else base.mesh
+        case = Case("laplacian", mesh, base.rule, base.u[: mesh.n_verts], K=np.ascontiguousarray(base.K[:, :C]))
+    else:
+        case = laplacian_cube_case(C, seed=s)
+    if spec["kind"] == "adjoint":
+        s_adj, = _streams(s + 7919, 1)
+        case.adj = s_adj.uniform(-1.0, 1.0, size=(case.dim + 1, case.n_cells))
+    case.name = f"req{spec['rid']}_{spec['physics']}{dim}d_{spec['kind']}_{C}"
+    return case
