@@ -158,6 +158,38 @@ fem_status fem_adjoint_laplacian(int dim, int64_t n_cells, int64_t n_verts, cons
                                  void *scratch, fem_precision prec, fem_stream stream);
 
 /* ---------------------------------------------------------------------------------
+ * fem_adjoint_laplacian_noalloc -- fem_adjoint_laplacian for callers that cannot
+ * allocate device memory. The paper has no counterpart; this is a library convenience.
+ *
+ * Who needs it: callers that have no workspace buffer to pass as `scratch` and cannot
+ * get one -- code handed only the input and output pointers (a plugin or callback in
+ * a host framework that owns all device memory), or a loop that must not call
+ * cudaMalloc because of the device-wide synchronisation it implies.
+ *
+ * The workspace comes from a fixed array of FEM_NOALLOC_SCRATCH_BYTES in the library's
+ * own device memory (a file-scope __device__ object, held by every GPU that loads the
+ * library until the process exits). Nothing is allocated: no cudaMalloc, no cudaFree.
+ *   - Limit: (dim+1) * n_cells * sizeof(value) must not exceed FEM_NOALLOC_SCRATCH_BYTES
+ *     (16 MiB: up to 1,048,576 tets or 1,398,101 triangles in the float32 forms,
+ *     524,288 tets or 699,050 triangles in float64); larger calls return FEM_ERR_SHAPE
+ *     with a message and launch nothing.
+ *   - Set-up: the first call on a device looks up the array's device address
+ *     (cudaGetSymbolAddress) with that device current; make that first call before
+ *     any stream capture.
+ *   - Sharing: every call on a device uses the same array, which keeps the last call's
+ *     contents. Each call writes every entry it reads before reading it, so nothing
+ *     needs clearing; but calls that overlap on the GPU (different streams, or host
+ *     threads) race on the array and must be serialised by the caller.
+ * Arguments, layouts and results are those of fem_adjoint_laplacian without `scratch`.
+ * ------------------------------------------------------------------------------- */
+#define FEM_NOALLOC_SCRATCH_BYTES (16u << 20)
+fem_status fem_adjoint_laplacian_noalloc(int dim, int64_t n_cells, int64_t n_verts, const double *coords,
+                                         const int32_t *conn, const void *u, const void *K, int n_q,
+                                         const double *qpts, const double *qw, const void *lambda, void *dK,
+                                         void *du, const int32_t *node_ptr, const int32_t *node_idx,
+                                         fem_precision prec, fem_stream stream);
+
+/* ---------------------------------------------------------------------------------
  * fem_build_node2cell -- vertex-to-(cell, local vertex) lists: the transpose of conn,
  * i.e. the assembly operator E_e of Eq. 2 stored as lists. Built on the device,
  * deterministically:

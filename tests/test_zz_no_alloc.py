@@ -1,0 +1,74 @@
+"""fem_adjoint_laplacian_noalloc: the adjoint for callers that cannot allocate device
+memory (a plugin or callback handed only input and output pointers, or a loop that
+must avoid cudaMalloc's device-wide synchronisation). Its workspace is a fixed array
+inside the library, so it takes no scratch argument.
+
+Called here through the C ABI (ctypes, raw device pointers) and compared with
+fem_adjoint_laplacian, which takes a caller-owned workspace, on two calls in a row with
+different adjoint weights: the second call reuses the array the first one wrote.
+This file is named to be collected last; it also passes on its own in a fresh process.
+"""
+
+import ctypes
+
+import numpy as np
+import pytest
+import torch
+
+import paper_1607_04245_gb300 as fem
+import workloads
+from gpu_util import TOL, device_arrays, rel_err
+from paper_1607_04245_gb300 import binding
+
+pytestmark = pytest.mark.gpu
+
+
+def _noalloc(c, d, lam, ptr, idx, prec):
+    L = binding.lib()
+    f = L.fem_adjoint_laplacian_noalloc
+    P, i64, ci = ctypes.c_void_p, ctypes.c_int64, ctypes.c_int
+    f.argtypes = [ci, i64, i64, P, P, P, P, ci, P, P, P, P, P, P, P, ci, P]
+    f.restype = ci
+    dt = fem.value_dtype(prec)
+    dK = torch.full((c.rule.n_q, c.n_cells), float("nan"), dtype=dt, device="cuda")
+    du = torch.full((c.n_verts,), float("nan"), dtype=dt, device="cuda")
+    qp = np.ascontiguousarray(c.rule.points)
+    qw = np.ascontiguousarray(c.rule.weights)
+    st = f(c.dim, c.n_cells, c.n_verts, d["coords"].data_ptr(), d["conn"].data_ptr(), d["u"].data_ptr(),
+           d["K"].data_ptr(), c.rule.n_q, qp.ctypes.data, qw.ctypes.data, lam.data_ptr(), dK.data_ptr(),
+           du.data_ptr(), ptr.data_ptr(), idx.data_ptr(), binding.precision(prec),
+           torch.cuda.current_stream().cuda_stream)
+    assert st == 0, L.fem_last_error().decode()
+    return dK, du
+
+
+@pytest.mark.parametrize("dim,prec", [(3, "fp64"), (3, "mixed"), (2, "mixed")])
+def test_noalloc_matches_workspace_entry_point_twice(dim, prec):
+    case = workloads.adjoint_case(6 * 40 ** 3) if dim == 3 else workloads.laplacian_square_case(256)
+    c, d = device_arrays(case, prec)
+    ptr, idx = fem.fem_build_node2cell(d["conn"], c.n_verts)
+    dt = fem.value_dtype(prec)
+    rng = np.random.default_rng(42)
+    for call in range(2):
+        lam = torch.from_numpy(rng.uniform(-1, 1, (dim + 1, c.n_cells))).to("cuda", dt)
+        dK, du = _noalloc(c, d, lam, ptr, idx, prec)
+        rK, ru = fem.fem_adjoint_laplacian(d["coords"], d["conn"], d["u"], d["K"], c.rule.points, c.rule.weights,
+                                           lam, ptr, idx, prec=prec)
+        torch.cuda.synchronize()
+        rK, ru = rK.double().cpu().numpy(), ru.double().cpu().numpy()
+        assert rel_err(dK, rK) <= TOL[prec], (call, "dK")
+        assert rel_err(du, ru) <= TOL[prec], (call, "du")
+
+
+def test_noalloc_rejects_sizes_beyond_its_array():
+    L = binding.lib()
+    f = L.fem_adjoint_laplacian_noalloc
+    P, i64, ci = ctypes.c_void_p, ctypes.c_int64, ctypes.c_int
+    f.argtypes = [ci, i64, i64, P, P, P, P, ci, P, P, P, P, P, P, P, ci, P]
+    f.restype = ci
+    limit = 16 << 20
+    too_many = limit // (4 * 8) + 1  # 3D float64: 4 values of 8 bytes per cell
+    qw = np.full(4, 1 / 24)
+    st = f(3, too_many, 10, None, None, None, None, 4, None, qw.ctypes.data, None, None, None, None, None, 0, None)
+    assert st == -2
+    assert b"fixed" in L.fem_last_error()
