@@ -242,6 +242,22 @@ int64_t fem_arena_capacity(fem_arena *arena);
  * ------------------------------------------------------------------------------- */
 fem_status fem_probe(int kind, int64_t n_threads, int iters, void *out, fem_stream stream);
 
+/* ---------------------------------------------------------------------------------
+ * fem_device_error -- bounded device-side waits (not in the paper). The staged kernels
+ * wait on the bulk copies of their inputs with a time budget (0.5 s per wait); a wait
+ * that runs out stops that CTA without writing the tile it waited for and sets a bit in
+ * a per-device error word. fem_device_error synchronises `stream`, reads and clears the
+ * word of the current device, and returns FEM_ERR_TIMEOUT if any wait gave up since the
+ * last call (outputs of the calls in between are then incomplete), else FEM_OK.
+ * ------------------------------------------------------------------------------- */
+fem_status fem_device_error(fem_stream stream);
+
+/* fem_selftest_wait -- launches one CTA that waits, with the bounded wait of the staged
+ * kernels and a budget of budget_ns (0 .. 10 s), for a barrier phase that never
+ * completes, so that the next fem_device_error() returns FEM_ERR_TIMEOUT. For tests of
+ * the timeout path; it faults nothing and leaves the context usable. */
+fem_status fem_selftest_wait(int64_t budget_ns, fem_stream stream);
+
 /* status text and the thread-local message of the last failing call */
 const char *fem_status_string(fem_status st);
 const char *fem_last_error(void);

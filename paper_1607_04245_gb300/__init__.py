@@ -17,11 +17,13 @@ from .binding import (  # noqa: F401
     fem_adjoint_laplacian,
     fem_build_node2cell,
     fem_check_mesh,
+    fem_device_error,
     fem_gather_nodes,
     fem_get_mixed_threshold,
     fem_integrate_elasticity,
     fem_integrate_laplacian,
     fem_probe,
+    fem_selftest_wait,
     fem_set_mixed_threshold,
     fem_status_string,
     fem_version,

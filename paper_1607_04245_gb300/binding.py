@@ -51,6 +51,8 @@ def lib():
             "fem_check_mesh": [ci, i64, i64, P, P, P, P],
             "fem_probe": [ci, i64, ci, P, P],
             "fem_set_mixed_threshold": [cd],
+            "fem_device_error": [P],
+            "fem_selftest_wait": [i64, P],
         }
         for name, args in sig.items():
             f = getattr(L, name)
@@ -249,6 +251,17 @@ def fem_probe(kind: int, n_threads: int, iters: int, out=None, stream=None) -> t
     st = lib().fem_probe(kind, n_threads, iters, _dev(out, "out", dt, (n_threads,)), _stream(stream))
     _check("fem_probe", st)
     return out
+
+
+def fem_device_error(stream=None) -> int:
+    """Synchronise `stream`; return (and clear) the device error status: 0 (FEM_OK) or
+    -6 (FEM_ERR_TIMEOUT) when a kernel gave up a bounded device-side wait."""
+    return int(lib().fem_device_error(_stream(stream)))
+
+
+def fem_selftest_wait(budget_ns: int, stream=None) -> None:
+    """Launch the bounded-wait self-test (a wait that can never succeed, `budget_ns` long)."""
+    _check("fem_selftest_wait", lib().fem_selftest_wait(int(budget_ns), _stream(stream)))
 
 
 def fem_set_mixed_threshold(tau: float) -> None:

@@ -14,6 +14,7 @@
 #include <cfloat>
 #include <type_traits>
 
+#include "fem_f2.cuh"
 #include "fem_internal.cuh"
 
 namespace fem {
@@ -78,6 +79,35 @@ __device__ __forceinline__ void store_row(double *p, const double (&v)[CPT]) {
     }
 }
 
+// ------------------------------------------------------------------ generic arithmetic
+// The cell algebra below is written once for double, float and f2 (two cells per value).
+
+// (both overloads are declared here: an unqualified fma() inside namespace fem must never
+// resolve a double call to the float version)
+__device__ __forceinline__ double fma(double a, double b, double c) { return ::fma(a, b, c); }
+__device__ __forceinline__ float fma(float a, float b, float c) { return fmaf(a, b, c); }
+
+// a*b - c*d
+__device__ __forceinline__ double diffprod(double a, double b, double c, double d) { return fma(a, b, -(c * d)); }
+__device__ __forceinline__ float diffprod(float a, float b, float c, float d) { return fmaf(a, b, -(c * d)); }
+__device__ __forceinline__ f2 diffprod(f2 a, f2 b, f2 c, f2 d) { return a * b - c * d; }
+
+// num / |den|: one correctly-rounded division in float64, the fast reciprocal in float32
+__device__ __forceinline__ double quot_abs(double num, double den) { return num / fabs(den); }
+__device__ __forceinline__ float quot_abs(float num, float den) { return __fdividef(num, fabsf(den)); }
+__device__ __forceinline__ f2 quot_abs(f2 num, f2 den) {
+    return f2_make(__fdividef(f2_x(num), fabsf(f2_x(den))), __fdividef(f2_y(num), fabsf(f2_y(den))));
+}
+
+__device__ __forceinline__ double neg(double x) { return -x; }
+__device__ __forceinline__ float neg(float x) { return -x; }
+__device__ __forceinline__ f2 neg(f2 x) { return f2{0ull} - x; }
+
+template <class T> __device__ __forceinline__ T zero();
+template <> __device__ __forceinline__ double zero<double>() { return 0.0; }
+template <> __device__ __forceinline__ float zero<float>() { return 0.0f; }
+template <> __device__ __forceinline__ f2 zero<f2>() { return f2{0ull}; }
+
 // ------------------------------------------------------------------ geometry
 
 template <int DIM, class T>
@@ -85,16 +115,16 @@ __device__ __forceinline__ T adjugate_rows(const T (&e)[DIM][DIM], T (&n)[DIM][D
     if constexpr (DIM == 2) {
         n[0][0] = e[1][1], n[0][1] = -e[1][0];
         n[1][0] = -e[0][1], n[1][1] = e[0][0];
-        return e[0][0] * e[1][1] - e[0][1] * e[1][0];
+        return diffprod(e[0][0], e[1][1], e[0][1], e[1][0]);
     } else {
 #pragma unroll
         for (int j = 0; j < 3; ++j) {
             const T *a = e[(j + 1) % 3], *b = e[(j + 2) % 3];
-            n[j][0] = a[1] * b[2] - a[2] * b[1];
-            n[j][1] = a[2] * b[0] - a[0] * b[2];
-            n[j][2] = a[0] * b[1] - a[1] * b[0];
+            n[j][0] = diffprod(a[1], b[2], a[2], b[1]);
+            n[j][1] = diffprod(a[2], b[0], a[0], b[2]);
+            n[j][2] = diffprod(a[0], b[1], a[1], b[0]);
         }
-        return e[0][0] * n[0][0] + e[0][1] * n[0][1] + e[0][2] * n[0][2];
+        return fma(e[0][2], n[0][2], fma(e[0][1], n[0][1], e[0][0] * n[0][0]));
     }
 }
 
@@ -102,60 +132,103 @@ template <int DIM, class T>
 __device__ __forceinline__ T dotv(const T *a, const T *b) {
     T s = a[0] * b[0];
 #pragma unroll
-    for (int i = 1; i < DIM; ++i) s += a[i] * b[i];
+    for (int i = 1; i < DIM; ++i) s = fma(a[i], b[i], s);
     return s;
 }
 
-// Float64 Jacobian columns of a cell from the coordinate arrays.
+// Gather the float64 coordinates of a cell's vertices: x[b][k] = X[k][v[b]].
 template <int DIM>
-__device__ __forceinline__ void columns_f64(const double *const (&X)[DIM], const uint32_t (&v)[DIM + 1],
-                                            double (&e)[DIM][DIM]) {
-    double x0[DIM];
+__device__ __forceinline__ void gather_coords(const double *const (&X)[DIM], const uint32_t (&v)[DIM + 1],
+                                              double (&x)[DIM + 1][DIM]) {
 #pragma unroll
-    for (int k = 0; k < DIM; ++k) x0[k] = ld_gather(X[k] + v[0]);
+    for (int b = 0; b <= DIM; ++b)
+#pragma unroll
+        for (int k = 0; k < DIM; ++k) x[b][k] = ld_gather(X[k] + v[b]);
+}
+
+// Float64 Jacobian columns e_j = x_j - x_0.
+template <int DIM>
+__device__ __forceinline__ void columns_f64(const double (&x)[DIM + 1][DIM], double (&e)[DIM][DIM]) {
 #pragma unroll
     for (int j = 0; j < DIM; ++j)
 #pragma unroll
-        for (int k = 0; k < DIM; ++k) e[j][k] = ld_gather(X[k] + v[j + 1]) - x0[k];
+        for (int k = 0; k < DIM; ++k) e[j][k] = x[j + 1][k] - x[0][k];
 }
 
 // Float32 Jacobian columns from float64 coordinates split into (hi, lo) pairs:
 // e_jk = (hi_jk - hi_0k) + (lo_jk - lo_0k); exact up to float32 rounding of the result.
 template <int DIM>
-__device__ __forceinline__ void columns_mixed(const double *const (&X)[DIM], const uint32_t (&v)[DIM + 1],
-                                              float (&e)[DIM][DIM]) {
+__device__ __forceinline__ void columns_mixed(const double (&x)[DIM + 1][DIM], float (&e)[DIM][DIM]) {
     float hi[DIM + 1][DIM], lo[DIM + 1][DIM];
 #pragma unroll
     for (int b = 0; b <= DIM; ++b)
 #pragma unroll
-        for (int k = 0; k < DIM; ++k) {
-            double x = ld_gather(X[k] + v[b]);
-            split_f64(static_cast<uint32_t>(__double2loint(x)), static_cast<uint32_t>(__double2hiint(x)),
+        for (int k = 0; k < DIM; ++k)
+            split_f64(static_cast<uint32_t>(__double2loint(x[b][k])), static_cast<uint32_t>(__double2hiint(x[b][k])),
                       hi[b][k], lo[b][k]);
-        }
 #pragma unroll
     for (int j = 0; j < DIM; ++j)
 #pragma unroll
         for (int k = 0; k < DIM; ++k) e[j][k] = fmaf(lo[j + 1][k] - lo[0][k], 0x1p-23f, hi[j + 1][k] - hi[0][k]);
 }
 
-// Float32 Jacobian columns from coordinates rounded to float32 (FP32 ablation).
+// The same for two cells at once (lane x: cell xa, lane y: cell xb).
 template <int DIM>
-__device__ __forceinline__ void columns_f32(const double *const (&X)[DIM], const uint32_t (&v)[DIM + 1],
-                                            float (&e)[DIM][DIM]) {
-    float x[DIM + 1][DIM];
+__device__ __forceinline__ void columns_mixed2(const double (&xa)[DIM + 1][DIM], const double (&xb)[DIM + 1][DIM],
+                                               f2 (&e)[DIM][DIM]) {
+    f2 hi[DIM + 1][DIM], lo[DIM + 1][DIM];
 #pragma unroll
     for (int b = 0; b <= DIM; ++b)
 #pragma unroll
         for (int k = 0; k < DIM; ++k) {
-            double d = ld_gather(X[k] + v[b]);
-            x[b][k] = round_f64_to_f32(static_cast<uint32_t>(__double2loint(d)),
-                                       static_cast<uint32_t>(__double2hiint(d)));
+            float ha, la, hb, lb;
+            split_f64(static_cast<uint32_t>(__double2loint(xa[b][k])), static_cast<uint32_t>(__double2hiint(xa[b][k])),
+                      ha, la);
+            split_f64(static_cast<uint32_t>(__double2loint(xb[b][k])), static_cast<uint32_t>(__double2hiint(xb[b][k])),
+                      hb, lb);
+            hi[b][k] = f2_make(ha, hb);
+            lo[b][k] = f2_make(la, lb);
         }
+    const f2 scale = f2_splat(0x1p-23f);
 #pragma unroll
     for (int j = 0; j < DIM; ++j)
 #pragma unroll
-        for (int k = 0; k < DIM; ++k) e[j][k] = x[j + 1][k] - x[0][k];
+        for (int k = 0; k < DIM; ++k) e[j][k] = fma(lo[j + 1][k] - lo[0][k], scale, hi[j + 1][k] - hi[0][k]);
+}
+
+// Float32 Jacobian columns from coordinates rounded to float32 (FP32 ablation).
+template <int DIM>
+__device__ __forceinline__ void columns_f32(const double (&x)[DIM + 1][DIM], float (&e)[DIM][DIM]) {
+    float xf[DIM + 1][DIM];
+#pragma unroll
+    for (int b = 0; b <= DIM; ++b)
+#pragma unroll
+        for (int k = 0; k < DIM; ++k)
+            xf[b][k] = round_f64_to_f32(static_cast<uint32_t>(__double2loint(x[b][k])),
+                                        static_cast<uint32_t>(__double2hiint(x[b][k])));
+#pragma unroll
+    for (int j = 0; j < DIM; ++j)
+#pragma unroll
+        for (int k = 0; k < DIM; ++k) e[j][k] = xf[j + 1][k] - xf[0][k];
+}
+
+// The same for two cells at once.
+template <int DIM>
+__device__ __forceinline__ void columns_f32_2(const double (&xa)[DIM + 1][DIM], const double (&xb)[DIM + 1][DIM],
+                                              f2 (&e)[DIM][DIM]) {
+    f2 xf[DIM + 1][DIM];
+#pragma unroll
+    for (int b = 0; b <= DIM; ++b)
+#pragma unroll
+        for (int k = 0; k < DIM; ++k)
+            xf[b][k] = f2_make(round_f64_to_f32(static_cast<uint32_t>(__double2loint(xa[b][k])),
+                                                static_cast<uint32_t>(__double2hiint(xa[b][k]))),
+                               round_f64_to_f32(static_cast<uint32_t>(__double2loint(xb[b][k])),
+                                                static_cast<uint32_t>(__double2hiint(xb[b][k]))));
+#pragma unroll
+    for (int j = 0; j < DIM; ++j)
+#pragma unroll
+        for (int k = 0; k < DIM; ++k) e[j][k] = xf[j + 1][k] - xf[0][k];
 }
 
 // Shape test of the mixed form: det^2 >= tau^2 prod_j |e_j|^2 (Hadamard ratio >= tau),
@@ -167,6 +240,19 @@ __device__ __forceinline__ bool shape_ok(const float (&e)[DIM][DIM], float det, 
     for (int j = 1; j < DIM; ++j) p *= dotv<DIM>(e[j], e[j]);
     float d2 = det * det;
     return d2 >= fmaxf(tau2 * p, FLT_MIN) && d2 <= FLT_MAX;
+}
+
+// The shape test for two cells: (ok of lane x, ok of lane y).
+template <int DIM>
+__device__ __forceinline__ void shape_ok2(const f2 (&e)[DIM][DIM], f2 det, float tau2, bool &oka, bool &okb) {
+    f2 p = dotv<DIM>(e[0], e[0]);
+#pragma unroll
+    for (int j = 1; j < DIM; ++j) p = p * dotv<DIM>(e[j], e[j]);
+    const f2 d2 = det * det;
+    const f2 lim = p * f2_splat(tau2);
+    const float da = f2_x(d2), db = f2_y(d2);
+    oka = da >= fmaxf(f2_x(lim), FLT_MIN) && da <= FLT_MAX;
+    okb = db >= fmaxf(f2_y(lim), FLT_MIN) && db <= FLT_MAX;
 }
 
 // ------------------------------------------------------------------ quadrature sums
@@ -194,6 +280,38 @@ struct Dot2Sum {
     }
     __device__ __forceinline__ float value() const { return s + c; }
     __device__ __forceinline__ double value_f64() const { return static_cast<double>(s) + static_cast<double>(c); }
+};
+
+// Dot2 for two cells at once; the weight is the same in both lanes, so -w is a constant
+// and TwoProduct needs no negation.
+struct Dot2Sum2 {
+    f2 s, c;
+    __device__ __forceinline__ void first(float w, f2 x) {
+        s = f2_splat(w) * x;
+        c = fma(f2_splat(w), x, f2_splat(-w) * x);
+    }
+    __device__ __forceinline__ void add(float w, f2 x) {
+        const f2 p = f2_splat(w) * x;
+        const f2 pe = fma(f2_splat(w), x, f2_splat(-w) * x);
+        const f2 t = s + p;
+        const f2 bb = t - s;
+        const f2 se = (s - (t - bb)) + (p - bb);
+        s = t;
+        c = c + (pe + se);
+    }
+    __device__ __forceinline__ f2 value() const { return s + c; }
+    __device__ __forceinline__ double value_f64_x() const { return double(f2_x(s)) + double(f2_x(c)); }
+    __device__ __forceinline__ double value_f64_y() const { return double(f2_y(s)) + double(f2_y(c)); }
+};
+
+// sum_q w_q c_q in plain f32x2 (FP32 ablation)
+struct PlainSum2 {
+    f2 s;
+    __device__ __forceinline__ void first(float w, f2 x) { s = f2_splat(w) * x; }
+    __device__ __forceinline__ void add(float w, f2 x) { s = fma(f2_splat(w), x, s); }
+    __device__ __forceinline__ f2 value() const { return s; }
+    __device__ __forceinline__ double value_f64_x() const { return double(f2_x(s)); }
+    __device__ __forceinline__ double value_f64_y() const { return double(f2_y(s)); }
 };
 
 template <int P>

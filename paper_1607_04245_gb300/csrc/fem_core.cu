@@ -1,13 +1,17 @@
 // fem_core.cu -- status handling, argument checks, quadrature loading, launch sizing,
 // and the ALU-rate probes used for the rooflines of the float64 kernels.
 #include <atomic>
+#include <map>
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
 #include <mutex>
 #include <unordered_map>
 
-#include "fem_internal.cuh"
+#include "fem_pipe.cuh"
+
+// Device error word of the staged kernels (see fem_pipe.cuh); one per device.
+static __device__ unsigned g_fem_device_error = 0u;
 
 namespace fem {
 
@@ -72,6 +76,25 @@ fem_status check_common(int dim, int64_t n_cells, int64_t n_verts, const double 
 
 float mixed_tau() { return g_mixed_tau.load(std::memory_order_relaxed); }
 
+// Device address of g_fem_device_error on the current device, looked up once per device
+// (host code cannot use the symbol itself as a device pointer).
+unsigned *device_error_word() {
+    static std::mutex mu;
+    static unsigned *cached[64] = {nullptr};
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return nullptr;
+    std::lock_guard<std::mutex> lk(mu);
+    if (!cached[dev]) {
+        void *p = nullptr;
+        if (cudaGetSymbolAddress(&p, g_fem_device_error) != cudaSuccess) {
+            cudaGetLastError();
+            return nullptr;
+        }
+        cached[dev] = static_cast<unsigned *>(p);
+    }
+    return cached[dev];
+}
+
 static int sm_count() {
     static int cached[64] = {0};
     int dev = 0;
@@ -105,6 +128,39 @@ int grid_for(int64_t n_threads, int block, const void *kernel) {
     int64_t cap = int64_t(8) * occ * sm_count();
     int64_t g = need < cap ? need : cap;
     return static_cast<int>(g < 1 ? 1 : g);
+}
+
+// Persistent grid of a staged kernel with `smem` bytes of dynamic shared memory: as many
+// CTAs as fit on the device at once, at most one per tile. Raises the kernel's dynamic
+// shared-memory limit on first use (per device and kernel).
+fem_status staged_grid(const void *kernel, size_t smem, int64_t n_tiles, int &grid) {
+    static std::mutex mu;
+    static std::map<std::pair<const void *, size_t>, int> occ_cache[64];
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return fail(FEM_ERR_CUDA, "cudaGetDevice failed");
+    int occ = 0;
+    {
+        std::lock_guard<std::mutex> lk(mu);
+        auto &cache = occ_cache[dev];
+        const auto key = std::make_pair(kernel, smem);
+        auto it = cache.find(key);
+        if (it == cache.end()) {
+            cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                 static_cast<int>(smem));
+            if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kernel, kBlock, smem);
+            if (e != cudaSuccess || occ < 1) {
+                cudaGetLastError();
+                return fail(FEM_ERR_CUDA, "staged kernel does not fit: %zu bytes of shared memory (%s)", smem,
+                            cudaGetErrorString(e));
+            }
+            it = cache.emplace(key, occ).first;
+        }
+        occ = it->second;
+    }
+    int64_t g = int64_t(occ) * sm_count();
+    if (n_tiles < g) g = n_tiles;
+    grid = static_cast<int>(g < 1 ? 1 : g);
+    return FEM_OK;
 }
 
 // ------------------------------------------------------------------ probes
@@ -161,9 +217,45 @@ __global__ void __launch_bounds__(256) probe_kernel(int iters, void *out) {
     }
 }
 
+// Self-test of the bounded wait: one thread initialises an mbarrier that expects two
+// arrivals, arrives once, and waits for a phase that can never complete.
+__global__ void selftest_wait_kernel(uint64_t budget_ns, unsigned *err) {
+    __shared__ uint64_t bar;
+    if (threadIdx.x != 0) return;
+    mbar_init(&bar, 2);
+    fence_barrier_init();
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_addr(&bar)) : "memory");
+    if (!mbar_wait_bounded(&bar, 0, budget_ns)) record_device_error(err, FEM_DEVERR_TIMEOUT);
+}
+
 }  // namespace fem
 
 using namespace fem;
+
+extern "C" fem_status fem_device_error(fem_stream stream) {
+    unsigned *w = device_error_word();
+    if (!w) return fail(FEM_ERR_CUDA, "fem_device_error: device error word unavailable");
+    cudaError_t e = cudaStreamSynchronize(stream);
+    if (e != cudaSuccess) return fail(FEM_ERR_CUDA, "fem_device_error: %s", cudaGetErrorString(e));
+    unsigned v = 0;
+    e = cudaMemcpy(&v, w, sizeof(v), cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess && v != 0u) {
+        const unsigned zero = 0u;
+        e = cudaMemcpy(w, &zero, sizeof(zero), cudaMemcpyHostToDevice);
+    }
+    if (e != cudaSuccess) return fail(FEM_ERR_CUDA, "fem_device_error: %s", cudaGetErrorString(e));
+    if (v & FEM_DEVERR_TIMEOUT) return fail(FEM_ERR_TIMEOUT, "a kernel gave up a bounded device-side wait");
+    return FEM_OK;
+}
+
+extern "C" fem_status fem_selftest_wait(int64_t budget_ns, fem_stream stream) {
+    if (budget_ns < 0 || budget_ns > int64_t(10) * 1000 * 1000 * 1000)
+        return fail(FEM_ERR_ARG, "budget_ns must lie in [0, 10 s]");
+    unsigned *w = device_error_word();
+    if (!w) return fail(FEM_ERR_CUDA, "fem_selftest_wait: device error word unavailable");
+    selftest_wait_kernel<<<1, 32, 0, stream>>>(static_cast<uint64_t>(budget_ns), w);
+    return check_launch("fem_selftest_wait");
+}
 
 extern "C" fem_status fem_probe(int kind, int64_t n_threads, int iters, void *out, fem_stream stream) {
     if (kind < 0 || kind > 3) return fail(FEM_ERR_ARG, "probe kind %d", kind);

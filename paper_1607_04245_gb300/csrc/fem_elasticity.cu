@@ -123,16 +123,18 @@ __global__ void __launch_bounds__(kBlock) el_kernel(const __grid_constant__ ElAr
 #pragma unroll
                 for (int k = 0; k < DIM; ++k) uu[b][k] = ld_gather(u + k * V + v[b]);
             }
+            double xs[NB][DIM];
+            gather_coords<DIM>(X, v, xs);
             T rr[NB][DIM];
             if constexpr (P == FEM_FP64) {
                 double e[DIM][DIM], n[DIM][DIM];
-                columns_f64<DIM>(X, v, e);
+                columns_f64<DIM>(xs, e);
                 double det = adjugate_rows<DIM>(e, n);
                 el_element<DIM>(n, det, uu, ls[i].value(), ms[i].value(), rr);
             } else {
                 float e[DIM][DIM], n[DIM][DIM];
-                if constexpr (P == FEM_FP32_MIXED) columns_mixed<DIM>(X, v, e);
-                else columns_f32<DIM>(X, v, e);
+                if constexpr (P == FEM_FP32_MIXED) columns_mixed<DIM>(xs, e);
+                else columns_f32<DIM>(xs, e);
                 float det = adjugate_rows<DIM>(e, n);
                 bool ok = true;
                 if constexpr (P == FEM_FP32_MIXED) ok = shape_ok<DIM>(e, det, a.tau2);
@@ -140,7 +142,7 @@ __global__ void __launch_bounds__(kBlock) el_kernel(const __grid_constant__ ElAr
                     el_element<DIM>(n, det, uu, ls[i].value(), ms[i].value(), rr);
                 } else {
                     double e64[DIM][DIM], n64[DIM][DIM], u64[NB][DIM], r64[NB][DIM];
-                    columns_f64<DIM>(X, v, e64);
+                    columns_f64<DIM>(xs, e64);
                     double det64 = adjugate_rows<DIM>(e64, n64);
 #pragma unroll
                     for (int b = 0; b < NB; ++b)

@@ -1,0 +1,71 @@
+// fem_f2.cuh -- packed pairs of float32 values (two cells in one 64-bit register).
+//
+// sm_100-family GPUs execute add / sub / mul / fma on .f32x2 operands as one
+// instruction, so the float32 cell arithmetic of two cells runs at half the issue cost.
+// The kernels process cells in pairs: every float32 quantity of the per-cell algebra
+// (Jacobian, adjugate, field gradient, quadrature sums, element vector) is an f2 whose
+// two lanes belong to two different cells. All operations round to nearest, one
+// rounding per operation (no contraction), so the error-free transformations of the
+// compensated sums stay exact.
+#pragma once
+
+#include <stdint.h>
+
+namespace fem {
+
+struct f2 {
+    unsigned long long v;
+};
+
+__device__ __forceinline__ f2 f2_make(float a, float b) {
+    f2 r;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(r.v) : "f"(a), "f"(b));
+    return r;
+}
+
+__device__ __forceinline__ f2 f2_splat(float a) { return f2_make(a, a); }
+
+__device__ __forceinline__ float f2_x(f2 a) {
+    float x, y;
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(x), "=f"(y) : "l"(a.v));
+    return x;
+}
+
+__device__ __forceinline__ float f2_y(f2 a) {
+    float x, y;
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(x), "=f"(y) : "l"(a.v));
+    return y;
+}
+
+__device__ __forceinline__ f2 operator+(f2 a, f2 b) {
+    f2 r;
+    asm("add.rn.f32x2 %0, %1, %2;" : "=l"(r.v) : "l"(a.v), "l"(b.v));
+    return r;
+}
+
+__device__ __forceinline__ f2 operator-(f2 a, f2 b) {
+    f2 r;
+    asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(r.v) : "l"(a.v), "l"(b.v));
+    return r;
+}
+
+__device__ __forceinline__ f2 operator*(f2 a, f2 b) {
+    f2 r;
+    asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(r.v) : "l"(a.v), "l"(b.v));
+    return r;
+}
+
+__device__ __forceinline__ f2 operator-(f2 a) {
+    // flip both sign bits (exact)
+    f2 r;
+    r.v = a.v ^ 0x8000000080000000ull;
+    return r;
+}
+
+__device__ __forceinline__ f2 fma(f2 a, f2 b, f2 c) {
+    f2 r;
+    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(r.v) : "l"(a.v), "l"(b.v), "l"(c.v));
+    return r;
+}
+
+}  // namespace fem

@@ -12,7 +12,10 @@
 //     dJ/dK_{e,q}  = w_q |det J| (sum_b lambda_b G_b) . g = w_q (h_lambda . h_u) / |det J|
 //     dJ/du_{e,a}  = (Kbar / |det J|) n_a . h_lambda   (the residual of the field lambda_e)
 // The second is written per element to scratch and summed per vertex afterwards.
+#include <algorithm>
+
 #include "fem_cell.cuh"
+#include "fem_pipe.cuh"
 
 namespace fem {
 
@@ -30,29 +33,31 @@ struct LapArgs {
     QuadW w;
 };
 
-// r_b from the adjugate rows, the determinant, the nodal values and Kbar.
+// r_b from the adjugate rows, the determinant, the nodal values and Kbar (T = double,
+// float, or f2 for two cells at once).
 template <int DIM, class T>
 __device__ __forceinline__ void lap_element(const T (&n)[DIM][DIM], T det, const T (&uu)[DIM + 1], T kbar,
                                             T (&r)[DIM + 1]) {
     T h[DIM];
+    {
+        const T du = uu[1] - uu[0];
 #pragma unroll
-    for (int i = 0; i < DIM; ++i) h[i] = T(0);
+        for (int i = 0; i < DIM; ++i) h[i] = du * n[0][i];
+    }
 #pragma unroll
-    for (int j = 0; j < DIM; ++j) {
-        T du = uu[j + 1] - uu[0];
+    for (int j = 1; j < DIM; ++j) {
+        const T du = uu[j + 1] - uu[0];
 #pragma unroll
         for (int i = 0; i < DIM; ++i) h[i] = fma(du, n[j][i], h[i]);
     }
-    T s;
-    if constexpr (std::is_same<T, double>::value) s = kbar / fabs(det);
-    else s = __fdividef(kbar, fabsf(det));
-    T sum = T(0);
+    const T s = quot_abs(kbar, det);
+    T sum = zero<T>();
 #pragma unroll
     for (int j = 0; j < DIM; ++j) {
         r[j + 1] = s * dotv<DIM>(n[j], h);
-        sum += r[j + 1];
+        sum = sum + r[j + 1];
     }
-    r[0] = -sum;
+    r[0] = neg(sum);
 }
 
 // h_lambda . h_u / |det J|
@@ -61,16 +66,14 @@ __device__ __forceinline__ T lap_dk_factor(const T (&n)[DIM][DIM], T det, const 
                                            const T (&ll)[DIM + 1]) {
     T hu[DIM], hl[DIM];
 #pragma unroll
-    for (int i = 0; i < DIM; ++i) hu[i] = T(0), hl[i] = T(0);
+    for (int i = 0; i < DIM; ++i) hu[i] = zero<T>(), hl[i] = zero<T>();
 #pragma unroll
     for (int j = 0; j < DIM; ++j) {
-        T du = uu[j + 1] - uu[0], dl = ll[j + 1] - ll[0];
+        const T du = uu[j + 1] - uu[0], dl = ll[j + 1] - ll[0];
 #pragma unroll
         for (int i = 0; i < DIM; ++i) hu[i] = fma(du, n[j][i], hu[i]), hl[i] = fma(dl, n[j][i], hl[i]);
     }
-    T t = dotv<DIM>(hl, hu);
-    if constexpr (std::is_same<T, double>::value) return t / fabs(det);
-    else return __fdividef(t, fabsf(det));
+    return quot_abs(dotv<DIM>(hl, hu), det);
 }
 
 template <int P>
@@ -79,6 +82,64 @@ __device__ __forceinline__ val_t<P> weight(const QuadW &w, int q) {
     else return w.wf[q];
 }
 
+// One cell: vertex coordinates xs, nodal values uu (adjoint: ll = lambda_e), the
+// quadrature sum of the coefficient ks; writes the element vector rr and (adjoint) the
+// dK factor tf.
+template <int DIM, int P, bool ADJ>
+__device__ __forceinline__ void lap_cell(const double (&xs)[DIM + 1][DIM],
+                                         const val_t<P> (&uu)[DIM + 1], const val_t<P> (&ll)[DIM + 1],
+                                         const qsum_t<P> &ks, float tau2, val_t<P> (&rr)[DIM + 1], val_t<P> &tf) {
+    constexpr int NB = DIM + 1;
+    if constexpr (P == FEM_FP64) {
+        double e[DIM][DIM], n[DIM][DIM];
+        columns_f64<DIM>(xs, e);
+        double det = adjugate_rows<DIM>(e, n);
+        if constexpr (ADJ) {
+            lap_element<DIM>(n, det, ll, ks.value(), rr);
+            tf = lap_dk_factor<DIM>(n, det, uu, ll);
+        } else {
+            lap_element<DIM>(n, det, uu, ks.value(), rr);
+        }
+    } else {
+        float e[DIM][DIM], n[DIM][DIM];
+        if constexpr (P == FEM_FP32_MIXED) columns_mixed<DIM>(xs, e);
+        else columns_f32<DIM>(xs, e);
+        float det = adjugate_rows<DIM>(e, n);
+        bool ok = true;
+        if constexpr (P == FEM_FP32_MIXED) ok = shape_ok<DIM>(e, det, tau2);
+        if (ok) {
+            if constexpr (ADJ) {
+                lap_element<DIM>(n, det, ll, ks.value(), rr);
+                tf = lap_dk_factor<DIM>(n, det, uu, ll);
+            } else {
+                lap_element<DIM>(n, det, uu, ks.value(), rr);
+            }
+        } else {
+            // badly shaped (or under/overflowing) cell: float64 geometry and sums
+            double e64[DIM][DIM], n64[DIM][DIM], u64[NB], r64[NB];
+            columns_f64<DIM>(xs, e64);
+            double det64 = adjugate_rows<DIM>(e64, n64);
+            const double kb64 = ks.value_f64();
+#pragma unroll
+            for (int b = 0; b < NB; ++b) u64[b] = uu[b];
+            if constexpr (ADJ) {
+                double l64[NB];
+#pragma unroll
+                for (int b = 0; b < NB; ++b) l64[b] = ll[b];
+                lap_element<DIM>(n64, det64, l64, kb64, r64);
+                tf = static_cast<float>(lap_dk_factor<DIM>(n64, det64, u64, l64));
+            } else {
+                lap_element<DIM>(n64, det64, u64, kb64, r64);
+            }
+#pragma unroll
+            for (int b = 0; b < NB; ++b) rr[b] = static_cast<float>(r64[b]);
+        }
+    }
+}
+
+// Direct kernel: one thread owns CPT consecutive cells and reads the cell-indexed rows
+// with (vector) loads from global memory. Used for any quadrature size, for inputs whose
+// rows are not 16-byte aligned, and where the staged kernel's stages do not fit.
 template <int DIM, int P, int CPT, bool ADJ>
 __global__ void __launch_bounds__(kBlock) lap_kernel(const __grid_constant__ LapArgs a) {
     constexpr int NB = DIM + 1;
@@ -131,55 +192,13 @@ __global__ void __launch_bounds__(kBlock) lap_kernel(const __grid_constant__ Lap
             for (int b = 0; b < NB; ++b) {
                 v[b] = clamp_vid(vid[b][i], a.V);
                 uu[b] = ld_gather(u + v[b]);
-                if constexpr (ADJ) ll[b] = lamv[b][i];
+                ll[b] = ADJ ? lamv[ADJ ? b : 0][i] : T(0);
             }
+            double xs[NB][DIM];
+            gather_coords<DIM>(X, v, xs);
             T rr[NB];
             T tf = T(0);
-            if constexpr (P == FEM_FP64) {
-                double e[DIM][DIM], n[DIM][DIM];
-                columns_f64<DIM>(X, v, e);
-                double det = adjugate_rows<DIM>(e, n);
-                if constexpr (ADJ) {
-                    lap_element<DIM>(n, det, ll, ks[i].value(), rr);
-                    tf = lap_dk_factor<DIM>(n, det, uu, ll);
-                } else {
-                    lap_element<DIM>(n, det, uu, ks[i].value(), rr);
-                }
-            } else {
-                float e[DIM][DIM], n[DIM][DIM];
-                if constexpr (P == FEM_FP32_MIXED) columns_mixed<DIM>(X, v, e);
-                else columns_f32<DIM>(X, v, e);
-                float det = adjugate_rows<DIM>(e, n);
-                bool ok = true;
-                if constexpr (P == FEM_FP32_MIXED) ok = shape_ok<DIM>(e, det, a.tau2);
-                if (ok) {
-                    if constexpr (ADJ) {
-                        lap_element<DIM>(n, det, ll, ks[i].value(), rr);
-                        tf = lap_dk_factor<DIM>(n, det, uu, ll);
-                    } else {
-                        lap_element<DIM>(n, det, uu, ks[i].value(), rr);
-                    }
-                } else {
-                    // badly shaped (or under/overflowing) cell: float64 geometry and sums
-                    double e64[DIM][DIM], n64[DIM][DIM], u64[NB], r64[NB];
-                    columns_f64<DIM>(X, v, e64);
-                    double det64 = adjugate_rows<DIM>(e64, n64);
-                    const double kb64 = ks[i].value_f64();
-                    if constexpr (ADJ) {
-                        double l64[NB];
-#pragma unroll
-                        for (int b = 0; b < NB; ++b) u64[b] = uu[b], l64[b] = ll[b];
-                        lap_element<DIM>(n64, det64, l64, kb64, r64);
-                        tf = static_cast<float>(lap_dk_factor<DIM>(n64, det64, u64, l64));
-                    } else {
-#pragma unroll
-                        for (int b = 0; b < NB; ++b) u64[b] = uu[b];
-                        lap_element<DIM>(n64, det64, u64, kb64, r64);
-                    }
-#pragma unroll
-                    for (int b = 0; b < NB; ++b) rr[b] = static_cast<float>(r64[b]);
-                }
-            }
+            lap_cell<DIM, P, ADJ>(xs, uu, ll, ks[i], a.tau2, rr, tf);
 #pragma unroll
             for (int b = 0; b < NB; ++b) r[b][i] = rr[b];
             tfac[i] = tf;
@@ -199,9 +218,330 @@ __global__ void __launch_bounds__(kBlock) lap_kernel(const __grid_constant__ Lap
     }
 }
 
+// ------------------------------------------------------------------ staged kernel
+
+// Float64 recomputation of one cell of the mixed form (badly shaped or non-finite):
+// float64 geometry and sums from the gathered coordinates and the float32 values.
+template <int DIM, bool ADJ>
+__device__ __forceinline__ void lap_cell_f64(const double (&xs)[DIM + 1][DIM], const float (&uf)[DIM + 1],
+                                             const float (&lf)[DIM + 1], double kbar, double (&r)[DIM + 1],
+                                             double &tf) {
+    constexpr int NB = DIM + 1;
+    double e[DIM][DIM], n[DIM][DIM], u64[NB], l64[NB];
+    columns_f64<DIM>(xs, e);
+    const double det = adjugate_rows<DIM>(e, n);
+#pragma unroll
+    for (int b = 0; b < NB; ++b) u64[b] = uf[b], l64[b] = lf[b];
+    if constexpr (ADJ) {
+        lap_element<DIM>(n, det, l64, kbar, r);
+        tf = lap_dk_factor<DIM>(n, det, u64, l64);
+    } else {
+        lap_element<DIM>(n, det, u64, kbar, r);
+        tf = 0.0;
+    }
+}
+
+template <int P>
+using qsum2_t = typename std::conditional<P == FEM_FP32_MIXED, Dot2Sum2, PlainSum2>::type;
+
+// Two cells of a float32 form at once (lane x: cell a, lane y: cell b), vertex ids va,
+// vb. The coordinates are gathered here and are dead once split into float32; the rare
+// float64 recomputation gathers them again (cache hits) instead of keeping them live.
+template <int DIM, int P, bool ADJ>
+__device__ __forceinline__ void lap_pair(const double *const (&X)[DIM], const uint32_t (&va)[DIM + 1],
+                                         const uint32_t (&vb)[DIM + 1], const f2 (&uu)[DIM + 1],
+                                         const f2 (&ll)[DIM + 1], const qsum2_t<P> &ks, float tau2,
+                                         f2 (&rr)[DIM + 1], f2 &tf) {
+    constexpr int NB = DIM + 1;
+    f2 e[DIM][DIM], n[DIM][DIM];
+    {
+        double xa[NB][DIM], xb[NB][DIM];
+        gather_coords<DIM>(X, va, xa);
+        gather_coords<DIM>(X, vb, xb);
+        if constexpr (P == FEM_FP32_MIXED) columns_mixed2<DIM>(xa, xb, e);
+        else columns_f32_2<DIM>(xa, xb, e);
+    }
+    const f2 det = adjugate_rows<DIM>(e, n);
+    if constexpr (ADJ) {
+        lap_element<DIM>(n, det, ll, ks.value(), rr);
+        tf = lap_dk_factor<DIM>(n, det, uu, ll);
+    } else {
+        lap_element<DIM>(n, det, uu, ks.value(), rr);
+    }
+    if constexpr (P == FEM_FP32_MIXED) {
+        bool oka, okb;
+        shape_ok2<DIM>(e, det, tau2, oka, okb);
+        if (!(oka && okb)) {
+            float ua[NB], ub[NB], la[NB], lb[NB];
+#pragma unroll
+            for (int b = 0; b < NB; ++b) {
+                ua[b] = f2_x(uu[b]), ub[b] = f2_y(uu[b]);
+                la[b] = f2_x(ll[b]), lb[b] = f2_y(ll[b]);
+            }
+            float tx = f2_x(tf), ty = f2_y(tf);
+            float rx[NB], ry[NB];
+#pragma unroll
+            for (int b = 0; b < NB; ++b) rx[b] = f2_x(rr[b]), ry[b] = f2_y(rr[b]);
+            double r64[NB], t64, xs[NB][DIM];
+            if (!oka) {
+                gather_coords<DIM>(X, va, xs);
+                lap_cell_f64<DIM, ADJ>(xs, ua, la, ks.value_f64_x(), r64, t64);
+#pragma unroll
+                for (int b = 0; b < NB; ++b) rx[b] = static_cast<float>(r64[b]);
+                tx = static_cast<float>(t64);
+            }
+            if (!okb) {
+                gather_coords<DIM>(X, vb, xs);
+                lap_cell_f64<DIM, ADJ>(xs, ub, lb, ks.value_f64_y(), r64, t64);
+#pragma unroll
+                for (int b = 0; b < NB; ++b) ry[b] = static_cast<float>(r64[b]);
+                ty = static_cast<float>(t64);
+            }
+#pragma unroll
+            for (int b = 0; b < NB; ++b) rr[b] = f2_make(rx[b], ry[b]);
+            tf = f2_make(tx, ty);
+        }
+    }
+}
+
+// four consecutive values of a cell-indexed row in shared memory
+__device__ __forceinline__ void lds4(const int32_t *p, int32_t (&v)[4]) {
+    const int4 t = *reinterpret_cast<const int4 *>(p);
+    v[0] = t.x, v[1] = t.y, v[2] = t.z, v[3] = t.w;
+}
+__device__ __forceinline__ void lds4(const float *p, float (&v)[4]) {
+    const float4 t = *reinterpret_cast<const float4 *>(p);
+    v[0] = t.x, v[1] = t.y, v[2] = t.z, v[3] = t.w;
+}
+__device__ __forceinline__ void lds4(const double *p, double (&v)[4]) {
+    const double2 t0 = reinterpret_cast<const double2 *>(p)[0], t1 = reinterpret_cast<const double2 *>(p)[1];
+    v[0] = t0.x, v[1] = t0.y, v[2] = t1.x, v[3] = t1.y;
+}
+
+// Staged kernel (fem_pipe.cuh): persistent CTAs, tiles of kTile consecutive cells, the
+// tile's connectivity, coefficient (and adjoint-weight) rows brought into a ring of
+// shared-memory stages by the bulk-copy engine, `stages` tiles ahead. Within a tile each
+// thread owns 4 consecutive cells: 128-bit shared-memory reads of every row, 128-bit
+// streaming stores of every output row, and (float32 forms) the cells processed as two
+// f32x2 pairs. NQ > 0 fixes the quadrature size at compile time; NQ = 0 reads it from
+// the arguments.
+#ifndef FEM_STAGED_MIN_CTAS
+#define FEM_STAGED_MIN_CTAS 2
+#endif
+#ifndef FEM_STAGED_BUDGET_KB
+#define FEM_STAGED_BUDGET_KB 72
+#endif
+constexpr int kTile = 4 * kBlock;
+constexpr int kMaxStages = 4;
+
+template <class T>
+__host__ __device__ constexpr uint32_t lap_stage_bytes(int nb, int nq, bool adj) {
+    return uint32_t(kTile) * (4u * nb + uint32_t(sizeof(T)) * (nq + (adj ? nb : 0)));
+}
+
+template <int DIM, int P, int NQ, bool ADJ>
+__global__ void __launch_bounds__(kBlock, FEM_STAGED_MIN_CTAS)
+    lap_staged_kernel(const __grid_constant__ LapArgs a, int stages, unsigned *err) {
+    constexpr int NB = DIM + 1;
+    using T = val_t<P>;
+    extern __shared__ __align__(128) unsigned char smem[];
+    __shared__ uint64_t full[kMaxStages];
+    __shared__ int s_abort;
+
+    const int64_t C = a.C;
+    const int nq = NQ > 0 ? NQ : a.w.nq;
+    const int64_t ntiles = (C + kTile - 1) / kTile;
+    const uint32_t stage_bytes = lap_stage_bytes<T>(NB, nq, ADJ);
+    const T *__restrict__ u = static_cast<const T *>(a.u);
+    const double *X[DIM];
+#pragma unroll
+    for (int k = 0; k < DIM; ++k) X[k] = a.X[k];
+
+    // stage layout: conn[NB][kTile] int32 | K[nq][kTile] T | lambda[NB][kTile] T
+    auto stage_conn = [&](int s) { return reinterpret_cast<int32_t *>(smem + size_t(s) * stage_bytes); };
+    auto stage_K = [&](int s) { return reinterpret_cast<T *>(stage_conn(s) + NB * kTile); };
+    auto stage_lam = [&](int s) { return stage_K(s) + nq * kTile; };
+
+    // one elected thread fills stage s with tile t
+    auto issue = [&](int64_t t, int s, uint64_t pol) {
+        const int64_t c0 = t * kTile;
+        const uint32_t n = static_cast<uint32_t>(C - c0 < int64_t(kTile) ? C - c0 : int64_t(kTile));
+        const uint32_t bytes = n * (4u * NB + uint32_t(sizeof(T)) * (nq + (ADJ ? NB : 0)));
+        mbar_arrive_expect_tx(&full[s], bytes);
+        for (int b = 0; b < NB; ++b) bulk_copy_g2s(stage_conn(s) + b * kTile, a.conn + b * C + c0, n * 4u, &full[s], pol);
+        const T *K = static_cast<const T *>(a.K);
+        for (int q = 0; q < nq; ++q)
+            bulk_copy_g2s(stage_K(s) + q * kTile, K + q * C + c0, n * uint32_t(sizeof(T)), &full[s], pol);
+        if constexpr (ADJ) {
+            const T *L = static_cast<const T *>(a.lam);
+            for (int b = 0; b < NB; ++b)
+                bulk_copy_g2s(stage_lam(s) + b * kTile, L + b * C + c0, n * uint32_t(sizeof(T)), &full[s], pol);
+        }
+    };
+
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < stages; ++s) mbar_init(&full[s], 1);
+        fence_barrier_init();
+        s_abort = 0;
+    }
+    __syncthreads();
+    uint64_t pol = 0;
+    if (threadIdx.x == 0) {
+        pol = l2_evict_first_policy();
+        for (int s = 0; s < stages; ++s) {
+            const int64_t t = blockIdx.x + int64_t(s) * gridDim.x;
+            if (t < ntiles) issue(t, s, pol);
+        }
+    }
+
+    T *__restrict__ out = static_cast<T *>(a.out);
+    T *__restrict__ dK = static_cast<T *>(a.dK);
+    const int j0 = 4 * threadIdx.x;
+    int64_t t = blockIdx.x;
+    for (int64_t i = 0; t < ntiles; ++i, t += gridDim.x) {
+        const int s = static_cast<int>(i % stages);
+        const uint32_t parity = static_cast<uint32_t>((i / stages) & 1);
+        const int64_t c0 = t * kTile;
+        const int n = static_cast<int>(C - c0 < int64_t(kTile) ? C - c0 : int64_t(kTile));
+        if (mbar_wait_bounded(&full[s], parity, kWaitBudgetNs)) {
+            if (j0 < n) {  // n is a multiple of 4: a thread's four cells are all present or all absent
+                const int32_t *sc = stage_conn(s) + j0;
+                const T *sK = stage_K(s) + j0;
+                uint32_t v[4][NB];
+#pragma unroll
+                for (int b = 0; b < NB; ++b) {
+                    int32_t id[4];
+                    lds4(sc + b * kTile, id);
+#pragma unroll
+                    for (int c = 0; c < 4; ++c) v[c][b] = clamp_vid(id[c], a.V);
+                }
+                T lv[4][NB];
+                if constexpr (ADJ) {
+#pragma unroll
+                    for (int b = 0; b < NB; ++b) {
+                        T l4[4];
+                        lds4(stage_lam(s) + j0 + b * kTile, l4);
+#pragma unroll
+                        for (int c = 0; c < 4; ++c) lv[c][b] = l4[c];
+                    }
+                }
+                T r[NB][4], tfv[4];
+                if constexpr (P == FEM_FP64) {
+                    qsum_t<P> ks[4];
+                    for (int q = 0; q < nq; ++q) {
+                        T k4[4];
+                        lds4(sK + q * kTile, k4);
+#pragma unroll
+                        for (int c = 0; c < 4; ++c) {
+                            if (q == 0) ks[c].first(weight<P>(a.w, 0), k4[c]);
+                            else ks[c].add(weight<P>(a.w, q), k4[c]);
+                        }
+                    }
+#pragma unroll
+                    for (int c = 0; c < 4; ++c) {
+                        double xs[NB][DIM];
+                        T uu[NB], rr[NB], tf = T(0), ll[NB];
+#pragma unroll
+                        for (int b = 0; b < NB; ++b) {
+                            uu[b] = ld_gather(u + v[c][b]);
+                            ll[b] = ADJ ? lv[c][b] : T(0);
+                        }
+                        gather_coords<DIM>(X, v[c], xs);
+                        lap_cell<DIM, P, ADJ>(xs, uu, ll, ks[c], a.tau2, rr, tf);
+#pragma unroll
+                        for (int b = 0; b < NB; ++b) r[b][c] = rr[b];
+                        tfv[c] = tf;
+                    }
+                } else {
+                    qsum2_t<P> ks[2];
+#pragma unroll(NQ > 0 ? NQ : 1)
+                    for (int q = 0; q < nq; ++q) {
+                        T k4[4];
+                        lds4(sK + q * kTile, k4);
+                        const float wq = a.w.wf[q];
+#pragma unroll
+                        for (int p = 0; p < 2; ++p) {
+                            const f2 kp = f2_make(k4[2 * p], k4[2 * p + 1]);
+                            if (q == 0) ks[p].first(wq, kp);
+                            else ks[p].add(wq, kp);
+                        }
+                    }
+#pragma unroll
+                    for (int p = 0; p < 2; ++p) {
+                        f2 uu[NB], ll[NB], rr[NB], tf = zero<f2>();
+#pragma unroll
+                        for (int b = 0; b < NB; ++b) {
+                            uu[b] = f2_make(ld_gather(u + v[2 * p][b]), ld_gather(u + v[2 * p + 1][b]));
+                            ll[b] = ADJ ? f2_make(lv[2 * p][b], lv[2 * p + 1][b]) : zero<f2>();
+                        }
+                        lap_pair<DIM, P, ADJ>(X, v[2 * p], v[2 * p + 1], uu, ll, ks[p], a.tau2, rr, tf);
+#pragma unroll
+                        for (int b = 0; b < NB; ++b) r[b][2 * p] = f2_x(rr[b]), r[b][2 * p + 1] = f2_y(rr[b]);
+                        tfv[2 * p] = f2_x(tf), tfv[2 * p + 1] = f2_y(tf);
+                    }
+                }
+#pragma unroll
+                for (int b = 0; b < NB; ++b) store_row<4>(out + b * C + c0 + j0, r[b]);
+                if constexpr (ADJ) {
+                    for (int q = 0; q < nq; ++q) {
+                        const T wq = weight<P>(a.w, q);
+                        T row[4];
+#pragma unroll
+                        for (int c = 0; c < 4; ++c) row[c] = wq * tfv[c];
+                        store_row<4>(dK + q * C + c0 + j0, row);
+                    }
+                }
+            }
+        } else {
+            s_abort = 1;
+        }
+        __syncthreads();  // every thread is done with stage s (or the wait gave up)
+        if (s_abort) break;
+        if (threadIdx.x == 0) {
+            const int64_t tn = t + int64_t(stages) * gridDim.x;
+            if (tn < ntiles) issue(tn, s, pol);
+        }
+    }
+    if (s_abort && threadIdx.x == 0) {
+        // drain: wait (bounded) for every stage copy still in flight, then report
+        int64_t tt = t;
+        for (int i2 = 0; i2 < stages && tt < ntiles; ++i2, tt += gridDim.x) {
+            const int64_t idx = (tt - blockIdx.x) / gridDim.x;
+            mbar_wait_bounded(&full[idx % stages], static_cast<uint32_t>((idx / stages) & 1), kWaitBudgetNs);
+        }
+        record_device_error(err, FEM_DEVERR_TIMEOUT);
+    }
+}
+
+// Shared-memory budget of the staged kernel's ring (per CTA).
+constexpr uint32_t kStageBudget = uint32_t(FEM_STAGED_BUDGET_KB) << 10;
+constexpr uint32_t kStageMax = 200u << 10;
+
+template <int DIM, int P, int NQ, bool ADJ>
+static fem_status launch_staged(const LapArgs &a, uint32_t sb, cudaStream_t s) {
+    auto k = lap_staged_kernel<DIM, P, NQ, ADJ>;
+    const int stages = static_cast<int>(std::min<uint32_t>(kMaxStages, std::max<uint32_t>(2u, kStageBudget / sb)));
+    const size_t smem = size_t(stages) * sb;
+    unsigned *err = device_error_word();
+    if (!err) return fail(FEM_ERR_CUDA, "device error word unavailable");
+    int grid = 0;
+    fem_status st = staged_grid(reinterpret_cast<const void *>(k), smem, (a.C + kTile - 1) / kTile, grid);
+    if (st != FEM_OK) return st;
+    k<<<grid, kBlock, smem, s>>>(a, stages, err);
+    return FEM_OK;
+}
+
 template <int DIM, int P, bool ADJ>
 static fem_status launch_lap(const LapArgs &a, bool vec, cudaStream_t s) {
-    if (vec) {
+    using T = val_t<P>;
+    const uint32_t sb = lap_stage_bytes<T>(DIM + 1, a.w.nq, ADJ);
+    fem_status st = FEM_OK;
+    if (vec && 2u * sb <= kStageMax) {
+        // the quadrature size of the workloads' rules (3 points in 2D, 4 in 3D) is compiled in
+        if (a.w.nq == DIM + 1 && DIM == 3) st = launch_staged<DIM, P, 4, ADJ>(a, sb, s);
+        else if (a.w.nq == 3 && DIM == 2) st = launch_staged<DIM, P, 3, ADJ>(a, sb, s);
+        else st = launch_staged<DIM, P, 0, ADJ>(a, sb, s);
+    } else if (vec) {
         auto k = lap_kernel<DIM, P, 4, ADJ>;
         int grid = grid_for((a.C + 3) / 4, kBlock, reinterpret_cast<const void *>(k));
         k<<<grid, kBlock, 0, s>>>(a);
@@ -210,6 +550,7 @@ static fem_status launch_lap(const LapArgs &a, bool vec, cudaStream_t s) {
         int grid = grid_for(a.C, kBlock, reinterpret_cast<const void *>(k));
         k<<<grid, kBlock, 0, s>>>(a);
     }
+    if (st != FEM_OK) return st;
     return check_launch(ADJ ? "fem_adjoint_laplacian" : "fem_integrate_laplacian");
 }
 

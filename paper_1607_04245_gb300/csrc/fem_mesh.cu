@@ -237,8 +237,9 @@ __global__ void check_mesh_kernel(const double *X0, int64_t C, uint32_t V, const
             v[b] = clamp_vid(id, V);
         }
         if (!ids_ok) continue;
-        double e[DIM][DIM], n[DIM][DIM];
-        columns_f64<DIM>(X, v, e);
+        double xs[NB][DIM], e[DIM][DIM], n[DIM][DIM];
+        gather_coords<DIM>(X, v, xs);
+        columns_f64<DIM>(xs, e);
         double det = adjugate_rows<DIM>(e, n);
         // degenerate to rounding: |det J| <= 16 eps_64 prod_j |e_j| (FMA contraction can
         // leave a rounding residue instead of an exact zero for repeated vertices)
@@ -249,7 +250,7 @@ __global__ void check_mesh_kernel(const double *X0, int64_t C, uint32_t V, const
         if (degenerate) ++c_degen;
         else if (det < 0.0) ++c_neg;
         float ef[DIM][DIM], nf[DIM][DIM];
-        columns_mixed<DIM>(X, v, ef);
+        columns_mixed<DIM>(xs, ef);
         float detf = adjugate_rows<DIM>(ef, nf);
         if (!shape_ok<DIM>(ef, detf, tau2)) ++c_fallback;
     }
