@@ -62,6 +62,8 @@ template <int CPT>
 __device__ __forceinline__ void store_row(float *p, const float (&v)[CPT]) {
     if constexpr (CPT == 4) {
         __stcs(reinterpret_cast<float4 *>(p), make_float4(v[0], v[1], v[2], v[3]));
+    } else if constexpr (CPT == 2) {
+        __stcs(reinterpret_cast<float2 *>(p), make_float2(v[0], v[1]));
     } else {
 #pragma unroll
         for (int i = 0; i < CPT; ++i) __stcs(p + i, v[i]);
@@ -73,6 +75,8 @@ __device__ __forceinline__ void store_row(double *p, const double (&v)[CPT]) {
     if constexpr (CPT == 4) {
         __stcs(reinterpret_cast<double2 *>(p), make_double2(v[0], v[1]));
         __stcs(reinterpret_cast<double2 *>(p) + 1, make_double2(v[2], v[3]));
+    } else if constexpr (CPT == 2) {
+        __stcs(reinterpret_cast<double2 *>(p), make_double2(v[0], v[1]));
     } else {
 #pragma unroll
         for (int i = 0; i < CPT; ++i) __stcs(p + i, v[i]);

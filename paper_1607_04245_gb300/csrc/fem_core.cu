@@ -2,6 +2,7 @@
 // and the ALU-rate probes used for the rooflines of the float64 kernels.
 #include <atomic>
 #include <map>
+#include <tuple>
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
@@ -133,21 +134,21 @@ int grid_for(int64_t n_threads, int block, const void *kernel) {
 // Persistent grid of a staged kernel with `smem` bytes of dynamic shared memory: as many
 // CTAs as fit on the device at once, at most one per tile. Raises the kernel's dynamic
 // shared-memory limit on first use (per device and kernel).
-fem_status staged_grid(const void *kernel, size_t smem, int64_t n_tiles, int &grid) {
+fem_status staged_grid(const void *kernel, int block, size_t smem, int64_t n_tiles, int &grid) {
     static std::mutex mu;
-    static std::map<std::pair<const void *, size_t>, int> occ_cache[64];
+    static std::map<std::tuple<const void *, int, size_t>, int> occ_cache[64];
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return fail(FEM_ERR_CUDA, "cudaGetDevice failed");
     int occ = 0;
     {
         std::lock_guard<std::mutex> lk(mu);
         auto &cache = occ_cache[dev];
-        const auto key = std::make_pair(kernel, smem);
+        const auto key = std::make_tuple(kernel, block, smem);
         auto it = cache.find(key);
         if (it == cache.end()) {
             cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                                  static_cast<int>(smem));
-            if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kernel, kBlock, smem);
+            if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kernel, block, smem);
             if (e != cudaSuccess || occ < 1) {
                 cudaGetLastError();
                 return fail(FEM_ERR_CUDA, "staged kernel does not fit: %zu bytes of shared memory (%s)", smem,

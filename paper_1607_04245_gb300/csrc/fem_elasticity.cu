@@ -72,7 +72,9 @@ __device__ __forceinline__ val_t<P> el_weight(const QuadW &w, int q) {
     else return w.wf[q];
 }
 
-template <int DIM, int P, int CPT>
+// NQ > 0: quadrature size fixed at compile time, every coefficient row load issued
+// before the first sum; NQ = 0: read from the arguments.
+template <int DIM, int P, int CPT, int NQ>
 __global__ void __launch_bounds__(kBlock) el_kernel(const __grid_constant__ ElArgs a) {
     constexpr int NB = DIM + 1;
     using T = val_t<P>;
@@ -95,21 +97,35 @@ __global__ void __launch_bounds__(kBlock) el_kernel(const __grid_constant__ ElAr
         for (int b = 0; b < NB; ++b) load_row<CPT>(a.conn + b * C + c0, vid[b]);
 
         qsum_t<P> ls[CPT], ms[CPT];
-        {
-            T lq[CPT], mq[CPT];
-            load_row<CPT>(lam + c0, lq);
-            load_row<CPT>(mu + c0, mq);
-            const T w0 = el_weight<P>(a.w, 0);
+        if constexpr (NQ > 0) {
+            T lq[NQ][CPT], mq[NQ][CPT];
 #pragma unroll
-            for (int i = 0; i < CPT; ++i) ls[i].first(w0, lq[i]), ms[i].first(w0, mq[i]);
-        }
-        for (int q = 1; q < a.w.nq; ++q) {
-            T lq[CPT], mq[CPT];
-            load_row<CPT>(lam + q * C + c0, lq);
-            load_row<CPT>(mu + q * C + c0, mq);
-            const T wq = el_weight<P>(a.w, q);
+            for (int q = 0; q < NQ; ++q) load_row<CPT>(lam + q * C + c0, lq[q]), load_row<CPT>(mu + q * C + c0, mq[q]);
 #pragma unroll
-            for (int i = 0; i < CPT; ++i) ls[i].add(wq, lq[i]), ms[i].add(wq, mq[i]);
+            for (int i = 0; i < CPT; ++i)
+                ls[i].first(el_weight<P>(a.w, 0), lq[0][i]), ms[i].first(el_weight<P>(a.w, 0), mq[0][i]);
+#pragma unroll
+            for (int q = 1; q < NQ; ++q)
+#pragma unroll
+                for (int i = 0; i < CPT; ++i)
+                    ls[i].add(el_weight<P>(a.w, q), lq[q][i]), ms[i].add(el_weight<P>(a.w, q), mq[q][i]);
+        } else {
+            {
+                T lq[CPT], mq[CPT];
+                load_row<CPT>(lam + c0, lq);
+                load_row<CPT>(mu + c0, mq);
+                const T w0 = el_weight<P>(a.w, 0);
+#pragma unroll
+                for (int i = 0; i < CPT; ++i) ls[i].first(w0, lq[i]), ms[i].first(w0, mq[i]);
+            }
+            for (int q = 1; q < a.w.nq; ++q) {
+                T lq[CPT], mq[CPT];
+                load_row<CPT>(lam + q * C + c0, lq);
+                load_row<CPT>(mu + q * C + c0, mq);
+                const T wq = el_weight<P>(a.w, q);
+#pragma unroll
+                for (int i = 0; i < CPT; ++i) ls[i].add(wq, lq[i]), ms[i].add(wq, mq[i]);
+            }
         }
 
         T r[NB * DIM][CPT];
@@ -167,11 +183,15 @@ __global__ void __launch_bounds__(kBlock) el_kernel(const __grid_constant__ ElAr
 
 template <int DIM, int P>
 static fem_status launch_el(const ElArgs &a, bool vec, cudaStream_t s) {
-    if (vec) {
-        auto k = el_kernel<DIM, P, 4>;
+    // the quadrature size of the workloads' rules (3 points in 2D, 4 in 3D) is compiled in
+    if (vec && a.w.nq == DIM + 1) {
+        auto k = el_kernel<DIM, P, 4, DIM + 1>;
+        k<<<grid_for((a.C + 3) / 4, kBlock, reinterpret_cast<const void *>(k)), kBlock, 0, s>>>(a);
+    } else if (vec) {
+        auto k = el_kernel<DIM, P, 4, 0>;
         k<<<grid_for((a.C + 3) / 4, kBlock, reinterpret_cast<const void *>(k)), kBlock, 0, s>>>(a);
     } else {
-        auto k = el_kernel<DIM, P, 1>;
+        auto k = el_kernel<DIM, P, 1, 0>;
         k<<<grid_for(a.C, kBlock, reinterpret_cast<const void *>(k)), kBlock, 0, s>>>(a);
     }
     return check_launch("fem_integrate_elasticity");

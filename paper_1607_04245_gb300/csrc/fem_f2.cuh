@@ -25,17 +25,9 @@ __device__ __forceinline__ f2 f2_make(float a, float b) {
 
 __device__ __forceinline__ f2 f2_splat(float a) { return f2_make(a, a); }
 
-__device__ __forceinline__ float f2_x(f2 a) {
-    float x, y;
-    asm("mov.b64 {%0, %1}, %2;" : "=f"(x), "=f"(y) : "l"(a.v));
-    return x;
-}
+__device__ __forceinline__ float f2_x(f2 a) { return __uint_as_float(static_cast<uint32_t>(a.v)); }
 
-__device__ __forceinline__ float f2_y(f2 a) {
-    float x, y;
-    asm("mov.b64 {%0, %1}, %2;" : "=f"(x), "=f"(y) : "l"(a.v));
-    return y;
-}
+__device__ __forceinline__ float f2_y(f2 a) { return __uint_as_float(static_cast<uint32_t>(a.v >> 32)); }
 
 __device__ __forceinline__ f2 operator+(f2 a, f2 b) {
     f2 r;

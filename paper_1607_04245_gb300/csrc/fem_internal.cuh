@@ -102,6 +102,6 @@ __device__ __forceinline__ T ld_gather(const T *p) { return __ldg(p); }
 // Grid size: enough CTAs to cover the work, capped at a whole number of waves of the
 // device's SMs (the kernels are grid-stride loops).
 int grid_for(int64_t n_threads, int block, const void *kernel);
-fem_status staged_grid(const void *kernel, size_t smem, int64_t n_tiles, int &grid);
+fem_status staged_grid(const void *kernel, int block, size_t smem, int64_t n_tiles, int &grid);
 
 }  // namespace fem

@@ -140,7 +140,7 @@ __device__ __forceinline__ void lap_cell(const double (&xs)[DIM + 1][DIM],
 // Direct kernel: one thread owns CPT consecutive cells and reads the cell-indexed rows
 // with (vector) loads from global memory. Used for any quadrature size, for inputs whose
 // rows are not 16-byte aligned, and where the staged kernel's stages do not fit.
-template <int DIM, int P, int CPT, bool ADJ>
+template <int DIM, int P, int CPT, int NQ, bool ADJ>
 __global__ void __launch_bounds__(kBlock) lap_kernel(const __grid_constant__ LapArgs a) {
     constexpr int NB = DIM + 1;
     using T = val_t<P>;
@@ -160,20 +160,33 @@ __global__ void __launch_bounds__(kBlock) lap_kernel(const __grid_constant__ Lap
 #pragma unroll
         for (int b = 0; b < NB; ++b) load_row<CPT>(a.conn + b * C + c0, vid[b]);
 
-        // quadrature sum of the coefficient: Kbar = sum_q w_q K_q
+        // quadrature sum of the coefficient: Kbar = sum_q w_q K_q (with NQ > 0 every row
+        // load is issued before the first sum)
         qsum_t<P> ks[CPT];
-        {
-            T kq[CPT];
-            load_row<CPT>(K + c0, kq);
+        if constexpr (NQ > 0) {
+            T kq[NQ][CPT];
 #pragma unroll
-            for (int i = 0; i < CPT; ++i) ks[i].first(weight<P>(a.w, 0), kq[i]);
-        }
-        for (int q = 1; q < a.w.nq; ++q) {
-            T kq[CPT];
-            load_row<CPT>(K + q * C + c0, kq);
-            const T wq = weight<P>(a.w, q);
+            for (int q = 0; q < NQ; ++q) load_row<CPT>(K + q * C + c0, kq[q]);
 #pragma unroll
-            for (int i = 0; i < CPT; ++i) ks[i].add(wq, kq[i]);
+            for (int i = 0; i < CPT; ++i) ks[i].first(weight<P>(a.w, 0), kq[0][i]);
+#pragma unroll
+            for (int q = 1; q < NQ; ++q)
+#pragma unroll
+                for (int i = 0; i < CPT; ++i) ks[i].add(weight<P>(a.w, q), kq[q][i]);
+        } else {
+            {
+                T kq[CPT];
+                load_row<CPT>(K + c0, kq);
+#pragma unroll
+                for (int i = 0; i < CPT; ++i) ks[i].first(weight<P>(a.w, 0), kq[i]);
+            }
+            for (int q = 1; q < a.w.nq; ++q) {
+                T kq[CPT];
+                load_row<CPT>(K + q * C + c0, kq);
+                const T wq = weight<P>(a.w, q);
+#pragma unroll
+                for (int i = 0; i < CPT; ++i) ks[i].add(wq, kq[i]);
+            }
         }
 
         T lamv[ADJ ? NB : 1][CPT];
@@ -244,18 +257,49 @@ __device__ __forceinline__ void lap_cell_f64(const double (&xs)[DIM + 1][DIM], c
 template <int P>
 using qsum2_t = typename std::conditional<P == FEM_FP32_MIXED, Dot2Sum2, PlainSum2>::type;
 
+// Float64 recomputation of cell c of the mixed form, stored over the float32 result that
+// the caller has already written (same thread, program order). Everything is read again
+// from global memory: the path is rare and kept out of line so that none of its state
+// occupies registers on the common path.
+template <int DIM, bool ADJ>
+__device__ __noinline__ void lap_fallback_store(const LapArgs &a, int64_t c, double kbar) {
+    constexpr int NB = DIM + 1;
+    const int64_t C = a.C;
+    uint32_t v[NB];
+    float uf[NB], lf[NB];
+#pragma unroll
+    for (int b = 0; b < NB; ++b) {
+        v[b] = clamp_vid(a.conn[b * C + c], a.V);
+        uf[b] = static_cast<const float *>(a.u)[v[b]];
+        lf[b] = ADJ ? static_cast<const float *>(a.lam)[b * C + c] : 0.0f;
+    }
+    const double *X[DIM];
+#pragma unroll
+    for (int k = 0; k < DIM; ++k) X[k] = a.X[k];
+    double xs[NB][DIM], r64[NB], t64;
+    gather_coords<DIM>(X, v, xs);
+    lap_cell_f64<DIM, ADJ>(xs, uf, lf, kbar, r64, t64);
+    float *out = static_cast<float *>(a.out);
+#pragma unroll
+    for (int b = 0; b < NB; ++b) out[b * C + c] = static_cast<float>(r64[b]);
+    if constexpr (ADJ) {
+        float *dK = static_cast<float *>(a.dK);
+        for (int q = 0; q < a.w.nq; ++q) dK[q * C + c] = static_cast<float>(a.w.wd[q] * t64);
+    }
+}
+
 // Two cells of a float32 form at once (lane x: cell a, lane y: cell b), vertex ids va,
-// vb. The coordinates are gathered here and are dead once split into float32; the rare
-// float64 recomputation gathers them again (cache hits) instead of keeping them live.
+// vb. The coordinates are gathered here and are dead once split into float32. In the
+// mixed form, oka / okb report whether each cell passed the shape test; a failing cell's
+// result here is meaningless and the caller recomputes it (lap_fallback_store).
 template <int DIM, int P, bool ADJ>
 __device__ __forceinline__ void lap_pair(const double *const (&X)[DIM], const uint32_t (&va)[DIM + 1],
                                          const uint32_t (&vb)[DIM + 1], const f2 (&uu)[DIM + 1],
                                          const f2 (&ll)[DIM + 1], const qsum2_t<P> &ks, float tau2,
-                                         f2 (&rr)[DIM + 1], f2 &tf) {
-    constexpr int NB = DIM + 1;
+                                         f2 (&rr)[DIM + 1], f2 &tf, bool &oka, bool &okb) {
     f2 e[DIM][DIM], n[DIM][DIM];
     {
-        double xa[NB][DIM], xb[NB][DIM];
+        double xa[DIM + 1][DIM], xb[DIM + 1][DIM];
         gather_coords<DIM>(X, va, xa);
         gather_coords<DIM>(X, vb, xb);
         if constexpr (P == FEM_FP32_MIXED) columns_mixed2<DIM>(xa, xb, e);
@@ -268,248 +312,273 @@ __device__ __forceinline__ void lap_pair(const double *const (&X)[DIM], const ui
     } else {
         lap_element<DIM>(n, det, uu, ks.value(), rr);
     }
-    if constexpr (P == FEM_FP32_MIXED) {
-        bool oka, okb;
-        shape_ok2<DIM>(e, det, tau2, oka, okb);
-        if (!(oka && okb)) {
-            float ua[NB], ub[NB], la[NB], lb[NB];
-#pragma unroll
-            for (int b = 0; b < NB; ++b) {
-                ua[b] = f2_x(uu[b]), ub[b] = f2_y(uu[b]);
-                la[b] = f2_x(ll[b]), lb[b] = f2_y(ll[b]);
-            }
-            float tx = f2_x(tf), ty = f2_y(tf);
-            float rx[NB], ry[NB];
-#pragma unroll
-            for (int b = 0; b < NB; ++b) rx[b] = f2_x(rr[b]), ry[b] = f2_y(rr[b]);
-            double r64[NB], t64, xs[NB][DIM];
-            if (!oka) {
-                gather_coords<DIM>(X, va, xs);
-                lap_cell_f64<DIM, ADJ>(xs, ua, la, ks.value_f64_x(), r64, t64);
-#pragma unroll
-                for (int b = 0; b < NB; ++b) rx[b] = static_cast<float>(r64[b]);
-                tx = static_cast<float>(t64);
-            }
-            if (!okb) {
-                gather_coords<DIM>(X, vb, xs);
-                lap_cell_f64<DIM, ADJ>(xs, ub, lb, ks.value_f64_y(), r64, t64);
-#pragma unroll
-                for (int b = 0; b < NB; ++b) ry[b] = static_cast<float>(r64[b]);
-                ty = static_cast<float>(t64);
-            }
-#pragma unroll
-            for (int b = 0; b < NB; ++b) rr[b] = f2_make(rx[b], ry[b]);
-            tf = f2_make(tx, ty);
-        }
+    oka = okb = true;
+    if constexpr (P == FEM_FP32_MIXED) shape_ok2<DIM>(e, det, tau2, oka, okb);
+}
+
+// CPT consecutive values of a cell-indexed row in shared memory (one vector load)
+template <int CPT, class T>
+__device__ __forceinline__ void lds_row(const T *p, T (&v)[CPT]) {
+    static_assert(CPT == 2 || CPT == 4, "two or four cells per thread");
+    if constexpr (sizeof(T) * CPT == 8) {
+        const uint2 t = *reinterpret_cast<const uint2 *>(p);
+        memcpy(&v[0], &t.x, 4), memcpy(&v[1], &t.y, 4);
+    } else if constexpr (sizeof(T) * CPT == 16) {
+        const uint4 t = *reinterpret_cast<const uint4 *>(p);
+        memcpy(&v[0], &t, 16);
+    } else {
+        const uint4 t0 = reinterpret_cast<const uint4 *>(p)[0], t1 = reinterpret_cast<const uint4 *>(p)[1];
+        memcpy(&v[0], &t0, 16), memcpy(&v[2], &t1, 16);
     }
 }
 
-// four consecutive values of a cell-indexed row in shared memory
-__device__ __forceinline__ void lds4(const int32_t *p, int32_t (&v)[4]) {
-    const int4 t = *reinterpret_cast<const int4 *>(p);
-    v[0] = t.x, v[1] = t.y, v[2] = t.z, v[3] = t.w;
-}
-__device__ __forceinline__ void lds4(const float *p, float (&v)[4]) {
-    const float4 t = *reinterpret_cast<const float4 *>(p);
-    v[0] = t.x, v[1] = t.y, v[2] = t.z, v[3] = t.w;
-}
-__device__ __forceinline__ void lds4(const double *p, double (&v)[4]) {
-    const double2 t0 = reinterpret_cast<const double2 *>(p)[0], t1 = reinterpret_cast<const double2 *>(p)[1];
-    v[0] = t0.x, v[1] = t0.y, v[2] = t1.x, v[3] = t1.y;
-}
-
-// Staged kernel (fem_pipe.cuh): persistent CTAs, tiles of kTile consecutive cells, the
-// tile's connectivity, coefficient (and adjoint-weight) rows brought into a ring of
-// shared-memory stages by the bulk-copy engine, `stages` tiles ahead. Within a tile each
-// thread owns 4 consecutive cells: 128-bit shared-memory reads of every row, 128-bit
-// streaming stores of every output row, and (float32 forms) the cells processed as two
-// f32x2 pairs. NQ > 0 fixes the quadrature size at compile time; NQ = 0 reads it from
-// the arguments.
+// Staged kernel (fem_pipe.cuh): persistent CTAs walk the chunks of kTile consecutive
+// cells round-robin (chunk blockIdx.x, blockIdx.x + gridDim.x, ...), so that at any time
+// the CTAs of the device work on one contiguous front of the cell arrays (DRAM pages and
+// the L2-resident vertices of neighbouring chunks are shared). The CTA is warp-
+// specialised: one producer warp brings each chunk's connectivity, coefficient (and
+// adjoint-weight) rows into a ring of shared-memory stages with the bulk-copy engine
+// ("full" barriers count the bytes), and kConsumerWarps consumer warps compute. Consumer
+// warps release a stage on its "empty" barrier as soon as they are done with it; there
+// is no CTA-wide barrier per chunk, so the warps drift apart and one warp's vertex
+// gathers overlap other warps' arithmetic. Within a chunk each consumer thread owns kCPT
+// consecutive cells: vector shared-memory reads of every row, vector streaming stores
+// of every output row, and (float32 forms) the cells processed as f32x2 pairs. NQ > 0
+// fixes the quadrature size at compile time; NQ = 0 reads it from the arguments.
+// Tuning (measured on the 1,572,864-tet workload): 4 cells per consumer thread, 8
+// consumer warps, 2 CTAs per SM and a 64 KB stage budget.
 #ifndef FEM_STAGED_MIN_CTAS
 #define FEM_STAGED_MIN_CTAS 2
 #endif
 #ifndef FEM_STAGED_BUDGET_KB
-#define FEM_STAGED_BUDGET_KB 72
+#define FEM_STAGED_BUDGET_KB 64
 #endif
-constexpr int kTile = 4 * kBlock;
+#ifndef FEM_STAGED_CPT
+#define FEM_STAGED_CPT 4
+#endif
+#ifndef FEM_STAGED_CWARPS
+#define FEM_STAGED_CWARPS 8
+#endif
+constexpr int kCPT = FEM_STAGED_CPT;
+constexpr int kConsumerWarps = FEM_STAGED_CWARPS;
+constexpr int kTile = kCPT * 32 * kConsumerWarps;
 constexpr int kMaxStages = 4;
+constexpr int kStagedThreads = 32 * kConsumerWarps + 32;  // consumers + one producer warp
+static_assert(kCPT == 2 || kCPT == 4, "two or four cells per thread");
 
 template <class T>
 __host__ __device__ constexpr uint32_t lap_stage_bytes(int nb, int nq, bool adj) {
     return uint32_t(kTile) * (4u * nb + uint32_t(sizeof(T)) * (nq + (adj ? nb : 0)));
 }
 
+// Streaming stores of kCPT consecutive cells starting at cell c: element vectors and
+// (adjoint) dK = w_q * factor.
+template <int DIM, int P, bool ADJ>
+__device__ __forceinline__ void store_cells(const LapArgs &a, int nq, int64_t c, const val_t<P> (&r)[DIM + 1][kCPT],
+                                            const val_t<P> (&tfv)[kCPT]) {
+    using T = val_t<P>;
+    const int64_t C = a.C;
+    T *__restrict__ out = static_cast<T *>(a.out);
+#pragma unroll
+    for (int b = 0; b <= DIM; ++b) store_row<kCPT>(out + b * C + c, r[b]);
+    if constexpr (ADJ) {
+        T *__restrict__ dK = static_cast<T *>(a.dK);
+        for (int q = 0; q < nq; ++q) {
+            const T wq = weight<P>(a.w, q);
+            T row[kCPT];
+#pragma unroll
+            for (int i = 0; i < kCPT; ++i) row[i] = wq * tfv[i];
+            store_row<kCPT>(dK + q * C + c, row);
+        }
+    }
+}
+
+// The consumer work of one chunk: thread j0/kCPT's cells j0 .. j0+kCPT-1 of the chunk
+// starting at cell c0, rows read from one shared-memory stage.
 template <int DIM, int P, int NQ, bool ADJ>
-__global__ void __launch_bounds__(kBlock, FEM_STAGED_MIN_CTAS)
+__device__ __forceinline__ void lap_chunk(const LapArgs &a, const double *const (&X)[DIM], int nq,
+                                          const int32_t *sc, const val_t<P> *sK, const val_t<P> *sL, int j0,
+                                          int64_t c0) {
+    constexpr int NB = DIM + 1;
+    using T = val_t<P>;
+    const int64_t C = a.C;
+    const T *__restrict__ u = static_cast<const T *>(a.u);
+    uint32_t v[kCPT][NB];
+#pragma unroll
+    for (int b = 0; b < NB; ++b) {
+        int32_t id[kCPT];
+        lds_row<kCPT>(sc + b * kTile + j0, id);
+#pragma unroll
+        for (int c = 0; c < kCPT; ++c) v[c][b] = clamp_vid(id[c], a.V);
+    }
+    T lv[kCPT][NB];
+    if constexpr (ADJ) {
+#pragma unroll
+        for (int b = 0; b < NB; ++b) {
+            T lr[kCPT];
+            lds_row<kCPT>(sL + b * kTile + j0, lr);
+#pragma unroll
+            for (int c = 0; c < kCPT; ++c) lv[c][b] = lr[c];
+        }
+    }
+    T r[NB][kCPT], tfv[kCPT];
+    if constexpr (P == FEM_FP64) {
+        qsum_t<P> ks[kCPT];
+#pragma unroll(NQ > 0 ? NQ : 1)
+        for (int q = 0; q < nq; ++q) {
+            T kr[kCPT];
+            lds_row<kCPT>(sK + q * kTile + j0, kr);
+#pragma unroll
+            for (int c = 0; c < kCPT; ++c) {
+                if (q == 0) ks[c].first(weight<P>(a.w, 0), kr[c]);
+                else ks[c].add(weight<P>(a.w, q), kr[c]);
+            }
+        }
+#pragma unroll
+        for (int c = 0; c < kCPT; ++c) {
+            double xs[NB][DIM];
+            T uu[NB], rr[NB], tf = T(0), ll[NB];
+#pragma unroll
+            for (int b = 0; b < NB; ++b) {
+                uu[b] = ld_gather(u + v[c][b]);
+                ll[b] = ADJ ? lv[c][b] : T(0);
+            }
+            gather_coords<DIM>(X, v[c], xs);
+            lap_cell<DIM, P, ADJ>(xs, uu, ll, ks[c], a.tau2, rr, tf);
+#pragma unroll
+            for (int b = 0; b < NB; ++b) r[b][c] = rr[b];
+            tfv[c] = tf;
+        }
+    } else {
+        constexpr int NP = kCPT / 2;
+        qsum2_t<P> ks[NP];
+#pragma unroll(NQ > 0 ? NQ : 1)
+        for (int q = 0; q < nq; ++q) {
+            T kr[kCPT];
+            lds_row<kCPT>(sK + q * kTile + j0, kr);
+            const float wq = a.w.wf[q];
+#pragma unroll
+            for (int p = 0; p < NP; ++p) {
+                const f2 kp = f2_make(kr[2 * p], kr[2 * p + 1]);
+                if (q == 0) ks[p].first(wq, kp);
+                else ks[p].add(wq, kp);
+            }
+        }
+        bool ok[kCPT];
+#pragma unroll
+        for (int p = 0; p < NP; ++p) {
+            f2 uu[NB], ll[NB], rr[NB], tf = zero<f2>();
+#pragma unroll
+            for (int b = 0; b < NB; ++b) {
+                uu[b] = f2_make(ld_gather(u + v[2 * p][b]), ld_gather(u + v[2 * p + 1][b]));
+                ll[b] = ADJ ? f2_make(lv[2 * p][b], lv[2 * p + 1][b]) : zero<f2>();
+            }
+            lap_pair<DIM, P, ADJ>(X, v[2 * p], v[2 * p + 1], uu, ll, ks[p], a.tau2, rr, tf, ok[2 * p],
+                                  ok[2 * p + 1]);
+#pragma unroll
+            for (int b = 0; b < NB; ++b) r[b][2 * p] = f2_x(rr[b]), r[b][2 * p + 1] = f2_y(rr[b]);
+            tfv[2 * p] = f2_x(tf), tfv[2 * p + 1] = f2_y(tf);
+        }
+        store_cells<DIM, P, ADJ>(a, nq, c0 + j0, r, tfv);
+        if constexpr (P == FEM_FP32_MIXED) {
+#pragma unroll
+            for (int c = 0; c < kCPT; ++c)
+                if (!ok[c])
+                    lap_fallback_store<DIM, ADJ>(a, c0 + j0 + c,
+                                                 (c & 1) ? ks[c / 2].value_f64_y() : ks[c / 2].value_f64_x());
+        }
+        return;
+    }
+    store_cells<DIM, P, ADJ>(a, nq, c0 + j0, r, tfv);
+}
+
+template <int DIM, int P, int NQ, bool ADJ>
+__global__ void __launch_bounds__(kStagedThreads, FEM_STAGED_MIN_CTAS)
     lap_staged_kernel(const __grid_constant__ LapArgs a, int stages, unsigned *err) {
     constexpr int NB = DIM + 1;
     using T = val_t<P>;
     extern __shared__ __align__(128) unsigned char smem[];
-    __shared__ uint64_t full[kMaxStages];
-    __shared__ int s_abort;
+    __shared__ uint64_t full[kMaxStages], empty[kMaxStages];
+    __shared__ volatile int s_abort;
 
     const int64_t C = a.C;
     const int nq = NQ > 0 ? NQ : a.w.nq;
     const int64_t ntiles = (C + kTile - 1) / kTile;
+    // this CTA's chunks: tiles blockIdx.x + i * gridDim.x, i < nchunks
+    const int64_t nchunks = ntiles > blockIdx.x ? (ntiles - blockIdx.x + gridDim.x - 1) / gridDim.x : 0;
     const uint32_t stage_bytes = lap_stage_bytes<T>(NB, nq, ADJ);
-    const T *__restrict__ u = static_cast<const T *>(a.u);
-    const double *X[DIM];
-#pragma unroll
-    for (int k = 0; k < DIM; ++k) X[k] = a.X[k];
 
     // stage layout: conn[NB][kTile] int32 | K[nq][kTile] T | lambda[NB][kTile] T
     auto stage_conn = [&](int s) { return reinterpret_cast<int32_t *>(smem + size_t(s) * stage_bytes); };
     auto stage_K = [&](int s) { return reinterpret_cast<T *>(stage_conn(s) + NB * kTile); };
     auto stage_lam = [&](int s) { return stage_K(s) + nq * kTile; };
-
-    // one elected thread fills stage s with tile t
-    auto issue = [&](int64_t t, int s, uint64_t pol) {
-        const int64_t c0 = t * kTile;
-        const uint32_t n = static_cast<uint32_t>(C - c0 < int64_t(kTile) ? C - c0 : int64_t(kTile));
-        const uint32_t bytes = n * (4u * NB + uint32_t(sizeof(T)) * (nq + (ADJ ? NB : 0)));
-        mbar_arrive_expect_tx(&full[s], bytes);
-        for (int b = 0; b < NB; ++b) bulk_copy_g2s(stage_conn(s) + b * kTile, a.conn + b * C + c0, n * 4u, &full[s], pol);
-        const T *K = static_cast<const T *>(a.K);
-        for (int q = 0; q < nq; ++q)
-            bulk_copy_g2s(stage_K(s) + q * kTile, K + q * C + c0, n * uint32_t(sizeof(T)), &full[s], pol);
-        if constexpr (ADJ) {
-            const T *L = static_cast<const T *>(a.lam);
-            for (int b = 0; b < NB; ++b)
-                bulk_copy_g2s(stage_lam(s) + b * kTile, L + b * C + c0, n * uint32_t(sizeof(T)), &full[s], pol);
-        }
+    auto chunk_start = [&](int64_t i) { return (blockIdx.x + i * gridDim.x) * int64_t(kTile); };
+    auto chunk_cells = [&](int64_t i) {
+        const int64_t c0 = chunk_start(i);
+        return static_cast<uint32_t>(C - c0 < int64_t(kTile) ? C - c0 : int64_t(kTile));
     };
 
     if (threadIdx.x == 0) {
-        for (int s = 0; s < stages; ++s) mbar_init(&full[s], 1);
+        for (int s = 0; s < stages; ++s) mbar_init(&full[s], 1), mbar_init(&empty[s], kConsumerWarps);
         fence_barrier_init();
         s_abort = 0;
     }
     __syncthreads();
-    uint64_t pol = 0;
-    if (threadIdx.x == 0) {
-        pol = l2_evict_first_policy();
-        for (int s = 0; s < stages; ++s) {
-            const int64_t t = blockIdx.x + int64_t(s) * gridDim.x;
-            if (t < ntiles) issue(t, s, pol);
-        }
-    }
 
-    T *__restrict__ out = static_cast<T *>(a.out);
-    T *__restrict__ dK = static_cast<T *>(a.dK);
-    const int j0 = 4 * threadIdx.x;
-    int64_t t = blockIdx.x;
-    for (int64_t i = 0; t < ntiles; ++i, t += gridDim.x) {
-        const int s = static_cast<int>(i % stages);
-        const uint32_t parity = static_cast<uint32_t>((i / stages) & 1);
-        const int64_t c0 = t * kTile;
-        const int n = static_cast<int>(C - c0 < int64_t(kTile) ? C - c0 : int64_t(kTile));
-        if (mbar_wait_bounded(&full[s], parity, kWaitBudgetNs)) {
-            if (j0 < n) {  // n is a multiple of 4: a thread's four cells are all present or all absent
-                const int32_t *sc = stage_conn(s) + j0;
-                const T *sK = stage_K(s) + j0;
-                uint32_t v[4][NB];
-#pragma unroll
-                for (int b = 0; b < NB; ++b) {
-                    int32_t id[4];
-                    lds4(sc + b * kTile, id);
-#pragma unroll
-                    for (int c = 0; c < 4; ++c) v[c][b] = clamp_vid(id[c], a.V);
-                }
-                T lv[4][NB];
-                if constexpr (ADJ) {
-#pragma unroll
-                    for (int b = 0; b < NB; ++b) {
-                        T l4[4];
-                        lds4(stage_lam(s) + j0 + b * kTile, l4);
-#pragma unroll
-                        for (int c = 0; c < 4; ++c) lv[c][b] = l4[c];
-                    }
-                }
-                T r[NB][4], tfv[4];
-                if constexpr (P == FEM_FP64) {
-                    qsum_t<P> ks[4];
-                    for (int q = 0; q < nq; ++q) {
-                        T k4[4];
-                        lds4(sK + q * kTile, k4);
-#pragma unroll
-                        for (int c = 0; c < 4; ++c) {
-                            if (q == 0) ks[c].first(weight<P>(a.w, 0), k4[c]);
-                            else ks[c].add(weight<P>(a.w, q), k4[c]);
-                        }
-                    }
-#pragma unroll
-                    for (int c = 0; c < 4; ++c) {
-                        double xs[NB][DIM];
-                        T uu[NB], rr[NB], tf = T(0), ll[NB];
-#pragma unroll
-                        for (int b = 0; b < NB; ++b) {
-                            uu[b] = ld_gather(u + v[c][b]);
-                            ll[b] = ADJ ? lv[c][b] : T(0);
-                        }
-                        gather_coords<DIM>(X, v[c], xs);
-                        lap_cell<DIM, P, ADJ>(xs, uu, ll, ks[c], a.tau2, rr, tf);
-#pragma unroll
-                        for (int b = 0; b < NB; ++b) r[b][c] = rr[b];
-                        tfv[c] = tf;
-                    }
-                } else {
-                    qsum2_t<P> ks[2];
-#pragma unroll(NQ > 0 ? NQ : 1)
-                    for (int q = 0; q < nq; ++q) {
-                        T k4[4];
-                        lds4(sK + q * kTile, k4);
-                        const float wq = a.w.wf[q];
-#pragma unroll
-                        for (int p = 0; p < 2; ++p) {
-                            const f2 kp = f2_make(k4[2 * p], k4[2 * p + 1]);
-                            if (q == 0) ks[p].first(wq, kp);
-                            else ks[p].add(wq, kp);
-                        }
-                    }
-#pragma unroll
-                    for (int p = 0; p < 2; ++p) {
-                        f2 uu[NB], ll[NB], rr[NB], tf = zero<f2>();
-#pragma unroll
-                        for (int b = 0; b < NB; ++b) {
-                            uu[b] = f2_make(ld_gather(u + v[2 * p][b]), ld_gather(u + v[2 * p + 1][b]));
-                            ll[b] = ADJ ? f2_make(lv[2 * p][b], lv[2 * p + 1][b]) : zero<f2>();
-                        }
-                        lap_pair<DIM, P, ADJ>(X, v[2 * p], v[2 * p + 1], uu, ll, ks[p], a.tau2, rr, tf);
-#pragma unroll
-                        for (int b = 0; b < NB; ++b) r[b][2 * p] = f2_x(rr[b]), r[b][2 * p + 1] = f2_y(rr[b]);
-                        tfv[2 * p] = f2_x(tf), tfv[2 * p + 1] = f2_y(tf);
-                    }
-                }
-#pragma unroll
-                for (int b = 0; b < NB; ++b) store_row<4>(out + b * C + c0 + j0, r[b]);
-                if constexpr (ADJ) {
-                    for (int q = 0; q < nq; ++q) {
-                        const T wq = weight<P>(a.w, q);
-                        T row[4];
-#pragma unroll
-                        for (int c = 0; c < 4; ++c) row[c] = wq * tfv[c];
-                        store_row<4>(dK + q * C + c0 + j0, row);
-                    }
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (warp == kConsumerWarps) {
+        // ---------------- producer warp (one elected lane)
+        if (lane != 0) return;
+        const uint64_t pol = l2_evict_first_policy();
+        const T *K = static_cast<const T *>(a.K);
+        const T *L = static_cast<const T *>(a.lam);
+        int64_t issued = 0;
+        for (int64_t i = 0; i < nchunks; ++i, ++issued) {
+            const int s = static_cast<int>(i % stages);
+            if (i >= stages) {
+                // wait until every consumer warp has released the chunk i - stages
+                const uint32_t par = static_cast<uint32_t>(((i / stages) - 1) & 1);
+                if (s_abort || !mbar_wait_bounded(&empty[s], par, kWaitBudgetNs)) {
+                    s_abort = 1;
+                    break;
                 }
             }
-        } else {
-            s_abort = 1;
+            const int64_t c0 = chunk_start(i);
+            const uint32_t n = chunk_cells(i);
+            mbar_arrive_expect_tx(&full[s], n * (4u * NB + uint32_t(sizeof(T)) * (nq + (ADJ ? NB : 0))));
+            for (int b = 0; b < NB; ++b)
+                bulk_copy_g2s(stage_conn(s) + b * kTile, a.conn + b * C + c0, n * 4u, &full[s], pol);
+            for (int q = 0; q < nq; ++q)
+                bulk_copy_g2s(stage_K(s) + q * kTile, K + q * C + c0, n * uint32_t(sizeof(T)), &full[s], pol);
+            if constexpr (ADJ) {
+                for (int b = 0; b < NB; ++b)
+                    bulk_copy_g2s(stage_lam(s) + b * kTile, L + b * C + c0, n * uint32_t(sizeof(T)), &full[s], pol);
+            }
         }
-        __syncthreads();  // every thread is done with stage s (or the wait gave up)
-        if (s_abort) break;
-        if (threadIdx.x == 0) {
-            const int64_t tn = t + int64_t(stages) * gridDim.x;
-            if (tn < ntiles) issue(tn, s, pol);
-        }
+        // drain: the last copies issued into each stage have landed before this warp leaves
+        for (int64_t k = issued - stages < 0 ? 0 : issued - stages; k < issued; ++k)
+            mbar_wait_bounded(&full[k % stages], static_cast<uint32_t>((k / stages) & 1), kWaitBudgetNs);
+        if (s_abort) record_device_error(err, FEM_DEVERR_TIMEOUT);
+        return;
     }
-    if (s_abort && threadIdx.x == 0) {
-        // drain: wait (bounded) for every stage copy still in flight, then report
-        int64_t tt = t;
-        for (int i2 = 0; i2 < stages && tt < ntiles; ++i2, tt += gridDim.x) {
-            const int64_t idx = (tt - blockIdx.x) / gridDim.x;
-            mbar_wait_bounded(&full[idx % stages], static_cast<uint32_t>((idx / stages) & 1), kWaitBudgetNs);
+
+    // ---------------- consumer warps
+    const double *X[DIM];
+#pragma unroll
+    for (int k = 0; k < DIM; ++k) X[k] = a.X[k];
+    const int j0 = kCPT * threadIdx.x;
+    for (int64_t i = 0; i < nchunks; ++i) {
+        const int s = static_cast<int>(i % stages);
+        if (s_abort || !mbar_wait_bounded(&full[s], static_cast<uint32_t>((i / stages) & 1), kWaitBudgetNs)) {
+            s_abort = 1;
+            record_device_error(err, FEM_DEVERR_TIMEOUT);
+            return;
         }
-        record_device_error(err, FEM_DEVERR_TIMEOUT);
+        // n is a multiple of 4 (and of kCPT): a thread's cells are all present or all absent
+        if (j0 < static_cast<int>(chunk_cells(i)))
+            lap_chunk<DIM, P, NQ, ADJ>(a, X, nq, stage_conn(s), stage_K(s), stage_lam(s), j0, chunk_start(i));
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&empty[s]);
     }
 }
 
@@ -525,9 +594,9 @@ static fem_status launch_staged(const LapArgs &a, uint32_t sb, cudaStream_t s) {
     unsigned *err = device_error_word();
     if (!err) return fail(FEM_ERR_CUDA, "device error word unavailable");
     int grid = 0;
-    fem_status st = staged_grid(reinterpret_cast<const void *>(k), smem, (a.C + kTile - 1) / kTile, grid);
+    fem_status st = staged_grid(reinterpret_cast<const void *>(k), kStagedThreads, smem, (a.C + kTile - 1) / kTile, grid);
     if (st != FEM_OK) return st;
-    k<<<grid, kBlock, smem, s>>>(a, stages, err);
+    k<<<grid, kStagedThreads, smem, s>>>(a, stages, err);
     return FEM_OK;
 }
 
@@ -536,17 +605,25 @@ static fem_status launch_lap(const LapArgs &a, bool vec, cudaStream_t s) {
     using T = val_t<P>;
     const uint32_t sb = lap_stage_bytes<T>(DIM + 1, a.w.nq, ADJ);
     fem_status st = FEM_OK;
+    // the quadrature size of the workloads' rules (3 points in 2D, 4 in 3D) is compiled in
+    const bool native_nq = (DIM == 3 && a.w.nq == 4) || (DIM == 2 && a.w.nq == 3);
+#ifndef FEM_LAP_DIRECT
     if (vec && 2u * sb <= kStageMax) {
-        // the quadrature size of the workloads' rules (3 points in 2D, 4 in 3D) is compiled in
         if (a.w.nq == DIM + 1 && DIM == 3) st = launch_staged<DIM, P, 4, ADJ>(a, sb, s);
         else if (a.w.nq == 3 && DIM == 2) st = launch_staged<DIM, P, 3, ADJ>(a, sb, s);
         else st = launch_staged<DIM, P, 0, ADJ>(a, sb, s);
+    } else
+#endif
+    if (vec && native_nq) {
+        auto k = lap_kernel<DIM, P, 4, DIM + 1, ADJ>;
+        int grid = grid_for((a.C + 3) / 4, kBlock, reinterpret_cast<const void *>(k));
+        k<<<grid, kBlock, 0, s>>>(a);
     } else if (vec) {
-        auto k = lap_kernel<DIM, P, 4, ADJ>;
+        auto k = lap_kernel<DIM, P, 4, 0, ADJ>;
         int grid = grid_for((a.C + 3) / 4, kBlock, reinterpret_cast<const void *>(k));
         k<<<grid, kBlock, 0, s>>>(a);
     } else {
-        auto k = lap_kernel<DIM, P, 1, ADJ>;
+        auto k = lap_kernel<DIM, P, 1, 0, ADJ>;
         int grid = grid_for(a.C, kBlock, reinterpret_cast<const void *>(k));
         k<<<grid, kBlock, 0, s>>>(a);
     }
