@@ -46,6 +46,12 @@ HEADLINE_CELLS = 1572864
 HEADLINE_KERNEL = ("lap_staged_kernel<3, FP32_MIXED, NQ=4> (persistent; cp.async.bulk-staged connectivity and "
                    "coefficient rows; 8 consumer warps x 4 cells/thread + 1 producer warp)")
 FLUSH_BYTES = 512 << 20
+# float64 instructions per cell of the float64 3D Laplacian kernel (ncu sass counters,
+# profiles/lap3d_fp64_1572864.md): DFMA 33, DADD 17, DMUL 21
+FP64_INST_PER_CELL_LAP3D = {"dfma": 33, "dadd": 17, "dmul": 21}
+# FP64 peak: 1.25 TFLOP/s nominal for GB300 = 0.625 T FMA instructions/s, i.e. 2 float64
+# instructions per clock per SM at 2070 MHz on 152 SMs
+FP64_NOMINAL_TFLOPS = 1.25
 TOL = {"fp64": 1e-12, "mixed": 2e-5, "fp32": 1e-3}
 
 
@@ -315,6 +321,38 @@ def measure_residual(case, prec, device, stream, flush, steps, warmup, peak, ora
     return row, ms, wall, clocks
 
 
+def measure_geometry_path(case, prec, device, stream, flush, steps, warmup, peak, oracle_mod=None):
+    """The paper's layout: J^{-1} and det J precomputed once per mesh (not timed), then the
+    residual from conn, u, K and the geometry (timed)."""
+    import torch
+
+    import paper_1607_04245_gb300 as fem
+
+    c, d = device_case(case, prec, device)
+    q = c.rule
+    dt = fem.value_dtype(prec)
+    with torch.cuda.stream(stream):
+        geom = fem.fem_precompute_geometry(d["coords"], d["conn"], prec=prec, stream=stream)
+        out = torch.empty((c.dim + 1, c.n_cells), dtype=dt, device=device)
+        fn = lambda: fem.fem_integrate_laplacian_geom(d["conn"], c.n_verts, d["u"], d["K"], q.points, q.weights, geom,
+                                                      out=out, prec=prec, stream=stream)
+        ms, _, _ = timed_steps(fn, steps, warmup, stream, flush)
+    t = statistics.mean(ms) * 1e-3
+    s = 8 if prec == "fp64" else 4
+    nb = c.dim + 1
+    nbytes = nb * 4 * c.n_cells + q.n_q * s * c.n_cells + (c.dim * c.dim + 1) * s * c.n_cells + nb * s * c.n_cells \
+        + s * c.n_verts
+    row = {"physics": "laplacian_precomputed_geometry", "dim": c.dim, "prec": prec, "cells": c.n_cells,
+           "ms_per_launch": round(statistics.mean(ms), 6), "cells_per_s": c.n_cells / t,
+           "alg_bytes_per_launch": nbytes, "alg_gbs": nbytes / t / 1e9, "hbm_frac_of_measured": nbytes / t / 1e9 / peak,
+           "alg_bytes_per_cell": "conn 16 + K 4s + geom 10s + out 4s + (V/C) u s (s = value bytes); geometry "
+                                 "precomputed once per mesh, not timed"}
+    if oracle_mod is not None:
+        torch.cuda.synchronize()
+        row["rel_maxnorm_err_vs_oracle"] = rel_err(out, oracle_mod.residual_for(c))
+    return row
+
+
 def measure_adjoint(case, prec, device, stream, flush, steps, warmup, peak, oracle_mod=None):
     import torch
 
@@ -539,11 +577,28 @@ def run_ours(args):
                 "alg_bytes_per_launch": nbytes,
                 "alg_bytes_per_cell": "conn 16 + K 16 + out 16 + (V/C)(coords 24 + u 4)"}
 
+    fp64_inst = sum(FP64_INST_PER_CELL_LAP3D.values()) * case.n_cells
+    fp64_flops = (2 * FP64_INST_PER_CELL_LAP3D["dfma"] + FP64_INST_PER_CELL_LAP3D["dadd"] +
+                  FP64_INST_PER_CELL_LAP3D["dmul"]) * case.n_cells
+    t64 = row64["ms_per_launch"] * 1e-3
+    sm_mhz = (clocks or {}).get("sm_mhz") or 2070.0
+    peak_inst = FP64_NOMINAL_TFLOPS / 2 * (sm_mhz / 2070.0)  # T instructions/s at the sampled clock
+    roofline_fp64 = {"bound": "alu", "achieved": fp64_inst / t64 / 1e12, "peak": peak_inst,
+                     "unit": "T float64 instructions/s", "frac": fp64_inst / t64 / 1e12 / peak_inst,
+                     "achieved_tflops": fp64_flops / t64 / 1e12,
+                     "peak_kind": f"nominal {FP64_NOMINAL_TFLOPS} TFLOP/s float64 = 2 FMA instructions/clock/SM, "
+                                  f"at the sampled {sm_mhz:.0f} MHz",
+                     "kernel": "lap_staged_kernel<3, FP64, NQ=4>",
+                     "inst_per_cell": FP64_INST_PER_CELL_LAP3D}
+
     rows = {"fp64": row64}
     if args.rows == "all":
         rsteps = max(3, args.steps // 50)
         rows["fp32_ablation"] = measure_residual(case, "fp32", device, stream, flush, rsteps, args.warmup, peak,
                                                  oracle)[0]
+        for prec in ("mixed", "fp64"):
+            rows[f"lap3d_precomputed_geometry_{prec}"] = measure_geometry_path(case, prec, device, stream, flush, rsteps,
+                                                                              args.warmup, peak, oracle)
         rows["lap2d_8192_fp64"] = measure_residual(workloads.laplacian_square_case(), "fp64", device, stream, flush,
                                                    rsteps, args.warmup, peak, oracle)[0]
         for dim in (2, 3):
@@ -583,7 +638,7 @@ def run_ours(args):
                      "alg_gbs": row64["alg_gbs"], "hbm_frac_of_measured": row64["hbm_frac_of_measured"],
                      "rel_maxnorm_err_vs_oracle": row64.get("rel_maxnorm_err_vs_oracle")},
             "speedup_fp32_mixed_over_fp64": row["cells_per_s"] / row64["cells_per_s"],
-            "roofline": roofline,
+            "roofline": roofline, "roofline_fp64": roofline_fp64,
             "cpu_baseline": cpu_baseline(case) if (ws == 1 and not args.no_cpu_baseline) else None,
             "e2e": e2e, "gpu_launches": args.steps,
             "clocks": clocks, "rows": rows,

@@ -114,6 +114,27 @@ fem_status fem_integrate_elasticity(int dim, int64_t n_cells, int64_t n_verts, c
                                     fem_precision prec, fem_stream stream);
 
 /* ---------------------------------------------------------------------------------
+ * The paper's precomputed-geometry layout (Sec. 3 and the Appendix load J^{-1} and det J
+ * per cell rather than computing them), as an alternate entry for the Laplacian:
+ *
+ * fem_precompute_geometry -- per-mesh pass writing geom [dim*dim + 1][C] in the value
+ *   type of prec: rows i*dim + j hold (J^{-1})_{ij} (row-major), row dim*dim holds det J
+ *   (signed). Computed in float64, rounded once to float32 for the float32 forms.
+ * fem_integrate_laplacian_geom -- the Laplacian element residual of
+ *   fem_integrate_laplacian from conn, u, K and that geom (no coordinates):
+ *   r_b = (sum_q w_q K_q) |det J| G_b . g, G_b = J^{-T} grad_ref phi_b, g = sum_b u_b G_b.
+ *   Both float32 forms integrate float32 geometry (FEM_FP32_MIXED keeps its compensated
+ *   quadrature sum; there is no float64 recomputation without coordinates).
+ * Arguments otherwise as fem_integrate_laplacian; geom is a caller-owned device array.
+ * ------------------------------------------------------------------------------- */
+fem_status fem_precompute_geometry(int dim, int64_t n_cells, int64_t n_verts, const double *coords,
+                                   const int32_t *conn, void *geom, fem_precision prec, fem_stream stream);
+fem_status fem_integrate_laplacian_geom(int dim, int64_t n_cells, int64_t n_verts, const int32_t *conn,
+                                        const void *u, const void *K, int n_q, const double *qpts,
+                                        const double *qw, const void *geom, void *elem_out,
+                                        fem_precision prec, fem_stream stream);
+
+/* ---------------------------------------------------------------------------------
  * fem_set_mixed_threshold / fem_get_mixed_threshold -- the shape-test threshold tau of
  * FEM_FP32_MIXED (default 0.05). tau = 0 sends no cell to the float64 path, tau > 1
  * sends every cell. Process-wide; set it between calls, not during them.

@@ -22,6 +22,8 @@ from .binding import (  # noqa: F401
     fem_get_mixed_threshold,
     fem_integrate_elasticity,
     fem_integrate_laplacian,
+    fem_integrate_laplacian_geom,
+    fem_precompute_geometry,
     fem_probe,
     fem_selftest_wait,
     fem_set_mixed_threshold,

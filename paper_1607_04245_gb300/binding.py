@@ -52,6 +52,8 @@ def lib():
             "fem_probe": [ci, i64, ci, P, P],
             "fem_set_mixed_threshold": [cd],
             "fem_device_error": [P],
+            "fem_precompute_geometry": [ci, i64, i64, P, P, P, ci, P],
+            "fem_integrate_laplacian_geom": [ci, i64, i64, P, P, P, ci, P, P, P, P, ci, P],
             "fem_selftest_wait": [i64, P],
         }
         for name, args in sig.items():
@@ -168,6 +170,38 @@ def fem_integrate_elasticity(coords, conn, u, lam, mu, qpts, qw, out=None, prec=
         _dev(u, "u", dt, (dim, V), dev), _dev(lam, "lam", dt, (nq, C), dev), _dev(mu, "mu", dt, (nq, C), dev),
         nq, qp.ptr, w.ptr, _dev(out, "out", dt, ((dim + 1) * dim, C), dev), p, _stream(stream))
     _check("fem_integrate_elasticity", st)
+    return out
+
+
+def fem_precompute_geometry(coords, conn, geom=None, prec="mixed", stream=None) -> torch.Tensor:
+    """Per-cell geometry [dim*dim + 1][C]: J^{-1} rows (row-major) then det J."""
+    p = precision(prec)
+    dt = value_dtype(p)
+    dim, V, C = _mesh_sizes(coords, conn)
+    dev = coords.device
+    geom = torch.empty((dim * dim + 1, C), dtype=dt, device=dev) if geom is None else geom
+    st = lib().fem_precompute_geometry(dim, C, V, _dev(coords, "coords", torch.float64, device=dev),
+                                       _dev(conn, "conn", torch.int32, device=dev),
+                                       _dev(geom, "geom", dt, (dim * dim + 1, C), dev), p, _stream(stream))
+    _check("fem_precompute_geometry", st)
+    return geom
+
+
+def fem_integrate_laplacian_geom(conn, n_verts: int, u, K, qpts, qw, geom, out=None, prec="mixed",
+                                 stream=None) -> torch.Tensor:
+    """Laplacian element residuals [dim+1][C] from the precomputed geometry."""
+    p = precision(prec)
+    dt = value_dtype(p)
+    dim, C = int(conn.shape[0]) - 1, int(conn.shape[1])
+    nq = int(np.asarray(qw).shape[0]) if not isinstance(qw, torch.Tensor) else int(qw.shape[0])
+    dev = conn.device
+    out = torch.empty((dim + 1, C), dtype=dt, device=dev) if out is None else out
+    qp, w = _HostTable(qpts, (nq, dim), "qpts"), _HostTable(qw, (nq,), "qw")
+    st = lib().fem_integrate_laplacian_geom(
+        dim, C, int(n_verts), _dev(conn, "conn", torch.int32, device=dev), _dev(u, "u", dt, (n_verts,), dev),
+        _dev(K, "K", dt, (nq, C), dev), nq, qp.ptr, w.ptr, _dev(geom, "geom", dt, (dim * dim + 1, C), dev),
+        _dev(out, "out", dt, (dim + 1, C), dev), p, _stream(stream))
+    _check("fem_integrate_laplacian_geom", st)
     return out
 
 

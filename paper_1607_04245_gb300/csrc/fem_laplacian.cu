@@ -401,7 +401,6 @@ __device__ __forceinline__ void lap_chunk(const LapArgs &a, const double *const 
                                           int64_t c0) {
     constexpr int NB = DIM + 1;
     using T = val_t<P>;
-    const int64_t C = a.C;
     const T *__restrict__ u = static_cast<const T *>(a.u);
     uint32_t v[kCPT][NB];
 #pragma unroll
