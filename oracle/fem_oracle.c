@@ -325,3 +325,71 @@ int oracle_adjoint_laplacian(int dim, int64_t n_cells, int64_t n_verts, const do
     free(du_e);
     return bad ? ORA_ERR_BADMESH : ORA_OK;
 }
+
+/* Reaction-diffusion with an auxiliary coefficient field: the full bracket of Eq. 2,
+ *     r_{e,b} = sum_q w_q |det J| [ phi_b(xi_q) f0(q) + G_b(q) . f1(q) ],
+ * with the pointwise functions of Eq. 8 taking the auxiliary field a:
+ *     f1(u, grad u, a) = a grad u,      f0(u, a) = c u,
+ * evaluated at each quadrature point from the tabulated basis:
+ *     u(q) = sum_b phi_b(xi_q) u_b,  grad u(q) = sum_b u_b G_b(q),
+ *     a(q) = sum_b phi_b(xi_q) a_b   (a_space = 1: a in P1, nodal values a[V])
+ *     a(q) = a_e                     (a_space = 0: a in P0, one value per cell a[C])
+ * c [n_q][C] is the reaction coefficient per quadrature point; c = NULL drops f0. */
+int oracle_reaction_diffusion(int dim, int64_t n_cells, int64_t n_verts, const double *coords,
+                              const int32_t *conn, const double *u, const double *a, int a_space,
+                              const double *c, int n_q, const double *qpts, const double *qw, double *out) {
+    int st = check_args(dim, n_cells, n_verts, n_q);
+    if (st) return st;
+    if (a_space != 0 && a_space != 1) return ORA_ERR_ARG;
+    if (n_cells == 0) return ORA_OK;
+    if (!coords || !conn || !u || !a || !qpts || !qw || !out) return ORA_ERR_ARG;
+    if ((st = check_conn(dim, n_cells, n_verts, conn))) return st;
+    const int nb = dim + 1;
+    double phi[ORA_MAX_Q][4], dphi[ORA_MAX_Q][4][3];
+    tabulate_p1(dim, n_q, qpts, phi, dphi);
+    int bad = 0;
+#pragma omp parallel for schedule(static)
+    for (int64_t e = 0; e < n_cells; ++e) {
+        double J[3][3], invJ[3][3];
+        double detJ = cell_geometry(dim, e, n_cells, n_verts, coords, conn, J, invJ);
+        if (detJ == 0.0) {
+#pragma omp atomic write
+            bad = 1;
+            continue;
+        }
+        double ub[4], ab[4];
+        for (int b = 0; b < nb; ++b) {
+            int64_t v = conn[(int64_t)b * n_cells + e];
+            ub[b] = u[v];
+            ab[b] = a_space == 1 ? a[v] : a[e];
+        }
+        /* quadrature phase: f0 and f1 at every point, scaled by w_q |det J| */
+        double f0[ORA_MAX_Q], f1[ORA_MAX_Q][3];
+        for (int q = 0; q < n_q; ++q) {
+            double uq = 0.0, aq = 0.0, gradU[3] = {0.0, 0.0, 0.0};
+            for (int b = 0; b < nb; ++b) {
+                double G[3];
+                phys_grad(dim, invJ, dphi[q][b], G);
+                uq += phi[q][b] * ub[b];
+                aq += phi[q][b] * ab[b];
+                for (int i = 0; i < dim; ++i) gradU[i] += ub[b] * G[i];
+            }
+            if (a_space == 0) aq = ab[0];
+            double scale = qw[q] * fabs(detJ);
+            f0[q] = c ? c[(int64_t)q * n_cells + e] * uq * scale : 0.0;
+            for (int i = 0; i < dim; ++i) f1[q][i] = aq * gradU[i] * scale;
+        }
+        /* basis phase: e_b = sum_q phi_b(q) f0(q) + G_b(q) . f1(q) */
+        for (int b = 0; b < nb; ++b) {
+            double r = 0.0;
+            for (int q = 0; q < n_q; ++q) {
+                double G[3];
+                phys_grad(dim, invJ, dphi[q][b], G);
+                r += phi[q][b] * f0[q];
+                for (int i = 0; i < dim; ++i) r += G[i] * f1[q][i];
+            }
+            out[(int64_t)b * n_cells + e] = r;
+        }
+    }
+    return bad ? ORA_ERR_BADMESH : ORA_OK;
+}
