@@ -114,6 +114,27 @@ fem_status fem_integrate_elasticity(int dim, int64_t n_cells, int64_t n_verts, c
                                     fem_precision prec, fem_stream stream);
 
 /* ---------------------------------------------------------------------------------
+ * fem_integrate_reaction_diffusion -- element vectors of the full bracket of Eq. 2 (both
+ * the f0 and the f1 term) with pointwise functions that take an auxiliary field a
+ * (Eq. 8; Sec. 4 allows a in the space of u or in P0):
+ *     f1 = a grad u,  f0 = c u,
+ *     r_b = sum_q w_q |det J| [ phi_b(xi_q) c_q u(xi_q) + G_b . a(xi_q) grad u ]
+ *   u          [V] nodal values
+ *   a          a_space = 1: [V] nodal values of a P1 field, a(xi_q) = sum_b phi_b(xi_q) a_b
+ *              a_space = 0: [C] one value per cell (P0)
+ *   c          [n_q][C] reaction coefficient per quadrature point, or NULL (no f0 term)
+ *   qpts       required here (phi_b(xi_q) enters both terms)
+ *   elem_out   [dim+1][C]
+ * Other arguments and returns as fem_integrate_laplacian. The FP32_MIXED form computes
+ * sum_q w_q a(xi_q) with the compensated sum and recomputes badly shaped cells in
+ * float64; the f0 sum is a plain float32 sum.
+ * ------------------------------------------------------------------------------- */
+fem_status fem_integrate_reaction_diffusion(int dim, int64_t n_cells, int64_t n_verts, const double *coords,
+                                            const int32_t *conn, const void *u, const void *a, int a_space,
+                                            const void *c, int n_q, const double *qpts, const double *qw,
+                                            void *elem_out, fem_precision prec, fem_stream stream);
+
+/* ---------------------------------------------------------------------------------
  * The paper's precomputed-geometry layout (Sec. 3 and the Appendix load J^{-1} and det J
  * per cell rather than computing them), as an alternate entry for the Laplacian:
  *

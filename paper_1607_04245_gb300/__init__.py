@@ -23,6 +23,7 @@ from .binding import (  # noqa: F401
     fem_integrate_elasticity,
     fem_integrate_laplacian,
     fem_integrate_laplacian_geom,
+    fem_integrate_reaction_diffusion,
     fem_precompute_geometry,
     fem_probe,
     fem_selftest_wait,

@@ -53,6 +53,7 @@ def lib():
             "fem_set_mixed_threshold": [cd],
             "fem_device_error": [P],
             "fem_precompute_geometry": [ci, i64, i64, P, P, P, ci, P],
+            "fem_integrate_reaction_diffusion": [ci, i64, i64, P, P, P, P, ci, P, ci, P, P, P, ci, P],
             "fem_integrate_laplacian_geom": [ci, i64, i64, P, P, P, ci, P, P, P, P, ci, P],
             "fem_selftest_wait": [i64, P],
         }
@@ -170,6 +171,28 @@ def fem_integrate_elasticity(coords, conn, u, lam, mu, qpts, qw, out=None, prec=
         _dev(u, "u", dt, (dim, V), dev), _dev(lam, "lam", dt, (nq, C), dev), _dev(mu, "mu", dt, (nq, C), dev),
         nq, qp.ptr, w.ptr, _dev(out, "out", dt, ((dim + 1) * dim, C), dev), p, _stream(stream))
     _check("fem_integrate_elasticity", st)
+    return out
+
+
+def fem_integrate_reaction_diffusion(coords, conn, u, a, qpts, qw, c=None, a_space=1, out=None, prec="mixed",
+                                     stream=None) -> torch.Tensor:
+    """Element vectors [dim+1][C] of f1 = a grad u, f0 = c u (Eqs. 2 and 8): a is P1 nodal
+    ([V], a_space=1) or P0 ([C], a_space=0); c is [n_q][C] or None."""
+    p = precision(prec)
+    dt = value_dtype(p)
+    dim, V, C = _mesh_sizes(coords, conn)
+    nq = int(np.asarray(qw).shape[0]) if not isinstance(qw, torch.Tensor) else int(qw.shape[0])
+    dev = coords.device
+    if qpts is None:
+        raise ValueError("qpts is required")
+    out = torch.empty((dim + 1, C), dtype=dt, device=dev) if out is None else out
+    qp, w = _HostTable(qpts, (nq, dim), "qpts"), _HostTable(qw, (nq,), "qw")
+    st = lib().fem_integrate_reaction_diffusion(
+        dim, C, V, _dev(coords, "coords", torch.float64, device=dev), _dev(conn, "conn", torch.int32, device=dev),
+        _dev(u, "u", dt, (V,), dev), _dev(a, "a", dt, (V,) if a_space == 1 else (C,), dev), int(a_space),
+        None if c is None else _dev(c, "c", dt, (nq, C), dev), nq, qp.ptr, w.ptr,
+        _dev(out, "out", dt, (dim + 1, C), dev), p, _stream(stream))
+    _check("fem_integrate_reaction_diffusion", st)
     return out
 
 

@@ -1,0 +1,243 @@
+// fem_reaction.cu -- reaction-diffusion with an auxiliary coefficient field: the full
+// bracket of Eq. 2 (both the f0 and the f1 term) with the pointwise functions of Eq. 8
+// taking an auxiliary field a:
+//     f1(u, grad u, a) = a grad u,   f0(u, a) = c u,
+// a in P1 (nodal values, a(xi_q) = sum_b phi_b(xi_q) a_b) or in P0 (one value per cell),
+// c per quadrature point (optional).
+//
+// For P1 the gradients are constant on a cell, so the f1 part is the Laplacian element
+// vector of fem_laplacian.cu with Kbar = sum_q w_q a(xi_q) = sum_b m_b a_b, where
+// m_b = sum_q w_q phi_b(xi_q) (P1 a) or Kbar = a_e sum_q w_q (P0 a). The f0 part uses the
+// basis tabulation phi_b(xi_q) (the matrix B of Eq. 2):
+//     r_b += |det J| sum_q phi_b(xi_q) w_q c_q u(xi_q),  u(xi_q) = sum_a phi_a(xi_q) u_a.
+#include "fem_cell.cuh"
+
+namespace fem {
+
+// P1 basis tabulation at the quadrature points and its weighted column sums
+struct BasisTab {
+    double phid[FEM_MAX_QPTS][4];
+    float phif[FEM_MAX_QPTS][4];
+    double md[4];
+    float mf[4];
+    double wsumd;
+    float wsumf;
+};
+
+struct RdArgs {
+    const double *X[3];
+    const int32_t *conn;
+    const void *u;
+    const void *a;  // [V] (P1) or [C] (P0)
+    const void *c;  // [n_q][C] or NULL
+    void *out;      // [dim+1][C]
+    int64_t C;
+    uint32_t V;
+    float tau2;
+    QuadW w;
+    BasisTab t;
+};
+
+template <int P> __device__ __forceinline__ val_t<P> tab_phi(const BasisTab &t, int q, int b);
+template <> __device__ __forceinline__ double tab_phi<FEM_FP64>(const BasisTab &t, int q, int b) { return t.phid[q][b]; }
+template <> __device__ __forceinline__ float tab_phi<FEM_FP32_MIXED>(const BasisTab &t, int q, int b) { return t.phif[q][b]; }
+template <> __device__ __forceinline__ float tab_phi<FEM_FP32>(const BasisTab &t, int q, int b) { return t.phif[q][b]; }
+
+template <int P> __device__ __forceinline__ val_t<P> tab_m(const BasisTab &t, int b) {
+    if constexpr (P == FEM_FP64) return t.md[b];
+    else return t.mf[b];
+}
+template <int P> __device__ __forceinline__ val_t<P> tab_wsum(const BasisTab &t) {
+    if constexpr (P == FEM_FP64) return t.wsumd;
+    else return t.wsumf;
+}
+template <int P> __device__ __forceinline__ val_t<P> rd_weight(const QuadW &w, int q) {
+    if constexpr (P == FEM_FP64) return w.wd[q];
+    else return w.wf[q];
+}
+
+// f1 part (Laplacian with Kbar) and f0 part of one cell from its adjugate rows and det J
+template <int DIM, int P, class T, bool REACT>
+__device__ __forceinline__ void rd_element(const RdArgs &a, const T (&n)[DIM][DIM], T det, const T (&uu)[DIM + 1],
+                                           T kbar, const T (&cq)[FEM_MAX_QPTS], int nq, T (&r)[DIM + 1]) {
+    constexpr int NB = DIM + 1;
+    T h[DIM];
+#pragma unroll
+    for (int i = 0; i < DIM; ++i) h[i] = zero<T>();
+#pragma unroll
+    for (int j = 0; j < DIM; ++j) {
+        const T du = uu[j + 1] - uu[0];
+#pragma unroll
+        for (int i = 0; i < DIM; ++i) h[i] = fma(du, n[j][i], h[i]);
+    }
+    const T s = quot_abs(kbar, det);
+    T sum = zero<T>();
+#pragma unroll
+    for (int j = 0; j < DIM; ++j) {
+        r[j + 1] = s * dotv<DIM>(n[j], h);
+        sum = sum + r[j + 1];
+    }
+    r[0] = -sum;
+    if constexpr (REACT) {
+        const T ad = det < T(0) ? -det : det;
+        T m[NB];
+#pragma unroll
+        for (int b = 0; b < NB; ++b) m[b] = zero<T>();
+        for (int q = 0; q < nq; ++q) {
+            T uq = zero<T>();
+#pragma unroll
+            for (int b = 0; b < NB; ++b) uq = fma(T(tab_phi<P>(a.t, q, b)), uu[b], uq);
+            const T tq = T(rd_weight<P>(a.w, q)) * cq[q] * uq;
+#pragma unroll
+            for (int b = 0; b < NB; ++b) m[b] = fma(T(tab_phi<P>(a.t, q, b)), tq, m[b]);
+        }
+#pragma unroll
+        for (int b = 0; b < NB; ++b) r[b] = fma(ad, m[b], r[b]);
+    }
+}
+
+// One thread per cell (grid-stride). A_P1: the coefficient field is nodal.
+template <int DIM, int P, bool A_P1, bool REACT>
+__global__ void __launch_bounds__(kBlock) rd_kernel(const __grid_constant__ RdArgs a) {
+    constexpr int NB = DIM + 1;
+    using T = val_t<P>;
+    const int64_t C = a.C;
+    const int nq = a.w.nq;
+    const T *__restrict__ u = static_cast<const T *>(a.u);
+    const T *__restrict__ af = static_cast<const T *>(a.a);
+    const T *__restrict__ cf = static_cast<const T *>(a.c);
+    T *__restrict__ out = static_cast<T *>(a.out);
+    const double *X[DIM];
+#pragma unroll
+    for (int k = 0; k < DIM; ++k) X[k] = a.X[k];
+    const int64_t stride = int64_t(gridDim.x) * blockDim.x;
+    for (int64_t e = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; e < C; e += stride) {
+        uint32_t v[NB];
+        T uu[NB];
+#pragma unroll
+        for (int b = 0; b < NB; ++b) {
+            v[b] = clamp_vid(ld_stream(a.conn + b * C + e), a.V);
+            uu[b] = ld_gather(u + v[b]);
+        }
+        // Kbar = sum_q w_q a(xi_q)
+        qsum_t<P> ks;
+        if constexpr (A_P1) {
+            ks.first(tab_m<P>(a.t, 0), ld_gather(af + v[0]));
+#pragma unroll
+            for (int b = 1; b < NB; ++b) ks.add(tab_m<P>(a.t, b), ld_gather(af + v[b]));
+        } else {
+            ks.first(tab_wsum<P>(a.t), ld_stream(af + e));
+        }
+        T cq[FEM_MAX_QPTS];
+        if constexpr (REACT) {
+            for (int q = 0; q < nq; ++q) cq[q] = ld_stream(cf + q * C + e);
+        }
+        double xs[NB][DIM];
+        gather_coords<DIM>(X, v, xs);
+        T r[NB];
+        if constexpr (P == FEM_FP64) {
+            double ee[DIM][DIM], n[DIM][DIM];
+            columns_f64<DIM>(xs, ee);
+            const double det = adjugate_rows<DIM>(ee, n);
+            rd_element<DIM, P, double, REACT>(a, n, det, uu, ks.value(), cq, nq, r);
+        } else {
+            float ee[DIM][DIM], n[DIM][DIM];
+            if constexpr (P == FEM_FP32_MIXED) columns_mixed<DIM>(xs, ee);
+            else columns_f32<DIM>(xs, ee);
+            const float det = adjugate_rows<DIM>(ee, n);
+            bool ok = true;
+            if constexpr (P == FEM_FP32_MIXED) ok = shape_ok<DIM>(ee, det, a.tau2);
+            if (ok) {
+                rd_element<DIM, P, float, REACT>(a, n, det, uu, ks.value(), cq, nq, r);
+            } else {
+                // badly shaped cell: float64 geometry and sums, float64 tables
+                double e64[DIM][DIM], n64[DIM][DIM], u64[NB], r64[NB], c64[FEM_MAX_QPTS];
+                columns_f64<DIM>(xs, e64);
+                const double det64 = adjugate_rows<DIM>(e64, n64);
+#pragma unroll
+                for (int b = 0; b < NB; ++b) u64[b] = uu[b];
+                if constexpr (REACT) {
+                    for (int q = 0; q < nq; ++q) c64[q] = cq[q];
+                }
+                rd_element<DIM, FEM_FP64, double, REACT>(a, n64, det64, u64, ks.value_f64(), c64, nq, r64);
+#pragma unroll
+                for (int b = 0; b < NB; ++b) r[b] = static_cast<float>(r64[b]);
+            }
+        }
+#pragma unroll
+        for (int b = 0; b < NB; ++b) __stcs(out + b * C + e, r[b]);
+    }
+}
+
+template <int DIM, int P>
+static fem_status launch_rd(const RdArgs &a, bool a_p1, bool react, cudaStream_t s) {
+    const void *k;
+    if (a_p1) k = react ? reinterpret_cast<const void *>(rd_kernel<DIM, P, true, true>)
+                        : reinterpret_cast<const void *>(rd_kernel<DIM, P, true, false>);
+    else k = react ? reinterpret_cast<const void *>(rd_kernel<DIM, P, false, true>)
+                   : reinterpret_cast<const void *>(rd_kernel<DIM, P, false, false>);
+    const int grid = grid_for(a.C, kBlock, k);
+    if (a_p1 && react) rd_kernel<DIM, P, true, true><<<grid, kBlock, 0, s>>>(a);
+    else if (a_p1) rd_kernel<DIM, P, true, false><<<grid, kBlock, 0, s>>>(a);
+    else if (react) rd_kernel<DIM, P, false, true><<<grid, kBlock, 0, s>>>(a);
+    else rd_kernel<DIM, P, false, false><<<grid, kBlock, 0, s>>>(a);
+    return check_launch("fem_integrate_reaction_diffusion");
+}
+
+}  // namespace fem
+
+using namespace fem;
+
+extern "C" fem_status fem_integrate_reaction_diffusion(int dim, int64_t n_cells, int64_t n_verts, const double *coords,
+                                                       const int32_t *conn, const void *u, const void *a,
+                                                       int a_space, const void *c, int n_q, const double *qpts,
+                                                       const double *qw, void *elem_out, fem_precision prec,
+                                                       fem_stream stream) {
+    fem_status st = check_common(dim, n_cells, n_verts, coords, conn);
+    if (st != FEM_OK) return st;
+    if (prec != FEM_FP64 && prec != FEM_FP32_MIXED && prec != FEM_FP32)
+        return fail(FEM_ERR_ARG, "unknown precision %d", static_cast<int>(prec));
+    if (a_space != 0 && a_space != 1) return fail(FEM_ERR_ARG, "a_space = %d, must be 0 (P0) or 1 (P1)", a_space);
+    if (!qpts) return fail(FEM_ERR_ARG, "qpts is required: the f0 term and a P1 coefficient use phi_b(xi_q)");
+    RdArgs r;
+    if ((st = load_quadrature(dim, n_q, qpts, qw, r.w)) != FEM_OK) return st;
+    if (n_cells == 0) return FEM_OK;
+    if (!u || !a || !elem_out) return fail(FEM_ERR_ARG, "u, a or elem_out is NULL");
+    // P1 basis at the quadrature points: phi_0 = 1 - sum_k xi_k, phi_b = xi_{b-1}
+    for (int b = 0; b < 4; ++b) r.t.md[b] = 0.0;
+    r.t.wsumd = 0.0;
+    for (int q = 0; q < FEM_MAX_QPTS; ++q)
+        for (int b = 0; b < 4; ++b) r.t.phid[q][b] = 0.0;
+    for (int q = 0; q < n_q; ++q) {
+        double s = 0.0;
+        for (int k = 0; k < dim; ++k) s += qpts[q * dim + k];
+        r.t.phid[q][0] = 1.0 - s;
+        for (int b = 1; b <= dim; ++b) r.t.phid[q][b] = qpts[q * dim + b - 1];
+        for (int b = 0; b <= dim; ++b) r.t.md[b] += qw[q] * r.t.phid[q][b];
+        r.t.wsumd += qw[q];
+    }
+    for (int q = 0; q < FEM_MAX_QPTS; ++q)
+        for (int b = 0; b < 4; ++b) r.t.phif[q][b] = static_cast<float>(r.t.phid[q][b]);
+    for (int b = 0; b < 4; ++b) r.t.mf[b] = static_cast<float>(r.t.md[b]);
+    r.t.wsumf = static_cast<float>(r.t.wsumd);
+    for (int k = 0; k < 3; ++k) r.X[k] = coords + (k < dim ? k : 0) * n_verts;
+    r.conn = conn;
+    r.u = u;
+    r.a = a;
+    r.c = c;
+    r.out = elem_out;
+    r.C = n_cells;
+    r.V = static_cast<uint32_t>(n_verts);
+    const float tau = mixed_tau();
+    r.tau2 = tau * tau;
+    const bool p1 = a_space == 1, react = c != nullptr;
+    switch (dim * 10 + static_cast<int>(prec)) {
+        case 20: return launch_rd<2, FEM_FP64>(r, p1, react, stream);
+        case 21: return launch_rd<2, FEM_FP32_MIXED>(r, p1, react, stream);
+        case 22: return launch_rd<2, FEM_FP32>(r, p1, react, stream);
+        case 30: return launch_rd<3, FEM_FP64>(r, p1, react, stream);
+        case 31: return launch_rd<3, FEM_FP32_MIXED>(r, p1, react, stream);
+        case 32: return launch_rd<3, FEM_FP32>(r, p1, react, stream);
+    }
+    return fail(FEM_ERR_ARG, "unsupported dim/precision");
+}
