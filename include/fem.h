@@ -135,6 +135,31 @@ fem_status fem_integrate_reaction_diffusion(int dim, int64_t n_cells, int64_t n_
                                             void *elem_out, fem_precision prec, fem_stream stream);
 
 /* ---------------------------------------------------------------------------------
+ * fem_pcg_laplacian -- solve A x = b with a matrix-free Jacobi-preconditioned conjugate
+ * gradient, A the assembled operator of Eq. 2 for the variable-coefficient Laplacian
+ * (element residuals of fem_integrate_laplacian summed per vertex, E^T r_e(x)), not in
+ * the paper. Vertices with fixed[v] != 0 are Dirichlet vertices: they keep the value
+ * that x holds on entry, and the system is solved on the other vertices.
+ *   K, n_q, qpts, qw, coords, conn   as fem_integrate_laplacian
+ *   node_ptr, node_idx   from fem_build_node2cell for conn
+ *   fixed      [V] uint8 Dirichlet mask
+ *   b          [V] right-hand side (load vector), or NULL for zero
+ *   x          [V] in: initial guess and Dirichlet values; out: the solution
+ *   max_iter, rtol       stop when ||r||_2 <= rtol ||r_0||_2 or after max_iter iterations
+ *   work       caller-owned device workspace of fem_pcg_work_bytes() bytes, 256-byte aligned
+ *   iters_out, resid_out (host, may be NULL) iterations taken and ||r|| / ||r_0||
+ * Value arrays are float64 for FEM_FP64 and float32 otherwise; dot products accumulate
+ * in float64 in a fixed order (reproducible). Unlike the other entry points this one
+ * synchronises `stream` once per iteration to test convergence.
+ * ------------------------------------------------------------------------------- */
+int64_t fem_pcg_work_bytes(int dim, int64_t n_cells, int64_t n_verts, fem_precision prec);
+fem_status fem_pcg_laplacian(int dim, int64_t n_cells, int64_t n_verts, const double *coords,
+                             const int32_t *conn, const void *K, int n_q, const double *qpts, const double *qw,
+                             const int32_t *node_ptr, const int32_t *node_idx, const uint8_t *fixed,
+                             const void *b, void *x, int max_iter, double rtol, void *work, int64_t work_bytes,
+                             int *iters_out, double *resid_out, fem_precision prec, fem_stream stream);
+
+/* ---------------------------------------------------------------------------------
  * The paper's precomputed-geometry layout (Sec. 3 and the Appendix load J^{-1} and det J
  * per cell rather than computing them), as an alternate entry for the Laplacian:
  *

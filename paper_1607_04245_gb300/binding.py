@@ -54,6 +54,7 @@ def lib():
             "fem_device_error": [P],
             "fem_precompute_geometry": [ci, i64, i64, P, P, P, ci, P],
             "fem_integrate_reaction_diffusion": [ci, i64, i64, P, P, P, P, ci, P, ci, P, P, P, ci, P],
+            "fem_pcg_laplacian": [ci, i64, i64, P, P, P, ci, P, P, P, P, P, P, P, ci, cd, P, i64, P, P, ci, P],
             "fem_integrate_laplacian_geom": [ci, i64, i64, P, P, P, ci, P, P, P, P, ci, P],
             "fem_selftest_wait": [i64, P],
         }
@@ -63,6 +64,8 @@ def lib():
             f.restype = ci
         L.fem_get_mixed_threshold.argtypes = []
         L.fem_get_mixed_threshold.restype = cd
+        L.fem_pcg_work_bytes.argtypes = [ci, i64, i64, ci]
+        L.fem_pcg_work_bytes.restype = i64
         L.fem_node2cell_work_size.argtypes = [i64]
         L.fem_node2cell_work_size.restype = i64
         for name in ("fem_last_error", "fem_version"):
@@ -194,6 +197,31 @@ def fem_integrate_reaction_diffusion(coords, conn, u, a, qpts, qw, c=None, a_spa
         _dev(out, "out", dt, (dim + 1, C), dev), p, _stream(stream))
     _check("fem_integrate_reaction_diffusion", st)
     return out
+
+
+def fem_pcg_laplacian(coords, conn, K, qpts, qw, node_ptr, node_idx, fixed, x, b=None, max_iter=1000, rtol=1e-8,
+                      work=None, prec="fp64", stream=None):
+    """Solve the assembled Laplacian system on the free vertices (Dirichlet values in x).
+    Returns (x, iterations, relative residual)."""
+    p = precision(prec)
+    dt = value_dtype(p)
+    dim, V, C = _mesh_sizes(coords, conn)
+    nq = int(np.asarray(qw).shape[0]) if not isinstance(qw, torch.Tensor) else int(qw.shape[0])
+    dev = coords.device
+    need = int(lib().fem_pcg_work_bytes(dim, C, V, p))
+    if work is None:
+        work = torch.empty(max(need, 1), dtype=torch.uint8, device=dev)
+    qp, w = _HostTable(qpts, (nq, dim), "qpts"), _HostTable(qw, (nq,), "qw")
+    iters, resid = ctypes.c_int(0), ctypes.c_double(0.0)
+    st = lib().fem_pcg_laplacian(
+        dim, C, V, _dev(coords, "coords", torch.float64, device=dev), _dev(conn, "conn", torch.int32, device=dev),
+        _dev(K, "K", dt, (nq, C), dev), nq, qp.ptr, w.ptr, _dev(node_ptr, "node_ptr", torch.int32, (V + 1,), dev),
+        _dev(node_idx, "node_idx", torch.int32, ((dim + 1) * C,), dev), _dev(fixed, "fixed", torch.uint8, (V,), dev),
+        None if b is None else _dev(b, "b", dt, (V,), dev), _dev(x, "x", dt, (V,), dev), int(max_iter), float(rtol),
+        _dev(work, "work", torch.uint8, None, dev), int(work.numel()), ctypes.byref(iters), ctypes.byref(resid), p,
+        _stream(stream))
+    _check("fem_pcg_laplacian", st)
+    return x, int(iters.value), float(resid.value)
 
 
 def fem_precompute_geometry(coords, conn, geom=None, prec="mixed", stream=None) -> torch.Tensor:

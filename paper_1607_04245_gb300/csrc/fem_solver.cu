@@ -1,0 +1,271 @@
+// fem_solver.cu -- a matrix-free Jacobi-preconditioned conjugate-gradient solve with the
+// assembled Laplacian operator of Eq. 2: A v = E^T r_e(v), the element residuals of the
+// variable-coefficient Laplacian summed into the vertices through the vertex-to-cell
+// lists (fem_build_node2cell). Dirichlet vertices keep their value from the initial x.
+//
+// Kernels here: the assembled diagonal (element diagonals A_bb = Kbar |n_b|^2 / |det J|,
+// summed per vertex), a deterministic two-level dot product, and the vector updates of
+// CG with their scalars read from device memory. The iteration itself is driven from the
+// host, which reads the residual norm after every iteration to test convergence.
+#include <cmath>
+#include <cstring>
+
+#include "fem_cell.cuh"
+
+namespace fem {
+
+fem_status launch_gather(int dim, int n_comp, int64_t C, int64_t V, const void *elem, const int32_t *node_ptr,
+                         const int32_t *node_idx, void *out, fem_precision prec, cudaStream_t s);
+
+constexpr int kDotBlocks = 1024;  // fixed: the partial sums and their order do not depend on the device
+
+// element diagonals of the Laplacian stiffness: out[b][e] = Kbar |n_b|^2 / |det J|
+template <int DIM, class T>
+__global__ void lap_diag_kernel(const double *X0, int64_t C, uint32_t V, const int32_t *conn, const T *K, int nq,
+                                QuadW w, T *out) {
+    constexpr int NB = DIM + 1;
+    const double *X[DIM];
+#pragma unroll
+    for (int k = 0; k < DIM; ++k) X[k] = X0 + int64_t(k) * V;
+    const int64_t stride = int64_t(gridDim.x) * blockDim.x;
+    for (int64_t e = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; e < C; e += stride) {
+        uint32_t v[NB];
+#pragma unroll
+        for (int b = 0; b < NB; ++b) v[b] = clamp_vid(conn[b * C + e], V);
+        double kbar = 0.0;
+        for (int q = 0; q < nq; ++q) kbar += w.wd[q] * static_cast<double>(K[q * C + e]);
+        double xs[NB][DIM], ee[DIM][DIM], n[DIM][DIM];
+        gather_coords<DIM>(X, v, xs);
+        columns_f64<DIM>(xs, ee);
+        const double det = adjugate_rows<DIM>(ee, n);
+        const double s = kbar / fabs(det);
+        double n0[DIM];
+#pragma unroll
+        for (int i = 0; i < DIM; ++i) {
+            n0[i] = 0.0;
+#pragma unroll
+            for (int j = 0; j < DIM; ++j) n0[i] -= n[j][i];
+        }
+        out[e] = static_cast<T>(s * dotv<DIM>(n0, n0));
+#pragma unroll
+        for (int j = 0; j < DIM; ++j) out[(j + 1) * C + e] = static_cast<T>(s * dotv<DIM>(n[j], n[j]));
+    }
+}
+
+// block partial sums of x . y (float64 accumulation), fixed grid and order
+template <class T>
+__global__ void __launch_bounds__(256) dot_partial_kernel(int64_t n, const T *x, const T *y, double *partial) {
+    __shared__ double s[256];
+    double acc = 0.0;
+    for (int64_t i = int64_t(blockIdx.x) * 256 + threadIdx.x; i < n; i += int64_t(kDotBlocks) * 256)
+        acc += static_cast<double>(x[i]) * static_cast<double>(y[i]);
+    s[threadIdx.x] = acc;
+    __syncthreads();
+    for (int o = 128; o > 0; o >>= 1) {
+        if (threadIdx.x < o) s[threadIdx.x] += s[threadIdx.x + o];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) partial[blockIdx.x] = s[0];
+}
+
+__global__ void __launch_bounds__(256) dot_final_kernel(const double *partial, double *result) {
+    __shared__ double s[256];
+    double acc = 0.0;
+    for (int i = threadIdx.x; i < kDotBlocks; i += 256) acc += partial[i];
+    s[threadIdx.x] = acc;
+    __syncthreads();
+    for (int o = 128; o > 0; o >>= 1) {
+        if (threadIdx.x < o) s[threadIdx.x] += s[threadIdx.x + o];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) *result = s[0];
+}
+
+// scalars[] layout: 0 rz, 1 pq, 2 rz_new, 3 rr
+enum { S_RZ = 0, S_PQ = 1, S_RZNEW = 2, S_RR = 3, S_COUNT = 4 };
+
+// r = b - Ax (free vertices), 0 on fixed ones; z = r / D; p = z
+template <class T>
+__global__ void cg_init_kernel(int64_t V, const T *b, const T *Ax, const T *D, const uint8_t *fixed, T *r, T *z,
+                               T *p) {
+    const int64_t stride = int64_t(gridDim.x) * blockDim.x;
+    for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < V; i += stride) {
+        const T ri = fixed[i] ? T(0) : (b ? b[i] : T(0)) - Ax[i];
+        const T zi = ri / D[i];
+        r[i] = ri, z[i] = zi, p[i] = zi;
+    }
+}
+
+// q = 0 on fixed vertices (the operator is restricted to the free ones)
+template <class T>
+__global__ void mask_kernel(int64_t V, const uint8_t *fixed, T *q) {
+    const int64_t stride = int64_t(gridDim.x) * blockDim.x;
+    for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < V; i += stride)
+        if (fixed[i]) q[i] = T(0);
+}
+
+// alpha = rz / pq; x += alpha p; r -= alpha q; z = r / D
+template <class T>
+__global__ void cg_step_kernel(int64_t V, const double *sc, const T *p, const T *q, const T *D, T *x, T *r, T *z) {
+    const double alpha = sc[S_PQ] != 0.0 ? sc[S_RZ] / sc[S_PQ] : 0.0;
+    const int64_t stride = int64_t(gridDim.x) * blockDim.x;
+    for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < V; i += stride) {
+        x[i] = static_cast<T>(x[i] + alpha * p[i]);
+        const T ri = static_cast<T>(r[i] - alpha * q[i]);
+        r[i] = ri;
+        z[i] = ri / D[i];
+    }
+}
+
+// beta = rz_new / rz; p = z + beta p; rz = rz_new (one thread updates the scalar after all reads)
+template <class T>
+__global__ void cg_dir_kernel(int64_t V, const double *sc, const T *z, T *p) {
+    const double beta = sc[S_RZ] != 0.0 ? sc[S_RZNEW] / sc[S_RZ] : 0.0;
+    const int64_t stride = int64_t(gridDim.x) * blockDim.x;
+    for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < V; i += stride)
+        p[i] = static_cast<T>(z[i] + beta * p[i]);
+}
+
+__global__ void copy_scalar_kernel(double *sc, int dst, int src) { sc[dst] = sc[src]; }
+
+// fixed vertices get D = 1 (their rows are the identity)
+template <class T>
+__global__ void diag_fix_kernel(int64_t V, const uint8_t *fixed, T *D) {
+    const int64_t stride = int64_t(gridDim.x) * blockDim.x;
+    for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < V; i += stride)
+        if (fixed[i] || !(D[i] > T(0))) D[i] = T(1);
+}
+
+static size_t align256(size_t n) { return (n + 255) & ~size_t(255); }
+
+struct Workspace {
+    void *elem, *D, *r, *z, *p, *q;
+    double *partial, *scalars;
+};
+
+static size_t carve(int64_t C, int64_t V, int dim, size_t vs, void *base, Workspace *w) {
+    size_t off = 0;
+    char *b = static_cast<char *>(base);
+    auto take = [&](size_t bytes) {
+        void *p = b ? b + off : nullptr;
+        off += align256(bytes);
+        return p;
+    };
+    void *elem = take(size_t(dim + 1) * size_t(C) * vs);
+    void *D = take(size_t(V) * vs), *r = take(size_t(V) * vs), *z = take(size_t(V) * vs);
+    void *p = take(size_t(V) * vs), *q = take(size_t(V) * vs);
+    double *partial = static_cast<double *>(take(sizeof(double) * kDotBlocks));
+    double *scalars = static_cast<double *>(take(sizeof(double) * S_COUNT));
+    if (w) *w = Workspace{elem, D, r, z, p, q, partial, scalars};
+    return off;
+}
+
+template <class T>
+static fem_status pcg_run(int dim, int64_t C, int64_t V, const double *coords, const int32_t *conn, const void *K,
+                          int n_q, const double *qpts, const double *qw, const int32_t *ptr, const int32_t *idx,
+                          const uint8_t *fixed, const void *b, void *x, int max_iter, double rtol, const Workspace &w,
+                          int *iters_out, double *resid_out, fem_precision prec, cudaStream_t s) {
+    T *X = static_cast<T *>(x);
+    T *D = static_cast<T *>(w.D), *r = static_cast<T *>(w.r), *z = static_cast<T *>(w.z);
+    T *p = static_cast<T *>(w.p), *q = static_cast<T *>(w.q);
+    const T *B = static_cast<const T *>(b);
+    const int gV = static_cast<int>(std::min<int64_t>((V + 255) / 256, 4096));
+    QuadW qwt;
+    fem_status st = load_quadrature(dim, n_q, qpts, qw, qwt);
+    if (st != FEM_OK) return st;
+    // assembled diagonal
+    {
+        const int g = static_cast<int>(std::min<int64_t>((C + 255) / 256, 4096));
+        if (dim == 2) lap_diag_kernel<2, T><<<g, 256, 0, s>>>(coords, C, static_cast<uint32_t>(V), conn,
+                                                                static_cast<const T *>(K), n_q, qwt,
+                                                                static_cast<T *>(w.elem));
+        else lap_diag_kernel<3, T><<<g, 256, 0, s>>>(coords, C, static_cast<uint32_t>(V), conn,
+                                                       static_cast<const T *>(K), n_q, qwt, static_cast<T *>(w.elem));
+        if ((st = check_launch("fem_pcg_laplacian diagonal")) != FEM_OK) return st;
+        if ((st = launch_gather(dim, 1, C, V, w.elem, ptr, idx, D, prec, s)) != FEM_OK) return st;
+        diag_fix_kernel<T><<<gV, 256, 0, s>>>(V, fixed, D);
+    }
+    auto matvec = [&](const T *v, T *out) -> fem_status {
+        fem_status e = fem_integrate_laplacian(dim, C, V, coords, conn, v, K, n_q, qpts, qw, w.elem, prec, s);
+        if (e != FEM_OK) return e;
+        return launch_gather(dim, 1, C, V, w.elem, ptr, idx, out, prec, s);
+    };
+    auto dot = [&](const T *a, const T *c, int slot) {
+        dot_partial_kernel<T><<<kDotBlocks, 256, 0, s>>>(V, a, c, w.partial);
+        dot_final_kernel<<<1, 256, 0, s>>>(w.partial, w.scalars + slot);
+    };
+    auto read = [&](int slot, double &v) -> fem_status {
+        cudaError_t e = cudaMemcpyAsync(&v, w.scalars + slot, sizeof(double), cudaMemcpyDeviceToHost, s);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+        if (e != cudaSuccess) return fail(FEM_ERR_CUDA, "fem_pcg_laplacian: %s", cudaGetErrorString(e));
+        return FEM_OK;
+    };
+    // r0 = b - A x0 on the free vertices
+    if ((st = matvec(X, q)) != FEM_OK) return st;
+    cg_init_kernel<T><<<gV, 256, 0, s>>>(V, B, q, D, fixed, r, z, p);
+    dot(r, z, S_RZ);
+    dot(r, r, S_RR);
+    double rr0 = 0.0;
+    if ((st = read(S_RR, rr0)) != FEM_OK) return st;
+    const double r0 = std::sqrt(rr0);
+    double rn = r0;
+    int it = 0;
+    while (it < max_iter && rn > rtol * r0 && rn > 0.0) {
+        if ((st = matvec(p, q)) != FEM_OK) return st;
+        mask_kernel<T><<<gV, 256, 0, s>>>(V, fixed, q);
+        dot(p, q, S_PQ);
+        cg_step_kernel<T><<<gV, 256, 0, s>>>(V, w.scalars, p, q, D, X, r, z);
+        dot(r, z, S_RZNEW);
+        cg_dir_kernel<T><<<gV, 256, 0, s>>>(V, w.scalars, z, p);
+        copy_scalar_kernel<<<1, 1, 0, s>>>(w.scalars, S_RZ, S_RZNEW);
+        dot(r, r, S_RR);
+        double rr = 0.0;
+        if ((st = read(S_RR, rr)) != FEM_OK) return st;
+        rn = std::sqrt(rr);
+        ++it;
+    }
+    if ((st = check_launch("fem_pcg_laplacian")) != FEM_OK) return st;
+    if (iters_out) *iters_out = it;
+    if (resid_out) *resid_out = r0 > 0.0 ? rn / r0 : 0.0;
+    return FEM_OK;
+}
+
+}  // namespace fem
+
+using namespace fem;
+
+extern "C" int64_t fem_pcg_work_bytes(int dim, int64_t n_cells, int64_t n_verts, fem_precision prec) {
+    if ((dim != 2 && dim != 3) || n_cells < 0 || n_verts < 0) return -1;
+    return static_cast<int64_t>(carve(n_cells, n_verts, dim, prec == FEM_FP64 ? 8 : 4, nullptr, nullptr));
+}
+
+extern "C" fem_status fem_pcg_laplacian(int dim, int64_t n_cells, int64_t n_verts, const double *coords,
+                                        const int32_t *conn, const void *K, int n_q, const double *qpts,
+                                        const double *qw, const int32_t *node_ptr, const int32_t *node_idx,
+                                        const uint8_t *fixed, const void *b, void *x, int max_iter, double rtol,
+                                        void *work, int64_t work_bytes, int *iters_out, double *resid_out,
+                                        fem_precision prec, fem_stream stream) {
+    fem_status st = check_common(dim, n_cells, n_verts, coords, conn);
+    if (st != FEM_OK) return st;
+    if (prec != FEM_FP64 && prec != FEM_FP32_MIXED && prec != FEM_FP32)
+        return fail(FEM_ERR_ARG, "unknown precision %d", static_cast<int>(prec));
+    if (max_iter < 0 || !(rtol >= 0.0)) return fail(FEM_ERR_ARG, "max_iter must be >= 0 and rtol >= 0");
+    if (n_verts == 0) {
+        if (iters_out) *iters_out = 0;
+        if (resid_out) *resid_out = 0.0;
+        return FEM_OK;
+    }
+    if (!K || !node_ptr || !node_idx || !fixed || !x || !work) return fail(FEM_ERR_ARG, "a NULL array argument");
+    const int64_t need = fem_pcg_work_bytes(dim, n_cells, n_verts, prec);
+    if (work_bytes < need)
+        return fail(FEM_ERR_OOM, "fem_pcg_laplacian: workspace of %lld bytes, %lld needed",
+                    static_cast<long long>(work_bytes), static_cast<long long>(need));
+    if (reinterpret_cast<uintptr_t>(work) & 255u) return fail(FEM_ERR_ARG, "work must be 256-byte aligned");
+    Workspace w;
+    carve(n_cells, n_verts, dim, prec == FEM_FP64 ? 8 : 4, work, &w);
+    if (prec == FEM_FP64)
+        return pcg_run<double>(dim, n_cells, n_verts, coords, conn, K, n_q, qpts, qw, node_ptr, node_idx, fixed, b, x,
+                               max_iter, rtol, w, iters_out, resid_out, prec, stream);
+    return pcg_run<float>(dim, n_cells, n_verts, coords, conn, K, n_q, qpts, qw, node_ptr, node_idx, fixed, b, x,
+                          max_iter, rtol, w, iters_out, resid_out, prec, stream);
+}

@@ -1,0 +1,110 @@
+"""The matrix-free Jacobi-preconditioned CG solve with the assembled Laplacian (Eq. 2:
+E^T of the element residuals), against the patch test (a linear field is the exact
+discrete solution for a constant coefficient) and against a dense direct solve of the
+operator assembled from the CPU oracle's element vectors."""
+
+import numpy as np
+import pytest
+import torch
+
+import oracle
+import paper_1607_04245_gb300 as fem
+import workloads
+from gpu_util import to_dev
+
+pytestmark = pytest.mark.gpu
+
+
+def _mesh(dim, n):
+    return workloads.square_mesh(n, jitter=0.2, seed=3) if dim == 2 else workloads.cube_mesh(n, jitter=0.15, seed=3)
+
+
+def _boundary(mesh):
+    x = mesh.coords
+    return np.any((np.abs(x) < 1e-14) | (np.abs(x - 1.0) < 1e-14), axis=0)
+
+
+def _oracle_operator(mesh, K, rule):
+    V = mesh.n_verts
+    A = np.zeros((V, V))
+    for j in range(V):
+        e = np.zeros(V)
+        e[j] = 1.0
+        r = oracle.laplacian(mesh.coords, mesh.conn, e, K, rule.points, rule.weights)
+        np.add.at(A[:, j], mesh.conn.ravel(), r.ravel())
+    return A
+
+
+def _solve(mesh, K, rule, fixed, x0, b, prec, rtol):
+    dt = fem.value_dtype(prec)
+    coords, conn = to_dev(mesh.coords, torch.float64), to_dev(mesh.conn, torch.int32)
+    ptr, idx = fem.fem_build_node2cell(conn, mesh.n_verts)
+    x = to_dev(x0, dt)
+    return fem.fem_pcg_laplacian(coords, conn, to_dev(K, dt), rule.points, rule.weights, ptr, idx,
+                                 to_dev(fixed.astype(np.uint8), torch.uint8), x,
+                                 b=None if b is None else to_dev(b, dt), max_iter=5000, rtol=rtol, prec=prec)
+
+
+@pytest.mark.parametrize("dim,n", [(2, 24), (3, 8)])
+def test_patch_test_linear_solution(dim, n):
+    mesh = _mesh(dim, n)
+    rule = workloads.rule_for_dim(dim)
+    K = np.full((rule.n_q, mesh.n_cells), 1.7)
+    coef = np.array([1.0, 2.0, -3.0, 0.5][: dim + 1])
+    g = coef[0] + coef[1:] @ mesh.coords
+    fixed = _boundary(mesh)
+    x0 = np.where(fixed, g, 0.0)
+    x, iters, resid = _solve(mesh, K, rule, fixed, x0, None, "fp64", 1e-13)
+    err = np.abs(x.cpu().numpy() - g).max() / np.abs(g).max()
+    assert resid <= 1e-13 and iters > 0
+    assert err <= 1e-10, err
+
+
+@pytest.mark.parametrize("dim,n", [(2, 12), (3, 4)])
+@pytest.mark.parametrize("prec,rtol,tol", [("fp64", 1e-12, 1e-9), ("mixed", 1e-5, 1e-4)])
+def test_matches_dense_solve_of_oracle_operator(dim, n, prec, rtol, tol):
+    mesh = _mesh(dim, n)
+    rule = workloads.rule_for_dim(dim)
+    rng = np.random.default_rng(dim)
+    K = rng.lognormal(0.0, 1.0, (rule.n_q, mesh.n_cells))
+    if prec != "fp64":
+        K = K.astype(np.float32).astype(np.float64)
+    fixed = _boundary(mesh)
+    g = np.sin(mesh.coords[0] * 3.0) + mesh.coords[1]
+    b = np.where(fixed, 0.0, rng.uniform(-1, 1, mesh.n_verts) / mesh.n_verts)
+    if prec != "fp64":
+        b = b.astype(np.float32).astype(np.float64)
+        g = g.astype(np.float32).astype(np.float64)
+    x0 = np.where(fixed, g, 0.0)
+    x, iters, resid = _solve(mesh, K, rule, fixed, x0, b, prec, rtol)
+    A = _oracle_operator(mesh, K, rule)
+    free = ~fixed
+    ref = x0.copy()
+    ref[free] = np.linalg.solve(A[np.ix_(free, free)], b[free] - A[np.ix_(free, fixed)] @ g[fixed])
+    err = np.abs(x.cpu().numpy().astype(np.float64) - ref).max() / np.abs(ref).max()
+    assert resid <= rtol
+    assert err <= tol, (err, iters, resid)
+
+
+def test_solve_is_reproducible():
+    mesh = _mesh(2, 16)
+    rule = workloads.rule_for_dim(2)
+    K = np.random.default_rng(1).lognormal(0.0, 1.0, (rule.n_q, mesh.n_cells))
+    fixed = _boundary(mesh)
+    x0 = np.where(fixed, mesh.coords[0], 0.0)
+    a = _solve(mesh, K, rule, fixed, x0, None, "fp64", 1e-10)[0].cpu().numpy()
+    b = _solve(mesh, K, rule, fixed, x0, None, "fp64", 1e-10)[0].cpu().numpy()
+    assert np.array_equal(a, b)
+
+
+def test_workspace_too_small_is_rejected():
+    mesh = _mesh(2, 4)
+    rule = workloads.rule_for_dim(2)
+    coords, conn = to_dev(mesh.coords, torch.float64), to_dev(mesh.conn, torch.int32)
+    ptr, idx = fem.fem_build_node2cell(conn, mesh.n_verts)
+    K = torch.ones((rule.n_q, mesh.n_cells), dtype=torch.float64, device="cuda")
+    fixed = torch.zeros(mesh.n_verts, dtype=torch.uint8, device="cuda")
+    x = torch.zeros(mesh.n_verts, dtype=torch.float64, device="cuda")
+    with pytest.raises(fem.FemError):
+        fem.fem_pcg_laplacian(coords, conn, K, rule.points, rule.weights, ptr, idx, fixed, x,
+                              work=torch.empty(16, dtype=torch.uint8, device="cuda"), prec="fp64")
