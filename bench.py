@@ -353,6 +353,53 @@ def measure_geometry_path(case, prec, device, stream, flush, steps, warmup, peak
     return row
 
 
+def measure_transposed(case, prec, device, stream, flush, steps, warmup, peak, oracle_mod=None,
+                       configs=((32, 1), (32, 4), (32, 16), (64, 1), (64, 4), (64, 16), (128, 1), (128, 4), (128, 16),
+                                (256, 1), (256, 4), (256, 16))):
+    """The paper's thread-transposition kernel on its own data layout (J^{-1}, det J and
+    the element coefficients u_e per cell): a sweep over cells per batch and batches per
+    block (the analogue of the paper's Table 2). Timed: the kernel; also timed: the
+    closure u -> u_e that a new u costs (the paper performs it on the host)."""
+    import torch
+
+    import paper_1607_04245_gb300 as fem
+
+    c, d = device_case(case, prec, device)
+    q = c.rule
+    dt = fem.value_dtype(prec)
+    s = 8 if prec == "fp64" else 4
+    nb = c.dim + 1
+    nbytes = nb * s * c.n_cells + q.n_q * s * c.n_cells + (c.dim * c.dim + 1) * s * c.n_cells + nb * s * c.n_cells
+    with torch.cuda.stream(stream):
+        geom = fem.fem_precompute_geometry(d["coords"], d["conn"], prec=prec, stream=stream)
+        ue = fem.fem_element_values(d["conn"], c.n_verts, d["u"], prec=prec, stream=stream)
+        out = torch.empty((nb, c.n_cells), dtype=dt, device=device)
+        sweep = {}
+        for cpb, bpb in configs:
+            if prec == "fp64" and cpb > 128:
+                continue
+            fn = lambda: fem.fem_integrate_laplacian_transposed(ue, d["K"], q.points, q.weights, geom, cpb, bpb,
+                                                                out=out, prec=prec, stream=stream)
+            ms, _, _ = timed_steps(fn, steps, warmup, stream, flush)
+            t = statistics.mean(ms) * 1e-3
+            sweep[f"{cpb}x{bpb}"] = {"ms": round(statistics.mean(ms), 6), "cells_per_s": c.n_cells / t,
+                                     "alg_gbs": nbytes / t / 1e9, "hbm_frac_of_measured": nbytes / t / 1e9 / peak}
+        closure = lambda: fem.fem_element_values(d["conn"], c.n_verts, d["u"], ue=ue, prec=prec, stream=stream)
+        ms_c, _, _ = timed_steps(closure, steps, warmup, stream, flush)
+    best = min(sweep, key=lambda k: sweep[k]["ms"])
+    row = {"physics": "laplacian_thread_transposition", "dim": c.dim, "prec": prec, "cells": c.n_cells,
+           "alg_bytes_per_cell": "u_e 4s + K 4s + geom 10s + out 4s (s = value bytes); geometry once per mesh",
+           "best": best, "best_ms": sweep[best]["ms"], "best_cells_per_s": sweep[best]["cells_per_s"],
+           "best_hbm_frac_of_measured": sweep[best]["hbm_frac_of_measured"],
+           "closure_ms": round(statistics.mean(ms_c), 6), "sweep_cells_per_batch_x_batches": sweep}
+    if oracle_mod is not None:
+        fem.fem_integrate_laplacian_transposed(ue, d["K"], q.points, q.weights, geom, 64, 4, out=out, prec=prec,
+                                               stream=stream)
+        torch.cuda.synchronize()
+        row["rel_maxnorm_err_vs_oracle"] = rel_err(out, oracle_mod.residual_for(c))
+    return row
+
+
 def measure_adjoint(case, prec, device, stream, flush, steps, warmup, peak, oracle_mod=None):
     import torch
 
@@ -599,6 +646,9 @@ def run_ours(args):
         for prec in ("mixed", "fp64"):
             rows[f"lap3d_precomputed_geometry_{prec}"] = measure_geometry_path(case, prec, device, stream, flush, rsteps,
                                                                               args.warmup, peak, oracle)
+        for prec in ("fp32", "fp64"):
+            rows[f"lap3d_thread_transposition_{prec}"] = measure_transposed(case, prec, device, stream, flush, rsteps,
+                                                                           args.warmup, peak, oracle)
         rows["lap2d_8192_fp64"] = measure_residual(workloads.laplacian_square_case(), "fp64", device, stream, flush,
                                                    rsteps, args.warmup, peak, oracle)[0]
         for dim in (2, 3):

@@ -135,6 +135,46 @@ fem_status fem_integrate_reaction_diffusion(int dim, int64_t n_cells, int64_t n_
                                             void *elem_out, fem_precision prec, fem_stream stream);
 
 /* ---------------------------------------------------------------------------------
+ * fem_integrate_laplacian_host -- fem_integrate_laplacian for arrays in HOST memory
+ * (coords_h, conn_h, u_h, K_h in, out_h [dim+1][C] out; same layouts). The vertex arrays
+ * are copied to the device once; the cells are then processed in `chunks` pieces on two
+ * library-owned streams, so that uploads, kernels and downloads of different chunks
+ * overlap. All device buffers come from `work` (fem_host_work_bytes() bytes, 256-byte
+ * aligned, caller-owned); nothing is allocated. Host arrays should be page-locked
+ * (cudaHostAlloc / pinned) for the copies to be asynchronous; pageable memory works but
+ * the copies then serialise. The call returns after enqueueing; the results are in out_h
+ * once `stream` has completed. Calls from several host threads on one device must be
+ * serialised by the caller (the library's two streams and events are shared).
+ * ------------------------------------------------------------------------------- */
+int64_t fem_host_work_bytes(int dim, int64_t n_cells, int64_t n_verts, int n_q, fem_precision prec, int chunks);
+fem_status fem_integrate_laplacian_host(int dim, int64_t n_cells, int64_t n_verts, const double *coords_h,
+                                        const int32_t *conn_h, const void *u_h, const void *K_h, int n_q,
+                                        const double *qpts, const double *qw, void *out_h, void *work,
+                                        int64_t work_bytes, int chunks, fem_precision prec, fem_stream stream);
+
+/* ---------------------------------------------------------------------------------
+ * The paper's thread-transposition kernel (Sec. 3, Figs. 1-3), rebuilt as an ablation:
+ *
+ * fem_element_values -- the closure of a nodal field: ue[b][e] = u[conn[b][e]], [dim+1][C]
+ *   (the element-local basis coefficients the paper's kernel reads).
+ * fem_integrate_laplacian_transposed -- the Laplacian element residual from ue, K and the
+ *   geometry of fem_precompute_geometry, computed the paper's way: per batch of
+ *   cells_per_batch cells (32, 64, 128; 256 in the float32 forms) the inputs go to shared
+ *   memory, one thread per (cell, quadrature point) evaluates f1 (Sec. 3.1), a barrier,
+ *   one thread per (cell, basis function) contracts (Sec. 3.2); a thread block runs
+ *   batches_per_block batches in turn. Requires n_q = dim + 1 (= N_b, as in the rules
+ *   used here). Value type float64 for FEM_FP64, float32 otherwise (no compensation).
+ * Results equal fem_integrate_laplacian's up to rounding; this path exists to measure
+ * the paper's design on GB300 (Table 2 analogue: a sweep over both batch parameters).
+ * ------------------------------------------------------------------------------- */
+fem_status fem_element_values(int dim, int64_t n_cells, int64_t n_verts, const int32_t *conn, const void *u,
+                              void *ue, fem_precision prec, fem_stream stream);
+fem_status fem_integrate_laplacian_transposed(int dim, int64_t n_cells, const void *ue, const void *K, int n_q,
+                                              const double *qpts, const double *qw, const void *geom,
+                                              void *elem_out, int cells_per_batch, int batches_per_block,
+                                              fem_precision prec, fem_stream stream);
+
+/* ---------------------------------------------------------------------------------
  * fem_pcg_laplacian -- solve A x = b with a matrix-free Jacobi-preconditioned conjugate
  * gradient, A the assembled operator of Eq. 2 for the variable-coefficient Laplacian
  * (element residuals of fem_integrate_laplacian summed per vertex, E^T r_e(x)), not in

@@ -18,11 +18,15 @@ from .binding import (  # noqa: F401
     fem_build_node2cell,
     fem_check_mesh,
     fem_device_error,
+    fem_element_values,
     fem_gather_nodes,
     fem_get_mixed_threshold,
     fem_integrate_elasticity,
+    fem_host_work_bytes,
     fem_integrate_laplacian,
+    fem_integrate_laplacian_host,
     fem_integrate_laplacian_geom,
+    fem_integrate_laplacian_transposed,
     fem_integrate_reaction_diffusion,
     fem_precompute_geometry,
     fem_pcg_laplacian,

@@ -54,6 +54,9 @@ def lib():
             "fem_device_error": [P],
             "fem_precompute_geometry": [ci, i64, i64, P, P, P, ci, P],
             "fem_integrate_reaction_diffusion": [ci, i64, i64, P, P, P, P, ci, P, ci, P, P, P, ci, P],
+            "fem_element_values": [ci, i64, i64, P, P, P, ci, P],
+            "fem_integrate_laplacian_host": [ci, i64, i64, P, P, P, P, ci, P, P, P, P, i64, ci, ci, P],
+            "fem_integrate_laplacian_transposed": [ci, i64, P, P, ci, P, P, P, P, ci, ci, ci, P],
             "fem_pcg_laplacian": [ci, i64, i64, P, P, P, ci, P, P, P, P, P, P, P, ci, cd, P, i64, P, P, ci, P],
             "fem_integrate_laplacian_geom": [ci, i64, i64, P, P, P, ci, P, P, P, P, ci, P],
             "fem_selftest_wait": [i64, P],
@@ -64,6 +67,8 @@ def lib():
             f.restype = ci
         L.fem_get_mixed_threshold.argtypes = []
         L.fem_get_mixed_threshold.restype = cd
+        L.fem_host_work_bytes.argtypes = [ci, i64, i64, ci, ci, ci]
+        L.fem_host_work_bytes.restype = i64
         L.fem_pcg_work_bytes.argtypes = [ci, i64, i64, ci]
         L.fem_pcg_work_bytes.restype = i64
         L.fem_node2cell_work_size.argtypes = [i64]
@@ -222,6 +227,75 @@ def fem_pcg_laplacian(coords, conn, K, qpts, qw, node_ptr, node_idx, fixed, x, b
         _stream(stream))
     _check("fem_pcg_laplacian", st)
     return x, int(iters.value), float(resid.value)
+
+
+def _host(t: torch.Tensor, name: str, dtype: torch.dtype, shape) -> int:
+    if t.is_cuda:
+        raise ValueError(f"{name} must be a host tensor")
+    if t.dtype != dtype:
+        raise ValueError(f"{name} must be {dtype}, got {t.dtype}")
+    if not t.is_contiguous():
+        raise ValueError(f"{name} must be contiguous")
+    if tuple(t.shape) != tuple(shape):
+        raise ValueError(f"{name} has shape {tuple(t.shape)}, expected {tuple(shape)}")
+    return t.data_ptr() if t.numel() else 0
+
+
+def fem_integrate_laplacian_host(coords_h, conn_h, u_h, K_h, qpts, qw, out_h, work, chunks=4, prec="mixed",
+                                 stream=None) -> torch.Tensor:
+    """Laplacian element residuals from host tensors (pinned for overlap) into out_h; `work`
+    is a device uint8 tensor of at least fem_host_work_bytes() bytes. Results are valid
+    once `stream` has completed."""
+    p = precision(prec)
+    dt = value_dtype(p)
+    dim, V = int(coords_h.shape[0]), int(coords_h.shape[1])
+    C = int(conn_h.shape[1])
+    nq = int(np.asarray(qw).shape[0]) if not isinstance(qw, torch.Tensor) else int(qw.shape[0])
+    qp, w = _HostTable(qpts, (nq, dim), "qpts"), _HostTable(qw, (nq,), "qw")
+    st = lib().fem_integrate_laplacian_host(
+        dim, C, V, _host(coords_h, "coords_h", torch.float64, (dim, V)), _host(conn_h, "conn_h", torch.int32,
+                                                                              (dim + 1, C)),
+        _host(u_h, "u_h", dt, (V,)), _host(K_h, "K_h", dt, (nq, C)), nq, qp.ptr, w.ptr,
+        _host(out_h, "out_h", dt, (dim + 1, C)), _dev(work, "work", torch.uint8, None), int(work.numel()),
+        int(chunks), p, _stream(stream))
+    _check("fem_integrate_laplacian_host", st)
+    return out_h
+
+
+def fem_host_work_bytes(dim: int, n_cells: int, n_verts: int, n_q: int, prec="mixed", chunks: int = 4) -> int:
+    return int(lib().fem_host_work_bytes(dim, n_cells, n_verts, n_q, precision(prec), chunks))
+
+
+def fem_element_values(conn, n_verts: int, u, ue=None, prec="mixed", stream=None) -> torch.Tensor:
+    """Element basis coefficients ue[b][e] = u[conn[b][e]]."""
+    p = precision(prec)
+    dt = value_dtype(p)
+    dim, C = int(conn.shape[0]) - 1, int(conn.shape[1])
+    dev = conn.device
+    ue = torch.empty((dim + 1, C), dtype=dt, device=dev) if ue is None else ue
+    st = lib().fem_element_values(dim, C, int(n_verts), _dev(conn, "conn", torch.int32, device=dev),
+                                  _dev(u, "u", dt, (n_verts,), dev), _dev(ue, "ue", dt, (dim + 1, C), dev), p,
+                                  _stream(stream))
+    _check("fem_element_values", st)
+    return ue
+
+
+def fem_integrate_laplacian_transposed(ue, K, qpts, qw, geom, cells_per_batch=64, batches_per_block=4, out=None,
+                                       prec="mixed", stream=None) -> torch.Tensor:
+    """The paper's thread-transposition kernel: element residuals [dim+1][C]."""
+    p = precision(prec)
+    dt = value_dtype(p)
+    dim, C = int(ue.shape[0]) - 1, int(ue.shape[1])
+    nq = int(np.asarray(qw).shape[0]) if not isinstance(qw, torch.Tensor) else int(qw.shape[0])
+    dev = ue.device
+    out = torch.empty((dim + 1, C), dtype=dt, device=dev) if out is None else out
+    qp, w = _HostTable(qpts, (nq, dim), "qpts"), _HostTable(qw, (nq,), "qw")
+    st = lib().fem_integrate_laplacian_transposed(
+        dim, C, _dev(ue, "ue", dt, (dim + 1, C), dev), _dev(K, "K", dt, (nq, C), dev), nq, qp.ptr, w.ptr,
+        _dev(geom, "geom", dt, (dim * dim + 1, C), dev), _dev(out, "out", dt, (dim + 1, C), dev),
+        int(cells_per_batch), int(batches_per_block), p, _stream(stream))
+    _check("fem_integrate_laplacian_transposed", st)
+    return out
 
 
 def fem_precompute_geometry(coords, conn, geom=None, prec="mixed", stream=None) -> torch.Tensor:

@@ -1,9 +1,11 @@
-"""Host-buffer entry point: integrate numpy arrays that live in host memory.
+"""Host-buffer entry point: integrate arrays that live in host memory.
 
-HostIntegrator keeps reusable device buffers and pinned host staging buffers, and
-per call copies the inputs host -> device, runs the CUDA residual, and copies the
-element vectors back, all on one stream. This is the call a user with host data
-makes; the benchmark's end-to-end figure is measured through it.
+HostIntegrator keeps pinned host staging buffers and a device workspace. The Laplacian
+goes through libfem's host entry (fem_integrate_laplacian_host): the vertex arrays are
+uploaded once per call and the cells stream through in chunks on two library streams,
+so that uploads, kernels and downloads overlap. Elasticity copies everything, runs the
+kernel and copies back on one stream. This is the call a user with host data makes; the
+benchmark's end-to-end figure is measured through it.
 """
 
 from __future__ import annotations
@@ -13,7 +15,7 @@ from typing import Dict, Tuple
 import numpy as np
 import torch
 
-from .binding import fem_integrate_elasticity, fem_integrate_laplacian, value_dtype
+from .binding import (fem_host_work_bytes, fem_integrate_elasticity, fem_integrate_laplacian_host, value_dtype)
 
 
 class HostIntegrator:
@@ -46,21 +48,21 @@ class HostIntegrator:
         self.h2d_bytes += host.numel() * host.element_size()
         return d
 
-    def laplacian(self, coords_h, conn_h, u_h, K_h, qpts, qw, prec="mixed", out_h=None) -> torch.Tensor:
+    def laplacian(self, coords_h, conn_h, u_h, K_h, qpts, qw, prec="mixed", out_h=None, chunks=4) -> torch.Tensor:
         """All arguments are pinned host tensors (see pinned()); returns the element
         vectors in a pinned host tensor, valid after self.stream is synchronised."""
-        with torch.cuda.stream(self.stream):
-            coords = self._upload("coords", coords_h)
-            conn = self._upload("conn", conn_h)
-            u = self._upload("u", u_h)
-            K = self._upload("K", K_h)
-            dt = value_dtype(prec)
-            out = self._buf(self._dev, "out", (conn.shape[0], conn.shape[1]), dt, False)
-            fem_integrate_laplacian(coords, conn, u, K, qpts, qw, out=out, prec=prec, stream=self.stream)
-            if out_h is None:
-                out_h = self._buf(self._pin, "out_h", out.shape, dt, True)
-            out_h.copy_(out, non_blocking=True)
-            self.d2h_bytes += out.numel() * out.element_size()
+        dt = value_dtype(prec)
+        dim, V = int(coords_h.shape[0]), int(coords_h.shape[1])
+        C, nq = int(conn_h.shape[1]), int(K_h.shape[0])
+        need = fem_host_work_bytes(dim, C, V, nq, prec, chunks)
+        work = self._buf(self._dev, "host_work", (max(need, 1),), torch.uint8, False)
+        if out_h is None:
+            out_h = self._buf(self._pin, "out_h", (dim + 1, C), dt, True)
+        fem_integrate_laplacian_host(coords_h, conn_h, u_h, K_h, qpts, qw, out_h, work, chunks=chunks, prec=prec,
+                                     stream=self.stream)
+        for t in (coords_h, conn_h, u_h, K_h):
+            self.h2d_bytes += t.numel() * t.element_size()
+        self.d2h_bytes += out_h.numel() * out_h.element_size()
         return out_h
 
     def elasticity(self, coords_h, conn_h, u_h, lam_h, mu_h, qpts, qw, prec="mixed", out_h=None) -> torch.Tensor:
