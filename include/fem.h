@@ -76,7 +76,14 @@ typedef enum {
     FEM_FP32_MIXED = 1,
     /* ablation: float32 values, coordinates rounded to float32 before the Jacobian,
      * plain float32 sums, no float64 fallback */
-    FEM_FP32 = 2
+    FEM_FP32 = 2,
+    /* float64 values (as FEM_FP64) with float64-class accuracy computed on the float32
+     * pipe: the Jacobian columns are formed in float64, every other intermediate is a
+     * pair of float32 values (hi + lo, double-length arithmetic from TwoSum/TwoProduct),
+     * the outputs are widened back to float64. Values must lie in float32's normal range
+     * (|x| in [2^-126, 2^128), or zero). fem_integrate_laplacian only; the other entry
+     * points return FEM_ERR_ARG for it. */
+    FEM_FP64_DF = 3
 } fem_precision;
 
 #define FEM_MAX_QPTS 32

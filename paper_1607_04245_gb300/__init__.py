@@ -12,6 +12,7 @@ from .binding import (  # noqa: F401
     FEM_FP32,
     FEM_FP32_MIXED,
     FEM_FP64,
+    FEM_FP64_DF,
     FEM_MAX_QPTS,
     FemError,
     fem_adjoint_laplacian,

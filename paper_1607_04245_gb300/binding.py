@@ -20,8 +20,9 @@ import torch
 _PKG = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_PKG, "libfem.so")
 
-FEM_FP64, FEM_FP32_MIXED, FEM_FP32 = 0, 1, 2
-_PREC_NAMES = {"fp64": FEM_FP64, "mixed": FEM_FP32_MIXED, "fp32_mixed": FEM_FP32_MIXED, "fp32": FEM_FP32}
+FEM_FP64, FEM_FP32_MIXED, FEM_FP32, FEM_FP64_DF = 0, 1, 2, 3
+_PREC_NAMES = {"fp64": FEM_FP64, "mixed": FEM_FP32_MIXED, "fp32_mixed": FEM_FP32_MIXED, "fp32": FEM_FP32,
+               "fp64_df": FEM_FP64_DF}
 FEM_MAX_QPTS = 32
 
 _lib = None
@@ -89,13 +90,13 @@ def _check(fn: str, st: int):
 def precision(p: Union[int, str]) -> int:
     if isinstance(p, str):
         return _PREC_NAMES[p.lower()]
-    if p not in (FEM_FP64, FEM_FP32_MIXED, FEM_FP32):
+    if p not in (FEM_FP64, FEM_FP32_MIXED, FEM_FP32, FEM_FP64_DF):
         raise ValueError(f"unknown precision {p}")
     return int(p)
 
 
 def value_dtype(prec) -> torch.dtype:
-    return torch.float64 if precision(prec) == FEM_FP64 else torch.float32
+    return torch.float64 if precision(prec) in (FEM_FP64, FEM_FP64_DF) else torch.float32
 
 
 def _stream(stream) -> int:

@@ -78,13 +78,13 @@ __device__ __forceinline__ float round_f64_to_f32(uint32_t lo_w, uint32_t hi_w) 
 // Error-free transformations (Knuth's TwoSum; TwoProduct via FMA), used for the
 // compensated quadrature sum of Ogita, Rump and Oishi's Dot2 algorithm.
 __device__ __forceinline__ void two_sum(float a, float b, float &s, float &e) {
-    s = a + b;
-    float bb = s - a;
-    e = (a - (s - bb)) + (b - bb);
+    s = __fadd_rn(a, b);
+    float bb = __fsub_rn(s, a);
+    e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
 }
 
 __device__ __forceinline__ void two_prod(float a, float b, float &p, float &e) {
-    p = a * b;
+    p = __fmul_rn(a, b);  // never contracted into a later add: p must be the rounded product
     e = fmaf(a, b, -p);
 }
 

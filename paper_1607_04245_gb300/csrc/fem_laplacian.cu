@@ -674,10 +674,24 @@ static fem_status fill_args(LapArgs &a, int dim, int64_t n_cells, int64_t n_vert
 
 using namespace fem;
 
+namespace fem {
+fem_status launch_lap_df(int dim, int64_t n_cells, int64_t n_verts, const double *coords, const int32_t *conn,
+                         const void *u, const void *K, int n_q, const double *qw, void *elem_out,
+                         cudaStream_t stream);
+}
+
 extern "C" fem_status fem_integrate_laplacian(int dim, int64_t n_cells, int64_t n_verts, const double *coords,
                                               const int32_t *conn, const void *u, const void *K, int n_q,
                                               const double *qpts, const double *qw, void *elem_out,
                                               fem_precision prec, fem_stream stream) {
+    if (prec == FEM_FP64_DF) {
+        fem_status st = check_common(dim, n_cells, n_verts, coords, conn);
+        QuadW w;
+        if (st == FEM_OK) st = load_quadrature(dim, n_q, qpts, qw, w);
+        if (st != FEM_OK || n_cells == 0) return st;
+        if (!u || !K || !elem_out) return fail(FEM_ERR_ARG, "u, K or elem_out is NULL");
+        return launch_lap_df(dim, n_cells, n_verts, coords, conn, u, K, n_q, qw, elem_out, stream);
+    }
     LapArgs a;
     fem_status st = fill_args(a, dim, n_cells, n_verts, coords, conn, u, K, n_q, qpts, qw, prec);
     if (st != FEM_OK) return st;
