@@ -286,26 +286,27 @@ struct Dot2Sum {
     __device__ __forceinline__ double value_f64() const { return static_cast<double>(s) + static_cast<double>(c); }
 };
 
-// Dot2 for two cells at once; the weight is the same in both lanes, so -w is a constant
-// and TwoProduct needs no negation.
+// Dot2 for two cells at once. The compensation is kept negated (m = -c): TwoProduct's
+// error term then comes out of one FMA, m_p = fma(-w, x, p) = p - w x exactly, with p
+// the correctly rounded product (mul_rn_exact), and no negation is needed anywhere.
 struct Dot2Sum2 {
-    f2 s, c;
+    f2 s, m;
     __device__ __forceinline__ void first(float w, f2 x) {
-        s = f2_splat(w) * x;
-        c = fma(f2_splat(w), x, f2_splat(-w) * x);
+        s = mul_rn_exact(f2_splat(w), x);
+        m = fma(f2_splat(-w), x, s);
     }
     __device__ __forceinline__ void add(float w, f2 x) {
-        const f2 p = f2_splat(w) * x;
-        const f2 pe = fma(f2_splat(w), x, f2_splat(-w) * x);
+        const f2 p = mul_rn_exact(f2_splat(w), x);
+        const f2 mp = fma(f2_splat(-w), x, p);
         const f2 t = s + p;
         const f2 bb = t - s;
         const f2 se = (s - (t - bb)) + (p - bb);
         s = t;
-        c = c + (pe + se);
+        m = m + (mp - se);
     }
-    __device__ __forceinline__ f2 value() const { return s + c; }
-    __device__ __forceinline__ double value_f64_x() const { return double(f2_x(s)) + double(f2_x(c)); }
-    __device__ __forceinline__ double value_f64_y() const { return double(f2_y(s)) + double(f2_y(c)); }
+    __device__ __forceinline__ f2 value() const { return s - m; }
+    __device__ __forceinline__ double value_f64_x() const { return double(f2_x(s)) - double(f2_x(m)); }
+    __device__ __forceinline__ double value_f64_y() const { return double(f2_y(s)) - double(f2_y(m)); }
 };
 
 // sum_q w_q c_q in plain f32x2 (FP32 ablation)

@@ -4,9 +4,14 @@
 // instruction, so the float32 cell arithmetic of two cells runs at half the issue cost.
 // The kernels process cells in pairs: every float32 quantity of the per-cell algebra
 // (Jacobian, adjugate, field gradient, quadrature sums, element vector) is an f2 whose
-// two lanes belong to two different cells. All operations round to nearest, one
-// rounding per operation (no contraction), so the error-free transformations of the
-// compensated sums stay exact.
+// two lanes belong to two different cells. Every operation rounds to nearest.
+//
+// The rounded product of a packed multiply is NOT reliably kept as such: bitwise checks
+// on sm_103a found the result of mul.rn.f32x2, when consumed by later packed adds, to
+// differ from the scalar correctly rounded product in longer dependent sequences (and
+// to agree in short ones), as if the multiply had been fused into its consumer. An
+// error-free transformation needs the rounded product itself, so TwoProduct takes it
+// from mul_rn_exact below: two scalar __fmul_rn, which are never contracted.
 #pragma once
 
 #include <stdint.h>
@@ -45,6 +50,11 @@ __device__ __forceinline__ f2 operator*(f2 a, f2 b) {
     f2 r;
     asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(r.v) : "l"(a.v), "l"(b.v));
     return r;
+}
+
+// the correctly rounded product per lane, for error-free transformations (see above)
+__device__ __forceinline__ f2 mul_rn_exact(f2 a, f2 b) {
+    return f2_make(__fmul_rn(f2_x(a), f2_x(b)), __fmul_rn(f2_y(a), f2_y(b)));
 }
 
 __device__ __forceinline__ f2 operator-(f2 a) {
