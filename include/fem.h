@@ -144,14 +144,18 @@ fem_status fem_integrate_reaction_diffusion(int dim, int64_t n_cells, int64_t n_
 /* ---------------------------------------------------------------------------------
  * fem_integrate_laplacian_host -- fem_integrate_laplacian for arrays in HOST memory
  * (coords_h, conn_h, u_h, K_h in, out_h [dim+1][C] out; same layouts). The vertex arrays
- * are copied to the device once; the cells are then processed in `chunks` pieces on two
- * library-owned streams, so that uploads, kernels and downloads of different chunks
- * overlap. All device buffers come from `work` (fem_host_work_bytes() bytes, 256-byte
- * aligned, caller-owned); nothing is allocated. Host arrays should be page-locked
- * (cudaHostAlloc / pinned) for the copies to be asynchronous; pageable memory works but
- * the copies then serialise. The call returns after enqueueing; the results are in out_h
- * once `stream` has completed. Calls from several host threads on one device must be
- * serialised by the caller (the library's two streams and events are shared).
+ * are copied to the device once. Then, with chunks >= 1, the cells are processed in
+ * `chunks` pieces on two library-owned streams, so that uploads, kernels and downloads of
+ * different chunks overlap; with chunks == 0 nothing more is copied: the kernel reads
+ * conn_h and K_h and writes out_h directly across the host link (these three must then be
+ * page-locked and device-mapped, e.g. cudaHostAlloc / pinned tensors; otherwise
+ * FEM_ERR_ARG). All device buffers come from `work` (fem_host_work_bytes() bytes for the
+ * same `chunks`, 256-byte aligned, caller-owned); nothing is allocated. With chunks >= 1
+ * the host arrays should be page-locked for the copies to be asynchronous; pageable
+ * memory works but the copies then serialise. The call returns after enqueueing; the
+ * results are in out_h once `stream` has completed. Calls from several host threads on
+ * one device must be serialised by the caller (the library's two streams and events are
+ * shared). FEM_FP64, FEM_FP32_MIXED and FEM_FP32 only.
  * ------------------------------------------------------------------------------- */
 int64_t fem_host_work_bytes(int dim, int64_t n_cells, int64_t n_verts, int n_q, fem_precision prec, int chunks);
 fem_status fem_integrate_laplacian_host(int dim, int64_t n_cells, int64_t n_verts, const double *coords_h,

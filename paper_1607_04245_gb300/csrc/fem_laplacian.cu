@@ -600,14 +600,14 @@ static fem_status launch_staged(const LapArgs &a, uint32_t sb, cudaStream_t s) {
 }
 
 template <int DIM, int P, bool ADJ>
-static fem_status launch_lap(const LapArgs &a, bool vec, cudaStream_t s) {
+static fem_status launch_lap(const LapArgs &a, bool vec, cudaStream_t s, bool staged_ok = true) {
     using T = val_t<P>;
     const uint32_t sb = lap_stage_bytes<T>(DIM + 1, a.w.nq, ADJ);
     fem_status st = FEM_OK;
     // the quadrature size of the workloads' rules (3 points in 2D, 4 in 3D) is compiled in
     const bool native_nq = (DIM == 3 && a.w.nq == 4) || (DIM == 2 && a.w.nq == 3);
 #ifndef FEM_LAP_DIRECT
-    if (vec && 2u * sb <= kStageMax) {
+    if (staged_ok && vec && 2u * sb <= kStageMax) {
         if (a.w.nq == DIM + 1 && DIM == 3) st = launch_staged<DIM, P, 4, ADJ>(a, sb, s);
         else if (a.w.nq == 3 && DIM == 2) st = launch_staged<DIM, P, 3, ADJ>(a, sb, s);
         else st = launch_staged<DIM, P, 0, ADJ>(a, sb, s);
@@ -631,18 +631,19 @@ static fem_status launch_lap(const LapArgs &a, bool vec, cudaStream_t s) {
 }
 
 template <bool ADJ>
-static fem_status dispatch_lap(int dim, fem_precision prec, const LapArgs &a, bool vec, cudaStream_t s) {
+static fem_status dispatch_lap(int dim, fem_precision prec, const LapArgs &a, bool vec, cudaStream_t s,
+                               bool staged_ok = true) {
     if (dim == 2) {
         switch (prec) {
-            case FEM_FP64: return launch_lap<2, FEM_FP64, ADJ>(a, vec, s);
-            case FEM_FP32_MIXED: return launch_lap<2, FEM_FP32_MIXED, ADJ>(a, vec, s);
-            case FEM_FP32: return launch_lap<2, FEM_FP32, ADJ>(a, vec, s);
+            case FEM_FP64: return launch_lap<2, FEM_FP64, ADJ>(a, vec, s, staged_ok);
+            case FEM_FP32_MIXED: return launch_lap<2, FEM_FP32_MIXED, ADJ>(a, vec, s, staged_ok);
+            case FEM_FP32: return launch_lap<2, FEM_FP32, ADJ>(a, vec, s, staged_ok);
         }
     } else {
         switch (prec) {
-            case FEM_FP64: return launch_lap<3, FEM_FP64, ADJ>(a, vec, s);
-            case FEM_FP32_MIXED: return launch_lap<3, FEM_FP32_MIXED, ADJ>(a, vec, s);
-            case FEM_FP32: return launch_lap<3, FEM_FP32, ADJ>(a, vec, s);
+            case FEM_FP64: return launch_lap<3, FEM_FP64, ADJ>(a, vec, s, staged_ok);
+            case FEM_FP32_MIXED: return launch_lap<3, FEM_FP32_MIXED, ADJ>(a, vec, s, staged_ok);
+            case FEM_FP32: return launch_lap<3, FEM_FP32, ADJ>(a, vec, s, staged_ok);
         }
     }
     return fail(FEM_ERR_ARG, "unknown precision %d", static_cast<int>(prec));
@@ -703,6 +704,20 @@ extern "C" fem_status fem_integrate_laplacian(int dim, int64_t n_cells, int64_t 
 }
 
 namespace fem {
+// The residual with plain (vector) loads and stores only -- never the bulk-copy staged
+// kernel -- for connectivity, coefficient and output arrays that live in page-locked host
+// memory and are reached across the host link (fem_integrate_laplacian_host, chunks = 0).
+fem_status integrate_laplacian_plain(int dim, int64_t n_cells, int64_t n_verts, const double *coords,
+                                     const int32_t *conn, const void *u, const void *K, int n_q, const double *qpts,
+                                     const double *qw, void *elem_out, fem_precision prec, cudaStream_t stream) {
+    LapArgs a;
+    fem_status st = fill_args(a, dim, n_cells, n_verts, coords, conn, u, K, n_q, qpts, qw, prec);
+    if (st != FEM_OK || n_cells == 0) return st;
+    a.out = elem_out;
+    const bool vec = n_cells % 4 == 0 && aligned16(conn) && aligned16(K) && aligned16(elem_out);
+    return dispatch_lap<false>(dim, prec, a, vec, stream, false);
+}
+
 fem_status launch_gather(int dim, int n_comp, int64_t C, int64_t V, const void *elem, const int32_t *node_ptr,
                          const int32_t *node_idx, void *out, fem_precision prec, cudaStream_t s);
 }

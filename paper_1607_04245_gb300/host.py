@@ -2,9 +2,12 @@
 
 HostIntegrator keeps pinned host staging buffers and a device workspace. The Laplacian
 goes through libfem's host entry (fem_integrate_laplacian_host): the vertex arrays are
-uploaded once per call and the cells stream through in chunks on two library streams,
-so that uploads, kernels and downloads overlap. Elasticity copies everything, runs the
-kernel and copies back on one stream. This is the call a user with host data makes; the
+uploaded once per call; by default (chunks = 0) the kernel then reads the connectivity and
+coefficient rows from the pinned host buffers and writes the element vectors into a pinned
+host buffer across the host link, so both directions stream for the whole kernel; with
+chunks >= 1 the cells instead go through copy-engine transfers in chunks on two library
+streams, overlapped with the kernels. Elasticity copies everything, runs the kernel and
+copies back on one stream. This is the call a user with host data makes; the
 benchmark's end-to-end figure is measured through it.
 """
 
@@ -48,7 +51,7 @@ class HostIntegrator:
         self.h2d_bytes += host.numel() * host.element_size()
         return d
 
-    def laplacian(self, coords_h, conn_h, u_h, K_h, qpts, qw, prec="mixed", out_h=None, chunks=4) -> torch.Tensor:
+    def laplacian(self, coords_h, conn_h, u_h, K_h, qpts, qw, prec="mixed", out_h=None, chunks=0) -> torch.Tensor:
         """All arguments are pinned host tensors (see pinned()); returns the element
         vectors in a pinned host tensor, valid after self.stream is synchronised."""
         dt = value_dtype(prec)
