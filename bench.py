@@ -508,10 +508,30 @@ def measure_serving(device, n_requests, seed=0):
                         "cells": st.cells}}
 
 
-def cpu_baseline(case, min_seconds=10.0, max_reps=200):
+def cpu_model() -> str:
+    """The host CPU as /proc/cpuinfo names it (model name on x86; implementer/part on Arm)."""
+    import platform
+
+    info = {}
+    try:
+        for line in open("/proc/cpuinfo"):
+            if ":" in line:
+                k, v = line.split(":", 1)
+                info.setdefault(k.strip(), v.strip())
+    except OSError:
+        pass
+    name = info.get("model name") or (
+        f"implementer {info.get('CPU implementer', '?')} part {info.get('CPU part', '?')}")
+    return f"{platform.machine()}, {os.cpu_count()} logical CPUs, {name}"
+
+
+def cpu_baseline(case, min_seconds=10.0, max_reps=200, single_seconds=4.0):
+    """The oracle on the host cores: all threads over the full workload (about
+    min_seconds), then one thread on a slice of it (about single_seconds)."""
     import oracle
 
     oracle.build()
+    threads = oracle.num_threads()
     reps, t0 = 0, time.perf_counter()
     while reps < max_reps:
         oracle.residual_for(case)
@@ -519,9 +539,29 @@ def cpu_baseline(case, min_seconds=10.0, max_reps=200):
         if time.perf_counter() - t0 >= min_seconds:
             break
     dt = time.perf_counter() - t0
-    return {"value": case.n_cells * reps / dt, "unit": "cells/s", "cores": oracle.num_threads(), "kind": "oracle",
+    # one thread: the first S cells, S sized from the all-thread rate
+    rate_all = case.n_cells * reps / dt
+    S = int(min(case.n_cells, max(4096, rate_all / max(1, threads) * single_seconds / 2)))
+    m, q = case.mesh, case.rule
+    conn = np.ascontiguousarray(m.conn[:, :S])
+    K = np.ascontiguousarray(case.K[:, :S])
+    oracle.set_threads(1)
+    try:
+        reps1, t1 = 0, time.perf_counter()
+        while True:
+            oracle.laplacian(m.coords, conn, case.u, K, q.points, q.weights)
+            reps1 += 1
+            if time.perf_counter() - t1 >= single_seconds:
+                break
+        dt1 = time.perf_counter() - t1
+    finally:
+        oracle.set_threads(threads)
+    return {"value": rate_all, "unit": "cells/s", "cores": threads, "kind": "oracle",
             "sample": f"the full {case.n_cells}-cell workload x {reps} repetitions ({dt:.1f} s, float64, "
-                      f"OpenMP over cells)"}
+                      f"OpenMP over cells)",
+            "single_thread": {"value": S * reps1 / dt1, "unit": "cells/s", "cores": 1,
+                              "sample": f"the first {S} cells x {reps1} repetitions ({dt1:.1f} s)"},
+            "cpu": cpu_model()}
 
 
 # ----------------------------------------------------------------------------- arms

@@ -64,6 +64,8 @@ def _lib():
                   lib.oracle_reaction_diffusion):
             f.restype = ci
         lib.oracle_num_threads.restype = ci
+        lib.oracle_set_threads.argtypes = [ci]
+        lib.oracle_set_threads.restype = None
         _LIB = lib
     return _LIB
 
@@ -87,6 +89,11 @@ def _check(st):
 
 def num_threads() -> int:
     return int(_lib().oracle_num_threads())
+
+
+def set_threads(n: int) -> None:
+    """Threads of the loops over cells (timing only; results do not depend on it)."""
+    _lib().oracle_set_threads(int(n))
 
 
 def laplacian(coords, conn, u, K, qpts, qw) -> np.ndarray:

@@ -69,6 +69,16 @@ int oracle_num_threads(void) {
 #endif
 }
 
+/* Thread count of the loops over cells (timing only; the results do not depend on it:
+ * every cell is computed by one thread, in the same order of operations). */
+void oracle_set_threads(int n) {
+#ifdef _OPENMP
+    if (n > 0) omp_set_num_threads(n);
+#else
+    (void)n;
+#endif
+}
+
 /* P1 basis on the reference simplex, evaluated at the quadrature points:
  * phi_0 = 1 - sum_k xi_k, phi_b = xi_{b-1}; their reference gradients are
  * d phi_0 / d xi_k = -1 and d phi_b / d xi_k = [k == b-1].  The tables are built per
