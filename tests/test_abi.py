@@ -106,3 +106,21 @@ def test_binding_fails_loudly_without_library(monkeypatch, tmp_path):
     monkeypatch.setattr(binding, "LIB_PATH", str(tmp_path / "missing.so"))
     with pytest.raises(RuntimeError, match="libfem.so not found"):
         binding.lib()
+
+
+def test_host_work_bytes(lib):
+    """Workspace sizes of the host-buffer entry (pure host arithmetic)."""
+    a256 = lambda n: (n + 255) // 256 * 256
+    dim, C, V, nq = 3, 1000, 300, 4
+    # chunks = 0: the device copies of the vertex arrays only
+    assert lib.fem_host_work_bytes(dim, C, V, nq, 1, 0) == a256(dim * V * 8) + a256(V * 4)
+    assert lib.fem_host_work_bytes(dim, C, V, nq, 0, 0) == a256(dim * V * 8) + a256(V * 8)
+    # chunks >= 1: plus two buffers of conn, K and out rows for one chunk (a multiple of 4 cells)
+    per = (C + 3 - 1) // 3
+    per = (per + 3) // 4 * 4
+    want = a256(dim * V * 8) + a256(V * 4) + 2 * (a256(4 * per * 4) + a256(nq * per * 4) + a256(4 * per * 4))
+    assert lib.fem_host_work_bytes(dim, C, V, nq, 1, 3) == want
+    # invalid arguments
+    assert lib.fem_host_work_bytes(dim, C, V, nq, 1, -1) == -1
+    assert lib.fem_host_work_bytes(4, C, V, nq, 1, 1) == -1
+    assert lib.fem_host_work_bytes(dim, C, V, 0, 1, 1) == -1
