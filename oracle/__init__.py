@@ -59,7 +59,7 @@ def _lib():
         lib.oracle_laplacian.argtypes = [ci, i64, i64, P, P, P, P, ci, P, P, P]
         lib.oracle_elasticity.argtypes = [ci, i64, i64, P, P, P, P, P, ci, P, P, P]
         lib.oracle_adjoint_laplacian.argtypes = [ci, i64, i64, P, P, P, P, ci, P, P, P, P, P]
-        lib.oracle_reaction_diffusion.argtypes = [ci, i64, i64, P, P, P, P, ci, P, ci, P, P, P]
+        lib.oracle_reaction_diffusion.argtypes = [ci, i64, i64, P, P, P, P, ci, P, ctypes.c_double, ci, P, P, P]
         for f in (lib.oracle_laplacian, lib.oracle_elasticity, lib.oracle_adjoint_laplacian,
                   lib.oracle_reaction_diffusion):
             f.restype = ci
@@ -134,9 +134,9 @@ def adjoint_laplacian(coords, conn, u, K, qpts, qw, lam_adj):
     return dK, du
 
 
-def reaction_diffusion(coords, conn, u, a, a_space, c, qpts, qw) -> np.ndarray:
-    """Element vectors [dim+1][C] of f1 = a grad u, f0 = c u (a in P1: a_space=1, a[V];
-    in P0: a_space=0, a[C]; c [n_q][C] or None)."""
+def reaction_diffusion(coords, conn, u, a, a_space, c, qpts, qw, drift=0.0) -> np.ndarray:
+    """Element vectors [dim+1][C] of f1 = a grad u, f0 = c u + drift grad a . grad u (a in
+    P1: a_space=1, a[V]; in P0: a_space=0, a[C], grad a = 0; c [n_q][C] or None)."""
     coords, u, a, qpts, qw = map(_f64, (coords, u, a, qpts, qw))
     c = None if c is None else _f64(c)
     conn = np.ascontiguousarray(conn, dtype=np.int32)
@@ -145,7 +145,7 @@ def reaction_diffusion(coords, conn, u, a, a_space, c, qpts, qw) -> np.ndarray:
     nq = qw.shape[0]
     out = np.zeros((dim + 1, C), dtype=np.float64)
     _check(_lib().oracle_reaction_diffusion(dim, C, V, _ptr(coords), _ptr(conn), _ptr(u), _ptr(a), int(a_space),
-                                            _ptr(c), nq, _ptr(qpts), _ptr(qw), _ptr(out)))
+                                            _ptr(c), float(drift), nq, _ptr(qpts), _ptr(qw), _ptr(out)))
     return out
 
 

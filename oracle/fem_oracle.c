@@ -338,16 +338,19 @@ int oracle_adjoint_laplacian(int dim, int64_t n_cells, int64_t n_verts, const do
 
 /* Reaction-diffusion with an auxiliary coefficient field: the full bracket of Eq. 2,
  *     r_{e,b} = sum_q w_q |det J| [ phi_b(xi_q) f0(q) + G_b(q) . f1(q) ],
- * with the pointwise functions of Eq. 8 taking the auxiliary field a:
- *     f1(u, grad u, a) = a grad u,      f0(u, a) = c u,
+ * with the pointwise functions of Eq. 8 taking the auxiliary field a and its gradient:
+ *     f1(u, grad u, a) = a grad u,      f0(u, grad u, a, grad a) = c u + g grad a . grad u,
  * evaluated at each quadrature point from the tabulated basis:
  *     u(q) = sum_b phi_b(xi_q) u_b,  grad u(q) = sum_b u_b G_b(q),
- *     a(q) = sum_b phi_b(xi_q) a_b   (a_space = 1: a in P1, nodal values a[V])
- *     a(q) = a_e                     (a_space = 0: a in P0, one value per cell a[C])
- * c [n_q][C] is the reaction coefficient per quadrature point; c = NULL drops f0. */
+ *     a(q) = sum_b phi_b(xi_q) a_b,  grad a(q) = sum_b a_b G_b(q)
+ *                                    (a_space = 1: a in P1, nodal values a[V])
+ *     a(q) = a_e,  grad a(q) = 0     (a_space = 0: a in P0, one value per cell a[C])
+ * c [n_q][C] is the reaction coefficient per quadrature point (c = NULL: no reaction term);
+ * g (`drift`) scales the first-order term along grad a (g = 0: none). */
 int oracle_reaction_diffusion(int dim, int64_t n_cells, int64_t n_verts, const double *coords,
                               const int32_t *conn, const double *u, const double *a, int a_space,
-                              const double *c, int n_q, const double *qpts, const double *qw, double *out) {
+                              const double *c, double drift, int n_q, const double *qpts, const double *qw,
+                              double *out) {
     int st = check_args(dim, n_cells, n_verts, n_q);
     if (st) return st;
     if (a_space != 0 && a_space != 1) return ORA_ERR_ARG;
@@ -376,17 +379,25 @@ int oracle_reaction_diffusion(int dim, int64_t n_cells, int64_t n_verts, const d
         /* quadrature phase: f0 and f1 at every point, scaled by w_q |det J| */
         double f0[ORA_MAX_Q], f1[ORA_MAX_Q][3];
         for (int q = 0; q < n_q; ++q) {
-            double uq = 0.0, aq = 0.0, gradU[3] = {0.0, 0.0, 0.0};
+            double uq = 0.0, aq = 0.0, gradU[3] = {0.0, 0.0, 0.0}, gradA[3] = {0.0, 0.0, 0.0};
             for (int b = 0; b < nb; ++b) {
                 double G[3];
                 phys_grad(dim, invJ, dphi[q][b], G);
                 uq += phi[q][b] * ub[b];
                 aq += phi[q][b] * ab[b];
-                for (int i = 0; i < dim; ++i) gradU[i] += ub[b] * G[i];
+                for (int i = 0; i < dim; ++i) {
+                    gradU[i] += ub[b] * G[i];
+                    gradA[i] += ab[b] * G[i];
+                }
             }
-            if (a_space == 0) aq = ab[0];
+            if (a_space == 0) {
+                aq = ab[0];
+                for (int i = 0; i < dim; ++i) gradA[i] = 0.0;
+            }
             double scale = qw[q] * fabs(detJ);
-            f0[q] = c ? c[(int64_t)q * n_cells + e] * uq * scale : 0.0;
+            double f0q = c ? c[(int64_t)q * n_cells + e] * uq : 0.0;
+            for (int i = 0; i < dim; ++i) f0q += drift * gradA[i] * gradU[i];
+            f0[q] = f0q * scale;
             for (int i = 0; i < dim; ++i) f1[q][i] = aq * gradU[i] * scale;
         }
         /* basis phase: e_b = sum_q phi_b(q) f0(q) + G_b(q) . f1(q) */

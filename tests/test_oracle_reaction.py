@@ -1,10 +1,13 @@
 """Pins of the oracle's reaction-diffusion routine (Eq. 2 with both terms; Eq. 8: the
-pointwise functions take an auxiliary field a in P1 or P0): f1 = a grad u, f0 = c u.
+pointwise functions take an auxiliary field a in P1 or P0 and its gradient):
+f1 = a grad u, f0 = c u + g grad a . grad u.
 
 Each check compares against something other than the routine itself: the already
 pinned Laplacian routine (a in P0, no reaction), the exact P1 stiffness with the exact
 mean of a linear a, the closed-form P1 mass matrix, the exact integral of f0 over the
-cell, and symmetry of the assembled operator.
+cell, symmetry of the assembled operator, and for the grad a term the exact integral
+g (p.s) |T|/(d+1) for linear fields with gradients p and s, its symmetry in u and a, and
+its absence for a P0 coefficient.
 """
 
 import math
@@ -105,3 +108,63 @@ def test_assembled_operator_symmetric(ora, dim):
         np.add.at(A[:, j], mesh.conn.ravel(), r.ravel())
     assert np.abs(A - A.T).max() <= 1e-13 * np.abs(A).max()
     assert np.all(np.linalg.eigvalsh(0.5 * (A + A.T)) > 0)  # mass + stiffness: positive definite
+
+
+# ---- the first-order term along grad a (Eq. 8: f0 depends on grad a):
+#      f0 = c u + g grad a . grad u
+
+
+def _linear_fields(dim, coords, seed):
+    """u(x) = p.x + u0 and a(x) = s.x + a0 sampled at the vertices: exact P1 fields with
+    known constant gradients p and s."""
+    rng = np.random.default_rng(seed)
+    p, s = rng.normal(size=dim), rng.normal(size=dim)
+    u0, a0 = rng.normal(), rng.normal()
+    return p @ coords + u0, s @ coords + a0, p, s
+
+
+@pytest.mark.parametrize("dim", [2, 3])
+def test_drift_term_closed_form(ora, dim):
+    """For linear u and a the drift part is g (p.s) int_T phi_b = g (p.s) |T| / (d+1) for
+    every basis function (|T| = |det J| / d!), on random, arbitrarily oriented simplices."""
+    coords, conn = _random_simplices(dim, 50, 41 + dim)
+    rule = workloads.rule_for_dim(dim)
+    u, a, p, s = _linear_fields(dim, coords, 7 + dim)
+    g = 1.7
+    r_g = ora.reaction_diffusion(coords, conn, u, a, 1, None, rule.points, rule.weights, drift=g)
+    r_0 = ora.reaction_diffusion(coords, conn, u, a, 1, None, rule.points, rule.weights, drift=0.0)
+    X = coords.T[conn]  # [d+1][C][d]
+    J = np.stack([X[j + 1] - X[0] for j in range(dim)], axis=-1)  # [C][d][d], columns x_j - x_0
+    vol = np.abs(np.linalg.det(J)) / math.factorial(dim)
+    want = g * float(p @ s) * vol / (dim + 1)
+    d = r_g - r_0
+    assert np.abs(d - want[None, :]).max() <= 1e-13 * np.abs(want).max()
+
+
+@pytest.mark.parametrize("dim", [2, 3])
+def test_drift_term_symmetric_in_u_and_a(ora, dim):
+    """grad a . grad u is symmetric, so exchanging u and a leaves the drift part unchanged
+    (random nodal values: gradients differ from cell to cell)."""
+    coords, conn = _random_simplices(dim, 60, 51 + dim)
+    rule = workloads.rule_for_dim(dim)
+    rng = np.random.default_rng(dim + 30)
+    V = coords.shape[1]
+    u, a = rng.uniform(-1, 1, V), rng.uniform(-1, 1, V)
+    drift = lambda x, y: (ora.reaction_diffusion(coords, conn, x, y, 1, None, rule.points, rule.weights, drift=0.8)
+                          - ora.reaction_diffusion(coords, conn, x, y, 1, None, rule.points, rule.weights))
+    d_ua, d_au = drift(u, a), drift(a, u)
+    assert np.abs(d_ua).max() > 0
+    assert np.abs(d_ua - d_au).max() <= 1e-12 * np.abs(d_ua).max()
+
+
+@pytest.mark.parametrize("dim", [2, 3])
+def test_drift_term_vanishes_for_p0_coefficient(ora, dim):
+    """A P0 field is constant on each cell: grad a = 0 there, whatever g."""
+    coords, conn = _random_simplices(dim, 20, 61 + dim)
+    rule = workloads.rule_for_dim(dim)
+    rng = np.random.default_rng(dim + 40)
+    u, a = rng.uniform(-1, 1, coords.shape[1]), rng.lognormal(0, 1, conn.shape[1])
+    c = rng.uniform(0.5, 2.0, (rule.n_q, conn.shape[1]))
+    r_g = ora.reaction_diffusion(coords, conn, u, a, 0, c, rule.points, rule.weights, drift=3.0)
+    r_0 = ora.reaction_diffusion(coords, conn, u, a, 0, c, rule.points, rule.weights)
+    assert np.array_equal(r_g, r_0)
