@@ -437,6 +437,88 @@ def measure_adjoint(case, prec, device, stream, flush, steps, warmup, peak, orac
     return row
 
 
+def measure_reaction(case, prec, device, stream, flush, steps, warmup, peak, oracle_mod=None, drift=1.0):
+    """Reaction-diffusion with a P1 auxiliary field and its gradient (Eqs. 2 and 8):
+    f1 = a grad u, f0 = c u + drift grad a . grad u, on the case's mesh."""
+    import torch
+
+    import paper_1607_04245_gb300 as fem
+
+    c, d = device_case(case, prec, device)
+    a_np, c_np = workloads.reaction_inputs(c)
+    if prec != "fp64":
+        a_np, c_np = (x.astype(np.float32).astype(np.float64) for x in (a_np, c_np))
+    dt = fem.value_dtype(prec)
+    a_d = torch.from_numpy(a_np).to(device=device, dtype=dt)
+    c_d = torch.from_numpy(np.ascontiguousarray(c_np)).to(device=device, dtype=dt)
+    q = c.rule
+    out = torch.empty((c.dim + 1, c.n_cells), dtype=dt, device=device)
+    fn = lambda: fem.fem_integrate_reaction_diffusion(d["coords"], d["conn"], d["u"], a_d, q.points, q.weights,
+                                                      c=c_d, a_space=1, drift=drift, out=out, prec=prec, stream=stream)
+    with torch.cuda.stream(stream):
+        ms, _, _ = timed_steps(fn, steps, warmup, stream, flush)
+    t = statistics.mean(ms) * 1e-3
+    s = 8 if prec == "fp64" else 4
+    nb = c.dim + 1
+    nbytes = nb * 4 * c.n_cells + q.n_q * s * c.n_cells + nb * s * c.n_cells + (c.dim * 8 + 2 * s) * c.n_verts
+    row = {"physics": "reaction_diffusion_p1_grad_a", "dim": c.dim, "prec": prec, "cells": c.n_cells,
+           "drift": drift, "ms_per_launch": round(statistics.mean(ms), 6), "cells_per_s": c.n_cells / t,
+           "alg_bytes_per_launch": nbytes, "alg_gbs": nbytes / t / 1e9, "hbm_frac_of_measured": nbytes / t / 1e9 / peak,
+           "alg_bytes_per_cell": "conn 4(d+1) + c n_q s + out (d+1) s + (V/C)(coords 8d + u s + a s)"}
+    if oracle_mod is not None:
+        torch.cuda.synchronize()
+        ref = oracle_mod.reaction_diffusion(c.mesh.coords, c.mesh.conn, c.u, a_np, 1, c_np, q.points, q.weights,
+                                            drift=drift)
+        row["rel_maxnorm_err_vs_oracle"] = rel_err(out, ref)
+        row["tolerance"] = TOL[prec]
+    return row
+
+
+def measure_pcg(case, device, stream, peak, prec="fp64", rtol=1e-8, max_iter=5000, reps=2):
+    """The matrix-free Jacobi-PCG solve with the assembled float64 operator (Eq. 2, E^T of
+    the element residuals; prec "fp64_df": the residual in the double-float form) on the
+    case's mesh and coefficient, boundary held at a linear g. Per iteration (all on the
+    device, a CUDA graph WHILE loop): one residual launch, one vertex gather, the vector
+    updates and three dot products."""
+    import torch
+
+    import paper_1607_04245_gb300 as fem
+
+    c, d = device_case(case, prec, device)
+    q = c.rule
+    fixed_np, x0_np = workloads.dirichlet_problem(c)
+    ptr, idx = fem.fem_build_node2cell(d["conn"], c.n_verts)
+    fixed = torch.from_numpy(fixed_np).to(device)
+    x0 = torch.from_numpy(x0_np).to(device)
+    work = torch.empty(max(1, int(fem.binding.lib().fem_pcg_work_bytes(c.dim, c.n_cells, c.n_verts,
+                                                                         fem.binding.precision(prec)))),
+                       dtype=torch.uint8, device=device)
+    times, iters, resid = [], 0, 0.0
+    for _ in range(reps + 1):
+        x = x0.clone()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        _, iters, resid = fem.fem_pcg_laplacian(d["coords"], d["conn"], d["K"], q.points, q.weights, ptr, idx, fixed,
+                                                x, max_iter=max_iter, rtol=rtol, work=work, prec=prec,
+                                                stream=stream)
+        torch.cuda.synchronize()
+        times.append(time.perf_counter() - t0)
+    t = statistics.median(times[1:])  # the first solve warms up
+    C, V, nb = c.n_cells, c.n_verts, c.dim + 1
+    # per iteration: residual + gather (lists, element vectors, result) + mask, 3 dots,
+    # the update of x, r, z and the new direction (float64 vectors of V entries)
+    per_it = (algorithmic_bytes("laplacian", c.dim, "fp64", C, V, q.n_q)
+              + (V + 1) * 4 + nb * C * 4 + nb * C * 8 + V * 8
+              + V * (1 + 16) + 3 * V * 16 + V * (7 * 8 + 3 * 8) + V * 24)
+    return {"physics": "pcg_laplacian", "dim": c.dim, "prec": prec, "cells": C, "verts": V, "rtol": rtol,
+            "iterations": iters, "rel_residual": resid, "ms_per_solve": t * 1e3, "us_per_iteration": t / iters * 1e6,
+            "alg_bytes_per_iteration": per_it, "alg_gbs": per_it * iters / t / 1e9,
+            "hbm_frac_of_measured": per_it * iters / t / 1e9 / peak,
+            "timing": "host wall clock around the whole solve (two host synchronisations per solve; the "
+                      "iterations run as a device-side graph loop); median of 2 solves after one warm-up; L2 not "
+                      "flushed between iterations"}
+
+
 def measure_e2e(case, prec, device, steps, warmup):
     """Same metric through the host-buffer API: H2D of all inputs, kernel, D2H of the result."""
     import torch
@@ -710,6 +792,11 @@ def run_ours(args):
         for prec in ("mixed", "fp64"):
             rows[f"adjoint3d_{prec}"] = measure_adjoint(adj, prec, device, stream, flush, rsteps, args.warmup, peak,
                                                         oracle)
+        for prec in ("mixed", "fp64"):
+            rows[f"reaction3d_grad_a_{prec}"] = measure_reaction(case, prec, device, stream, flush, rsteps, args.warmup,
+                                                                 peak, oracle)
+        for prec in ("fp64", "fp64_df"):
+            rows[f"pcg_lap3d_{prec}"] = measure_pcg(case, device, stream, peak, prec)
         sweep = {}
         for e in range(16, 24):
             sc = workloads.laplacian_cube_case(1 << e)

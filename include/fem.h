@@ -122,14 +122,15 @@ fem_status fem_integrate_elasticity(int dim, int64_t n_cells, int64_t n_verts, c
 
 /* ---------------------------------------------------------------------------------
  * fem_integrate_reaction_diffusion -- element vectors of the full bracket of Eq. 2 (both
- * the f0 and the f1 term) with pointwise functions that take an auxiliary field a
- * (Eq. 8; Sec. 4 allows a in the space of u or in P0):
- *     f1 = a grad u,  f0 = c u,
- *     r_b = sum_q w_q |det J| [ phi_b(xi_q) c_q u(xi_q) + G_b . a(xi_q) grad u ]
+ * the f0 and the f1 term) with pointwise functions that take an auxiliary field a and
+ * its gradient (Eq. 8; Sec. 4 allows a in the space of u or in P0):
+ *     f1 = a grad u,  f0 = c u + drift grad a . grad u,
+ *     r_b = sum_q w_q |det J| [ phi_b(xi_q) f0(xi_q) + G_b . a(xi_q) grad u ]
  *   u          [V] nodal values
  *   a          a_space = 1: [V] nodal values of a P1 field, a(xi_q) = sum_b phi_b(xi_q) a_b
- *              a_space = 0: [C] one value per cell (P0)
- *   c          [n_q][C] reaction coefficient per quadrature point, or NULL (no f0 term)
+ *              a_space = 0: [C] one value per cell (P0; grad a = 0 inside a cell)
+ *   c          [n_q][C] reaction coefficient per quadrature point, or NULL (no c u term)
+ *   drift      scalar g of the first-order term along grad a (0: none; must be finite)
  *   qpts       required here (phi_b(xi_q) enters both terms)
  *   elem_out   [dim+1][C]
  * Other arguments and returns as fem_integrate_laplacian. The FP32_MIXED form computes
@@ -138,8 +139,9 @@ fem_status fem_integrate_elasticity(int dim, int64_t n_cells, int64_t n_verts, c
  * ------------------------------------------------------------------------------- */
 fem_status fem_integrate_reaction_diffusion(int dim, int64_t n_cells, int64_t n_verts, const double *coords,
                                             const int32_t *conn, const void *u, const void *a, int a_space,
-                                            const void *c, int n_q, const double *qpts, const double *qw,
-                                            void *elem_out, fem_precision prec, fem_stream stream);
+                                            const void *c, double drift, int n_q, const double *qpts,
+                                            const double *qw, void *elem_out, fem_precision prec,
+                                            fem_stream stream);
 
 /* ---------------------------------------------------------------------------------
  * fem_integrate_laplacian_host -- fem_integrate_laplacian for arrays in HOST memory
@@ -199,9 +201,13 @@ fem_status fem_integrate_laplacian_transposed(int dim, int64_t n_cells, const vo
  *   max_iter, rtol       stop when ||r||_2 <= rtol ||r_0||_2 or after max_iter iterations
  *   work       caller-owned device workspace of fem_pcg_work_bytes() bytes, 256-byte aligned
  *   iters_out, resid_out (host, may be NULL) iterations taken and ||r|| / ||r_0||
- * Value arrays are float64 for FEM_FP64 and float32 otherwise; dot products accumulate
- * in float64 in a fixed order (reproducible). Unlike the other entry points this one
- * synchronises `stream` once per iteration to test convergence.
+ * Value arrays are float64 for FEM_FP64 and FEM_FP64_DF (the residual then runs in the
+ * double-float form: float64-class accuracy at float32-pipe speed) and float32 otherwise;
+ * dot products accumulate in float64 in a fixed order (reproducible). The iterations run
+ * on the device as a CUDA graph with a WHILE node (one iteration captured as its body,
+ * the condition set by the body's last kernel), so the host does not wait per iteration;
+ * unlike the other entry points this one returns only after the solve: it synchronises
+ * `stream` twice (initial residual norm, final iteration count).
  * ------------------------------------------------------------------------------- */
 int64_t fem_pcg_work_bytes(int dim, int64_t n_cells, int64_t n_verts, fem_precision prec);
 fem_status fem_pcg_laplacian(int dim, int64_t n_cells, int64_t n_verts, const double *coords,

@@ -54,7 +54,7 @@ def lib():
             "fem_set_mixed_threshold": [cd],
             "fem_device_error": [P],
             "fem_precompute_geometry": [ci, i64, i64, P, P, P, ci, P],
-            "fem_integrate_reaction_diffusion": [ci, i64, i64, P, P, P, P, ci, P, ci, P, P, P, ci, P],
+            "fem_integrate_reaction_diffusion": [ci, i64, i64, P, P, P, P, ci, P, cd, ci, P, P, P, ci, P],
             "fem_element_values": [ci, i64, i64, P, P, P, ci, P],
             "fem_integrate_laplacian_host": [ci, i64, i64, P, P, P, P, ci, P, P, P, P, i64, ci, ci, P],
             "fem_integrate_laplacian_transposed": [ci, i64, P, P, ci, P, P, P, P, ci, ci, ci, P],
@@ -183,10 +183,11 @@ def fem_integrate_elasticity(coords, conn, u, lam, mu, qpts, qw, out=None, prec=
     return out
 
 
-def fem_integrate_reaction_diffusion(coords, conn, u, a, qpts, qw, c=None, a_space=1, out=None, prec="mixed",
-                                     stream=None) -> torch.Tensor:
-    """Element vectors [dim+1][C] of f1 = a grad u, f0 = c u (Eqs. 2 and 8): a is P1 nodal
-    ([V], a_space=1) or P0 ([C], a_space=0); c is [n_q][C] or None."""
+def fem_integrate_reaction_diffusion(coords, conn, u, a, qpts, qw, c=None, a_space=1, drift=0.0, out=None,
+                                     prec="mixed", stream=None) -> torch.Tensor:
+    """Element vectors [dim+1][C] of f1 = a grad u, f0 = c u + drift grad a . grad u (Eqs. 2
+    and 8): a is P1 nodal ([V], a_space=1) or P0 ([C], a_space=0, grad a = 0); c is
+    [n_q][C] or None."""
     p = precision(prec)
     dt = value_dtype(p)
     dim, V, C = _mesh_sizes(coords, conn)
@@ -199,7 +200,7 @@ def fem_integrate_reaction_diffusion(coords, conn, u, a, qpts, qw, c=None, a_spa
     st = lib().fem_integrate_reaction_diffusion(
         dim, C, V, _dev(coords, "coords", torch.float64, device=dev), _dev(conn, "conn", torch.int32, device=dev),
         _dev(u, "u", dt, (V,), dev), _dev(a, "a", dt, (V,) if a_space == 1 else (C,), dev), int(a_space),
-        None if c is None else _dev(c, "c", dt, (nq, C), dev), nq, qp.ptr, w.ptr,
+        None if c is None else _dev(c, "c", dt, (nq, C), dev), float(drift), nq, qp.ptr, w.ptr,
         _dev(out, "out", dt, (dim + 1, C), dev), p, _stream(stream))
     _check("fem_integrate_reaction_diffusion", st)
     return out

@@ -1,15 +1,20 @@
 // fem_reaction.cu -- reaction-diffusion with an auxiliary coefficient field: the full
 // bracket of Eq. 2 (both the f0 and the f1 term) with the pointwise functions of Eq. 8
-// taking an auxiliary field a:
-//     f1(u, grad u, a) = a grad u,   f0(u, a) = c u,
-// a in P1 (nodal values, a(xi_q) = sum_b phi_b(xi_q) a_b) or in P0 (one value per cell),
-// c per quadrature point (optional).
+// taking an auxiliary field a and its gradient:
+//     f1(u, grad u, a) = a grad u,   f0(u, grad u, a, grad a) = c u + g grad a . grad u,
+// a in P1 (nodal values, a(xi_q) = sum_b phi_b(xi_q) a_b) or in P0 (one value per cell,
+// grad a = 0 inside the cell), c per quadrature point (optional), g a scalar (0: none).
 //
 // For P1 the gradients are constant on a cell, so the f1 part is the Laplacian element
 // vector of fem_laplacian.cu with Kbar = sum_q w_q a(xi_q) = sum_b m_b a_b, where
 // m_b = sum_q w_q phi_b(xi_q) (P1 a) or Kbar = a_e sum_q w_q (P0 a). The f0 part uses the
 // basis tabulation phi_b(xi_q) (the matrix B of Eq. 2):
-//     r_b += |det J| sum_q phi_b(xi_q) w_q c_q u(xi_q),  u(xi_q) = sum_a phi_a(xi_q) u_a.
+//     r_b += |det J| sum_q phi_b(xi_q) w_q c_q u(xi_q),  u(xi_q) = sum_a phi_a(xi_q) u_a,
+// and, with grad u = h_u / det J and grad a = h_a / det J (h = sum_j (v_j - v_0) n_j over
+// the adjugate rows n_j), the constant first-order term integrates to
+//     r_b += m_b g (h_a . h_u) / |det J|.
+#include <cmath>
+
 #include "fem_cell.cuh"
 
 namespace fem {
@@ -34,6 +39,8 @@ struct RdArgs {
     int64_t C;
     uint32_t V;
     float tau2;
+    double gd;  // g of the grad a term (P1 a only)
+    float gf;
     QuadW w;
     BasisTab t;
 };
@@ -56,10 +63,12 @@ template <int P> __device__ __forceinline__ val_t<P> rd_weight(const QuadW &w, i
     else return w.wf[q];
 }
 
-// f1 part (Laplacian with Kbar) and f0 part of one cell from its adjugate rows and det J
-template <int DIM, int P, class T, bool REACT>
+// f1 part (Laplacian with Kbar) and f0 part of one cell from its adjugate rows and det J;
+// DRIFT: the grad a term, from the nodal values aa of a P1 coefficient
+template <int DIM, int P, class T, bool REACT, bool DRIFT>
 __device__ __forceinline__ void rd_element(const RdArgs &a, const T (&n)[DIM][DIM], T det, const T (&uu)[DIM + 1],
-                                           T kbar, const T (&cq)[FEM_MAX_QPTS], int nq, T (&r)[DIM + 1]) {
+                                           const T (&aa)[DIM + 1], T kbar, const T (&cq)[FEM_MAX_QPTS], int nq,
+                                           T (&r)[DIM + 1]) {
     constexpr int NB = DIM + 1;
     T h[DIM];
 #pragma unroll
@@ -78,6 +87,21 @@ __device__ __forceinline__ void rd_element(const RdArgs &a, const T (&n)[DIM][DI
         sum = sum + r[j + 1];
     }
     r[0] = -sum;
+    if constexpr (DRIFT) {
+        T ha[DIM];
+#pragma unroll
+        for (int i = 0; i < DIM; ++i) ha[i] = zero<T>();
+#pragma unroll
+        for (int j = 0; j < DIM; ++j) {
+            const T da = aa[j + 1] - aa[0];
+#pragma unroll
+            for (int i = 0; i < DIM; ++i) ha[i] = fma(da, n[j][i], ha[i]);
+        }
+        const T g = P == FEM_FP64 ? T(a.gd) : T(a.gf);
+        const T t = quot_abs(g * dotv<DIM>(ha, h), det);
+#pragma unroll
+        for (int b = 0; b < NB; ++b) r[b] = fma(T(tab_m<P>(a.t, b)), t, r[b]);
+    }
     if constexpr (REACT) {
         const T ad = det < T(0) ? -det : det;
         T m[NB];
@@ -96,9 +120,11 @@ __device__ __forceinline__ void rd_element(const RdArgs &a, const T (&n)[DIM][DI
     }
 }
 
-// One thread per cell (grid-stride). A_P1: the coefficient field is nodal.
-template <int DIM, int P, bool A_P1, bool REACT>
+// One thread per cell (grid-stride). A_P1: the coefficient field is nodal; DRIFT (P1
+// only): the grad a term.
+template <int DIM, int P, bool A_P1, bool REACT, bool DRIFT>
 __global__ void __launch_bounds__(kBlock) rd_kernel(const __grid_constant__ RdArgs a) {
+    static_assert(A_P1 || !DRIFT, "grad a vanishes inside a cell for a P0 field");
     constexpr int NB = DIM + 1;
     using T = val_t<P>;
     const int64_t C = a.C;
@@ -121,11 +147,16 @@ __global__ void __launch_bounds__(kBlock) rd_kernel(const __grid_constant__ RdAr
         }
         // Kbar = sum_q w_q a(xi_q)
         qsum_t<P> ks;
+        T aa[NB];
         if constexpr (A_P1) {
-            ks.first(tab_m<P>(a.t, 0), ld_gather(af + v[0]));
 #pragma unroll
-            for (int b = 1; b < NB; ++b) ks.add(tab_m<P>(a.t, b), ld_gather(af + v[b]));
+            for (int b = 0; b < NB; ++b) aa[b] = ld_gather(af + v[b]);
+            ks.first(tab_m<P>(a.t, 0), aa[0]);
+#pragma unroll
+            for (int b = 1; b < NB; ++b) ks.add(tab_m<P>(a.t, b), aa[b]);
         } else {
+#pragma unroll
+            for (int b = 0; b < NB; ++b) aa[b] = zero<T>();
             ks.first(tab_wsum<P>(a.t), ld_stream(af + e));
         }
         T cq[FEM_MAX_QPTS];
@@ -139,7 +170,7 @@ __global__ void __launch_bounds__(kBlock) rd_kernel(const __grid_constant__ RdAr
             double ee[DIM][DIM], n[DIM][DIM];
             columns_f64<DIM>(xs, ee);
             const double det = adjugate_rows<DIM>(ee, n);
-            rd_element<DIM, P, double, REACT>(a, n, det, uu, ks.value(), cq, nq, r);
+            rd_element<DIM, P, double, REACT, DRIFT>(a, n, det, uu, aa, ks.value(), cq, nq, r);
         } else {
             float ee[DIM][DIM], n[DIM][DIM];
             if constexpr (P == FEM_FP32_MIXED) columns_mixed<DIM>(xs, ee);
@@ -148,18 +179,19 @@ __global__ void __launch_bounds__(kBlock) rd_kernel(const __grid_constant__ RdAr
             bool ok = true;
             if constexpr (P == FEM_FP32_MIXED) ok = shape_ok<DIM>(ee, det, a.tau2);
             if (ok) {
-                rd_element<DIM, P, float, REACT>(a, n, det, uu, ks.value(), cq, nq, r);
+                rd_element<DIM, P, float, REACT, DRIFT>(a, n, det, uu, aa, ks.value(), cq, nq, r);
             } else {
                 // badly shaped cell: float64 geometry and sums, float64 tables
-                double e64[DIM][DIM], n64[DIM][DIM], u64[NB], r64[NB], c64[FEM_MAX_QPTS];
+                double e64[DIM][DIM], n64[DIM][DIM], u64[NB], a64[NB], r64[NB], c64[FEM_MAX_QPTS];
                 columns_f64<DIM>(xs, e64);
                 const double det64 = adjugate_rows<DIM>(e64, n64);
 #pragma unroll
-                for (int b = 0; b < NB; ++b) u64[b] = uu[b];
+                for (int b = 0; b < NB; ++b) u64[b] = uu[b], a64[b] = aa[b];
                 if constexpr (REACT) {
                     for (int q = 0; q < nq; ++q) c64[q] = cq[q];
                 }
-                rd_element<DIM, FEM_FP64, double, REACT>(a, n64, det64, u64, ks.value_f64(), c64, nq, r64);
+                rd_element<DIM, FEM_FP64, double, REACT, DRIFT>(a, n64, det64, u64, a64, ks.value_f64(), c64, nq,
+                                                                r64);
 #pragma unroll
                 for (int b = 0; b < NB; ++b) r[b] = static_cast<float>(r64[b]);
             }
@@ -169,18 +201,20 @@ __global__ void __launch_bounds__(kBlock) rd_kernel(const __grid_constant__ RdAr
     }
 }
 
+template <int DIM, int P, bool A_P1, bool REACT, bool DRIFT>
+static void launch_rd_one(const RdArgs &a, cudaStream_t s) {
+    auto k = rd_kernel<DIM, P, A_P1, REACT, DRIFT>;
+    k<<<grid_for(a.C, kBlock, reinterpret_cast<const void *>(k)), kBlock, 0, s>>>(a);
+}
+
 template <int DIM, int P>
-static fem_status launch_rd(const RdArgs &a, bool a_p1, bool react, cudaStream_t s) {
-    const void *k;
-    if (a_p1) k = react ? reinterpret_cast<const void *>(rd_kernel<DIM, P, true, true>)
-                        : reinterpret_cast<const void *>(rd_kernel<DIM, P, true, false>);
-    else k = react ? reinterpret_cast<const void *>(rd_kernel<DIM, P, false, true>)
-                   : reinterpret_cast<const void *>(rd_kernel<DIM, P, false, false>);
-    const int grid = grid_for(a.C, kBlock, k);
-    if (a_p1 && react) rd_kernel<DIM, P, true, true><<<grid, kBlock, 0, s>>>(a);
-    else if (a_p1) rd_kernel<DIM, P, true, false><<<grid, kBlock, 0, s>>>(a);
-    else if (react) rd_kernel<DIM, P, false, true><<<grid, kBlock, 0, s>>>(a);
-    else rd_kernel<DIM, P, false, false><<<grid, kBlock, 0, s>>>(a);
+static fem_status launch_rd(const RdArgs &a, bool a_p1, bool react, bool drift, cudaStream_t s) {
+    if (a_p1) {
+        if (drift) react ? launch_rd_one<DIM, P, true, true, true>(a, s) : launch_rd_one<DIM, P, true, false, true>(a, s);
+        else react ? launch_rd_one<DIM, P, true, true, false>(a, s) : launch_rd_one<DIM, P, true, false, false>(a, s);
+    } else {
+        react ? launch_rd_one<DIM, P, false, true, false>(a, s) : launch_rd_one<DIM, P, false, false, false>(a, s);
+    }
     return check_launch("fem_integrate_reaction_diffusion");
 }
 
@@ -190,7 +224,8 @@ using namespace fem;
 
 extern "C" fem_status fem_integrate_reaction_diffusion(int dim, int64_t n_cells, int64_t n_verts, const double *coords,
                                                        const int32_t *conn, const void *u, const void *a,
-                                                       int a_space, const void *c, int n_q, const double *qpts,
+                                                       int a_space, const void *c, double drift, int n_q,
+                                                       const double *qpts,
                                                        const double *qw, void *elem_out, fem_precision prec,
                                                        fem_stream stream) {
     fem_status st = check_common(dim, n_cells, n_verts, coords, conn);
@@ -198,6 +233,7 @@ extern "C" fem_status fem_integrate_reaction_diffusion(int dim, int64_t n_cells,
     if (prec != FEM_FP64 && prec != FEM_FP32_MIXED && prec != FEM_FP32)
         return fail(FEM_ERR_ARG, "unknown precision %d", static_cast<int>(prec));
     if (a_space != 0 && a_space != 1) return fail(FEM_ERR_ARG, "a_space = %d, must be 0 (P0) or 1 (P1)", a_space);
+    if (!std::isfinite(drift)) return fail(FEM_ERR_ARG, "drift must be finite");
     if (!qpts) return fail(FEM_ERR_ARG, "qpts is required: the f0 term and a P1 coefficient use phi_b(xi_q)");
     RdArgs r;
     if ((st = load_quadrature(dim, n_q, qpts, qw, r.w)) != FEM_OK) return st;
@@ -230,14 +266,17 @@ extern "C" fem_status fem_integrate_reaction_diffusion(int dim, int64_t n_cells,
     r.V = static_cast<uint32_t>(n_verts);
     const float tau = mixed_tau();
     r.tau2 = tau * tau;
-    const bool p1 = a_space == 1, react = c != nullptr;
+    r.gd = drift;
+    r.gf = static_cast<float>(drift);
+    // grad a vanishes inside a cell for a P0 field: the term is then absent
+    const bool p1 = a_space == 1, react = c != nullptr, with_drift = p1 && drift != 0.0;
     switch (dim * 10 + static_cast<int>(prec)) {
-        case 20: return launch_rd<2, FEM_FP64>(r, p1, react, stream);
-        case 21: return launch_rd<2, FEM_FP32_MIXED>(r, p1, react, stream);
-        case 22: return launch_rd<2, FEM_FP32>(r, p1, react, stream);
-        case 30: return launch_rd<3, FEM_FP64>(r, p1, react, stream);
-        case 31: return launch_rd<3, FEM_FP32_MIXED>(r, p1, react, stream);
-        case 32: return launch_rd<3, FEM_FP32>(r, p1, react, stream);
+        case 20: return launch_rd<2, FEM_FP64>(r, p1, react, with_drift, stream);
+        case 21: return launch_rd<2, FEM_FP32_MIXED>(r, p1, react, with_drift, stream);
+        case 22: return launch_rd<2, FEM_FP32>(r, p1, react, with_drift, stream);
+        case 30: return launch_rd<3, FEM_FP64>(r, p1, react, with_drift, stream);
+        case 31: return launch_rd<3, FEM_FP32_MIXED>(r, p1, react, with_drift, stream);
+        case 32: return launch_rd<3, FEM_FP32>(r, p1, react, with_drift, stream);
     }
     return fail(FEM_ERR_ARG, "unsupported dim/precision");
 }

@@ -5,10 +5,14 @@
 //
 // Kernels here: the assembled diagonal (element diagonals A_bb = Kbar |n_b|^2 / |det J|,
 // summed per vertex), a deterministic two-level dot product, and the vector updates of
-// CG with their scalars read from device memory. The iteration itself is driven from the
-// host, which reads the residual norm after every iteration to test convergence.
+// CG with their scalars read from device memory. The iteration loop runs on the device:
+// one CG iteration is captured once into the body of a CUDA graph WHILE node, and the
+// last kernel of the body counts the iteration and sets the loop condition (not
+// converged and fewer than max_iter iterations). The host synchronises twice per solve
+// (the initial residual norm, the final count) instead of once per iteration.
 #include <cmath>
 #include <cstring>
+#include <mutex>
 
 #include "fem_cell.cuh"
 
@@ -81,8 +85,8 @@ __global__ void __launch_bounds__(256) dot_final_kernel(const double *partial, d
     if (threadIdx.x == 0) *result = s[0];
 }
 
-// scalars[] layout: 0 rz, 1 pq, 2 rz_new, 3 rr
-enum { S_RZ = 0, S_PQ = 1, S_RZNEW = 2, S_RR = 3, S_COUNT = 4 };
+// scalars[] layout: 0 rz, 1 pq, 2 rz_new, 3 rr, 4 (rtol ||r_0||)^2, 5 iterations done
+enum { S_RZ = 0, S_PQ = 1, S_RZNEW = 2, S_RR = 3, S_TOL2 = 4, S_ITER = 5, S_COUNT = 6 };
 
 // r = b - Ax (free vertices), 0 on fixed ones; z = r / D; p = z
 template <class T>
@@ -128,6 +132,36 @@ __global__ void cg_dir_kernel(int64_t V, const double *sc, const T *z, T *p) {
 
 __global__ void copy_scalar_kernel(double *sc, int dst, int src) { sc[dst] = sc[src]; }
 
+__global__ void loop_init_kernel(double *sc, double tol2) {
+    sc[S_TOL2] = tol2;
+    sc[S_ITER] = 0.0;
+}
+
+// last kernel of the loop body: count the iteration and set the WHILE condition; the
+// count bounds the loop, and a NaN residual ends it too (every comparison is false)
+__global__ void cg_continue_kernel(double *sc, int max_iter, cudaGraphConditionalHandle loop) {
+    const double it = sc[S_ITER] + 1.0;
+    sc[S_ITER] = it;
+    const double rr = sc[S_RR];
+    const bool more = it < static_cast<double>(max_iter) && rr > sc[S_TOL2] && rr > 0.0;
+    cudaGraphSetConditional(loop, more ? 1u : 0u);
+}
+
+// a library stream per device to capture the loop body on (capture needs a stream other
+// than the legacy default one, which callers may pass)
+static cudaStream_t capture_stream() {
+    static std::mutex mu;
+    static cudaStream_t per_dev[64] = {nullptr};
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return nullptr;
+    std::lock_guard<std::mutex> lk(mu);
+    if (!per_dev[dev] && cudaStreamCreateWithFlags(&per_dev[dev], cudaStreamNonBlocking) != cudaSuccess) {
+        cudaGetLastError();
+        per_dev[dev] = nullptr;
+    }
+    return per_dev[dev];
+}
+
 // fixed vertices get D = 1 (their rows are the identity)
 template <class T>
 __global__ void diag_fix_kernel(int64_t V, const uint8_t *fixed, T *D) {
@@ -165,6 +199,9 @@ static fem_status pcg_run(int dim, int64_t C, int64_t V, const double *coords, c
                           int n_q, const double *qpts, const double *qw, const int32_t *ptr, const int32_t *idx,
                           const uint8_t *fixed, const void *b, void *x, int max_iter, double rtol, const Workspace &w,
                           int *iters_out, double *resid_out, fem_precision prec, cudaStream_t s) {
+    // the residual runs in `prec`; every other kernel sees the value type (FEM_FP64_DF
+    // values are float64)
+    const fem_precision vprec = prec == FEM_FP64_DF ? FEM_FP64 : prec;
     T *X = static_cast<T *>(x);
     T *D = static_cast<T *>(w.D), *r = static_cast<T *>(w.r), *z = static_cast<T *>(w.z);
     T *p = static_cast<T *>(w.p), *q = static_cast<T *>(w.q);
@@ -182,47 +219,84 @@ static fem_status pcg_run(int dim, int64_t C, int64_t V, const double *coords, c
         else lap_diag_kernel<3, T><<<g, 256, 0, s>>>(coords, C, static_cast<uint32_t>(V), conn,
                                                        static_cast<const T *>(K), n_q, qwt, static_cast<T *>(w.elem));
         if ((st = check_launch("fem_pcg_laplacian diagonal")) != FEM_OK) return st;
-        if ((st = launch_gather(dim, 1, C, V, w.elem, ptr, idx, D, prec, s)) != FEM_OK) return st;
+        if ((st = launch_gather(dim, 1, C, V, w.elem, ptr, idx, D, vprec, s)) != FEM_OK) return st;
         diag_fix_kernel<T><<<gV, 256, 0, s>>>(V, fixed, D);
     }
-    auto matvec = [&](const T *v, T *out) -> fem_status {
-        fem_status e = fem_integrate_laplacian(dim, C, V, coords, conn, v, K, n_q, qpts, qw, w.elem, prec, s);
+    auto matvec = [&](const T *v, T *out, cudaStream_t cs) -> fem_status {
+        fem_status e = fem_integrate_laplacian(dim, C, V, coords, conn, v, K, n_q, qpts, qw, w.elem, prec, cs);
         if (e != FEM_OK) return e;
-        return launch_gather(dim, 1, C, V, w.elem, ptr, idx, out, prec, s);
+        return launch_gather(dim, 1, C, V, w.elem, ptr, idx, out, vprec, cs);
     };
-    auto dot = [&](const T *a, const T *c, int slot) {
-        dot_partial_kernel<T><<<kDotBlocks, 256, 0, s>>>(V, a, c, w.partial);
-        dot_final_kernel<<<1, 256, 0, s>>>(w.partial, w.scalars + slot);
+    auto dot = [&](const T *a, const T *c, int slot, cudaStream_t cs) {
+        dot_partial_kernel<T><<<kDotBlocks, 256, 0, cs>>>(V, a, c, w.partial);
+        dot_final_kernel<<<1, 256, 0, cs>>>(w.partial, w.scalars + slot);
     };
-    auto read = [&](int slot, double &v) -> fem_status {
-        cudaError_t e = cudaMemcpyAsync(&v, w.scalars + slot, sizeof(double), cudaMemcpyDeviceToHost, s);
+    auto read = [&](int slot, int n, double *v) -> fem_status {
+        cudaError_t e = cudaMemcpyAsync(v, w.scalars + slot, n * sizeof(double), cudaMemcpyDeviceToHost, s);
         if (e == cudaSuccess) e = cudaStreamSynchronize(s);
         if (e != cudaSuccess) return fail(FEM_ERR_CUDA, "fem_pcg_laplacian: %s", cudaGetErrorString(e));
         return FEM_OK;
     };
     // r0 = b - A x0 on the free vertices
-    if ((st = matvec(X, q)) != FEM_OK) return st;
+    if ((st = matvec(X, q, s)) != FEM_OK) return st;
     cg_init_kernel<T><<<gV, 256, 0, s>>>(V, B, q, D, fixed, r, z, p);
-    dot(r, z, S_RZ);
-    dot(r, r, S_RR);
+    dot(r, z, S_RZ, s);
+    dot(r, r, S_RR, s);
     double rr0 = 0.0;
-    if ((st = read(S_RR, rr0)) != FEM_OK) return st;
+    if ((st = read(S_RR, 1, &rr0)) != FEM_OK) return st;
     const double r0 = std::sqrt(rr0);
     double rn = r0;
     int it = 0;
-    while (it < max_iter && rn > rtol * r0 && rn > 0.0) {
-        if ((st = matvec(p, q)) != FEM_OK) return st;
-        mask_kernel<T><<<gV, 256, 0, s>>>(V, fixed, q);
-        dot(p, q, S_PQ);
-        cg_step_kernel<T><<<gV, 256, 0, s>>>(V, w.scalars, p, q, D, X, r, z);
-        dot(r, z, S_RZNEW);
-        cg_dir_kernel<T><<<gV, 256, 0, s>>>(V, w.scalars, z, p);
-        copy_scalar_kernel<<<1, 1, 0, s>>>(w.scalars, S_RZ, S_RZNEW);
-        dot(r, r, S_RR);
-        double rr = 0.0;
-        if ((st = read(S_RR, rr)) != FEM_OK) return st;
-        rn = std::sqrt(rr);
-        ++it;
+    if (max_iter > 0 && rn > rtol * r0 && rn > 0.0) {
+        const double tol = rtol * r0;
+        loop_init_kernel<<<1, 1, 0, s>>>(w.scalars, tol * tol);
+        // the loop: a graph holding one WHILE node whose body is one CG iteration
+        cudaStream_t cs = capture_stream();
+        if (!cs) return fail(FEM_ERR_CUDA, "fem_pcg_laplacian: no capture stream");
+        cudaGraph_t graph = nullptr;
+        cudaGraphExec_t exec = nullptr;
+        cudaGraphConditionalHandle loop = 0;
+        cudaError_t e = cudaGraphCreate(&graph, 0);
+        if (e == cudaSuccess) e = cudaGraphConditionalHandleCreate(&loop, graph, 1u, cudaGraphCondAssignDefault);
+        cudaGraphNodeParams np = {cudaGraphNodeTypeConditional};
+        np.conditional.handle = loop;
+        np.conditional.type = cudaGraphCondTypeWhile;
+        np.conditional.size = 1;
+        cudaGraphNode_t node = nullptr;
+        if (e == cudaSuccess) e = cudaGraphAddNode(&node, graph, nullptr, nullptr, 0, &np);
+        if (e == cudaSuccess)
+            e = cudaStreamBeginCaptureToGraph(cs, np.conditional.phGraph_out[0], nullptr, nullptr, 0,
+                                              cudaStreamCaptureModeThreadLocal);
+        if (e == cudaSuccess) {
+            st = matvec(p, q, cs);
+            if (st == FEM_OK) {
+                mask_kernel<T><<<gV, 256, 0, cs>>>(V, fixed, q);
+                dot(p, q, S_PQ, cs);
+                cg_step_kernel<T><<<gV, 256, 0, cs>>>(V, w.scalars, p, q, D, X, r, z);
+                dot(r, z, S_RZNEW, cs);
+                cg_dir_kernel<T><<<gV, 256, 0, cs>>>(V, w.scalars, z, p);
+                copy_scalar_kernel<<<1, 1, 0, cs>>>(w.scalars, S_RZ, S_RZNEW);
+                dot(r, r, S_RR, cs);
+                cg_continue_kernel<<<1, 1, 0, cs>>>(w.scalars, max_iter, loop);
+            }
+            cudaGraph_t body = nullptr;
+            const cudaError_t e2 = cudaStreamEndCapture(cs, &body);
+            if (e2 != cudaSuccess) e = e2;
+        }
+        if (e == cudaSuccess && st == FEM_OK) e = cudaGraphInstantiate(&exec, graph, 0);
+        if (e == cudaSuccess && st == FEM_OK) e = cudaGraphLaunch(exec, s);
+        if (e == cudaSuccess && st == FEM_OK) e = cudaStreamSynchronize(s);
+        if (exec) cudaGraphExecDestroy(exec);
+        if (graph) cudaGraphDestroy(graph);
+        if (st != FEM_OK) return st;
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            return fail(FEM_ERR_CUDA, "fem_pcg_laplacian (iteration graph): %s", cudaGetErrorString(e));
+        }
+        double tail[3];  // rr, tol^2, iterations
+        if ((st = read(S_RR, 3, tail)) != FEM_OK) return st;
+        rn = std::sqrt(tail[0]);
+        it = static_cast<int>(tail[2]);
     }
     if ((st = check_launch("fem_pcg_laplacian")) != FEM_OK) return st;
     if (iters_out) *iters_out = it;
@@ -236,7 +310,8 @@ using namespace fem;
 
 extern "C" int64_t fem_pcg_work_bytes(int dim, int64_t n_cells, int64_t n_verts, fem_precision prec) {
     if ((dim != 2 && dim != 3) || n_cells < 0 || n_verts < 0) return -1;
-    return static_cast<int64_t>(carve(n_cells, n_verts, dim, prec == FEM_FP64 ? 8 : 4, nullptr, nullptr));
+    const size_t vs = prec == FEM_FP64 || prec == FEM_FP64_DF ? 8 : 4;
+    return static_cast<int64_t>(carve(n_cells, n_verts, dim, vs, nullptr, nullptr));
 }
 
 extern "C" fem_status fem_pcg_laplacian(int dim, int64_t n_cells, int64_t n_verts, const double *coords,
@@ -247,7 +322,7 @@ extern "C" fem_status fem_pcg_laplacian(int dim, int64_t n_cells, int64_t n_vert
                                         fem_precision prec, fem_stream stream) {
     fem_status st = check_common(dim, n_cells, n_verts, coords, conn);
     if (st != FEM_OK) return st;
-    if (prec != FEM_FP64 && prec != FEM_FP32_MIXED && prec != FEM_FP32)
+    if (prec != FEM_FP64 && prec != FEM_FP32_MIXED && prec != FEM_FP32 && prec != FEM_FP64_DF)
         return fail(FEM_ERR_ARG, "unknown precision %d", static_cast<int>(prec));
     if (max_iter < 0 || !(rtol >= 0.0)) return fail(FEM_ERR_ARG, "max_iter must be >= 0 and rtol >= 0");
     if (n_verts == 0) {
@@ -262,8 +337,9 @@ extern "C" fem_status fem_pcg_laplacian(int dim, int64_t n_cells, int64_t n_vert
                     static_cast<long long>(work_bytes), static_cast<long long>(need));
     if (reinterpret_cast<uintptr_t>(work) & 255u) return fail(FEM_ERR_ARG, "work must be 256-byte aligned");
     Workspace w;
-    carve(n_cells, n_verts, dim, prec == FEM_FP64 ? 8 : 4, work, &w);
-    if (prec == FEM_FP64)
+    const bool f64 = prec == FEM_FP64 || prec == FEM_FP64_DF;
+    carve(n_cells, n_verts, dim, f64 ? 8 : 4, work, &w);
+    if (f64)
         return pcg_run<double>(dim, n_cells, n_verts, coords, conn, K, n_q, qpts, qw, node_ptr, node_idx, fixed, b, x,
                                max_iter, rtol, w, iters_out, resid_out, prec, stream);
     return pcg_run<float>(dim, n_cells, n_verts, coords, conn, K, n_q, qpts, qw, node_ptr, node_idx, fixed, b, x,

@@ -61,18 +61,18 @@ def test_patch_test_linear_solution(dim, n):
 
 
 @pytest.mark.parametrize("dim,n", [(2, 12), (3, 4)])
-@pytest.mark.parametrize("prec,rtol,tol", [("fp64", 1e-12, 1e-9), ("mixed", 1e-5, 1e-4)])
+@pytest.mark.parametrize("prec,rtol,tol", [("fp64", 1e-12, 1e-9), ("fp64_df", 1e-12, 1e-9), ("mixed", 1e-5, 1e-4)])
 def test_matches_dense_solve_of_oracle_operator(dim, n, prec, rtol, tol):
     mesh = _mesh(dim, n)
     rule = workloads.rule_for_dim(dim)
     rng = np.random.default_rng(dim)
     K = rng.lognormal(0.0, 1.0, (rule.n_q, mesh.n_cells))
-    if prec != "fp64":
+    if prec == "mixed":
         K = K.astype(np.float32).astype(np.float64)
     fixed = _boundary(mesh)
     g = np.sin(mesh.coords[0] * 3.0) + mesh.coords[1]
     b = np.where(fixed, 0.0, rng.uniform(-1, 1, mesh.n_verts) / mesh.n_verts)
-    if prec != "fp64":
+    if prec == "mixed":
         b = b.astype(np.float32).astype(np.float64)
         g = g.astype(np.float32).astype(np.float64)
     x0 = np.where(fixed, g, 0.0)
@@ -108,3 +108,20 @@ def test_workspace_too_small_is_rejected():
     with pytest.raises(fem.FemError):
         fem.fem_pcg_laplacian(coords, conn, K, rule.points, rule.weights, ptr, idx, fixed, x,
                               work=torch.empty(16, dtype=torch.uint8, device="cuda"), prec="fp64")
+
+
+def test_double_float_residual_solves_like_float64():
+    """The solve with the double-float residual (float64 values, 4e-14 residual error)
+    takes the float64 solve's path: same iteration count to within a few, same solution
+    to 1e-10 on the 3D workload mesh's first 24^3 x 6 cells."""
+    mesh = _mesh(3, 24)
+    rule = workloads.rule_for_dim(3)
+    K = np.random.default_rng(5).lognormal(0.0, 1.0, (rule.n_q, mesh.n_cells))
+    fixed = _boundary(mesh)
+    x0 = np.where(fixed, 1.0 + 2.0 * mesh.coords[0] - 3.0 * mesh.coords[1], 0.0)
+    x64, it64, r64 = _solve(mesh, K, rule, fixed, x0, None, "fp64", 1e-10)
+    xdf, itdf, rdf = _solve(mesh, K, rule, fixed, x0, None, "fp64_df", 1e-10)
+    assert r64 <= 1e-10 and rdf <= 1e-10
+    assert abs(it64 - itdf) <= 3, (it64, itdf)
+    a, b = x64.cpu().numpy(), xdf.cpu().numpy()
+    assert np.abs(a - b).max() <= 1e-10 * np.abs(a).max()

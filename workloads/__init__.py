@@ -19,9 +19,13 @@ from .cases import (
     elasticity_case,
     adjoint_case,
     lame_from_young_poisson,
+    reaction_inputs,
+    dirichlet_problem,
 )
 
 __all__ = [
+    "reaction_inputs",
+    "dirichlet_problem",
     "Mesh",
     "square_mesh",
     "cube_mesh",

@@ -16,6 +16,11 @@ Recipes (sizes are parameters; the defaults are the full workloads):
                          displacements N(0, sigma = 1e-2) per component.
   adjoint_case           the 3D Laplacian case plus an adjoint weight per element dof,
                          U[-1, 1], shape (d+1, C).
+  reaction_inputs        for a case: an auxiliary P1 field a ~ lognormal(0, 0.5) per vertex
+                         and a reaction coefficient c ~ U[0.5, 2] per quadrature point.
+  dirichlet_problem      for a case: boundary vertices of the unit square/cube held at the
+                         linear function g(x) = 1 + 2 x_1 - 3 x_2 (+ 0.5 x_3), zero initial
+                         guess inside.
 
 Random streams: numpy's Philox generator, one independent stream per array, all
 derived from one integer seed, so every consumer sees identical arrays.
@@ -194,3 +199,22 @@ def serving_case(spec) -> Case:
         case.adj = s_adj.uniform(-1.0, 1.0, size=(case.dim + 1, case.n_cells))
     case.name = f"req{spec['rid']}_{spec['physics']}{dim}d_{spec['kind']}_{C}"
     return case
+
+
+def reaction_inputs(case: Case, seed: int = 0):
+    """(a, c): a P1 auxiliary field a[V] ~ lognormal(0, 0.5) and a reaction coefficient
+    c[n_q][C] ~ U[0.5, 2] for the case's mesh and rule."""
+    s_a, s_c = _streams(seed + 104729, 2)
+    a = s_a.lognormal(0.0, 0.5, size=case.n_verts)
+    c = s_c.uniform(0.5, 2.0, size=(case.rule.n_q, case.n_cells))
+    return a, c
+
+
+def dirichlet_problem(case: Case):
+    """(fixed, x0): the vertices on the boundary of the unit square/cube (uint8 mask) and
+    an initial vector holding g(x) = 1 + 2 x_1 - 3 x_2 (+ 0.5 x_3) there and 0 inside."""
+    x = case.mesh.coords
+    fixed = np.any((np.abs(x) < 1e-14) | (np.abs(x - 1.0) < 1e-14), axis=0)
+    coef = np.array([2.0, -3.0, 0.5])[: case.dim]
+    g = 1.0 + coef @ x
+    return fixed.astype(np.uint8), np.where(fixed, g, 0.0)
