@@ -65,9 +65,9 @@ template <int P> __device__ __forceinline__ val_t<P> rd_weight(const QuadW &w, i
 
 // f1 part (Laplacian with Kbar) and f0 part of one cell from its adjugate rows and det J;
 // DRIFT: the grad a term, from the nodal values aa of a P1 coefficient
-template <int DIM, int P, class T, bool REACT, bool DRIFT>
+template <int DIM, int P, class T, bool REACT, bool DRIFT, int NQA>
 __device__ __forceinline__ void rd_element(const RdArgs &a, const T (&n)[DIM][DIM], T det, const T (&uu)[DIM + 1],
-                                           const T (&aa)[DIM + 1], T kbar, const T (&cq)[FEM_MAX_QPTS], int nq,
+                                           const T (&aa)[DIM + 1], T kbar, const T (&cq)[NQA], int nq,
                                            T (&r)[DIM + 1]) {
     constexpr int NB = DIM + 1;
     T h[DIM];
@@ -120,15 +120,20 @@ __device__ __forceinline__ void rd_element(const RdArgs &a, const T (&n)[DIM][DI
     }
 }
 
-// One thread per cell (grid-stride). A_P1: the coefficient field is nodal; DRIFT (P1
-// only): the grad a term.
-template <int DIM, int P, bool A_P1, bool REACT, bool DRIFT>
+// Grid-stride over groups of CPT consecutive cells. A_P1: the coefficient field is nodal;
+// DRIFT (P1 only): the grad a term. CPT = 4 with NQ > 0 (the quadrature size fixed at
+// compile time) reads the connectivity, reaction and P0 coefficient rows and writes the
+// element vectors with 16-byte vector accesses; CPT = 1, NQ = 0 is the general form
+// (any n_q, unaligned rows, ragged sizes).
+template <int DIM, int P, bool A_P1, bool REACT, bool DRIFT, int CPT, int NQ>
 __global__ void __launch_bounds__(kBlock) rd_kernel(const __grid_constant__ RdArgs a) {
     static_assert(A_P1 || !DRIFT, "grad a vanishes inside a cell for a P0 field");
+    static_assert(CPT == 1 || NQ > 0, "vector rows need a compile-time quadrature size");
     constexpr int NB = DIM + 1;
+    constexpr int NQA = NQ > 0 ? NQ : FEM_MAX_QPTS;  // reaction values held per cell
     using T = val_t<P>;
     const int64_t C = a.C;
-    const int nq = a.w.nq;
+    const int nq = NQ > 0 ? NQ : a.w.nq;
     const T *__restrict__ u = static_cast<const T *>(a.u);
     const T *__restrict__ af = static_cast<const T *>(a.a);
     const T *__restrict__ cf = static_cast<const T *>(a.c);
@@ -136,84 +141,112 @@ __global__ void __launch_bounds__(kBlock) rd_kernel(const __grid_constant__ RdAr
     const double *X[DIM];
 #pragma unroll
     for (int k = 0; k < DIM; ++k) X[k] = a.X[k];
+    const int64_t ngroups = (C + CPT - 1) / CPT;
     const int64_t stride = int64_t(gridDim.x) * blockDim.x;
-    for (int64_t e = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; e < C; e += stride) {
-        uint32_t v[NB];
-        T uu[NB];
+    for (int64_t g = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; g < ngroups; g += stride) {
+        const int64_t c0 = g * CPT;
+        int32_t vid[NB][CPT];
 #pragma unroll
-        for (int b = 0; b < NB; ++b) {
-            v[b] = clamp_vid(ld_stream(a.conn + b * C + e), a.V);
-            uu[b] = ld_gather(u + v[b]);
-        }
-        // Kbar = sum_q w_q a(xi_q)
-        qsum_t<P> ks;
-        T aa[NB];
-        if constexpr (A_P1) {
-#pragma unroll
-            for (int b = 0; b < NB; ++b) aa[b] = ld_gather(af + v[b]);
-            ks.first(tab_m<P>(a.t, 0), aa[0]);
-#pragma unroll
-            for (int b = 1; b < NB; ++b) ks.add(tab_m<P>(a.t, b), aa[b]);
-        } else {
-#pragma unroll
-            for (int b = 0; b < NB; ++b) aa[b] = zero<T>();
-            ks.first(tab_wsum<P>(a.t), ld_stream(af + e));
-        }
-        T cq[FEM_MAX_QPTS];
+        for (int b = 0; b < NB; ++b) load_row<CPT>(a.conn + b * C + c0, vid[b]);
+        T a0[CPT];
+        if constexpr (!A_P1) load_row<CPT>(af + c0, a0);
+        T cq[REACT ? NQA : 1][CPT];
         if constexpr (REACT) {
-            for (int q = 0; q < nq; ++q) cq[q] = ld_stream(cf + q * C + e);
+#pragma unroll(NQ > 0 ? NQ : 1)
+            for (int q = 0; q < nq; ++q) load_row<CPT>(cf + q * C + c0, cq[q]);
         }
-        double xs[NB][DIM];
-        gather_coords<DIM>(X, v, xs);
-        T r[NB];
-        if constexpr (P == FEM_FP64) {
-            double ee[DIM][DIM], n[DIM][DIM];
-            columns_f64<DIM>(xs, ee);
-            const double det = adjugate_rows<DIM>(ee, n);
-            rd_element<DIM, P, double, REACT, DRIFT>(a, n, det, uu, aa, ks.value(), cq, nq, r);
-        } else {
-            float ee[DIM][DIM], n[DIM][DIM];
-            if constexpr (P == FEM_FP32_MIXED) columns_mixed<DIM>(xs, ee);
-            else columns_f32<DIM>(xs, ee);
-            const float det = adjugate_rows<DIM>(ee, n);
-            bool ok = true;
-            if constexpr (P == FEM_FP32_MIXED) ok = shape_ok<DIM>(ee, det, a.tau2);
-            if (ok) {
-                rd_element<DIM, P, float, REACT, DRIFT>(a, n, det, uu, aa, ks.value(), cq, nq, r);
-            } else {
-                // badly shaped cell: float64 geometry and sums, float64 tables
-                double e64[DIM][DIM], n64[DIM][DIM], u64[NB], a64[NB], r64[NB], c64[FEM_MAX_QPTS];
-                columns_f64<DIM>(xs, e64);
-                const double det64 = adjugate_rows<DIM>(e64, n64);
+        T r[NB][CPT];
 #pragma unroll
-                for (int b = 0; b < NB; ++b) u64[b] = uu[b], a64[b] = aa[b];
-                if constexpr (REACT) {
-                    for (int q = 0; q < nq; ++q) c64[q] = cq[q];
-                }
-                rd_element<DIM, FEM_FP64, double, REACT, DRIFT>(a, n64, det64, u64, a64, ks.value_f64(), c64, nq,
-                                                                r64);
+        for (int i = 0; i < CPT; ++i) {
+            uint32_t v[NB];
+            T uu[NB], aa[NB];
 #pragma unroll
-                for (int b = 0; b < NB; ++b) r[b] = static_cast<float>(r64[b]);
+            for (int b = 0; b < NB; ++b) {
+                v[b] = clamp_vid(vid[b][i], a.V);
+                uu[b] = ld_gather(u + v[b]);
             }
+            // Kbar = sum_q w_q a(xi_q)
+            qsum_t<P> ks;
+            if constexpr (A_P1) {
+#pragma unroll
+                for (int b = 0; b < NB; ++b) aa[b] = ld_gather(af + v[b]);
+                ks.first(tab_m<P>(a.t, 0), aa[0]);
+#pragma unroll
+                for (int b = 1; b < NB; ++b) ks.add(tab_m<P>(a.t, b), aa[b]);
+            } else {
+#pragma unroll
+                for (int b = 0; b < NB; ++b) aa[b] = zero<T>();
+                ks.first(tab_wsum<P>(a.t), a0[i]);
+            }
+            T ci[NQA];
+            if constexpr (REACT) {
+#pragma unroll(NQ > 0 ? NQ : 1)
+                for (int q = 0; q < nq; ++q) ci[q] = cq[q][i];
+            }
+            double xs[NB][DIM];
+            gather_coords<DIM>(X, v, xs);
+            T rr[NB];
+            if constexpr (P == FEM_FP64) {
+                double ee[DIM][DIM], n[DIM][DIM];
+                columns_f64<DIM>(xs, ee);
+                const double det = adjugate_rows<DIM>(ee, n);
+                rd_element<DIM, P, double, REACT, DRIFT, NQA>(a, n, det, uu, aa, ks.value(), ci, nq, rr);
+            } else {
+                float ee[DIM][DIM], n[DIM][DIM];
+                if constexpr (P == FEM_FP32_MIXED) columns_mixed<DIM>(xs, ee);
+                else columns_f32<DIM>(xs, ee);
+                const float det = adjugate_rows<DIM>(ee, n);
+                bool ok = true;
+                if constexpr (P == FEM_FP32_MIXED) ok = shape_ok<DIM>(ee, det, a.tau2);
+                if (ok) {
+                    rd_element<DIM, P, float, REACT, DRIFT, NQA>(a, n, det, uu, aa, ks.value(), ci, nq, rr);
+                } else {
+                    // badly shaped cell: float64 geometry and sums, float64 tables
+                    double e64[DIM][DIM], n64[DIM][DIM], u64[NB], a64[NB], r64[NB], c64[NQA];
+                    columns_f64<DIM>(xs, e64);
+                    const double det64 = adjugate_rows<DIM>(e64, n64);
+#pragma unroll
+                    for (int b = 0; b < NB; ++b) u64[b] = uu[b], a64[b] = aa[b];
+                    if constexpr (REACT) {
+                        for (int q = 0; q < nq; ++q) c64[q] = ci[q];
+                    }
+                    rd_element<DIM, FEM_FP64, double, REACT, DRIFT, NQA>(a, n64, det64, u64, a64, ks.value_f64(),
+                                                                        c64, nq, r64);
+#pragma unroll
+                    for (int b = 0; b < NB; ++b) rr[b] = static_cast<float>(r64[b]);
+                }
+            }
+#pragma unroll
+            for (int b = 0; b < NB; ++b) r[b][i] = rr[b];
         }
 #pragma unroll
-        for (int b = 0; b < NB; ++b) __stcs(out + b * C + e, r[b]);
+        for (int b = 0; b < NB; ++b) store_row<CPT>(out + b * C + c0, r[b]);
     }
 }
 
 template <int DIM, int P, bool A_P1, bool REACT, bool DRIFT>
-static void launch_rd_one(const RdArgs &a, cudaStream_t s) {
-    auto k = rd_kernel<DIM, P, A_P1, REACT, DRIFT>;
-    k<<<grid_for(a.C, kBlock, reinterpret_cast<const void *>(k)), kBlock, 0, s>>>(a);
+static void launch_rd_one(const RdArgs &a, bool vec, cudaStream_t s) {
+    constexpr int NQN = DIM + 1 == 4 ? 4 : 3;  // the workloads' rules: 3 points in 2D, 4 in 3D
+    // the float64 form is bound by the float64 pipe; four cells per thread only cost it
+    // occupancy (457 against 416 us on the 1,572,864-tet workload)
+    if (P != FEM_FP64 && vec && a.w.nq == NQN) {
+        auto k = rd_kernel<DIM, P, A_P1, REACT, DRIFT, 4, NQN>;
+        k<<<grid_for((a.C + 3) / 4, kBlock, reinterpret_cast<const void *>(k)), kBlock, 0, s>>>(a);
+    } else {
+        auto k = rd_kernel<DIM, P, A_P1, REACT, DRIFT, 1, 0>;
+        k<<<grid_for(a.C, kBlock, reinterpret_cast<const void *>(k)), kBlock, 0, s>>>(a);
+    }
 }
 
 template <int DIM, int P>
-static fem_status launch_rd(const RdArgs &a, bool a_p1, bool react, bool drift, cudaStream_t s) {
+static fem_status launch_rd(const RdArgs &a, bool a_p1, bool react, bool drift, bool vec, cudaStream_t s) {
     if (a_p1) {
-        if (drift) react ? launch_rd_one<DIM, P, true, true, true>(a, s) : launch_rd_one<DIM, P, true, false, true>(a, s);
-        else react ? launch_rd_one<DIM, P, true, true, false>(a, s) : launch_rd_one<DIM, P, true, false, false>(a, s);
+        if (drift) react ? launch_rd_one<DIM, P, true, true, true>(a, vec, s)
+                         : launch_rd_one<DIM, P, true, false, true>(a, vec, s);
+        else react ? launch_rd_one<DIM, P, true, true, false>(a, vec, s)
+                   : launch_rd_one<DIM, P, true, false, false>(a, vec, s);
     } else {
-        react ? launch_rd_one<DIM, P, false, true, false>(a, s) : launch_rd_one<DIM, P, false, false, false>(a, s);
+        react ? launch_rd_one<DIM, P, false, true, false>(a, vec, s) : launch_rd_one<DIM, P, false, false, false>(a, vec, s);
     }
     return check_launch("fem_integrate_reaction_diffusion");
 }
@@ -270,13 +303,16 @@ extern "C" fem_status fem_integrate_reaction_diffusion(int dim, int64_t n_cells,
     r.gf = static_cast<float>(drift);
     // grad a vanishes inside a cell for a P0 field: the term is then absent
     const bool p1 = a_space == 1, react = c != nullptr, with_drift = p1 && drift != 0.0;
+    // 16-byte rows: every cell-indexed array aligned and the cell count a multiple of 4
+    const bool vec = n_cells % 4 == 0 && aligned16(conn) && aligned16(elem_out) && (!react || aligned16(c)) &&
+                     (p1 || aligned16(a));
     switch (dim * 10 + static_cast<int>(prec)) {
-        case 20: return launch_rd<2, FEM_FP64>(r, p1, react, with_drift, stream);
-        case 21: return launch_rd<2, FEM_FP32_MIXED>(r, p1, react, with_drift, stream);
-        case 22: return launch_rd<2, FEM_FP32>(r, p1, react, with_drift, stream);
-        case 30: return launch_rd<3, FEM_FP64>(r, p1, react, with_drift, stream);
-        case 31: return launch_rd<3, FEM_FP32_MIXED>(r, p1, react, with_drift, stream);
-        case 32: return launch_rd<3, FEM_FP32>(r, p1, react, with_drift, stream);
+        case 20: return launch_rd<2, FEM_FP64>(r, p1, react, with_drift, vec, stream);
+        case 21: return launch_rd<2, FEM_FP32_MIXED>(r, p1, react, with_drift, vec, stream);
+        case 22: return launch_rd<2, FEM_FP32>(r, p1, react, with_drift, vec, stream);
+        case 30: return launch_rd<3, FEM_FP64>(r, p1, react, with_drift, vec, stream);
+        case 31: return launch_rd<3, FEM_FP32_MIXED>(r, p1, react, with_drift, vec, stream);
+        case 32: return launch_rd<3, FEM_FP32>(r, p1, react, with_drift, vec, stream);
     }
     return fail(FEM_ERR_ARG, "unsupported dim/precision");
 }
