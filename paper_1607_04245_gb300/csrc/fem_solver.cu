@@ -85,8 +85,19 @@ __global__ void __launch_bounds__(256) dot_final_kernel(const double *partial, d
     if (threadIdx.x == 0) *result = s[0];
 }
 
-// scalars[] layout: 0 rz, 1 pq, 2 rz_new, 3 rr, 4 (rtol ||r_0||)^2, 5 iterations done
-enum { S_RZ = 0, S_PQ = 1, S_RZNEW = 2, S_RR = 3, S_TOL2 = 4, S_ITER = 5, S_COUNT = 6 };
+// scalars[] layout: 0 rz, 1 pq, 2 rz_new, 3 rr, 4 (rtol ||r_0||)^2, 5 iterations done, 6 beta
+enum { S_RZ = 0, S_PQ = 1, S_RZNEW = 2, S_RR = 3, S_TOL2 = 4, S_ITER = 5, S_BETA = 6, S_COUNT = 7 };
+
+// Block-level sum of one double per thread (256 threads); thread 0 gets the total.
+__device__ __forceinline__ double block_sum256(double v, double *sh) {
+    sh[threadIdx.x] = v;
+    __syncthreads();
+    for (int o = 128; o > 0; o >>= 1) {
+        if (threadIdx.x < o) sh[threadIdx.x] += sh[threadIdx.x + o];
+        __syncthreads();
+    }
+    return sh[0];
+}
 
 // r = b - Ax (free vertices), 0 on fixed ones; z = r / D; p = z
 template <class T>
@@ -100,51 +111,87 @@ __global__ void cg_init_kernel(int64_t V, const T *b, const T *Ax, const T *D, c
     }
 }
 
-// q = 0 on fixed vertices (the operator is restricted to the free ones)
+
+// ---- the kernels of the device-side loop (q is restricted to the free vertices). The
+// reductions visit the vertices with dot_partial_kernel's fixed grid and order (block b,
+// thread t: i = 256 b + t + k 256 kDotBlocks) and finish like dot_final_kernel, so every
+// sum is reproducible and independent of the device.
+
+// q = 0 on fixed vertices; block partial sums of p . q
 template <class T>
-__global__ void mask_kernel(int64_t V, const uint8_t *fixed, T *q) {
-    const int64_t stride = int64_t(gridDim.x) * blockDim.x;
-    for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < V; i += stride)
-        if (fixed[i]) q[i] = T(0);
+__global__ void __launch_bounds__(256) mask_dot_kernel(int64_t V, const uint8_t *fixed, const T *p, T *q,
+                                                       double *partial) {
+    __shared__ double sh[256];
+    double acc = 0.0;
+    for (int64_t i = int64_t(blockIdx.x) * 256 + threadIdx.x; i < V; i += int64_t(kDotBlocks) * 256) {
+        T qi = q[i];
+        if (fixed[i]) q[i] = qi = T(0);
+        acc += static_cast<double>(p[i]) * static_cast<double>(qi);
+    }
+    const double t = block_sum256(acc, sh);
+    if (threadIdx.x == 0) partial[blockIdx.x] = t;
 }
 
-// alpha = rz / pq; x += alpha p; r -= alpha q; z = r / D
+// alpha = rz / pq; x += alpha p; r -= alpha q; z = r / D; block partial sums of r . z
+// (partial[0 .. kDotBlocks)) and r . r (partial[kDotBlocks .. 2 kDotBlocks))
 template <class T>
-__global__ void cg_step_kernel(int64_t V, const double *sc, const T *p, const T *q, const T *D, T *x, T *r, T *z) {
+__global__ void __launch_bounds__(256) step_dots_kernel(int64_t V, const double *sc, const T *p, const T *q,
+                                                        const T *D, T *x, T *r, T *z, double *partial) {
+    __shared__ double sh[256];
     const double alpha = sc[S_PQ] != 0.0 ? sc[S_RZ] / sc[S_PQ] : 0.0;
-    const int64_t stride = int64_t(gridDim.x) * blockDim.x;
-    for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < V; i += stride) {
+    double rz = 0.0, rr = 0.0;
+    for (int64_t i = int64_t(blockIdx.x) * 256 + threadIdx.x; i < V; i += int64_t(kDotBlocks) * 256) {
         x[i] = static_cast<T>(x[i] + alpha * p[i]);
         const T ri = static_cast<T>(r[i] - alpha * q[i]);
+        const T zi = ri / D[i];
         r[i] = ri;
-        z[i] = ri / D[i];
+        z[i] = zi;
+        rz += static_cast<double>(ri) * static_cast<double>(zi);
+        rr += static_cast<double>(ri) * static_cast<double>(ri);
+    }
+    const double t1 = block_sum256(rz, sh);
+    if (threadIdx.x == 0) partial[blockIdx.x] = t1;
+    __syncthreads();
+    const double t2 = block_sum256(rr, sh);
+    if (threadIdx.x == 0) partial[kDotBlocks + blockIdx.x] = t2;
+}
+
+// one block: rz_new and rr from the partials, beta = rz_new / rz, rz = rz_new, then count
+// the iteration and set the loop condition (not converged, fewer than max_iter; a NaN
+// residual ends the loop: every comparison with it is false)
+__global__ void __launch_bounds__(256) finish_iteration_kernel(const double *partial, double *sc, int max_iter,
+                                                               cudaGraphConditionalHandle loop) {
+    __shared__ double sh[256];
+    double a = 0.0, b = 0.0;
+    for (int i = threadIdx.x; i < kDotBlocks; i += 256) a += partial[i], b += partial[kDotBlocks + i];
+    const double rz_new = block_sum256(a, sh);
+    __syncthreads();
+    const double rr = block_sum256(b, sh);
+    if (threadIdx.x == 0) {
+        const double rz = sc[S_RZ];
+        sc[S_BETA] = rz != 0.0 ? rz_new / rz : 0.0;
+        sc[S_RZNEW] = rz_new;
+        sc[S_RZ] = rz_new;
+        sc[S_RR] = rr;
+        const double it = sc[S_ITER] + 1.0;
+        sc[S_ITER] = it;
+        const bool more = it < static_cast<double>(max_iter) && rr > sc[S_TOL2] && rr > 0.0;
+        cudaGraphSetConditional(loop, more ? 1u : 0u);
     }
 }
 
-// beta = rz_new / rz; p = z + beta p; rz = rz_new (one thread updates the scalar after all reads)
+// p = z + beta p
 template <class T>
-__global__ void cg_dir_kernel(int64_t V, const double *sc, const T *z, T *p) {
-    const double beta = sc[S_RZ] != 0.0 ? sc[S_RZNEW] / sc[S_RZ] : 0.0;
+__global__ void dir_kernel(int64_t V, const double *sc, const T *z, T *p) {
+    const double beta = sc[S_BETA];
     const int64_t stride = int64_t(gridDim.x) * blockDim.x;
     for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < V; i += stride)
         p[i] = static_cast<T>(z[i] + beta * p[i]);
 }
 
-__global__ void copy_scalar_kernel(double *sc, int dst, int src) { sc[dst] = sc[src]; }
-
 __global__ void loop_init_kernel(double *sc, double tol2) {
     sc[S_TOL2] = tol2;
     sc[S_ITER] = 0.0;
-}
-
-// last kernel of the loop body: count the iteration and set the WHILE condition; the
-// count bounds the loop, and a NaN residual ends it too (every comparison is false)
-__global__ void cg_continue_kernel(double *sc, int max_iter, cudaGraphConditionalHandle loop) {
-    const double it = sc[S_ITER] + 1.0;
-    sc[S_ITER] = it;
-    const double rr = sc[S_RR];
-    const bool more = it < static_cast<double>(max_iter) && rr > sc[S_TOL2] && rr > 0.0;
-    cudaGraphSetConditional(loop, more ? 1u : 0u);
 }
 
 // a library stream per device to capture the loop body on (capture needs a stream other
@@ -188,7 +235,7 @@ static size_t carve(int64_t C, int64_t V, int dim, size_t vs, void *base, Worksp
     void *elem = take(size_t(dim + 1) * size_t(C) * vs);
     void *D = take(size_t(V) * vs), *r = take(size_t(V) * vs), *z = take(size_t(V) * vs);
     void *p = take(size_t(V) * vs), *q = take(size_t(V) * vs);
-    double *partial = static_cast<double *>(take(sizeof(double) * kDotBlocks));
+    double *partial = static_cast<double *>(take(sizeof(double) * 2 * kDotBlocks));
     double *scalars = static_cast<double *>(take(sizeof(double) * S_COUNT));
     if (w) *w = Workspace{elem, D, r, z, p, q, partial, scalars};
     return off;
@@ -268,16 +315,15 @@ static fem_status pcg_run(int dim, int64_t C, int64_t V, const double *coords, c
             e = cudaStreamBeginCaptureToGraph(cs, np.conditional.phGraph_out[0], nullptr, nullptr, 0,
                                               cudaStreamCaptureModeThreadLocal);
         if (e == cudaSuccess) {
+            // one iteration in 7 kernels: residual, gather, q masked with p.q, pq, the
+            // updates with r.z and r.r, the scalars and the loop condition, the direction
             st = matvec(p, q, cs);
             if (st == FEM_OK) {
-                mask_kernel<T><<<gV, 256, 0, cs>>>(V, fixed, q);
-                dot(p, q, S_PQ, cs);
-                cg_step_kernel<T><<<gV, 256, 0, cs>>>(V, w.scalars, p, q, D, X, r, z);
-                dot(r, z, S_RZNEW, cs);
-                cg_dir_kernel<T><<<gV, 256, 0, cs>>>(V, w.scalars, z, p);
-                copy_scalar_kernel<<<1, 1, 0, cs>>>(w.scalars, S_RZ, S_RZNEW);
-                dot(r, r, S_RR, cs);
-                cg_continue_kernel<<<1, 1, 0, cs>>>(w.scalars, max_iter, loop);
+                mask_dot_kernel<T><<<kDotBlocks, 256, 0, cs>>>(V, fixed, p, q, w.partial);
+                dot_final_kernel<<<1, 256, 0, cs>>>(w.partial, w.scalars + S_PQ);
+                step_dots_kernel<T><<<kDotBlocks, 256, 0, cs>>>(V, w.scalars, p, q, D, X, r, z, w.partial);
+                finish_iteration_kernel<<<1, 256, 0, cs>>>(w.partial, w.scalars, max_iter, loop);
+                dir_kernel<T><<<gV, 256, 0, cs>>>(V, w.scalars, z, p);
             }
             cudaGraph_t body = nullptr;
             const cudaError_t e2 = cudaStreamEndCapture(cs, &body);
