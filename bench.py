@@ -305,6 +305,19 @@ def rel_err(gpu, ref):
     return float(np.abs(g - ref).max() / np.abs(ref).max())
 
 
+def oracle_timed(row, n_cells, fn):
+    """Run an oracle call, record its rate beside the GPU row (the CPU oracle on all host
+    threads, float64, the same workload) and return its result."""
+    import oracle
+
+    t0 = time.perf_counter()
+    ref = fn()
+    dt = time.perf_counter() - t0
+    row["oracle_cells_per_s"] = n_cells / dt
+    row["oracle_threads"] = oracle.num_threads()
+    return ref
+
+
 def measure_residual(case, prec, device, stream, flush, steps, warmup, peak, oracle_mod=None, dist=None, ws=1,
                      sampler=None):
     import torch
@@ -322,7 +335,8 @@ def measure_residual(case, prec, device, stream, flush, steps, warmup, peak, ora
            "paper_model_gflops": perfmodel.flops_per_cell(c.dim, c.rule.n_q, c.n_comp) * c.n_cells / t / 1e9}
     if oracle_mod is not None:
         torch.cuda.synchronize()
-        row["rel_maxnorm_err_vs_oracle"] = rel_err(out, oracle_mod.residual_for(c))
+        row["rel_maxnorm_err_vs_oracle"] = rel_err(out, oracle_timed(row, c.n_cells,
+                                                                     lambda: oracle_mod.residual_for(c)))
         row["tolerance"] = TOL[prec]
     return row, ms, wall, clocks
 
@@ -355,7 +369,8 @@ def measure_geometry_path(case, prec, device, stream, flush, steps, warmup, peak
                                  "precomputed once per mesh, not timed"}
     if oracle_mod is not None:
         torch.cuda.synchronize()
-        row["rel_maxnorm_err_vs_oracle"] = rel_err(out, oracle_mod.residual_for(c))
+        row["rel_maxnorm_err_vs_oracle"] = rel_err(out, oracle_timed(row, c.n_cells,
+                                                                     lambda: oracle_mod.residual_for(c)))
     return row
 
 
@@ -402,7 +417,8 @@ def measure_transposed(case, prec, device, stream, flush, steps, warmup, peak, o
         fem.fem_integrate_laplacian_transposed(ue, d["K"], q.points, q.weights, geom, 64, 4, out=out, prec=prec,
                                                stream=stream)
         torch.cuda.synchronize()
-        row["rel_maxnorm_err_vs_oracle"] = rel_err(out, oracle_mod.residual_for(c))
+        row["rel_maxnorm_err_vs_oracle"] = rel_err(out, oracle_timed(row, c.n_cells,
+                                                                     lambda: oracle_mod.residual_for(c)))
     return row
 
 
@@ -430,7 +446,7 @@ def measure_adjoint(case, prec, device, stream, flush, steps, warmup, peak, orac
            "kernels_per_step": 2}
     if oracle_mod is not None:
         torch.cuda.synchronize()
-        rK, ru = oracle_mod.adjoint_for(c)
+        rK, ru = oracle_timed(row, c.n_cells, lambda: oracle_mod.adjoint_for(c))
         row["rel_err_dK"] = rel_err(dK, rK)
         row["rel_err_du"] = rel_err(du, ru)
         row["tolerance"] = TOL[prec]
@@ -467,8 +483,8 @@ def measure_reaction(case, prec, device, stream, flush, steps, warmup, peak, ora
            "alg_bytes_per_cell": "conn 4(d+1) + c n_q s + out (d+1) s + (V/C)(coords 8d + u s + a s)"}
     if oracle_mod is not None:
         torch.cuda.synchronize()
-        ref = oracle_mod.reaction_diffusion(c.mesh.coords, c.mesh.conn, c.u, a_np, 1, c_np, q.points, q.weights,
-                                            drift=drift)
+        ref = oracle_timed(row, c.n_cells, lambda: oracle_mod.reaction_diffusion(
+            c.mesh.coords, c.mesh.conn, c.u, a_np, 1, c_np, q.points, q.weights, drift=drift))
         row["rel_maxnorm_err_vs_oracle"] = rel_err(out, ref)
         row["tolerance"] = TOL[prec]
     return row
