@@ -535,6 +535,45 @@ def measure_pcg(case, device, stream, peak, prec="fp64", rtol=1e-8, max_iter=500
                       "flushed between iterations"}
 
 
+def measure_fields(case, prec, device, stream, flush, steps, warmup, peak, oracle_mod=None, n_fields=8):
+    """n_fields nodal fields on one mesh and coefficient in one launch (the cell geometry
+    computed once per cell and reused for every field)."""
+    import torch
+
+    import paper_1607_04245_gb300 as fem
+
+    c, d = device_case(case, prec, device)
+    rng = np.random.default_rng(2024)
+    U = rng.uniform(-1.0, 1.0, (n_fields, c.n_verts))
+    if prec != "fp64":
+        U = U.astype(np.float32).astype(np.float64)
+    dt = fem.value_dtype(prec)
+    U_d = torch.from_numpy(U).to(device=device, dtype=dt)
+    q = c.rule
+    out = torch.empty((n_fields, c.dim + 1, c.n_cells), dtype=dt, device=device)
+    fn = lambda: fem.fem_integrate_laplacian_fields(d["coords"], d["conn"], U_d, d["K"], q.points, q.weights, out=out,
+                                                    prec=prec, stream=stream)
+    with torch.cuda.stream(stream):
+        ms, _, _ = timed_steps(fn, steps, warmup, stream, flush)
+    t = statistics.mean(ms) * 1e-3
+    sz = 8 if prec == "fp64" else 4
+    C, V, nb = c.n_cells, c.n_verts, c.dim + 1
+    nbytes = nb * 4 * C + q.n_q * sz * C + c.dim * 8 * V + n_fields * (sz * V + nb * sz * C)
+    row = {"physics": "laplacian_fields", "dim": c.dim, "prec": prec, "cells": C, "fields": n_fields,
+           "ms_per_launch": round(statistics.mean(ms), 6), "field_cells_per_s": n_fields * C / t,
+           "alg_bytes_per_launch": nbytes, "alg_gbs": nbytes / t / 1e9, "hbm_frac_of_measured": nbytes / t / 1e9 / peak,
+           "alg_bytes_per_cell": "conn 4(d+1) + K n_q s + (V/C) coords 8d + F ((V/C) u s + out (d+1) s)"}
+    if oracle_mod is not None:
+        torch.cuda.synchronize()
+        refs = oracle_timed(row, n_fields * C, lambda: [oracle_mod.laplacian(c.mesh.coords, c.mesh.conn, U[f], c.K,
+                                                                              q.points, q.weights)
+                                                         for f in range(n_fields)])
+        row["oracle_field_cells_per_s"] = row.pop("oracle_cells_per_s")
+        row["rel_maxnorm_err_vs_oracle"] = max(rel_err(out[f], refs[f]) for f in range(n_fields))
+        row["tolerance"] = TOL[prec]
+    return row
+
+
 def measure_e2e(case, prec, device, steps, warmup):
     """Same metric through the host-buffer API: H2D of all inputs, kernel, D2H of the result."""
     import torch
@@ -813,6 +852,9 @@ def run_ours(args):
                                                                  peak, oracle)
         for prec in ("fp64", "fp64_df"):
             rows[f"pcg_lap3d_{prec}"] = measure_pcg(case, device, stream, peak, prec)
+        for prec in ("mixed", "fp64"):
+            rows[f"lap3d_fields8_{prec}"] = measure_fields(case, prec, device, stream, flush, rsteps, args.warmup, peak,
+                                                           oracle)
         sweep = {}
         for e in range(16, 24):
             sc = workloads.laplacian_cube_case(1 << e)

@@ -81,8 +81,8 @@ typedef enum {
      * pipe: the Jacobian columns are formed in float64, every other intermediate is a
      * pair of float32 values (hi + lo, double-length arithmetic from TwoSum/TwoProduct),
      * the outputs are widened back to float64. Values must lie in float32's normal range
-     * (|x| in [2^-126, 2^128), or zero). fem_integrate_laplacian only; the other entry
-     * points return FEM_ERR_ARG for it. */
+     * (|x| in [2^-126, 2^128), or zero). fem_integrate_laplacian and (for its residual)
+     * fem_pcg_laplacian only; the other entry points return FEM_ERR_ARG for it. */
     FEM_FP64_DF = 3
 } fem_precision;
 
@@ -105,6 +105,24 @@ fem_status fem_integrate_laplacian(int dim, int64_t n_cells, int64_t n_verts, co
                                    const int32_t *conn, const void *u, const void *K, int n_q,
                                    const double *qpts, const double *qw, void *elem_out,
                                    fem_precision prec, fem_stream stream);
+
+/* ---------------------------------------------------------------------------------
+ * fem_integrate_laplacian_fields -- fem_integrate_laplacian for n_fields nodal fields on
+ * the same mesh and coefficient (Eq. 2 with f1 = K grad u, once per field): the geometry
+ * of each cell (coordinate gathers, J, det J, adjugate) and Kbar / |det J| are computed
+ * once and reused for every field, so each extra field costs its nodal gathers, the
+ * contraction and its element-vector stores.
+ *   u          [n_fields][n_verts] nodal values, field-major
+ *   elem_out   [n_fields][dim+1][n_cells] element vectors (written)
+ * Other arguments, precisions (not FEM_FP64_DF) and returns as fem_integrate_laplacian;
+ * n_fields = 0 is a no-op. Per field and cell the arithmetic is that of the single-field
+ * per-cell kernel, so results equal fem_integrate_laplacian's bit for bit in FEM_FP64
+ * (and in the float32 forms when that call takes its per-cell path).
+ * ------------------------------------------------------------------------------- */
+fem_status fem_integrate_laplacian_fields(int dim, int64_t n_cells, int64_t n_verts, const double *coords,
+                                          const int32_t *conn, int n_fields, const void *u, const void *K,
+                                          int n_q, const double *qpts, const double *qw, void *elem_out,
+                                          fem_precision prec, fem_stream stream);
 
 /* ---------------------------------------------------------------------------------
  * fem_integrate_elasticity -- element residuals of linear elasticity (Eq. 2 with f0 = 0

@@ -25,6 +25,7 @@ from .binding import (  # noqa: F401
     fem_integrate_elasticity,
     fem_host_work_bytes,
     fem_integrate_laplacian,
+    fem_integrate_laplacian_fields,
     fem_integrate_laplacian_host,
     fem_integrate_laplacian_geom,
     fem_integrate_laplacian_transposed,

@@ -45,6 +45,7 @@ def lib():
         P, i64, ci, cd = ctypes.c_void_p, ctypes.c_int64, ctypes.c_int, ctypes.c_double
         sig = {
             "fem_integrate_laplacian": [ci, i64, i64, P, P, P, P, ci, P, P, P, ci, P],
+            "fem_integrate_laplacian_fields": [ci, i64, i64, P, P, ci, P, P, ci, P, P, P, ci, P],
             "fem_integrate_elasticity": [ci, i64, i64, P, P, P, P, P, ci, P, P, P, ci, P],
             "fem_adjoint_laplacian": [ci, i64, i64, P, P, P, P, ci, P, P, P, P, P, P, P, P, ci, P],
             "fem_build_node2cell": [ci, i64, i64, P, P, P, P, P],
@@ -162,6 +163,26 @@ def fem_integrate_laplacian(coords, conn, u, K, qpts, qw, out=None, prec="mixed"
         _dev(u, "u", dt, (V,), dev), _dev(K, "K", dt, (nq, C), dev), nq, qp.ptr, w.ptr,
         _dev(out, "out", dt, (dim + 1, C), dev), p, _stream(stream))
     _check("fem_integrate_laplacian", st)
+    return out
+
+
+def fem_integrate_laplacian_fields(coords, conn, u, K, qpts, qw, out=None, prec="mixed", stream=None) -> torch.Tensor:
+    """Element residuals [F][dim+1][C] of the variable-coefficient Laplacian for F nodal
+    fields u [F][V] on one mesh (geometry computed once per cell)."""
+    p = precision(prec)
+    dt = value_dtype(p)
+    dim, V, C = _mesh_sizes(coords, conn)
+    nf = int(u.shape[0])
+    nq = int(np.asarray(qw).shape[0]) if not isinstance(qw, torch.Tensor) else int(qw.shape[0])
+    dev = coords.device
+    if out is None:
+        out = torch.empty((nf, dim + 1, C), dtype=dt, device=dev)
+    qp, w = _HostTable(qpts, (nq, dim), "qpts"), _HostTable(qw, (nq,), "qw")
+    st = lib().fem_integrate_laplacian_fields(
+        dim, C, V, _dev(coords, "coords", torch.float64, device=dev), _dev(conn, "conn", torch.int32, device=dev), nf,
+        _dev(u, "u", dt, (nf, V), dev), _dev(K, "K", dt, (nq, C), dev), nq, qp.ptr, w.ptr,
+        _dev(out, "out", dt, (nf, dim + 1, C), dev), p, _stream(stream))
+    _check("fem_integrate_laplacian_fields", st)
     return out
 
 

@@ -33,11 +33,10 @@ struct LapArgs {
     QuadW w;
 };
 
-// r_b from the adjugate rows, the determinant, the nodal values and Kbar (T = double,
-// float, or f2 for two cells at once).
+// r_b from the adjugate rows, the scale s = Kbar / |det J| and the nodal values (T =
+// double, float, or f2 for two cells at once).
 template <int DIM, class T>
-__device__ __forceinline__ void lap_element(const T (&n)[DIM][DIM], T det, const T (&uu)[DIM + 1], T kbar,
-                                            T (&r)[DIM + 1]) {
+__device__ __forceinline__ void lap_apply(const T (&n)[DIM][DIM], T s, const T (&uu)[DIM + 1], T (&r)[DIM + 1]) {
     T h[DIM];
     {
         const T du = uu[1] - uu[0];
@@ -50,7 +49,6 @@ __device__ __forceinline__ void lap_element(const T (&n)[DIM][DIM], T det, const
 #pragma unroll
         for (int i = 0; i < DIM; ++i) h[i] = fma(du, n[j][i], h[i]);
     }
-    const T s = quot_abs(kbar, det);
     T sum = zero<T>();
 #pragma unroll
     for (int j = 0; j < DIM; ++j) {
@@ -58,6 +56,13 @@ __device__ __forceinline__ void lap_element(const T (&n)[DIM][DIM], T det, const
         sum = sum + r[j + 1];
     }
     r[0] = neg(sum);
+}
+
+// r_b from the adjugate rows, the determinant, the nodal values and Kbar
+template <int DIM, class T>
+__device__ __forceinline__ void lap_element(const T (&n)[DIM][DIM], T det, const T (&uu)[DIM + 1], T kbar,
+                                            T (&r)[DIM + 1]) {
+    lap_apply<DIM>(n, quot_abs(kbar, det), uu, r);
 }
 
 // h_lambda . h_u / |det J|
@@ -229,6 +234,138 @@ __global__ void __launch_bounds__(kBlock) lap_kernel(const __grid_constant__ Lap
             }
         }
     }
+}
+
+// ------------------------------------------------------------------ several fields
+
+// Element residuals of n_fields nodal fields on one mesh and coefficient: the geometry
+// (coordinate gathers, adjugate rows, det J) and s = Kbar / |det J| are computed once per
+// cell and kept in registers; each field then costs its nodal gathers, the contraction
+// and its stores. u is [n_fields][V], out [n_fields][dim+1][C]. Per field and cell the
+// arithmetic is exactly that of the single-field per-cell routine (lap_cell).
+struct FieldsArgs {
+    LapArgs a;  // conn, K, coords, C, V, quadrature, tau2; a.u = u of field 0, a.out = out of field 0
+    int nf;
+};
+
+// badly shaped cell of the mixed form: float64 geometry and sums for every field
+template <int DIM>
+__device__ __noinline__ void lap_fields_fallback(const FieldsArgs &fa, int64_t c, double kbar) {
+    constexpr int NB = DIM + 1;
+    const LapArgs &a = fa.a;
+    const int64_t C = a.C;
+    uint32_t v[NB];
+#pragma unroll
+    for (int b = 0; b < NB; ++b) v[b] = clamp_vid(a.conn[b * C + c], a.V);
+    const double *X[DIM];
+#pragma unroll
+    for (int k = 0; k < DIM; ++k) X[k] = a.X[k];
+    double xs[NB][DIM], e64[DIM][DIM], n64[DIM][DIM];
+    gather_coords<DIM>(X, v, xs);
+    columns_f64<DIM>(xs, e64);
+    const double s = quot_abs(kbar, adjugate_rows<DIM>(e64, n64));
+    const float *u = static_cast<const float *>(a.u);
+    float *out = static_cast<float *>(a.out);
+    for (int f = 0; f < fa.nf; ++f) {
+        double u64[NB], r64[NB];
+#pragma unroll
+        for (int b = 0; b < NB; ++b) u64[b] = u[int64_t(f) * a.V + v[b]];
+        lap_apply<DIM>(n64, s, u64, r64);
+#pragma unroll
+        for (int b = 0; b < NB; ++b) out[(int64_t(f) * NB + b) * C + c] = static_cast<float>(r64[b]);
+    }
+}
+
+template <int DIM, int P, int CPT, int NQ>
+__global__ void __launch_bounds__(kBlock) lap_fields_kernel(const __grid_constant__ FieldsArgs fa) {
+    constexpr int NB = DIM + 1;
+    using T = val_t<P>;
+    const LapArgs &a = fa.a;
+    const int64_t C = a.C;
+    const int64_t V = a.V;
+    const T *__restrict__ u = static_cast<const T *>(a.u);
+    const T *__restrict__ K = static_cast<const T *>(a.K);
+    T *__restrict__ out = static_cast<T *>(a.out);
+    const double *X[DIM];
+#pragma unroll
+    for (int k = 0; k < DIM; ++k) X[k] = a.X[k];
+    const int nq = NQ > 0 ? NQ : a.w.nq;
+    const int64_t ngroups = (C + CPT - 1) / CPT;
+    const int64_t stride = int64_t(gridDim.x) * blockDim.x;
+    for (int64_t g = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; g < ngroups; g += stride) {
+        const int64_t c0 = g * CPT;
+        int32_t vid[NB][CPT];
+#pragma unroll
+        for (int b = 0; b < NB; ++b) load_row<CPT>(a.conn + b * C + c0, vid[b]);
+        qsum_t<P> ks[CPT];
+        {
+            T kq[CPT];
+            load_row<CPT>(K + c0, kq);
+#pragma unroll
+            for (int i = 0; i < CPT; ++i) ks[i].first(weight<P>(a.w, 0), kq[i]);
+        }
+#pragma unroll(NQ > 0 ? NQ - 1 : 1)
+        for (int q = 1; q < nq; ++q) {
+            T kq[CPT];
+            load_row<CPT>(K + q * C + c0, kq);
+#pragma unroll
+            for (int i = 0; i < CPT; ++i) ks[i].add(weight<P>(a.w, q), kq[i]);
+        }
+        // per-cell geometry, kept for all fields
+        uint32_t v[CPT][NB];
+        T n[CPT][DIM][DIM], s[CPT];
+        bool ok[CPT];
+#pragma unroll
+        for (int i = 0; i < CPT; ++i) {
+#pragma unroll
+            for (int b = 0; b < NB; ++b) v[i][b] = clamp_vid(vid[b][i], a.V);
+            double xs[NB][DIM];
+            gather_coords<DIM>(X, v[i], xs);
+            T e[DIM][DIM];
+            if constexpr (P == FEM_FP64) columns_f64<DIM>(xs, e);
+            else if constexpr (P == FEM_FP32_MIXED) columns_mixed<DIM>(xs, e);
+            else columns_f32<DIM>(xs, e);
+            const T det = adjugate_rows<DIM>(e, n[i]);
+            s[i] = quot_abs(ks[i].value(), det);
+            ok[i] = true;
+            if constexpr (P == FEM_FP32_MIXED) ok[i] = shape_ok<DIM>(e, det, a.tau2);
+        }
+        for (int f = 0; f < fa.nf; ++f) {
+            const T *uf = u + int64_t(f) * V;
+            T r[NB][CPT];
+#pragma unroll
+            for (int i = 0; i < CPT; ++i) {
+                T uu[NB], rr[NB];
+#pragma unroll
+                for (int b = 0; b < NB; ++b) uu[b] = ld_gather(uf + v[i][b]);
+                lap_apply<DIM>(n[i], s[i], uu, rr);
+#pragma unroll
+                for (int b = 0; b < NB; ++b) r[b][i] = rr[b];
+            }
+#pragma unroll
+            for (int b = 0; b < NB; ++b) store_row<CPT>(out + (int64_t(f) * NB + b) * C + c0, r[b]);
+        }
+        if constexpr (P == FEM_FP32_MIXED) {
+#pragma unroll
+            for (int i = 0; i < CPT; ++i)
+                if (!ok[i]) lap_fields_fallback<DIM>(fa, c0 + i, ks[i].value_f64());
+        }
+    }
+}
+
+template <int DIM, int P>
+static fem_status launch_fields(const FieldsArgs &fa, bool vec, cudaStream_t s) {
+    // float64 keeps two cells per thread (the geometry of four would crowd the registers)
+    constexpr int CPTV = P == FEM_FP64 ? 2 : 4;
+    constexpr int NQN = DIM == 3 ? 4 : 3;  // the workloads' rules
+    if (vec && fa.a.w.nq == NQN) {
+        auto k = lap_fields_kernel<DIM, P, CPTV, NQN>;
+        k<<<grid_for((fa.a.C + CPTV - 1) / CPTV, kBlock, reinterpret_cast<const void *>(k)), kBlock, 0, s>>>(fa);
+    } else {
+        auto k = lap_fields_kernel<DIM, P, 1, 0>;
+        k<<<grid_for(fa.a.C, kBlock, reinterpret_cast<const void *>(k)), kBlock, 0, s>>>(fa);
+    }
+    return check_launch("fem_integrate_laplacian_fields");
 }
 
 // ------------------------------------------------------------------ staged kernel
@@ -701,6 +838,34 @@ extern "C" fem_status fem_integrate_laplacian(int dim, int64_t n_cells, int64_t 
     a.out = elem_out;
     const bool vec = n_cells % 4 == 0 && aligned16(conn) && aligned16(K) && aligned16(elem_out);
     return dispatch_lap<false>(dim, prec, a, vec, stream);
+}
+
+extern "C" fem_status fem_integrate_laplacian_fields(int dim, int64_t n_cells, int64_t n_verts,
+                                                     const double *coords, const int32_t *conn, int n_fields,
+                                                     const void *u, const void *K, int n_q, const double *qpts,
+                                                     const double *qw, void *elem_out, fem_precision prec,
+                                                     fem_stream stream) {
+    FieldsArgs fa;
+    fem_status st = fill_args(fa.a, dim, n_cells, n_verts, coords, conn, u, K, n_q, qpts, qw, prec);
+    if (st != FEM_OK) return st;
+    if (n_fields < 0) return fail(FEM_ERR_ARG, "n_fields = %d, must be >= 0", n_fields);
+    if (int64_t(n_fields) * (dim + 1) * n_cells >= (int64_t(1) << 40) || int64_t(n_fields) * n_verts >= (int64_t(1) << 40))
+        return fail(FEM_ERR_SHAPE, "too many field values");
+    if (n_cells == 0 || n_fields == 0) return FEM_OK;
+    if (!u || !K || !elem_out) return fail(FEM_ERR_ARG, "u, K or elem_out is NULL");
+    fa.a.out = elem_out;
+    fa.nf = n_fields;
+    // vector rows: C a multiple of 4 keeps every field's rows 16-byte aligned
+    const bool vec = n_cells % 4 == 0 && aligned16(conn) && aligned16(K) && aligned16(elem_out);
+    switch (dim * 10 + static_cast<int>(prec)) {
+        case 20: return launch_fields<2, FEM_FP64>(fa, vec, stream);
+        case 21: return launch_fields<2, FEM_FP32_MIXED>(fa, vec, stream);
+        case 22: return launch_fields<2, FEM_FP32>(fa, vec, stream);
+        case 30: return launch_fields<3, FEM_FP64>(fa, vec, stream);
+        case 31: return launch_fields<3, FEM_FP32_MIXED>(fa, vec, stream);
+        case 32: return launch_fields<3, FEM_FP32>(fa, vec, stream);
+    }
+    return fail(FEM_ERR_ARG, "unsupported dim/precision");
 }
 
 namespace fem {
