@@ -12,7 +12,7 @@ Timing: W warm-up steps, then K steps, each launched after an L2 flush (a read o
 launching stream; barrier + synchronize around the timed loop; max over ranks.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
-                    [--rows all|none] [--no-cpu-baseline]
+                    [--rows all|none|PREFIX,...] [--no-cpu-baseline]
 
 Rank 0 prints one JSON line. With N > 1 (torchrun), every rank integrates its own
 copy of the workload (independent problems, no data-path collective): weak scaling.
@@ -826,35 +826,50 @@ def run_ours(args):
     row_df, _, _, _ = measure_residual(case, "fp64_df", device, stream, flush, fp64_steps, args.warmup, peak,
                                        oracle if rank == 0 else None)
     rows["fp64_df"] = row_df
-    if args.rows == "all":
-        rsteps = max(3, args.steps // 50)
+    # --rows all | none | comma-separated row-name prefixes (e.g. "lap3d_fields8,elast3d")
+    picked = None if args.rows in ("all", "none") else [x for x in args.rows.split(",") if x]
+    want = lambda name: args.rows == "all" or (picked is not None and any(name.startswith(x) for x in picked))
+    rsteps = max(3, args.steps // 50)
+    if want("fp32_ablation"):
         rows["fp32_ablation"] = measure_residual(case, "fp32", device, stream, flush, rsteps, args.warmup, peak,
                                                  oracle)[0]
-        for prec in ("mixed", "fp64"):
+    for prec in ("mixed", "fp64"):
+        if want(f"lap3d_precomputed_geometry_{prec}"):
             rows[f"lap3d_precomputed_geometry_{prec}"] = measure_geometry_path(case, prec, device, stream, flush, rsteps,
                                                                               args.warmup, peak, oracle)
-        for prec in ("fp32", "fp64"):
+    for prec in ("fp32", "fp64"):
+        if want(f"lap3d_thread_transposition_{prec}"):
             rows[f"lap3d_thread_transposition_{prec}"] = measure_transposed(case, prec, device, stream, flush, rsteps,
                                                                            args.warmup, peak, oracle)
+    if want("lap2d_8192_fp64"):
         rows["lap2d_8192_fp64"] = measure_residual(workloads.laplacian_square_case(), "fp64", device, stream, flush,
                                                    rsteps, args.warmup, peak, oracle)[0]
-        for dim in (2, 3):
-            el = workloads.elasticity_case(dim)
-            for prec in ("mixed", "fp64"):
+    for dim in (2, 3):
+        if not any(want(f"elast{dim}d_{prec}") for prec in ("mixed", "fp64")):
+            continue
+        el = workloads.elasticity_case(dim)
+        for prec in ("mixed", "fp64"):
+            if want(f"elast{dim}d_{prec}"):
                 rows[f"elast{dim}d_{prec}"] = measure_residual(el, prec, device, stream, flush, rsteps, args.warmup,
                                                                peak, oracle)[0]
+    if any(want(f"adjoint3d_{prec}") for prec in ("mixed", "fp64")):
         adj = workloads.adjoint_case(HEADLINE_CELLS)
         for prec in ("mixed", "fp64"):
-            rows[f"adjoint3d_{prec}"] = measure_adjoint(adj, prec, device, stream, flush, rsteps, args.warmup, peak,
-                                                        oracle)
-        for prec in ("mixed", "fp64"):
+            if want(f"adjoint3d_{prec}"):
+                rows[f"adjoint3d_{prec}"] = measure_adjoint(adj, prec, device, stream, flush, rsteps, args.warmup, peak,
+                                                            oracle)
+    for prec in ("mixed", "fp64"):
+        if want(f"reaction3d_grad_a_{prec}"):
             rows[f"reaction3d_grad_a_{prec}"] = measure_reaction(case, prec, device, stream, flush, rsteps, args.warmup,
                                                                  peak, oracle)
-        for prec in ("fp64", "fp64_df"):
+    for prec in ("fp64", "fp64_df"):
+        if want(f"pcg_lap3d_{prec}"):
             rows[f"pcg_lap3d_{prec}"] = measure_pcg(case, device, stream, peak, prec)
-        for prec in ("mixed", "fp64"):
+    for prec in ("mixed", "fp64"):
+        if want(f"lap3d_fields8_{prec}"):
             rows[f"lap3d_fields8_{prec}"] = measure_fields(case, prec, device, stream, flush, rsteps, args.warmup, peak,
                                                            oracle)
+    if want("sweep_lap3d_mixed"):
         sweep = {}
         for e in range(16, 24):
             sc = workloads.laplacian_cube_case(1 << e)
@@ -862,8 +877,8 @@ def run_ours(args):
             sweep[str(1 << e)] = {"cells_per_s": r["cells_per_s"], "alg_gbs": r["alg_gbs"],
                                   "hbm_frac_of_measured": r["hbm_frac_of_measured"], "ms": r["ms_per_launch"]}
         rows["sweep_lap3d_mixed"] = sweep
-        if args.serving_requests > 0:
-            rows["serving"] = measure_serving(device, args.serving_requests)
+    if want("serving") and args.serving_requests > 0:
+        rows["serving"] = measure_serving(device, args.serving_requests)
 
     e2e = measure_e2e(case, "mixed", device, max(3, args.steps // 100), 3)
 
@@ -903,7 +918,8 @@ def main(argv=None):
     ap.add_argument("--steps", type=int, default=10000)
     ap.add_argument("--warmup", type=int, default=20)
     ap.add_argument("--impl", choices=("ours", "reference"), default="ours")
-    ap.add_argument("--rows", choices=("all", "none"), default="all")
+    ap.add_argument("--rows", default="all",
+                    help="all, none, or comma-separated row-name prefixes to measure beside the headline")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--serving-requests", type=int, default=500)
     args = ap.parse_args(argv)
