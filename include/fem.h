@@ -17,9 +17,11 @@
  *
  * Conventions shared by every entry point:
  *  - All array arguments are DEVICE pointers owned by the caller, except qpts and qw,
- *    which are small HOST tables copied into the launch. No entry point allocates
- *    device memory or synchronises the stream: work is enqueued on `stream`
- *    (0 = the legacy default stream) and the call returns after the launch.
+ *    which are small HOST tables copied into the launch (and the host arrays of
+ *    fem_integrate_laplacian_host). No entry point allocates device memory for data or
+ *    synchronises the stream: work is enqueued on `stream` (0 = the legacy default
+ *    stream) and the call returns after the launch. The one exception is
+ *    fem_pcg_laplacian, which waits for its result and runs its loop as a CUDA graph.
  *  - Layouts are structure-of-arrays with the cell (or vertex) index fastest:
  *        coords [dim][n_verts]        always float64
  *        conn   [dim+1][n_cells]      int32 vertex ids in [0, n_verts)
@@ -27,7 +29,7 @@
  *        K, lam, mu [n_q][n_cells]    one coefficient per quadrature point
  *        out    [(dim+1)*n_comp][n_cells], row b*n_comp + k (n_comp = 1 or dim)
  *    Value arrays (u, K, lam, mu, out, lambda, dK, du, scratch) are float64 for
- *    FEM_FP64 and float32 for FEM_FP32_MIXED and FEM_FP32.
+ *    FEM_FP64 and FEM_FP64_DF and float32 for FEM_FP32_MIXED and FEM_FP32.
  *  - Reference simplex: vertices 0, e_1, ..., e_d. qpts [n_q][dim] are reference
  *    coordinates and qw [n_q] the weights (they sum to 1/d! for an exact rule).
  *    The P1 reference gradients are constant, so only the weights enter the
