@@ -80,3 +80,24 @@ def shared_bytes(d: int, s: TransposeSizes, word: int = 4) -> int:
     """Upper bound on shared memory per thread block (Sec. 3.3):
     M = word ((d^2 + 1) N_t + (d + 1) N_bt N_q + N_t N_bt + (d + 1) N_t N_sqc)."""
     return word * ((d * d + 1) * s.N_t + (d + 1) * s.N_bt * s.N_q + s.N_t * s.N_bt + (d + 1) * s.N_t * s.N_sqc)
+
+
+def collapsed_laplacian_flops(d: int, N_q: int) -> int:
+    """Floating-point operations per cell of this library's collapsed P1 Laplacian (an FMA
+    counts as 2), i.e. the arithmetic of r_b = (Kbar / |det J|) n_b . h that the kernels
+    execute in place of the per-point loops of the paper's model:
+      Jacobian columns x_j - x_0                      d^2 subtractions
+      adjugate rows n_j (2x2: negations; 3x3: cross products of two columns each)
+                                                      d = 3: 9 (mul + fma) = 27; d = 2: 0
+      det J = e_0 . n_0 (3D) or a 2x2 determinant     2d - 1
+      Kbar = sum_q w_q K_q                            2 N_q - 1
+      s = Kbar / |det J|                              1
+      du_j = u_j - u_0                                d
+      h = sum_j du_j n_j                              d (2d - 1)
+      n_j . h for j = 1..d                            d (2d - 1)
+      r_j = s (n_j . h)                               d
+      r_0 = -(r_1 + ... + r_d)                        d - 1
+    The compensated sum and the float64 fallback of the mixed form are not counted."""
+    adj = 27 if d == 3 else 0
+    det = 2 * d - 1 if d == 3 else 3
+    return d * d + adj + det + (2 * N_q - 1) + 1 + d + 2 * d * (2 * d - 1) + d + (d - 1)

@@ -48,3 +48,13 @@ def test_flops_per_cell_p1():
     assert pm.flops_per_cell(3, 4, 1) == 824
     assert pm.flops_per_cell(2, 3, 2) == 492
     assert pm.flops_per_cell(3, 4, 3) == 2472
+
+
+def test_collapsed_laplacian_flop_count():
+    """The collapsed P1 Laplacian's count (87 flops per tetrahedron with 4 points, 30 per
+    triangle with 3) against the paper model's per-point loops (824 per tetrahedron)."""
+    from paper_1607_04245_gb300 import perfmodel
+
+    assert perfmodel.collapsed_laplacian_flops(3, 4) == 87
+    assert perfmodel.collapsed_laplacian_flops(2, 3) == 30
+    assert perfmodel.flops_per_cell(3, 4, 1) > 9 * perfmodel.collapsed_laplacian_flops(3, 4)
