@@ -228,8 +228,8 @@ fem_status fem_integrate_laplacian_transposed(int dim, int64_t n_cells, const vo
  * the condition set by the body's last kernel), so the host does not wait per iteration;
  * unlike the other entry points this one returns only after the solve: it synchronises
  * `stream` twice (initial residual norm, final iteration count). The loop body is
- * captured on a library-owned stream per device, so concurrent calls from several host
- * threads on one device must be serialised by the caller.
+ * captured on a library-owned stream per device, one capture at a time (a lock), so
+ * calls from several host threads are safe.
  * ------------------------------------------------------------------------------- */
 int64_t fem_pcg_work_bytes(int dim, int64_t n_cells, int64_t n_verts, fem_precision prec);
 fem_status fem_pcg_laplacian(int dim, int64_t n_cells, int64_t n_verts, const double *coords,

@@ -311,6 +311,9 @@ static fem_status pcg_run(int dim, int64_t C, int64_t V, const double *coords, c
         np.conditional.size = 1;
         cudaGraphNode_t node = nullptr;
         if (e == cudaSuccess) e = cudaGraphAddNode(&node, graph, nullptr, nullptr, 0, &np);
+        // one capture at a time on the shared capture stream
+        static std::mutex capture_mu;
+        std::unique_lock<std::mutex> capture_lock(capture_mu);
         if (e == cudaSuccess)
             e = cudaStreamBeginCaptureToGraph(cs, np.conditional.phGraph_out[0], nullptr, nullptr, 0,
                                               cudaStreamCaptureModeThreadLocal);
@@ -329,6 +332,7 @@ static fem_status pcg_run(int dim, int64_t C, int64_t V, const double *coords, c
             const cudaError_t e2 = cudaStreamEndCapture(cs, &body);
             if (e2 != cudaSuccess) e = e2;
         }
+        capture_lock.unlock();
         if (e == cudaSuccess && st == FEM_OK) e = cudaGraphInstantiate(&exec, graph, 0);
         if (e == cudaSuccess && st == FEM_OK) e = cudaGraphLaunch(exec, s);
         if (e == cudaSuccess && st == FEM_OK) e = cudaStreamSynchronize(s);
