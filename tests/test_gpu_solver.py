@@ -125,3 +125,43 @@ def test_double_float_residual_solves_like_float64():
     assert abs(it64 - itdf) <= 3, (it64, itdf)
     a, b = x64.cpu().numpy(), xdf.cpu().numpy()
     assert np.abs(a - b).max() <= 1e-10 * np.abs(a).max()
+
+
+def test_concurrent_solves_from_two_threads():
+    """Two host threads solving on their own streams get the single-threaded results
+    (the loop captures are serialised inside the library)."""
+    import threading
+
+    mesh = _mesh(2, 16)
+    rule = workloads.rule_for_dim(2)
+    K = np.random.default_rng(2).lognormal(0.0, 1.0, (rule.n_q, mesh.n_cells))
+    fixed = _boundary(mesh)
+    x0 = np.where(fixed, mesh.coords[0] - mesh.coords[1], 0.0)
+    ref = _solve(mesh, K, rule, fixed, x0, None, "fp64", 1e-10)[0].cpu().numpy()
+    results, errors = [None, None], []
+
+    def worker(i):
+        try:
+            with torch.cuda.stream(torch.cuda.Stream()):
+                s = torch.cuda.current_stream()
+                coords, conn = to_dev(mesh.coords, torch.float64), to_dev(mesh.conn, torch.int32)
+                ptr, idx = fem.fem_build_node2cell(conn, mesh.n_verts, stream=s)
+                x = to_dev(x0, torch.float64)
+                for _ in range(3):
+                    x.copy_(to_dev(x0, torch.float64))
+                    fem.fem_pcg_laplacian(coords, conn, to_dev(K, torch.float64), rule.points, rule.weights, ptr, idx,
+                                          to_dev(fixed.astype(np.uint8), torch.uint8), x, max_iter=5000, rtol=1e-10,
+                                          prec="fp64", stream=s)
+                s.synchronize()
+                results[i] = x.cpu().numpy()
+        except Exception as exc:  # reported below
+            errors.append(exc)
+
+    threads = [threading.Thread(target=worker, args=(i,)) for i in range(2)]
+    for t in threads:
+        t.start()
+    for t in threads:
+        t.join()
+    assert not errors, errors
+    for r in results:
+        assert np.array_equal(r, ref)
