@@ -255,6 +255,25 @@ def test_assembled_elasticity_symmetric(ora, dim):
     assert np.abs(A - A.T).max() <= 1e-14 * np.abs(A).max()
 
 
+@pytest.mark.parametrize("dim", [2, 3])
+def test_assembled_elasticity_patch(ora, dim):
+    """Patch test: a linear displacement u = A x + b with constant lambda, mu has a constant
+    stress, so the assembled residual vanishes at every interior vertex."""
+    case = workloads.elasticity_case(dim, 2 * 6 * 6 if dim == 2 else 6 * 3 ** 3)
+    m, q = case.mesh, case.rule
+    rng = np.random.default_rng(dim + 11)
+    A = rng.normal(size=(dim, dim))
+    b = rng.normal(size=dim)
+    U = A @ m.coords + b[:, None]
+    lam = np.full_like(case.lam, 1.3)
+    mu = np.full_like(case.mu, 0.7)
+    R = exact.assemble(m.conn, ora.elasticity(m.coords, m.conn, U, lam, mu, q.points, q.weights), m.n_verts, dim)
+    interior = np.all((m.coords > 1e-12) & (m.coords < 1 - 1e-12), axis=0)
+    assert interior.any()
+    scale = np.abs(ora.elasticity(m.coords, m.conn, U, lam, mu, q.points, q.weights)).max()
+    assert np.abs(R[:, interior]).max() <= 1e-13 * scale
+
+
 def test_paper_listings_special_cases(ora):
     """K = 1 is the Laplacian listing (f1 = grad u); lambda = 0, mu = 1/2 is the 2D
     elasticity listing (f1 = symmetric gradient), both from Sec. 6."""
