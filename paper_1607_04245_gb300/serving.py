@@ -119,6 +119,10 @@ class Request:
     t_done: float = math.nan
     result: Dict[str, torch.Tensor] = dataclasses.field(default_factory=dict)
     error: str = ""
+    _arrays: Optional[list] = dataclasses.field(default=None, repr=False, compare=False)
+    _footprint: Optional[int] = dataclasses.field(default=None, repr=False, compare=False)
+    host_block: Optional[torch.Tensor] = dataclasses.field(default=None, repr=False, compare=False)
+    input_bytes: int = 0
 
     @property
     def n_comp(self) -> int:
@@ -129,7 +133,12 @@ class Request:
         return self.t_done - self.t_arrive
 
     def device_arrays(self):
-        """(name, shape, dtype) of every device array the request needs."""
+        """(name, shape, dtype) of every device array the request needs (computed once)."""
+        if self._arrays is None:
+            self._arrays = self._device_arrays()
+        return self._arrays
+
+    def _device_arrays(self):
         d, C, V, nq = self.dim, self.n_cells, self.n_verts, int(self.qw.shape[0])
         dt = value_dtype(self.prec)
         arrs = [("coords", (d, V), torch.float64), ("conn", (d + 1, C), torch.int32),
@@ -156,35 +165,52 @@ class Request:
                            "du": torch.empty(V, dtype=dt, pin_memory=True)}
 
 
+_ELEMENT_BYTES = {torch.float64: 8, torch.float32: 4, torch.int32: 4, torch.uint8: 1}
+
+
 def _nbytes(shape, dtype) -> int:
     n = 1
     for s in shape:
         n *= int(s)
-    return n * torch.empty((), dtype=dtype).element_size()
+    return n * _ELEMENT_BYTES[dtype]
 
 
 def footprint(req: Request) -> int:
-    """Device bytes of a request: every array rounded up to the 256-byte alignment."""
-    return sum((_nbytes(s, t) + ALIGN - 1) // ALIGN * ALIGN for _, s, t in req.device_arrays())
+    """Device bytes of a request: every array rounded up to the 256-byte alignment
+    (computed once per request)."""
+    if req._footprint is None:
+        req._footprint = sum((_nbytes(s, t) + ALIGN - 1) // ALIGN * ALIGN for _, s, t in req.device_arrays())
+    return req._footprint
 
 
 def make_request(rid, case, kind, prec="mixed", arrival=0.0, adj=None) -> Request:
-    """A request from a workloads.Case (values rounded to the precision's storage type)."""
+    """A request from a workloads.Case (values rounded to the precision's storage type).
+    Its inputs live in one pinned host block laid out like the leading (input) part of
+    the request's device block, so admission uploads them with a single copy."""
     dt = value_dtype(prec)
     c = case if prec == "fp64" else case.rounded_to_f32()
-    pin = lambda a, t: torch.from_numpy(np.ascontiguousarray(a)).to(t).pin_memory()
-    host = {"coords": pin(c.mesh.coords, torch.float64), "conn": pin(c.mesh.conn, torch.int32), "u": pin(c.u, dt)}
+    if kind == "adjoint" and c.physics != "laplacian":
+        raise ValueError("adjoint requests are Laplacian only")
+    values = {"coords": c.mesh.coords, "conn": c.mesh.conn, "u": c.u}
     if c.physics == "laplacian":
-        host["K"] = pin(c.K, dt)
+        values["K"] = c.K
     else:
-        host["lam"], host["mu"] = pin(c.lam, dt), pin(c.mu, dt)
+        values["lam"], values["mu"] = c.lam, c.mu
     if kind == "adjoint":
-        if c.physics != "laplacian":
-            raise ValueError("adjoint requests are Laplacian only")
-        a = c.adj if adj is None else adj
-        host["adj"] = pin(a if prec == "fp64" else np.asarray(a, dtype=np.float32), dt)
+        values["adj"] = c.adj if adj is None else adj
     r = Request(rid, kind, c.physics, c.dim, c.n_cells, c.n_verts, np.ascontiguousarray(c.rule.points),
-                np.ascontiguousarray(c.rule.weights), host, prec=prec, arrival=arrival)
+                np.ascontiguousarray(c.rule.weights), {}, prec=prec, arrival=arrival)
+    layout = r.device_arrays()[:len(values)]
+    assert [name for name, _, _ in layout] == list(values), "inputs lead the device layout"
+    r.input_bytes = sum((_nbytes(sh, t) + ALIGN - 1) // ALIGN * ALIGN for _, sh, t in layout)
+    r.host_block = torch.empty(max(1, r.input_bytes), dtype=torch.uint8, pin_memory=True)
+    off = 0
+    for name, shape, t in layout:
+        nb = _nbytes(shape, t)
+        view = r.host_block[off:off + nb].view(t).view(shape)
+        view.copy_(torch.from_numpy(np.ascontiguousarray(values[name])).to(t))
+        r.host[name] = view
+        off += (nb + ALIGN - 1) // ALIGN * ALIGN
     r.alloc_results()
     return r
 
@@ -193,8 +219,8 @@ def make_request(rid, case, kind, prec="mixed", arrival=0.0, adj=None) -> Reques
 
 
 class GpuExecutor:
-    """Runs admitted requests: one CUDA stream per slot, device arrays carved from one
-    preallocated buffer through the arena. Nothing is allocated per request."""
+    """Runs admitted requests: one CUDA stream per slot; each request's arrays are carved
+    from one arena block of the preallocated buffer. Nothing is allocated per request."""
 
     def __init__(self, device="cuda", capacity: int = 4 << 30, n_slots: int = 8):
         self.device = torch.device(device)
@@ -204,38 +230,45 @@ class GpuExecutor:
         self.free_slots = list(range(n_slots))
         self.inflight: Dict[int, tuple] = {}  # rid -> (req, slot, offsets, event)
         self.launches = 0
+        self.capacity = self.arena.capacity
 
     @property
     def n_slots(self) -> int:
         return len(self.streams)
 
     def fits_ever(self, req: Request) -> bool:
-        return footprint(req) <= self.arena.capacity
+        return footprint(req) <= self.capacity
+
+    def full(self) -> bool:
+        """No free slot: nothing can be admitted until a request completes."""
+        return not self.free_slots
 
     def try_admit(self, req: Request):
         if not self.free_slots:
             return None
-        offs = []
-        views = {}
+        # one arena block per request, its arrays carved at 256-byte boundaries
+        base = self.arena.alloc(footprint(req))
+        if base is None:
+            return None
+        views = {"_block": self.pool[base:base + footprint(req)]}
+        off = base
         for name, shape, dt in req.device_arrays():
             nb = _nbytes(shape, dt)
-            off = self.arena.alloc(nb)
-            if off is None:
-                for o in offs:
-                    self.arena.free(o)
-                return None
-            offs.append(off)
             views[name] = self.pool[off:off + nb].view(dt).view(shape) if nb else torch.empty(shape, dtype=dt,
                                                                                                 device=self.device)
+            off += (nb + ALIGN - 1) // ALIGN * ALIGN
         slot = self.free_slots.pop()
-        return slot, offs, views
+        return slot, [base], views
 
     def launch(self, req: Request, admitted) -> None:
         slot, offs, v = admitted
         s = self.streams[slot]
         with torch.cuda.stream(s):
-            for name, t in req.host.items():
-                v[name].copy_(t, non_blocking=True)
+            if req.host_block is not None:
+                v["_block"][:req.input_bytes].copy_(req.host_block[:req.input_bytes], non_blocking=True)
+            else:
+                for name, t in req.host.items():
+                    v[name].copy_(t, non_blocking=True)
             if req.kind == "residual":
                 if req.physics == "laplacian":
                     fem_integrate_laplacian(v["coords"], v["conn"], v["u"], v["K"], req.qpts, req.qw, out=v["out"],
@@ -311,24 +344,26 @@ class Scheduler:
         pending = collections.deque(sorted(requests, key=lambda r: r.arrival))
         queue: collections.deque = collections.deque()
         n, finished, max_inflight = len(requests), 0, 0
+        full = getattr(self.ex, "full", None)
         t0 = self.clock()
         while finished < n:
             now = self.clock()
             while pending and pending[0].arrival <= now - t0:
                 r = pending.popleft()
                 r.t_arrive = t0 + r.arrival
+                if not self.ex.fits_ever(r):  # can never run: rejected on arrival
+                    r.status, r.error = "rejected", "footprint exceeds the device arena"
+                    r.t_done = self.clock()
+                    finished += 1
+                    continue
                 r.status = "queued"
                 queue.append(r)
             progressed = False
             i = 0
             while i < len(queue):
+                if full is not None and full():
+                    break  # no slot: no request in the queue can be admitted now
                 r = queue[i]
-                if not self.ex.fits_ever(r):
-                    r.status, r.error = "rejected", "footprint exceeds the device arena"
-                    r.t_done = self.clock()
-                    del queue[i]
-                    finished += 1
-                    continue
                 adm = self.ex.try_admit(r)
                 if adm is not None:
                     del queue[i]
