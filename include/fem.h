@@ -379,6 +379,48 @@ int64_t fem_arena_largest_free(fem_arena *arena);
 int64_t fem_arena_capacity(fem_arena *arena);
 
 /* ---------------------------------------------------------------------------------
+ * Serving: the per-request launch of a continuous-batching loop (not in the paper).
+ * A request's device arrays live in one block (e.g. an fem_arena range of a caller-owned
+ * buffer); offset[] gives each array's byte offset in the block, indexed by the
+ * FEM_SERVE_* slots (unused slots are ignored). Its inputs (coords, conn, u, K or
+ * lambda and mu, adjoint weights) occupy the leading in_bytes of the block and are
+ * uploaded from host_in, a page-locked host block with the same layout.
+ *
+ * fem_serve_launch -- on `stream`: upload host_in (one copy), run the request's kernels
+ *   (kind 0: fem_integrate_laplacian or fem_integrate_elasticity; kind 1, Laplacian only:
+ *   fem_build_node2cell then fem_adjoint_laplacian), copy out_bytes[0] from slot OUT
+ *   (element vectors, or dK) to host_out[0] and out_bytes[1] from slot DU (du) to
+ *   host_out[1], then record `event` (from fem_serve_event_create). Returns after
+ *   enqueueing; errors as the entry points it calls.
+ * fem_serve_events_query -- done[i] = 1 if events[i] has completed, else 0.
+ * ------------------------------------------------------------------------------- */
+enum {
+    FEM_SERVE_COORDS = 0, FEM_SERVE_CONN = 1, FEM_SERVE_U = 2,
+    FEM_SERVE_K = 3,        /* K, or lambda for elasticity */
+    FEM_SERVE_MU = 4, FEM_SERVE_ADJ = 5,
+    FEM_SERVE_OUT = 6,      /* element vectors, or dK for the adjoint */
+    FEM_SERVE_DU = 7, FEM_SERVE_SCRATCH = 8, FEM_SERVE_NODE_PTR = 9, FEM_SERVE_NODE_IDX = 10,
+    FEM_SERVE_WORK = 11,    /* int32 workspace of fem_node2cell_work_size(n_verts) entries */
+    FEM_SERVE_SLOTS = 12
+};
+typedef struct {
+    int32_t kind;           /* 0 residual, 1 adjoint */
+    int32_t physics;        /* 0 Laplacian, 1 elasticity */
+    int32_t dim, n_q, prec, reserved;
+    int64_t n_cells, n_verts;
+    const double *qpts, *qw; /* host quadrature tables [n_q][dim], [n_q] */
+    const void *host_in;
+    int64_t in_bytes;
+    void *host_out[2];
+    int64_t out_bytes[2];
+    int64_t offset[FEM_SERVE_SLOTS];
+} fem_serve_request;
+fem_status fem_serve_event_create(void **event);
+void fem_serve_event_destroy(void *event);
+fem_status fem_serve_events_query(void *const *events, int n, int *done);
+fem_status fem_serve_launch(const fem_serve_request *request, void *block, void *event, fem_stream stream);
+
+/* ---------------------------------------------------------------------------------
  * Throughput probes for the roofline (not part of the method): each thread runs
  * `iters` iterations of 8 independent dependent chains of the chosen operation and
  * writes one value to out[thread] (float64 or float32 as the kind's type).

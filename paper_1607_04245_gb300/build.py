@@ -24,7 +24,7 @@ BUILD = os.path.join(PKG, "_build")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 SOURCES = ["fem_core.cu", "fem_laplacian.cu", "fem_elasticity.cu", "fem_mesh.cu", "fem_geometry.cu", "fem_reaction.cu",
            "fem_solver.cu", "fem_transpose.cu", "fem_host.cu", "fem_df.cu",
-           "fem_arena.cpp", "fem_noalloc.cu"]
+           "fem_arena.cpp", "fem_noalloc.cu", "fem_serve.cu"]
 
 
 def nvcc() -> str:

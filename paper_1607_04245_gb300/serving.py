@@ -11,8 +11,9 @@ Pieces:
   Arena           ctypes wrapper of libfem's host-side first-fit arena (fem_arena_*)
   Request         one evaluation with pinned host inputs and pinned host results
   footprint()     device bytes a request needs (every array rounded to 256 B)
-  GpuExecutor     carves a request's arrays out of one device buffer, launches the
-                  libfem kernels on the slot's stream, polls completion events
+  GpuExecutor     gives a request one arena block of a preallocated device buffer and
+                  launches it with one native call (fem_serve_launch: upload, kernels,
+                  download, event on the slot's stream); polls all events in one call
   Scheduler       the real-time admission loop (FIFO, optional backfill); it talks to
                   the executor through try_admit / launch / poll only
 """
@@ -31,8 +32,7 @@ import numpy as np
 import torch
 
 from . import binding
-from .binding import (fem_adjoint_laplacian, fem_build_node2cell, fem_integrate_elasticity, fem_integrate_laplacian,
-                      value_dtype)
+from .binding import value_dtype
 
 ALIGN = 256
 
@@ -97,6 +97,40 @@ class Arena:
             pass
 
 
+# ----------------------------------------------------------------------------- native launch
+
+SERVE_SLOTS = {"coords": 0, "conn": 1, "u": 2, "K": 3, "lam": 3, "mu": 4, "adj": 5, "out": 6, "dK": 6, "du": 7,
+               "scratch": 8, "node_ptr": 9, "node_idx": 10, "work": 11}
+
+
+class ServeRequestDesc(ctypes.Structure):
+    """ctypes mirror of fem_serve_request (include/fem.h)."""
+
+    _fields_ = [("kind", ctypes.c_int32), ("physics", ctypes.c_int32), ("dim", ctypes.c_int32),
+                ("n_q", ctypes.c_int32), ("prec", ctypes.c_int32), ("reserved", ctypes.c_int32),
+                ("n_cells", ctypes.c_int64), ("n_verts", ctypes.c_int64),
+                ("qpts", ctypes.c_void_p), ("qw", ctypes.c_void_p),
+                ("host_in", ctypes.c_void_p), ("in_bytes", ctypes.c_int64),
+                ("host_out", ctypes.c_void_p * 2), ("out_bytes", ctypes.c_int64 * 2),
+                ("offset", ctypes.c_int64 * 12)]
+
+
+def _serve_lib():
+    L = binding.lib()
+    if not getattr(L, "_serve_ready", False):
+        P = ctypes.c_void_p
+        L.fem_serve_event_create.argtypes = [ctypes.POINTER(P)]
+        L.fem_serve_event_create.restype = ctypes.c_int
+        L.fem_serve_event_destroy.argtypes = [P]
+        L.fem_serve_event_destroy.restype = None
+        L.fem_serve_events_query.argtypes = [ctypes.POINTER(P), ctypes.c_int, ctypes.POINTER(ctypes.c_int)]
+        L.fem_serve_events_query.restype = ctypes.c_int
+        L.fem_serve_launch.argtypes = [ctypes.POINTER(ServeRequestDesc), P, P, P]
+        L.fem_serve_launch.restype = ctypes.c_int
+        L._serve_ready = True
+    return L
+
+
 # ----------------------------------------------------------------------------- requests
 
 
@@ -123,6 +157,29 @@ class Request:
     _footprint: Optional[int] = dataclasses.field(default=None, repr=False, compare=False)
     host_block: Optional[torch.Tensor] = dataclasses.field(default=None, repr=False, compare=False)
     input_bytes: int = 0
+    _offsets: Optional[dict] = dataclasses.field(default=None, repr=False, compare=False)
+    desc: Optional[ServeRequestDesc] = dataclasses.field(default=None, repr=False, compare=False)
+
+    def build_desc(self) -> ServeRequestDesc:
+        """The request as the native launcher sees it (built once; the tensors it points
+        into are owned by the request)."""
+        d = ServeRequestDesc()
+        d.kind = 0 if self.kind == "residual" else 1
+        d.physics = 0 if self.physics == "laplacian" else 1
+        d.dim, d.n_q, d.prec = self.dim, int(self.qw.shape[0]), binding.precision(self.prec)
+        d.n_cells, d.n_verts = self.n_cells, self.n_verts
+        d.qpts, d.qw = self.qpts.ctypes.data, self.qw.ctypes.data
+        d.host_in = self.host_block.data_ptr() if self.host_block is not None else None
+        d.in_bytes = self.input_bytes
+        outs = ["out"] if self.kind == "residual" else ["dK", "du"]
+        for k, name in enumerate(outs):
+            t = self.result[name]
+            d.host_out[k] = t.data_ptr() if t.numel() else None
+            d.out_bytes[k] = t.numel() * t.element_size()
+        for name, off in self.offsets().items():
+            d.offset[SERVE_SLOTS[name]] = off
+        self.desc = d
+        return d
 
     @property
     def n_comp(self) -> int:
@@ -137,6 +194,15 @@ class Request:
         if self._arrays is None:
             self._arrays = self._device_arrays()
         return self._arrays
+
+    def offsets(self) -> Dict[str, int]:
+        """Byte offset of every array inside the request's device block (computed once)."""
+        if self._offsets is None:
+            off, self._offsets = 0, {}
+            for name, shape, dt in self.device_arrays():
+                self._offsets[name] = off
+                off += (_nbytes(shape, dt) + ALIGN - 1) // ALIGN * ALIGN
+        return self._offsets
 
     def _device_arrays(self):
         d, C, V, nq = self.dim, self.n_cells, self.n_verts, int(self.qw.shape[0])
@@ -212,6 +278,7 @@ def make_request(rid, case, kind, prec="mixed", arrival=0.0, adj=None) -> Reques
         r.host[name] = view
         off += (nb + ALIGN - 1) // ALIGN * ALIGN
     r.alloc_results()
+    r.build_desc()
     return r
 
 
@@ -219,8 +286,9 @@ def make_request(rid, case, kind, prec="mixed", arrival=0.0, adj=None) -> Reques
 
 
 class GpuExecutor:
-    """Runs admitted requests: one CUDA stream per slot; each request's arrays are carved
-    from one arena block of the preallocated buffer. Nothing is allocated per request."""
+    """Runs admitted requests: one CUDA stream and one completion event per slot; each
+    request's arrays sit in one arena block of the preallocated buffer, and its launch is
+    one native call. Nothing is allocated per request."""
 
     def __init__(self, device="cuda", capacity: int = 4 << 30, n_slots: int = 8):
         self.device = torch.device(device)
@@ -231,6 +299,15 @@ class GpuExecutor:
         self.inflight: Dict[int, tuple] = {}  # rid -> (req, slot, offsets, event)
         self.launches = 0
         self.capacity = self.arena.capacity
+        self.pool_ptr = self.pool.data_ptr()
+        self._L = _serve_lib()
+        self.events = []
+        for _ in range(n_slots):  # one completion event per slot, reused
+            e = ctypes.c_void_p()
+            st = self._L.fem_serve_event_create(ctypes.byref(e))
+            if st != 0:
+                raise binding.FemError("fem_serve_event_create", st, self._L.fem_last_error().decode())
+            self.events.append(e)
 
     @property
     def n_slots(self) -> int:
@@ -246,62 +323,52 @@ class GpuExecutor:
     def try_admit(self, req: Request):
         if not self.free_slots:
             return None
-        # one arena block per request, its arrays carved at 256-byte boundaries
+        # one arena block per request, its arrays at 256-byte boundaries (Request.offsets)
         base = self.arena.alloc(footprint(req))
         if base is None:
             return None
-        views = {"_block": self.pool[base:base + footprint(req)]}
-        off = base
-        for name, shape, dt in req.device_arrays():
-            nb = _nbytes(shape, dt)
-            views[name] = self.pool[off:off + nb].view(dt).view(shape) if nb else torch.empty(shape, dtype=dt,
-                                                                                                device=self.device)
-            off += (nb + ALIGN - 1) // ALIGN * ALIGN
-        slot = self.free_slots.pop()
-        return slot, [base], views
+        return self.free_slots.pop(), [base], base
 
     def launch(self, req: Request, admitted) -> None:
-        slot, offs, v = admitted
-        s = self.streams[slot]
-        with torch.cuda.stream(s):
-            if req.host_block is not None:
-                v["_block"][:req.input_bytes].copy_(req.host_block[:req.input_bytes], non_blocking=True)
-            else:
-                for name, t in req.host.items():
-                    v[name].copy_(t, non_blocking=True)
-            if req.kind == "residual":
-                if req.physics == "laplacian":
-                    fem_integrate_laplacian(v["coords"], v["conn"], v["u"], v["K"], req.qpts, req.qw, out=v["out"],
-                                            prec=req.prec, stream=s)
-                else:
-                    fem_integrate_elasticity(v["coords"], v["conn"], v["u"], v["lam"], v["mu"], req.qpts, req.qw,
-                                             out=v["out"], prec=req.prec, stream=s)
-                req.result["out"].copy_(v["out"], non_blocking=True)
-                self.launches += 1
-            else:
-                fem_build_node2cell(v["conn"], req.n_verts, node_ptr=v["node_ptr"], node_idx=v["node_idx"],
-                                    work=v["work"], stream=s)
-                fem_adjoint_laplacian(v["coords"], v["conn"], v["u"], v["K"], req.qpts, req.qw, v["adj"],
-                                      v["node_ptr"], v["node_idx"], dK=v["dK"], du=v["du"], scratch=v["scratch"],
-                                      prec=req.prec, stream=s)
-                req.result["dK"].copy_(v["dK"], non_blocking=True)
-                req.result["du"].copy_(v["du"], non_blocking=True)
-                self.launches += 9  # list build (count, 3 scan passes, copy, fill, sort) + element + gather
-            ev = torch.cuda.Event()
-            ev.record(s)
-        self.inflight[req.rid] = (req, slot, offs, ev)
+        """Upload, kernels, download and completion event of one request on its slot's
+        stream: one native call (fem_serve_launch) with pointers into the request's block."""
+        slot, offs, base = admitted
+        desc = req.desc if req.desc is not None else req.build_desc()
+        st = self._L.fem_serve_launch(ctypes.byref(desc), ctypes.c_void_p(self.pool_ptr + base), self.events[slot],
+                                      ctypes.c_void_p(self.streams[slot].cuda_stream))
+        if st != 0:
+            self.arena.free(base)
+            self.free_slots.append(slot)
+            raise binding.FemError("fem_serve_launch", st, self._L.fem_last_error().decode())
+        self.launches += 1 if req.kind == "residual" else 9  # adjoint: list build (7 kernels) + element + gather
+        self.inflight[req.rid] = (req, slot, offs, None)
 
     def poll(self) -> List[Request]:
-        done = []
-        for rid in list(self.inflight):
-            req, slot, offs, ev = self.inflight[rid]
-            if ev.query():
+        if not self.inflight:
+            return []
+        rids = list(self.inflight)
+        n = len(rids)
+        evs = (ctypes.c_void_p * n)(*[self.events[self.inflight[r][1]] for r in rids])
+        done = (ctypes.c_int * n)()
+        st = self._L.fem_serve_events_query(evs, n, done)
+        if st != 0:
+            raise binding.FemError("fem_serve_events_query", st, self._L.fem_last_error().decode())
+        out = []
+        for k, rid in enumerate(rids):
+            if done[k]:
+                req, slot, offs, _ = self.inflight.pop(rid)
                 for o in offs:
                     self.arena.free(o)
                 self.free_slots.append(slot)
-                del self.inflight[rid]
-                done.append(req)
-        return done
+                out.append(req)
+        return out
+
+    def __del__(self):
+        try:
+            for e in getattr(self, "events", []):
+                self._L.fem_serve_event_destroy(e)
+        except Exception:
+            pass
 
     def busy(self) -> bool:
         return bool(self.inflight)
