@@ -611,7 +611,8 @@ def measure_serving(device, n_requests, seed=0):
     """Serving stream: n requests (residual or adjoint, 2D/3D Laplacian and elasticity,
     log-uniform 1e3..1e6 cells, fresh seeded meshes), FP32-mixed. First all requests at
     t = 0 (saturation: the service capacity in requests/s), then Poisson arrivals at
-    85% of that capacity; p50/p99 latency from arrival to observed completion."""
+    85% of that capacity; p50/p99 latency from arrival to observed completion. Each
+    stream runs three times; the median run is reported beside all three."""
     from paper_1607_04245_gb300.serving import GpuExecutor, Scheduler, make_request, poisson_arrivals
 
     t_gen = time.time()
@@ -627,12 +628,20 @@ def measure_serving(device, n_requests, seed=0):
     warm = reqs[:8]
     reset([0.0] * len(reqs))
     Scheduler(ex).run(warm)
-    reset([0.0] * len(reqs))
-    sat = Scheduler(ex).run(reqs)
+    # the loop is host-bound and the host is shared, so each stream is run three times
+    # and the run with the median rate (saturation) or median p99 (Poisson) is reported
+    sats = []
+    for _ in range(3):
+        reset([0.0] * len(reqs))
+        sats.append(Scheduler(ex).run(reqs))
+    sat = sorted(sats, key=lambda x: x.req_per_s)[1]
     rate = 0.85 * sat.req_per_s
-    reset(poisson_arrivals(len(reqs), rate, seed=seed + 1))
-    ex.launches = 0
-    st = Scheduler(ex).run(reqs, arrival_rate=rate)
+    runs = []
+    for k in range(3):
+        reset(poisson_arrivals(len(reqs), rate, seed=seed + 1))
+        ex.launches = 0
+        runs.append(Scheduler(ex).run(reqs, arrival_rate=rate))
+    st = sorted(runs, key=lambda x: x.p99_ms)[1]
     kinds = {}
     for sp in specs:
         k = f"{sp['physics']}{sp['dim']}d_{sp['kind']}"
@@ -640,11 +649,12 @@ def measure_serving(device, n_requests, seed=0):
     return {"requests": n_requests, "generation_s": round(t_gen, 2), "mix": kinds,
             "arena_bytes": ex.arena.capacity, "slots": ex.n_slots,
             "saturation": {"req_per_s": sat.req_per_s, "cells_per_s": sat.cells_per_s, "p50_ms": sat.p50_ms,
-                           "p99_ms": sat.p99_ms, "makespan_s": sat.makespan_s},
+                           "p99_ms": sat.p99_ms, "makespan_s": sat.makespan_s,
+                           "req_per_s_of_3_runs": sorted(x.req_per_s for x in sats)},
             "poisson": {"arrival_rate_req_per_s": rate, "req_per_s": st.req_per_s, "cells_per_s": st.cells_per_s,
                         "p50_ms": st.p50_ms, "p99_ms": st.p99_ms, "mean_ms": st.mean_ms,
                         "max_inflight": st.max_inflight, "rejected": st.n_rejected, "makespan_s": st.makespan_s,
-                        "cells": st.cells}}
+                        "cells": st.cells, "p99_ms_of_3_runs": sorted(x.p99_ms for x in runs)}}
 
 
 def cpu_model() -> str:

@@ -23,6 +23,7 @@ from __future__ import annotations
 import collections
 import ctypes
 import dataclasses
+import gc
 import math
 import statistics
 import time
@@ -401,13 +402,25 @@ class Scheduler:
     passes and are admitted whenever a slot and enough arena memory are free; with
     backfill, a later request that fits may overtake a head that does not."""
 
-    def __init__(self, executor, backfill: bool = True, clock=time.perf_counter, idle_sleep: float = 20e-6):
+    def __init__(self, executor, backfill: bool = True, clock=time.perf_counter, idle_sleep: float = 0.0):
         self.ex = executor
         self.backfill = backfill
         self.clock = clock
         self.idle_sleep = idle_sleep
 
     def run(self, requests: List[Request], arrival_rate: float = math.nan) -> ServeStats:
+        # a real-time loop: Python's cyclic garbage collector is paused while it runs (its
+        # full passes over a large heap would stall admissions for milliseconds)
+        gc_was_enabled = gc.isenabled()
+        gc.collect()
+        gc.disable()
+        try:
+            return self._run(requests, arrival_rate)
+        finally:
+            if gc_was_enabled:
+                gc.enable()
+
+    def _run(self, requests: List[Request], arrival_rate: float) -> ServeStats:
         pending = collections.deque(sorted(requests, key=lambda r: r.arrival))
         queue: collections.deque = collections.deque()
         n, finished, max_inflight = len(requests), 0, 0
@@ -453,8 +466,10 @@ class Scheduler:
                     wait = pending[0].arrival - (self.clock() - t0)
                     if wait > 0:
                         time.sleep(min(wait, 1e-3))
-                else:
+                elif self.idle_sleep > 0:
                     time.sleep(self.idle_sleep)
+                # idle_sleep = 0: poll again at once (a short sleep costs the timer slack,
+                # ~50 us on Linux, on every completion)
         t1 = self.clock()
         done = [r for r in requests if r.status == "done"]
         lat = sorted(r.latency * 1e3 for r in done) or [math.nan]
