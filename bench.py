@@ -610,9 +610,10 @@ def measure_e2e(case, prec, device, steps, warmup):
 def measure_serving(device, n_requests, seed=0):
     """Serving stream: n requests (residual or adjoint, 2D/3D Laplacian and elasticity,
     log-uniform 1e3..1e6 cells, fresh seeded meshes), FP32-mixed. First all requests at
-    t = 0 (saturation: the service capacity in requests/s), then Poisson arrivals at
-    85% of that capacity; p50/p99 latency from arrival to observed completion. Each
-    stream runs three times; the median run is reported beside all three."""
+    t = 0 (saturation: the service capacity in requests/s), then Poisson arrivals at the
+    highest of 85/70/55/40 % of that capacity whose backlog stays bounded; p50/p99 latency
+    from arrival to observed completion. Each stream runs three times; the median run is
+    reported beside all three."""
     from paper_1607_04245_gb300.serving import GpuExecutor, Scheduler, make_request, poisson_arrivals
 
     t_gen = time.time()
@@ -625,23 +626,36 @@ def measure_serving(device, n_requests, seed=0):
         for r, a in zip(reqs, arrivals):
             r.arrival, r.status = float(a), "pending"
 
-    warm = reqs[:8]
+    # warm-up: every request once (the first device access to each pinned host block is
+    # slower than the later ones)
     reset([0.0] * len(reqs))
-    Scheduler(ex).run(warm)
+    Scheduler(ex).run(reqs)
     # the loop is host-bound and the host is shared, so each stream is run three times
-    # and the run with the median rate (saturation) or median p99 (Poisson) is reported
+    # and the median run is reported
     sats = []
     for _ in range(3):
         reset([0.0] * len(reqs))
         sats.append(Scheduler(ex).run(reqs))
     sat = sorted(sats, key=lambda x: x.req_per_s)[1]
-    rate = 0.85 * sat.req_per_s
-    runs = []
-    for k in range(3):
-        reset(poisson_arrivals(len(reqs), rate, seed=seed + 1))
-        ex.launches = 0
-        runs.append(Scheduler(ex).run(reqs, arrival_rate=rate))
-    st = sorted(runs, key=lambda x: x.p99_ms)[1]
+    # sustained rate: the highest of 85/70/55/40 % of the saturation rate at which the
+    # backlog stays bounded (served rate within 3 % of the offered rate in the median run)
+    sweep, st, rate = [], None, None
+    for frac in (0.85, 0.70, 0.55, 0.40):
+        r_off = frac * sat.req_per_s
+        runs = []
+        for _ in range(3):
+            reset(poisson_arrivals(len(reqs), r_off, seed=seed + 1))
+            ex.launches = 0
+            runs.append(Scheduler(ex).run(reqs, arrival_rate=r_off))
+        med = sorted(runs, key=lambda x: x.p99_ms)[1]
+        sweep.append({"fraction": frac, "offered_req_per_s": r_off, "served_req_per_s": med.req_per_s,
+                      "p50_ms": med.p50_ms, "p99_ms": med.p99_ms,
+                      "p99_ms_of_3_runs": sorted(x.p99_ms for x in runs)})
+        if med.req_per_s >= 0.97 * r_off:
+            st, rate = med, r_off
+            break
+    if st is None:
+        st, rate = med, r_off
     kinds = {}
     for sp in specs:
         k = f"{sp['physics']}{sp['dim']}d_{sp['kind']}"
@@ -654,7 +668,8 @@ def measure_serving(device, n_requests, seed=0):
             "poisson": {"arrival_rate_req_per_s": rate, "req_per_s": st.req_per_s, "cells_per_s": st.cells_per_s,
                         "p50_ms": st.p50_ms, "p99_ms": st.p99_ms, "mean_ms": st.mean_ms,
                         "max_inflight": st.max_inflight, "rejected": st.n_rejected, "makespan_s": st.makespan_s,
-                        "cells": st.cells, "p99_ms_of_3_runs": sorted(x.p99_ms for x in runs)}}
+                        "cells": st.cells, "p99_ms_of_3_runs": sweep[-1]["p99_ms_of_3_runs"]},
+            "rate_sweep": sweep}
 
 
 def cpu_model() -> str:
