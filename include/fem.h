@@ -415,6 +415,7 @@ typedef struct {
     int64_t out_bytes[2];
     int64_t offset[FEM_SERVE_SLOTS];
 } fem_serve_request;
+int64_t fem_serve_request_bytes(void); /* sizeof(fem_serve_request), for bindings to check their layout */
 fem_status fem_serve_event_create(void **event);
 void fem_serve_event_destroy(void *event);
 fem_status fem_serve_events_query(void *const *events, int n, int *done);

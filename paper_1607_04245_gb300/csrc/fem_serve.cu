@@ -10,6 +10,8 @@
 
 using namespace fem;
 
+extern "C" int64_t fem_serve_request_bytes(void) { return static_cast<int64_t>(sizeof(fem_serve_request)); }
+
 extern "C" fem_status fem_serve_event_create(void **event) {
     if (!event) return fail(FEM_ERR_ARG, "event is NULL");
     cudaEvent_t e = nullptr;

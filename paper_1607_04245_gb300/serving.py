@@ -128,6 +128,10 @@ def _serve_lib():
         L.fem_serve_events_query.restype = ctypes.c_int
         L.fem_serve_launch.argtypes = [ctypes.POINTER(ServeRequestDesc), P, P, P]
         L.fem_serve_launch.restype = ctypes.c_int
+        L.fem_serve_request_bytes.argtypes = []
+        L.fem_serve_request_bytes.restype = ctypes.c_int64
+        if L.fem_serve_request_bytes() != ctypes.sizeof(ServeRequestDesc):
+            raise RuntimeError("fem_serve_request layout differs between libfem and this binding")
         L._serve_ready = True
     return L
 

@@ -124,3 +124,25 @@ def test_host_work_bytes(lib):
     assert lib.fem_host_work_bytes(dim, C, V, nq, 1, -1) == -1
     assert lib.fem_host_work_bytes(4, C, V, nq, 1, 1) == -1
     assert lib.fem_host_work_bytes(dim, C, V, 0, 1, 1) == -1
+
+
+def test_serve_launch_validation(lib):
+    """Host-side checks of the serving launcher (no CUDA call is reached)."""
+    from paper_1607_04245_gb300.serving import ServeRequestDesc
+
+    P = ctypes.c_void_p
+    lib.fem_serve_launch.argtypes = [ctypes.POINTER(ServeRequestDesc), P, P, P]
+    lib.fem_serve_launch.restype = ctypes.c_int
+    lib.fem_serve_events_query.argtypes = [ctypes.POINTER(P), ctypes.c_int, ctypes.POINTER(ctypes.c_int)]
+    lib.fem_serve_events_query.restype = ctypes.c_int
+    fake = P(0x1000)  # never dereferenced
+    assert lib.fem_serve_launch(None, fake, fake, None) == -1
+    d = ServeRequestDesc()
+    d.kind = 2
+    assert lib.fem_serve_launch(ctypes.byref(d), fake, fake, None) == -1
+    d.kind, d.physics = 1, 1  # adjoint of elasticity
+    assert lib.fem_serve_launch(ctypes.byref(d), fake, fake, None) == -7
+    assert lib.fem_serve_events_query(None, 0, None) == 0
+    assert lib.fem_serve_events_query(None, 1, None) == -1
+    lib.fem_serve_request_bytes.restype = ctypes.c_int64
+    assert lib.fem_serve_request_bytes() == ctypes.sizeof(ServeRequestDesc) == 200
