@@ -4,8 +4,6 @@
 // event, all on the request's stream; a second call tests many completion events at
 // once. The host-side scheduler (arrival, admission by arena footprint, statistics) stays
 // above the C ABI; what it calls per request is these two functions.
-#include <new>
-
 #include "fem_internal.cuh"
 
 using namespace fem;
