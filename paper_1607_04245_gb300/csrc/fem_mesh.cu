@@ -123,11 +123,31 @@ __global__ void fill_kernel(const int32_t *conn, int64_t C, uint32_t V, int32_t 
 }
 
 // per-vertex insertion sort: the list order becomes cell order, independent of the
-// order in which the atomics above landed
+// order in which the atomics above landed. Lists of up to kSortLocal entries (every
+// vertex of the workloads' meshes: 6 in 2D, up to 24 in 3D) are sorted in a per-thread
+// array and written back once; longer ones in place.
+constexpr int kSortLocal = 32;
+
 __global__ void sort_segments_kernel(const int32_t *ptr, int32_t *idx, int64_t V) {
     const int64_t stride = int64_t(gridDim.x) * blockDim.x;
     for (int64_t n = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; n < V; n += stride) {
         const int32_t b = ptr[n], e = ptr[n + 1];
+        if (e - b <= kSortLocal) {
+            int32_t t[kSortLocal];
+            const int m = e - b;
+            for (int i = 0; i < m; ++i) t[i] = idx[b + i];
+            for (int i = 1; i < m; ++i) {
+                const int32_t x = t[i];
+                int j = i - 1;
+                while (j >= 0 && t[j] > x) {
+                    t[j + 1] = t[j];
+                    --j;
+                }
+                t[j + 1] = x;
+            }
+            for (int i = 0; i < m; ++i) idx[b + i] = t[i];
+            continue;
+        }
         for (int32_t i = b + 1; i < e; ++i) {
             int32_t x = idx[i], j = i - 1;
             while (j >= b && idx[j] > x) {
