@@ -872,10 +872,10 @@ def run_ours(args):
         rows["lap2d_8192_fp64"] = measure_residual(workloads.laplacian_square_case(), "fp64", device, stream, flush,
                                                    rsteps, args.warmup, peak, oracle)[0]
     for dim in (2, 3):
-        if not any(want(f"elast{dim}d_{prec}") for prec in ("mixed", "fp64")):
+        if not any(want(f"elast{dim}d_{prec}") for prec in ("mixed", "fp64", "fp64_df")):
             continue
         el = workloads.elasticity_case(dim)
-        for prec in ("mixed", "fp64"):
+        for prec in ("mixed", "fp64", "fp64_df"):
             if want(f"elast{dim}d_{prec}"):
                 rows[f"elast{dim}d_{prec}"] = measure_residual(el, prec, device, stream, flush, rsteps, args.warmup,
                                                                peak, oracle)[0]

@@ -186,4 +186,139 @@ fem_status launch_lap_df(int dim, int64_t n_cells, int64_t n_verts, const double
     return check_launch("fem_integrate_laplacian (FEM_FP64_DF)");
 }
 
+// ---- linear elasticity in the same form: f1 = lambda tr(eps) I + 2 mu eps. With the
+// adjugate rows n_j and H[k][i] = sum_j (u_{j,k} - u_{0,k}) n_j[i] (grad u = H / det J):
+//     T = Lbar tr(H) I + Mbar (H + H^T),  r_{b,k} = (T n_b)_k / |det J|,
+// r_0 = -(r_1 + ... + r_d) per component; Lbar, Mbar the weighted sums of lambda and mu.
+
+struct DfElArgs {
+    const double *X[3];
+    const int32_t *conn;
+    const double *u, *lam, *mu;  // u [dim][V]; lam, mu [n_q][C]
+    double *out;                 // [(dim+1)*dim][C]
+    int64_t C;
+    uint32_t V;
+    int nq;
+    float whi[FEM_MAX_QPTS], wlo[FEM_MAX_QPTS];
+};
+
+template <int DIM>
+__global__ void __launch_bounds__(kBlock) el_df_kernel(const __grid_constant__ DfElArgs a) {
+    constexpr int NB = DIM + 1;
+    const int64_t C = a.C;
+    const int64_t V = a.V;
+    const double *X[DIM];
+#pragma unroll
+    for (int k = 0; k < DIM; ++k) X[k] = a.X[k];
+    const int64_t stride = int64_t(gridDim.x) * blockDim.x;
+    for (int64_t c = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; c < C; c += stride) {
+        uint32_t v[NB];
+#pragma unroll
+        for (int b = 0; b < NB; ++b) v[b] = clamp_vid(ld_stream(a.conn + b * C + c), a.V);
+        // Lbar = sum_q w_q lambda_q, Mbar = sum_q w_q mu_q
+        dfl lbar = df_mul(dfl{a.whi[0], a.wlo[0]}, df_from_double(ld_stream(a.lam + c)));
+        dfl mbar = df_mul(dfl{a.whi[0], a.wlo[0]}, df_from_double(ld_stream(a.mu + c)));
+        for (int q = 1; q < a.nq; ++q) {
+            const dfl w{a.whi[q], a.wlo[q]};
+            lbar = df_add(lbar, df_mul(w, df_from_double(ld_stream(a.lam + q * C + c))));
+            mbar = df_add(mbar, df_mul(w, df_from_double(ld_stream(a.mu + q * C + c))));
+        }
+        // Jacobian columns in float64, then pairs
+        double xs[NB][DIM];
+        gather_coords<DIM>(X, v, xs);
+        dfl e[DIM][DIM];
+#pragma unroll
+        for (int j = 0; j < DIM; ++j)
+#pragma unroll
+            for (int k = 0; k < DIM; ++k) e[j][k] = df_from_double(xs[j + 1][k] - xs[0][k]);
+        dfl n[DIM][DIM], det;
+        if constexpr (DIM == 2) {
+            n[0][0] = e[1][1], n[0][1] = df_neg(e[1][0]);
+            n[1][0] = df_neg(e[0][1]), n[1][1] = e[0][0];
+            det = df_sub(df_mul(e[0][0], e[1][1]), df_mul(e[0][1], e[1][0]));
+        } else {
+#pragma unroll
+            for (int j = 0; j < 3; ++j) {
+                const dfl *p = e[(j + 1) % 3], *q = e[(j + 2) % 3];
+                n[j][0] = df_sub(df_mul(p[1], q[2]), df_mul(p[2], q[1]));
+                n[j][1] = df_sub(df_mul(p[2], q[0]), df_mul(p[0], q[2]));
+                n[j][2] = df_sub(df_mul(p[0], q[1]), df_mul(p[1], q[0]));
+            }
+            det = df_add(df_add(df_mul(e[0][0], n[0][0]), df_mul(e[0][1], n[0][1])), df_mul(e[0][2], n[0][2]));
+        }
+        // H[k][i] = sum_j (u_{j,k} - u_{0,k}) n_j[i]
+        dfl H[DIM][DIM];
+#pragma unroll
+        for (int k = 0; k < DIM; ++k) {
+            dfl u0 = df_from_double(ld_gather(a.u + k * V + v[0]));
+#pragma unroll
+            for (int i = 0; i < DIM; ++i) H[k][i] = dfl{0.0f, 0.0f};
+#pragma unroll
+            for (int j = 0; j < DIM; ++j) {
+                const dfl du = df_sub(df_from_double(ld_gather(a.u + k * V + v[j + 1])), u0);
+#pragma unroll
+                for (int i = 0; i < DIM; ++i) H[k][i] = df_add(H[k][i], df_mul(du, n[j][i]));
+            }
+        }
+        dfl tr = H[0][0];
+#pragma unroll
+        for (int k = 1; k < DIM; ++k) tr = df_add(tr, H[k][k]);
+        const dfl inv = df_div(dfl{1.0f, 0.0f}, df_abs(det));
+        const dfl ltr = df_mul(lbar, tr);
+        dfl Tm[DIM][DIM];
+#pragma unroll
+        for (int k = 0; k < DIM; ++k)
+#pragma unroll
+            for (int i = 0; i < DIM; ++i) {
+                dfl t = df_mul(mbar, df_add(H[k][i], H[i][k]));
+                if (k == i) t = df_add(t, ltr);
+                Tm[k][i] = df_mul(inv, t);
+            }
+        dfl r0[DIM];
+#pragma unroll
+        for (int k = 0; k < DIM; ++k) r0[k] = dfl{0.0f, 0.0f};
+#pragma unroll
+        for (int b = 1; b <= DIM; ++b)
+#pragma unroll
+            for (int k = 0; k < DIM; ++k) {
+                dfl rb = df_mul(Tm[k][0], n[b - 1][0]);
+#pragma unroll
+                for (int i = 1; i < DIM; ++i) rb = df_add(rb, df_mul(Tm[k][i], n[b - 1][i]));
+                r0[k] = df_sub(r0[k], rb);
+                __stcs(a.out + (b * DIM + k) * C + c, df_to_double(rb));
+            }
+#pragma unroll
+        for (int k = 0; k < DIM; ++k) __stcs(a.out + k * C + c, df_to_double(r0[k]));
+    }
+}
+
+// called by fem_integrate_elasticity for FEM_FP64_DF (arguments already validated there)
+fem_status launch_el_df(int dim, int64_t n_cells, int64_t n_verts, const double *coords, const int32_t *conn,
+                        const void *u, const void *lam, const void *mu, int n_q, const double *qw, void *elem_out,
+                        cudaStream_t stream) {
+    DfElArgs a;
+    for (int k = 0; k < 3; ++k) a.X[k] = coords + (k < dim ? k : 0) * n_verts;
+    a.conn = conn;
+    a.u = static_cast<const double *>(u);
+    a.lam = static_cast<const double *>(lam);
+    a.mu = static_cast<const double *>(mu);
+    a.out = static_cast<double *>(elem_out);
+    a.C = n_cells;
+    a.V = static_cast<uint32_t>(n_verts);
+    a.nq = n_q;
+    for (int q = 0; q < FEM_MAX_QPTS; ++q) {
+        const double w = q < n_q ? qw[q] : 0.0;
+        a.whi[q] = static_cast<float>(w);
+        a.wlo[q] = static_cast<float>(w - static_cast<double>(a.whi[q]));
+    }
+    if (dim == 2) {
+        auto k = el_df_kernel<2>;
+        k<<<grid_for(n_cells, kBlock, reinterpret_cast<const void *>(k)), kBlock, 0, stream>>>(a);
+    } else {
+        auto k = el_df_kernel<3>;
+        k<<<grid_for(n_cells, kBlock, reinterpret_cast<const void *>(k)), kBlock, 0, stream>>>(a);
+    }
+    return check_launch("fem_integrate_elasticity (FEM_FP64_DF)");
+}
+
 }  // namespace fem

@@ -201,19 +201,27 @@ static fem_status launch_el(const ElArgs &a, bool vec, cudaStream_t s) {
 
 using namespace fem;
 
+namespace fem {
+fem_status launch_el_df(int dim, int64_t n_cells, int64_t n_verts, const double *coords, const int32_t *conn,
+                        const void *u, const void *lam, const void *mu, int n_q, const double *qw, void *elem_out,
+                        cudaStream_t stream);
+}
+
 extern "C" fem_status fem_integrate_elasticity(int dim, int64_t n_cells, int64_t n_verts, const double *coords,
                                                const int32_t *conn, const void *u, const void *lam, const void *mu,
                                                int n_q, const double *qpts, const double *qw, void *elem_out,
                                                fem_precision prec, fem_stream stream) {
     fem_status st = check_common(dim, n_cells, n_verts, coords, conn);
     if (st != FEM_OK) return st;
-    if (prec != FEM_FP64 && prec != FEM_FP32_MIXED && prec != FEM_FP32)
+    if (prec != FEM_FP64 && prec != FEM_FP32_MIXED && prec != FEM_FP32 && prec != FEM_FP64_DF)
         return fail(FEM_ERR_ARG, "unknown precision %d", static_cast<int>(prec));
     if (int64_t(dim) * n_verts >= (int64_t(1) << 31)) return fail(FEM_ERR_SHAPE, "too many vertices");
     ElArgs a;
     if ((st = load_quadrature(dim, n_q, qpts, qw, a.w)) != FEM_OK) return st;
     if (n_cells == 0) return FEM_OK;
     if (!u || !lam || !mu || !elem_out) return fail(FEM_ERR_ARG, "u, lam, mu or elem_out is NULL");
+    if (prec == FEM_FP64_DF) return launch_el_df(dim, n_cells, n_verts, coords, conn, u, lam, mu, n_q, qw, elem_out,
+                                                 stream);
     for (int k = 0; k < 3; ++k) a.X[k] = coords + (k < dim ? k : 0) * n_verts;
     a.conn = conn;
     a.u = u;

@@ -1,7 +1,7 @@
-"""The float64-values, float32-pair-arithmetic form (FEM_FP64_DF) of the Laplacian residual
-against the oracle at the float64 tolerance, including the fine 2048 x 1024 grid where the
-Jacobian columns are 2^11 times smaller than the coordinates, inverted and skinny cells,
-and ragged sizes."""
+"""The float64-values, float32-pair-arithmetic form (FEM_FP64_DF) of the Laplacian and
+elasticity residuals against the oracle at the float64 tolerance, including the fine
+2048 x 1024 grid where the Jacobian columns are 2^11 times smaller than the coordinates,
+inverted and skinny cells, ragged sizes, and rigid motions."""
 
 import numpy as np
 import pytest
@@ -62,9 +62,59 @@ def test_df_ragged(n_cells):
     assert _res(case) <= TOL
 
 
-def test_df_is_laplacian_only():
-    case = workloads.elasticity_case(2, 512)
+def test_df_refused_where_not_offered():
+    """The reaction-diffusion entry has no double-float form: an argument error."""
+    case = workloads.laplacian_square_case(8)
     c, d = device_arrays(case, "fp64")
+    a = torch.ones(c.n_verts, dtype=torch.float64, device="cuda")
     with pytest.raises(fem.FemError):
-        fem.fem_integrate_elasticity(d["coords"], d["conn"], d["u"], d["lam"], d["mu"], c.rule.points,
+        fem.fem_integrate_reaction_diffusion(d["coords"], d["conn"], d["u"], a, c.rule.points, c.rule.weights,
+                                             prec="fp64_df")
+
+
+# ---- linear elasticity in the double-float form
+
+
+def _el_res(case):
+    c, d = device_arrays(case, "fp64")
+    r = fem.fem_integrate_elasticity(d["coords"], d["conn"], d["u"], d["lam"], d["mu"], c.rule.points,
                                      c.rule.weights, prec="fp64_df")
+    return r, rel_err(r, oracle.residual_for(c))
+
+
+@pytest.mark.parametrize("dim", [2, 3])
+def test_df_elasticity_full_size(dim):
+    """2^22 triangles / 2^21 tets, per-point Lame coefficients, against the oracle."""
+    r, err = _el_res(workloads.elasticity_case(dim))
+    assert err <= TOL, err
+
+
+@pytest.mark.parametrize("dim", [2, 3])
+@pytest.mark.parametrize("n_cells", [1, 3, 5, 1027])
+def test_df_elasticity_ragged(dim, n_cells):
+    base = workloads.elasticity_case(dim, 2 * 32 * 32 if dim == 2 else 6 * 12 ** 3)
+    mesh = workloads.first_cells(base.mesh, n_cells)
+    case = workloads.Case("elasticity", mesh, base.rule, base.u[:, : mesh.n_verts].copy(),
+                          lam=base.lam[:, :n_cells].copy(), mu=base.mu[:, :n_cells].copy())
+    assert _el_res(case)[1] <= TOL
+
+
+@pytest.mark.parametrize("dim", [2, 3])
+def test_df_elasticity_rigid_motions_and_sums(dim):
+    """Rigid motions give zero element vectors; every component's entries sum to zero."""
+    case = workloads.elasticity_case(dim, 2 * 32 * 32 if dim == 2 else 6 * 12 ** 3)
+    x = case.mesh.coords
+    if dim == 2:
+        U = np.stack([0.3 - 0.7 * x[1], -1.1 + 0.7 * x[0]])
+    else:
+        w = np.array([0.2, -0.5, 0.9])
+        U = np.array([0.1, 0.2, -0.3])[:, None] + np.cross(w, x.T).T
+    rigid = workloads.Case("elasticity", case.mesh, case.rule, U, lam=case.lam, mu=case.mu)
+    r, _ = _el_res(rigid)
+    # scale: the element vectors of a pure stretch of the same magnitude (u = x)
+    stretch = workloads.Case("elasticity", case.mesh, case.rule, x.copy(), lam=case.lam, mu=case.mu)
+    scale = np.abs(oracle.residual_for(stretch)).max()
+    assert r.abs().max().item() <= TOL * scale
+    r2, _ = _el_res(case)
+    sums = r2.view(dim + 1, dim, -1).sum(0).abs().max().item()
+    assert sums <= 1e-14 * r2.abs().max().item()
