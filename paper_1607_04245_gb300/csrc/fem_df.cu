@@ -1,9 +1,9 @@
-// fem_df.cu -- the Laplacian element residual with float64 values and float64-class
-// accuracy computed on the float32 pipe (FEM_FP64_DF).
+// fem_df.cu -- the Laplacian and linear-elasticity element residuals with float64 values
+// and float64-class accuracy computed on the float32 pipe (FEM_FP64_DF).
 //
 // GB300 executes float32 FMAs ~68x faster than float64 ones (0.53 T float64 FMA/s
-// against 35.9 T float32 FMA/s measured), so the float64 form of this kernel is bound by
-// the float64 pipe. This form keeps the inputs and outputs in float64 but carries every
+// against 35.9 T float32 FMA/s measured), so the float64 forms of these kernels are bound
+// by the float64 pipe. This form keeps the inputs and outputs in float64 but carries every
 // intermediate as an unevaluated pair of float32 values (hi + lo, a 47- to 48-bit
 // significand; Dekker's double-length arithmetic built from TwoSum / TwoProduct):
 //   * the Jacobian columns e_j = x_j - x_0 are formed in float64 (correctly rounded, no
@@ -13,7 +13,8 @@
 //     contraction run in pair arithmetic;
 //   * each element-vector entry is widened back to float64 (integer operations) and
 //     summed with one float64 add.
-// Per cell this issues 13 float64 additions instead of ~71 float64 operations. The
+// Per cell (3D Laplacian) this issues 13 float64 additions instead of ~71 float64
+// operations (elasticity: 21, the columns and 12 outputs). The
 // relative error against the exact element integral stays near 1e-14 on the workloads
 // (validated against the oracle at the float64 tolerance, 1e-12).
 #include "fem_cell.cuh"
