@@ -16,6 +16,8 @@ Pieces:
                   download, event on the slot's stream); polls all events in one call
   Scheduler       the real-time admission loop (FIFO, optional backfill); it talks to
                   the executor through try_admit / launch / poll only
+  request_log()   the served stream as records; save_request_log / replay_arrivals
+                  store it and serve the same arrivals again
 """
 
 from __future__ import annotations
@@ -295,8 +297,9 @@ class GpuExecutor:
     request's arrays sit in one arena block of the preallocated buffer, and its launch is
     one native call. Nothing is allocated per request."""
 
-    def __init__(self, device="cuda", capacity: int = 4 << 30, n_slots: int = 8):
+    def __init__(self, device="cuda", capacity: int = 4 << 30, n_slots: int = 8, nvtx: bool = False):
         self.device = torch.device(device)
+        self.nvtx = nvtx  # an NVTX range per request launch (for a timeline profiler)
         self.pool = torch.empty(int(capacity), dtype=torch.uint8, device=self.device)
         self.arena = Arena(capacity)
         self.streams = [torch.cuda.Stream(device=self.device) for _ in range(n_slots)]
@@ -339,8 +342,12 @@ class GpuExecutor:
         stream: one native call (fem_serve_launch) with pointers into the request's block."""
         slot, offs, base = admitted
         desc = req.desc if req.desc is not None else req.build_desc()
+        if self.nvtx:
+            torch.cuda.nvtx.range_push(f"{req.kind} {req.physics}{req.dim}d rid={req.rid} cells={req.n_cells}")
         st = self._L.fem_serve_launch(ctypes.byref(desc), ctypes.c_void_p(self.pool_ptr + base), self.events[slot],
                                       ctypes.c_void_p(self.streams[slot].cuda_stream))
+        if self.nvtx:
+            torch.cuda.nvtx.range_pop()
         if st != 0:
             self.arena.free(base)
             self.free_slots.append(slot)
@@ -489,6 +496,37 @@ class Scheduler:
                           req_per_s=len(done) / span if span > 0 else math.nan, p50_ms=pct(50), p99_ms=pct(99),
                           mean_ms=statistics.mean(lat) if done else math.nan, max_inflight=max_inflight,
                           arrival_rate=arrival_rate)
+
+
+def request_log(requests, t0: float = None) -> List[dict]:
+    """The served stream as plain records (arrival, admission and completion times in s
+    from the first arrival, status, size), for saving beside a run and replaying it."""
+    reqs = list(requests)
+    if t0 is None:
+        t0 = min((r.t_arrive for r in reqs if not math.isnan(r.t_arrive)), default=0.0)
+    rel = lambda t: None if t is None or math.isnan(t) else t - t0
+    return [{"rid": r.rid, "kind": getattr(r, "kind", None), "physics": getattr(r, "physics", None),
+             "n_cells": r.n_cells, "arrival": r.arrival, "t_arrive": rel(r.t_arrive), "t_admit": rel(r.t_admit),
+             "t_done": rel(r.t_done), "status": r.status, "error": r.error} for r in reqs]
+
+
+def save_request_log(path: str, requests) -> None:
+    import json
+
+    with open(path, "w") as f:
+        json.dump(request_log(requests), f)
+
+
+def replay_arrivals(path: str, requests) -> None:
+    """Set each request's arrival time from a saved log (matched by rid), so the same
+    stream can be served again."""
+    import json
+
+    with open(path) as f:
+        arrivals = {rec["rid"]: rec["arrival"] for rec in json.load(f)}
+    for r in requests:
+        if r.rid in arrivals:
+            r.arrival, r.status = float(arrivals[r.rid]), "pending"
 
 
 def poisson_arrivals(n: int, rate: float, seed: int = 0) -> np.ndarray:

@@ -151,3 +151,23 @@ def test_serving_specs_mix():
     assert 10 ** 4.2 < np.median(C) < 10 ** 4.8
     c = workloads.cases.serving_case(specs[0])
     assert c.n_cells == specs[0]["n_cells"]
+
+
+def test_request_log_save_and_replay(serving, tmp_path):
+    """A served stream's log (arrival, admission, completion, status) can be saved and its
+    arrivals replayed: the second run admits in the same order."""
+    rng = np.random.default_rng(7)
+    reqs = [FakeRequest(i, int(rng.integers(1000, 50000)), int(rng.integers(1, 30)), 0.0003 * i) for i in range(30)]
+    ex = FakeExecutor(capacity=100, n_slots=3)
+    serving.Scheduler(ex, backfill=False).run(reqs)
+    log = serving.request_log(reqs)
+    assert len(log) == 30 and all(rec["status"] == "done" for rec in log)
+    assert all(rec["t_done"] >= rec["t_admit"] >= rec["t_arrive"] >= 0 for rec in log)
+    path = str(tmp_path / "log.json")
+    serving.save_request_log(path, reqs)
+    again = [FakeRequest(i, r.n_cells, r.mem, 99.0) for i, r in enumerate(reqs)]
+    serving.replay_arrivals(path, again)
+    assert [r.arrival for r in again] == [r.arrival for r in reqs]
+    ex2 = FakeExecutor(capacity=100, n_slots=3)
+    serving.Scheduler(ex2, backfill=False).run(again)
+    assert ex2.order == ex.order
