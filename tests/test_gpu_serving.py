@@ -47,7 +47,7 @@ def test_mix_equals_alone_and_matches_oracle():
 def test_too_large_request_is_rejected():
     cases, reqs = _stream(6, seed=5, max_cells=20000)
     small = min(footprint(r) for r in reqs)
-    ex = GpuExecutor(capacity=small + 4096, n_slots=2)
+    ex = GpuExecutor(capacity=small + 4096, n_slots=2, nvtx=True)  # the NVTX ranges cost nothing unprofiled
     st = Scheduler(ex).run(reqs)
     assert st.n_rejected >= 1
     assert st.n_done + st.n_rejected == len(reqs)
