@@ -70,7 +70,7 @@ def algorithmic_bytes(physics, dim, prec, C, V, nq):
 def adjoint_bytes(dim, prec, C, V, nq):
     """Element kernel (conn, K, lambda, coords, u in; dK, per-element dJ/du out) plus the
     vertex gather (lists and per-element values in, dJ/du out)."""
-    s = 8 if prec == "fp64" else 4
+    s = 8 if prec in ("fp64", "fp64_df") else 4
     nb = dim + 1
     elem = nb * 4 * C + nq * s * C + nb * s * C + dim * 8 * V + s * V + nq * s * C + nb * s * C
     gather = (V + 1) * 4 + nb * C * 4 + nb * s * C + s * V
@@ -879,9 +879,9 @@ def run_ours(args):
             if want(f"elast{dim}d_{prec}"):
                 rows[f"elast{dim}d_{prec}"] = measure_residual(el, prec, device, stream, flush, rsteps, args.warmup,
                                                                peak, oracle)[0]
-    if any(want(f"adjoint3d_{prec}") for prec in ("mixed", "fp64")):
+    if any(want(f"adjoint3d_{prec}") for prec in ("mixed", "fp64", "fp64_df")):
         adj = workloads.adjoint_case(HEADLINE_CELLS)
-        for prec in ("mixed", "fp64"):
+        for prec in ("mixed", "fp64", "fp64_df"):
             if want(f"adjoint3d_{prec}"):
                 rows[f"adjoint3d_{prec}"] = measure_adjoint(adj, prec, device, stream, flush, rsteps, args.warmup, peak,
                                                             oracle)

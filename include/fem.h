@@ -83,9 +83,9 @@ typedef enum {
      * pipe: the Jacobian columns are formed in float64, every other intermediate is a
      * pair of float32 values (hi + lo, double-length arithmetic from TwoSum/TwoProduct),
      * the outputs are widened back to float64. Values must lie in float32's normal range
-     * (|x| in [2^-126, 2^128), or zero). fem_integrate_laplacian, fem_integrate_elasticity
-     * and (for its residual) fem_pcg_laplacian only; the other entry points return
-     * FEM_ERR_ARG for it. */
+     * (|x| in [2^-126, 2^128), or zero). fem_integrate_laplacian, fem_integrate_elasticity,
+     * fem_adjoint_laplacian (its element part; the vertex sum in float64) and (for its
+     * residual) fem_pcg_laplacian only; the other entry points return FEM_ERR_ARG for it. */
     FEM_FP64_DF = 3
 } fem_precision;
 

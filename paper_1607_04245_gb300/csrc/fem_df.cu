@@ -322,4 +322,125 @@ fem_status launch_el_df(int dim, int64_t n_cells, int64_t n_verts, const double 
     return check_launch("fem_integrate_elasticity (FEM_FP64_DF)");
 }
 
+// ---- the adjoint of the Laplacian residual in the same form: per element the residual of
+// the adjoint weights lambda_e (scratch, summed per vertex afterwards) and
+//     dK[q][e] = w_q (h_lambda . h_u) / |det J|.
+
+struct DfAdjArgs {
+    const double *X[3];
+    const int32_t *conn;
+    const double *u, *K, *lam;  // lam [dim+1][C]
+    double *scratch, *dK;       // [dim+1][C], [n_q][C]
+    int64_t C;
+    uint32_t V;
+    int nq;
+    float whi[FEM_MAX_QPTS], wlo[FEM_MAX_QPTS];
+};
+
+template <int DIM>
+__global__ void __launch_bounds__(kBlock) adj_df_kernel(const __grid_constant__ DfAdjArgs a) {
+    constexpr int NB = DIM + 1;
+    const int64_t C = a.C;
+    const double *X[DIM];
+#pragma unroll
+    for (int k = 0; k < DIM; ++k) X[k] = a.X[k];
+    const int64_t stride = int64_t(gridDim.x) * blockDim.x;
+    for (int64_t c = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; c < C; c += stride) {
+        uint32_t v[NB];
+        dfl uu[NB], ll[NB];
+#pragma unroll
+        for (int b = 0; b < NB; ++b) {
+            v[b] = clamp_vid(ld_stream(a.conn + b * C + c), a.V);
+            uu[b] = df_from_double(ld_gather(a.u + v[b]));
+            ll[b] = df_from_double(ld_stream(a.lam + b * C + c));
+        }
+        dfl kbar = df_mul(dfl{a.whi[0], a.wlo[0]}, df_from_double(ld_stream(a.K + c)));
+        for (int q = 1; q < a.nq; ++q)
+            kbar = df_add(kbar, df_mul(dfl{a.whi[q], a.wlo[q]}, df_from_double(ld_stream(a.K + q * C + c))));
+        double xs[NB][DIM];
+        gather_coords<DIM>(X, v, xs);
+        dfl e[DIM][DIM];
+#pragma unroll
+        for (int j = 0; j < DIM; ++j)
+#pragma unroll
+            for (int k = 0; k < DIM; ++k) e[j][k] = df_from_double(xs[j + 1][k] - xs[0][k]);
+        dfl n[DIM][DIM], det;
+        if constexpr (DIM == 2) {
+            n[0][0] = e[1][1], n[0][1] = df_neg(e[1][0]);
+            n[1][0] = df_neg(e[0][1]), n[1][1] = e[0][0];
+            det = df_sub(df_mul(e[0][0], e[1][1]), df_mul(e[0][1], e[1][0]));
+        } else {
+#pragma unroll
+            for (int j = 0; j < 3; ++j) {
+                const dfl *p = e[(j + 1) % 3], *q = e[(j + 2) % 3];
+                n[j][0] = df_sub(df_mul(p[1], q[2]), df_mul(p[2], q[1]));
+                n[j][1] = df_sub(df_mul(p[2], q[0]), df_mul(p[0], q[2]));
+                n[j][2] = df_sub(df_mul(p[0], q[1]), df_mul(p[1], q[0]));
+            }
+            det = df_add(df_add(df_mul(e[0][0], n[0][0]), df_mul(e[0][1], n[0][1])), df_mul(e[0][2], n[0][2]));
+        }
+        // h_u = sum_j (u_j - u_0) n_j, h_l = sum_j (lambda_j - lambda_0) n_j
+        dfl hu[DIM], hl[DIM];
+#pragma unroll
+        for (int j = 0; j < DIM; ++j) {
+            const dfl du = df_sub(uu[j + 1], uu[0]), dl = df_sub(ll[j + 1], ll[0]);
+#pragma unroll
+            for (int i = 0; i < DIM; ++i) {
+                hu[i] = j == 0 ? df_mul(du, n[0][i]) : df_add(hu[i], df_mul(du, n[j][i]));
+                hl[i] = j == 0 ? df_mul(dl, n[0][i]) : df_add(hl[i], df_mul(dl, n[j][i]));
+            }
+        }
+        const dfl inv = df_div(dfl{1.0f, 0.0f}, df_abs(det));
+        const dfl s = df_mul(kbar, inv);
+        // element residual of lambda_e: r_j = s n_j . h_l, r_0 = -(r_1 + ... + r_d)
+        dfl sum;
+#pragma unroll
+        for (int j = 0; j < DIM; ++j) {
+            dfl d = df_mul(n[j][0], hl[0]);
+#pragma unroll
+            for (int i = 1; i < DIM; ++i) d = df_add(d, df_mul(n[j][i], hl[i]));
+            const dfl rj = df_mul(s, d);
+            sum = j == 0 ? rj : df_add(sum, rj);
+            __stcs(a.scratch + (j + 1) * C + c, df_to_double(rj));
+        }
+        __stcs(a.scratch + c, -df_to_double(sum));
+        // dK[q] = w_q (h_l . h_u) / |det J|
+        dfl t = df_mul(hl[0], hu[0]);
+#pragma unroll
+        for (int i = 1; i < DIM; ++i) t = df_add(t, df_mul(hl[i], hu[i]));
+        const dfl tf = df_mul(t, inv);
+        for (int q = 0; q < a.nq; ++q) __stcs(a.dK + q * C + c, df_to_double(df_mul(dfl{a.whi[q], a.wlo[q]}, tf)));
+    }
+}
+
+// the element part of fem_adjoint_laplacian for FEM_FP64_DF (arguments validated by the caller)
+fem_status launch_adj_df(int dim, int64_t n_cells, int64_t n_verts, const double *coords, const int32_t *conn,
+                         const void *u, const void *K, int n_q, const double *qw, const void *lambda, void *dK,
+                         void *scratch, cudaStream_t stream) {
+    DfAdjArgs a;
+    for (int k = 0; k < 3; ++k) a.X[k] = coords + (k < dim ? k : 0) * n_verts;
+    a.conn = conn;
+    a.u = static_cast<const double *>(u);
+    a.K = static_cast<const double *>(K);
+    a.lam = static_cast<const double *>(lambda);
+    a.scratch = static_cast<double *>(scratch);
+    a.dK = static_cast<double *>(dK);
+    a.C = n_cells;
+    a.V = static_cast<uint32_t>(n_verts);
+    a.nq = n_q;
+    for (int q = 0; q < FEM_MAX_QPTS; ++q) {
+        const double w = q < n_q ? qw[q] : 0.0;
+        a.whi[q] = static_cast<float>(w);
+        a.wlo[q] = static_cast<float>(w - static_cast<double>(a.whi[q]));
+    }
+    if (dim == 2) {
+        auto k = adj_df_kernel<2>;
+        k<<<grid_for(n_cells, kBlock, reinterpret_cast<const void *>(k)), kBlock, 0, stream>>>(a);
+    } else {
+        auto k = adj_df_kernel<3>;
+        k<<<grid_for(n_cells, kBlock, reinterpret_cast<const void *>(k)), kBlock, 0, stream>>>(a);
+    }
+    return check_launch("fem_adjoint_laplacian (FEM_FP64_DF)");
+}
+
 }  // namespace fem

@@ -885,6 +885,9 @@ fem_status integrate_laplacian_plain(int dim, int64_t n_cells, int64_t n_verts, 
 
 fem_status launch_gather(int dim, int n_comp, int64_t C, int64_t V, const void *elem, const int32_t *node_ptr,
                          const int32_t *node_idx, void *out, fem_precision prec, cudaStream_t s);
+fem_status launch_adj_df(int dim, int64_t n_cells, int64_t n_verts, const double *coords, const int32_t *conn,
+                         const void *u, const void *K, int n_q, const double *qw, const void *lambda, void *dK,
+                         void *scratch, cudaStream_t stream);
 }
 
 extern "C" fem_status fem_adjoint_laplacian(int dim, int64_t n_cells, int64_t n_verts, const double *coords,
@@ -893,11 +896,19 @@ extern "C" fem_status fem_adjoint_laplacian(int dim, int64_t n_cells, int64_t n_
                                             void *du, const int32_t *node_ptr, const int32_t *node_idx,
                                             void *scratch, fem_precision prec, fem_stream stream) {
     LapArgs a;
-    fem_status st = fill_args(a, dim, n_cells, n_verts, coords, conn, u, K, n_q, qpts, qw, prec);
+    const bool df = prec == FEM_FP64_DF;  // values float64; the element part in double-float
+    fem_status st = fill_args(a, dim, n_cells, n_verts, coords, conn, u, K, n_q, qpts, qw, df ? FEM_FP64 : prec);
     if (st != FEM_OK) return st;
     if (n_verts > 0 && (!du || !node_ptr)) return fail(FEM_ERR_ARG, "du or node_ptr is NULL");
     if (n_cells > 0 && (!u || !K || !lambda || !dK || !node_idx || !scratch))
         return fail(FEM_ERR_ARG, "a NULL adjoint argument");
+    if (df) {
+        if (n_cells > 0 &&
+            (st = launch_adj_df(dim, n_cells, n_verts, coords, conn, u, K, n_q, qw, lambda, dK, scratch, stream)) !=
+                FEM_OK)
+            return st;
+        return launch_gather(dim, 1, n_cells, n_verts, scratch, node_ptr, node_idx, du, FEM_FP64, stream);
+    }
     if (n_cells > 0) {
         a.lam = lambda;
         a.out = scratch;

@@ -118,3 +118,39 @@ def test_df_elasticity_rigid_motions_and_sums(dim):
     r2, _ = _el_res(case)
     sums = r2.view(dim + 1, dim, -1).sum(0).abs().max().item()
     assert sums <= 1e-14 * r2.abs().max().item()
+
+
+# ---- the adjoint in the double-float form
+
+
+def _adj(case, prec):
+    c, d = device_arrays(case, "fp64")
+    q = c.rule
+    ptr, idx = fem.fem_build_node2cell(d["conn"], c.n_verts)
+    dK, du = fem.fem_adjoint_laplacian(d["coords"], d["conn"], d["u"], d["K"], q.points, q.weights, d["adj"], ptr,
+                                       idx, prec=prec)
+    return c, dK, du
+
+
+def test_df_adjoint_full_size():
+    """dJ/dK and dJ/du on the 1,572,864-tet workload against the oracle at the float64
+    tolerance, and against the float64 form."""
+    case = workloads.adjoint_case()
+    c, dK, du = _adj(case, "fp64_df")
+    rK, ru = oracle.adjoint_for(c)
+    assert rel_err(dK, rK) <= TOL and rel_err(du, ru) <= TOL
+    _, dK64, du64 = _adj(case, "fp64")
+    assert rel_err(dK, dK64.double().cpu().numpy()) <= TOL and rel_err(du, du64.double().cpu().numpy()) <= TOL
+
+
+@pytest.mark.parametrize("n_cells", [1, 5, 1027])
+def test_df_adjoint_ragged_and_reproducible(n_cells):
+    base = workloads.adjoint_case(6 * 12 ** 3)
+    mesh = workloads.first_cells(base.mesh, n_cells)
+    case = workloads.Case("laplacian", mesh, base.rule, base.u[: mesh.n_verts], K=base.K[:, :n_cells].copy(),
+                          adj=base.adj[:, :n_cells].copy())
+    c, dK, du = _adj(case, "fp64_df")
+    rK, ru = oracle.adjoint_for(c)
+    assert rel_err(dK, rK) <= TOL and rel_err(du, ru) <= TOL
+    _, dK2, du2 = _adj(case, "fp64_df")
+    assert torch.equal(dK, dK2) and torch.equal(du, du2)
