@@ -106,3 +106,30 @@ def test_one_cell_more_is_refused(base):
                                    fem.binding.precision("fp64"), None)
     assert st == -2  # FEM_ERR_SHAPE
     assert b"int32" in L.fem_last_error()
+
+
+def test_elasticity_max_size_mixed():
+    """3D elasticity at the largest cell count the int32 indexing admits (12 output rows of
+    536,870,908 cells, 51 GB in all): the 2^21-tet workload's rows repeated, every element
+    vector bitwise its base counterpart, a sample against the oracle."""
+    base = workloads.elasticity_case(3)
+    c, d = device_arrays(base, "mixed")
+    q = c.rule
+    ref = fem.fem_integrate_elasticity(d["coords"], d["conn"], d["u"], d["lam"], d["mu"], q.points, q.weights,
+                                       prec="mixed")
+    ref_ora = oracle.residual_for(c)
+    n = C_MAX - C_MAX % 4
+    conn, lam, mu = _tile(d["conn"], n), _tile(d["lam"], n), _tile(d["mu"], n)
+    out = fem.fem_integrate_elasticity(d["coords"], conn, d["u"], lam, mu, q.points, q.weights, prec="mixed")
+    torch.cuda.synchronize()
+    del conn, lam, mu
+    try:
+        assert _same_as_tiled(out, ref)
+        rng = np.random.default_rng(1)
+        cells = np.concatenate([rng.integers(0, n, 4096), [0, n - 1]])
+        got = out[:, torch.from_numpy(cells).to(out.device)].double().cpu().numpy()
+        assert np.abs(got - ref_ora[:, cells % c.n_cells]).max() / np.abs(ref_ora).max() <= TOL["mixed"]
+        assert fem.fem_device_error() == 0
+    finally:
+        del out
+        torch.cuda.empty_cache()
