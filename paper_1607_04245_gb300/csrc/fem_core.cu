@@ -96,7 +96,7 @@ unsigned *device_error_word() {
     return cached[dev];
 }
 
-static int sm_count() {
+int sm_count() {
     static int cached[64] = {0};
     int dev = 0;
     cudaGetDevice(&dev);

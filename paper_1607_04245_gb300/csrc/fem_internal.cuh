@@ -33,6 +33,7 @@ struct QuadW {
 
 fem_status load_quadrature(int dim, int n_q, const double *qpts, const double *qw, QuadW &out);
 fem_status check_common(int dim, int64_t n_cells, int64_t n_verts, const double *coords, const int32_t *conn);
+int sm_count();  // multiprocessors of the current device (cached)
 float mixed_tau();
 
 inline bool aligned16(const void *p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; }

@@ -743,6 +743,20 @@ static fem_status launch_lap(const LapArgs &a, bool vec, cudaStream_t s, bool st
     fem_status st = FEM_OK;
     // the quadrature size of the workloads' rules (3 points in 2D, 4 in 3D) is compiled in
     const bool native_nq = (DIM == 3 && a.w.nq == 4) || (DIM == 2 && a.w.nq == 3);
+    if constexpr (P == FEM_FP64) {
+        // few cells: 1024-cell tiles would leave most SMs idle while the float64 pipe, not
+        // memory, bounds the launch, so the cells are spread over every SM (one per thread)
+        const int64_t sms = sm_count();
+        if ((a.C + kTile - 1) / kTile < sms) {
+            const int64_t per = (a.C + 2 * sms - 1) / (2 * sms);
+            int block = static_cast<int>((per + 31) / 32 * 32);
+            block = block < 32 ? 32 : (block > kBlock ? kBlock : block);
+            const unsigned grid = static_cast<unsigned>((a.C + block - 1) / block);
+            if (native_nq) lap_kernel<DIM, P, 1, DIM + 1, ADJ><<<grid, block, 0, s>>>(a);
+            else lap_kernel<DIM, P, 1, 0, ADJ><<<grid, block, 0, s>>>(a);
+            return check_launch(ADJ ? "fem_adjoint_laplacian" : "fem_integrate_laplacian");
+        }
+    }
 #ifndef FEM_LAP_DIRECT
     if (staged_ok && vec && 2u * sb <= kStageMax) {
         if (a.w.nq == DIM + 1 && DIM == 3) st = launch_staged<DIM, P, 4, ADJ>(a, sb, s);
