@@ -10,7 +10,8 @@
 //     loss to cancellation), then split into pairs with integer operations;
 //   * u_b and K_q are split into pairs the same way; the weights are split on the host;
 //   * adjugate, determinant, field gradient, coefficient sum, the one division and the
-//     contraction run in pair arithmetic;
+//     contraction run in pair arithmetic, every sum of products as one compensated dot
+//     product with a single renormalisation;
 //   * each element-vector entry is widened back to float64 (integer operations) and
 //     summed with one float64 add.
 // Per cell (3D Laplacian) this issues 13 float64 additions instead of ~71 float64
@@ -63,6 +64,96 @@ __device__ __forceinline__ dfl df_div(dfl a, dfl b) {
     return df_fast(q1, q2);
 }
 
+// Compensated sums of pair products, sum_i a_i b_i: the high parts of the products are
+// added with TwoSum and every rounding error, with the cross terms a.hi b.lo + a.lo b.hi,
+// goes into one float32 accumulator; one renormalisation at the end (Ogita, Rump and
+// Oishi's Dot2 carried over to pair operands). The error stays at the pair precision,
+// ~(n + 2) 2^-48 sum_i |a_i b_i|, for about 12 instead of 18 operations per term.
+struct df_acc {
+    float s, err;
+};
+
+__device__ __forceinline__ df_acc acc_first(dfl a, dfl b) {
+    df_acc c;
+    two_prod(a.hi, b.hi, c.s, c.err);
+    c.err = fmaf(a.lo, b.hi, fmaf(a.hi, b.lo, c.err));
+    return c;
+}
+
+__device__ __forceinline__ void acc_add(df_acc &c, dfl a, dfl b) {
+    float p, ep, t;
+    two_prod(a.hi, b.hi, p, ep);
+    two_sum(c.s, p, c.s, t);
+    c.err = fmaf(a.lo, b.hi, fmaf(a.hi, b.lo, __fadd_rn(c.err, __fadd_rn(t, ep))));
+}
+
+__device__ __forceinline__ dfl acc_value(df_acc c) {
+    dfl r;
+    two_sum(c.s, c.err, r.hi, r.lo);
+    return r;
+}
+
+__device__ __forceinline__ dfl df_dot2(dfl a0, dfl b0, dfl a1, dfl b1) {
+    df_acc c = acc_first(a0, b0);
+    acc_add(c, a1, b1);
+    return acc_value(c);
+}
+
+__device__ __forceinline__ dfl df_dot3(dfl a0, dfl b0, dfl a1, dfl b1, dfl a2, dfl b2) {
+    df_acc c = acc_first(a0, b0);
+    acc_add(c, a1, b1);
+    acc_add(c, a2, b2);
+    return acc_value(c);
+}
+
+// adjugate rows n_j of the Jacobian with columns e_j, and det J = e_0 . n_0
+template <int DIM>
+__device__ __forceinline__ dfl df_adjugate(const dfl (&e)[DIM][DIM], dfl (&n)[DIM][DIM]) {
+    if constexpr (DIM == 2) {
+        n[0][0] = e[1][1], n[0][1] = df_neg(e[1][0]);
+        n[1][0] = df_neg(e[0][1]), n[1][1] = e[0][0];
+        return df_dot2(e[0][0], e[1][1], df_neg(e[0][1]), e[1][0]);
+    } else {
+#pragma unroll
+        for (int j = 0; j < 3; ++j) {
+            const dfl *p = e[(j + 1) % 3], *q = e[(j + 2) % 3];
+            n[j][0] = df_dot2(p[1], q[2], df_neg(p[2]), q[1]);
+            n[j][1] = df_dot2(p[2], q[0], df_neg(p[0]), q[2]);
+            n[j][2] = df_dot2(p[0], q[1], df_neg(p[1]), q[0]);
+        }
+        return df_dot3(e[0][0], n[0][0], e[0][1], n[0][1], e[0][2], n[0][2]);
+    }
+}
+
+// n_j . h over DIM components
+template <int DIM>
+__device__ __forceinline__ dfl df_dotv(const dfl (&a)[DIM], const dfl (&b)[DIM]) {
+    df_acc c = acc_first(a[0], b[0]);
+#pragma unroll
+    for (int i = 1; i < DIM; ++i) acc_add(c, a[i], b[i]);
+    return acc_value(c);
+}
+
+// sum_j d_j n_j[i] for every component i
+template <int DIM>
+__device__ __forceinline__ void df_combine(const dfl (&d)[DIM], const dfl (&n)[DIM][DIM], dfl (&h)[DIM]) {
+#pragma unroll
+    for (int i = 0; i < DIM; ++i) {
+        df_acc c = acc_first(d[0], n[0][i]);
+#pragma unroll
+        for (int j = 1; j < DIM; ++j) acc_add(c, d[j], n[j][i]);
+        h[i] = acc_value(c);
+    }
+}
+
+// sum_q w_q f_q for a float64 row f[q * C + c]
+__device__ __forceinline__ dfl df_weighted(const float *whi, const float *wlo, const double *f, int64_t C, int64_t c,
+                                           int nq) {
+    df_acc acc = acc_first(dfl{whi[0], wlo[0]}, df_from_double(ld_stream(f + c)));
+    for (int q = 1; q < nq; ++q) acc_add(acc, dfl{whi[q], wlo[q]}, df_from_double(ld_stream(f + q * C + c)));
+    return acc_value(acc);
+}
+
 // float -> float64 with integer operations (normal numbers; zero and float32 subnormals,
 // below 2^-126, widen to a signed zero)
 __device__ __forceinline__ double widen(float x) {
@@ -87,7 +178,7 @@ struct DfArgs {
 };
 
 template <int DIM>
-__global__ void __launch_bounds__(kBlock) lap_df_kernel(const __grid_constant__ DfArgs a) {
+__global__ void __launch_bounds__(kBlock, 5) lap_df_kernel(const __grid_constant__ DfArgs a) {
     constexpr int NB = DIM + 1;
     const int64_t C = a.C;
     const double *X[DIM];
@@ -103,9 +194,7 @@ __global__ void __launch_bounds__(kBlock) lap_df_kernel(const __grid_constant__ 
             uu[b] = df_from_double(ld_gather(a.u + v[b]));
         }
         // Kbar = sum_q w_q K_q
-        dfl kbar = df_mul(dfl{a.whi[0], a.wlo[0]}, df_from_double(ld_stream(a.K + c)));
-        for (int q = 1; q < a.nq; ++q)
-            kbar = df_add(kbar, df_mul(dfl{a.whi[q], a.wlo[q]}, df_from_double(ld_stream(a.K + q * C + c))));
+        const dfl kbar = df_weighted(a.whi, a.wlo, a.K, C, c, a.nq);
         // Jacobian columns in float64, then pairs
         double xs[NB][DIM];
         gather_coords<DIM>(X, v, xs);
@@ -115,43 +204,22 @@ __global__ void __launch_bounds__(kBlock) lap_df_kernel(const __grid_constant__ 
 #pragma unroll
             for (int k = 0; k < DIM; ++k) e[j][k] = df_from_double(xs[j + 1][k] - xs[0][k]);
         // adjugate rows n_j and det J
-        dfl n[DIM][DIM], det;
-        if constexpr (DIM == 2) {
-            n[0][0] = e[1][1], n[0][1] = df_neg(e[1][0]);
-            n[1][0] = df_neg(e[0][1]), n[1][1] = e[0][0];
-            det = df_sub(df_mul(e[0][0], e[1][1]), df_mul(e[0][1], e[1][0]));
-        } else {
-#pragma unroll
-            for (int j = 0; j < 3; ++j) {
-                const dfl *p = e[(j + 1) % 3], *q = e[(j + 2) % 3];
-                n[j][0] = df_sub(df_mul(p[1], q[2]), df_mul(p[2], q[1]));
-                n[j][1] = df_sub(df_mul(p[2], q[0]), df_mul(p[0], q[2]));
-                n[j][2] = df_sub(df_mul(p[0], q[1]), df_mul(p[1], q[0]));
-            }
-            det = df_add(df_add(df_mul(e[0][0], n[0][0]), df_mul(e[0][1], n[0][1])), df_mul(e[0][2], n[0][2]));
-        }
+        dfl n[DIM][DIM];
+        const dfl det = df_adjugate<DIM>(e, n);
         // h = sum_j (u_j - u_0) n_j
-        dfl h[DIM];
+        dfl du[DIM], h[DIM];
 #pragma unroll
-        for (int i = 0; i < DIM; ++i) h[i] = dfl{0.0f, 0.0f};
-#pragma unroll
-        for (int j = 0; j < DIM; ++j) {
-            const dfl du = df_sub(uu[j + 1], uu[0]);
-#pragma unroll
-            for (int i = 0; i < DIM; ++i) h[i] = df_add(h[i], df_mul(du, n[j][i]));
-        }
+        for (int j = 0; j < DIM; ++j) du[j] = df_sub(uu[j + 1], uu[0]);
+        df_combine<DIM>(du, n, h);
         // r_j = (Kbar / |det J|) n_j . h, r_0 = -(r_1 + ... + r_d)
         const dfl s = df_div(kbar, df_abs(det));
-        dfl sum = dfl{0.0f, 0.0f};
+        dfl sum;
         double r[NB];
 #pragma unroll
         for (int j = 0; j < DIM; ++j) {
-            dfl d = df_mul(n[j][0], h[0]);
-#pragma unroll
-            for (int i = 1; i < DIM; ++i) d = df_add(d, df_mul(n[j][i], h[i]));
-            const dfl rj = df_mul(s, d);
+            const dfl rj = df_mul(s, df_dotv<DIM>(n[j], h));
             r[j + 1] = df_to_double(rj);
-            sum = df_add(sum, rj);
+            sum = j == 0 ? rj : df_add(sum, rj);
         }
         r[0] = -df_to_double(sum);
 #pragma unroll
@@ -217,13 +285,8 @@ __global__ void __launch_bounds__(kBlock) el_df_kernel(const __grid_constant__ D
 #pragma unroll
         for (int b = 0; b < NB; ++b) v[b] = clamp_vid(ld_stream(a.conn + b * C + c), a.V);
         // Lbar = sum_q w_q lambda_q, Mbar = sum_q w_q mu_q
-        dfl lbar = df_mul(dfl{a.whi[0], a.wlo[0]}, df_from_double(ld_stream(a.lam + c)));
-        dfl mbar = df_mul(dfl{a.whi[0], a.wlo[0]}, df_from_double(ld_stream(a.mu + c)));
-        for (int q = 1; q < a.nq; ++q) {
-            const dfl w{a.whi[q], a.wlo[q]};
-            lbar = df_add(lbar, df_mul(w, df_from_double(ld_stream(a.lam + q * C + c))));
-            mbar = df_add(mbar, df_mul(w, df_from_double(ld_stream(a.mu + q * C + c))));
-        }
+        const dfl lbar = df_weighted(a.whi, a.wlo, a.lam, C, c, a.nq);
+        const dfl mbar = df_weighted(a.whi, a.wlo, a.mu, C, c, a.nq);
         // Jacobian columns in float64, then pairs
         double xs[NB][DIM];
         gather_coords<DIM>(X, v, xs);
@@ -232,34 +295,17 @@ __global__ void __launch_bounds__(kBlock) el_df_kernel(const __grid_constant__ D
         for (int j = 0; j < DIM; ++j)
 #pragma unroll
             for (int k = 0; k < DIM; ++k) e[j][k] = df_from_double(xs[j + 1][k] - xs[0][k]);
-        dfl n[DIM][DIM], det;
-        if constexpr (DIM == 2) {
-            n[0][0] = e[1][1], n[0][1] = df_neg(e[1][0]);
-            n[1][0] = df_neg(e[0][1]), n[1][1] = e[0][0];
-            det = df_sub(df_mul(e[0][0], e[1][1]), df_mul(e[0][1], e[1][0]));
-        } else {
-#pragma unroll
-            for (int j = 0; j < 3; ++j) {
-                const dfl *p = e[(j + 1) % 3], *q = e[(j + 2) % 3];
-                n[j][0] = df_sub(df_mul(p[1], q[2]), df_mul(p[2], q[1]));
-                n[j][1] = df_sub(df_mul(p[2], q[0]), df_mul(p[0], q[2]));
-                n[j][2] = df_sub(df_mul(p[0], q[1]), df_mul(p[1], q[0]));
-            }
-            det = df_add(df_add(df_mul(e[0][0], n[0][0]), df_mul(e[0][1], n[0][1])), df_mul(e[0][2], n[0][2]));
-        }
+        dfl n[DIM][DIM];
+        const dfl det = df_adjugate<DIM>(e, n);
         // H[k][i] = sum_j (u_{j,k} - u_{0,k}) n_j[i]
         dfl H[DIM][DIM];
 #pragma unroll
         for (int k = 0; k < DIM; ++k) {
-            dfl u0 = df_from_double(ld_gather(a.u + k * V + v[0]));
+            const dfl u0 = df_from_double(ld_gather(a.u + k * V + v[0]));
+            dfl du[DIM];
 #pragma unroll
-            for (int i = 0; i < DIM; ++i) H[k][i] = dfl{0.0f, 0.0f};
-#pragma unroll
-            for (int j = 0; j < DIM; ++j) {
-                const dfl du = df_sub(df_from_double(ld_gather(a.u + k * V + v[j + 1])), u0);
-#pragma unroll
-                for (int i = 0; i < DIM; ++i) H[k][i] = df_add(H[k][i], df_mul(du, n[j][i]));
-            }
+            for (int j = 0; j < DIM; ++j) du[j] = df_sub(df_from_double(ld_gather(a.u + k * V + v[j + 1])), u0);
+            df_combine<DIM>(du, n, H[k]);
         }
         dfl tr = H[0][0];
 #pragma unroll
@@ -282,9 +328,7 @@ __global__ void __launch_bounds__(kBlock) el_df_kernel(const __grid_constant__ D
         for (int b = 1; b <= DIM; ++b)
 #pragma unroll
             for (int k = 0; k < DIM; ++k) {
-                dfl rb = df_mul(Tm[k][0], n[b - 1][0]);
-#pragma unroll
-                for (int i = 1; i < DIM; ++i) rb = df_add(rb, df_mul(Tm[k][i], n[b - 1][i]));
+                const dfl rb = df_dotv<DIM>(Tm[k], n[b - 1]);
                 r0[k] = df_sub(r0[k], rb);
                 __stcs(a.out + (b * DIM + k) * C + c, df_to_double(rb));
             }
@@ -354,9 +398,7 @@ __global__ void __launch_bounds__(kBlock) adj_df_kernel(const __grid_constant__ 
             uu[b] = df_from_double(ld_gather(a.u + v[b]));
             ll[b] = df_from_double(ld_stream(a.lam + b * C + c));
         }
-        dfl kbar = df_mul(dfl{a.whi[0], a.wlo[0]}, df_from_double(ld_stream(a.K + c)));
-        for (int q = 1; q < a.nq; ++q)
-            kbar = df_add(kbar, df_mul(dfl{a.whi[q], a.wlo[q]}, df_from_double(ld_stream(a.K + q * C + c))));
+        const dfl kbar = df_weighted(a.whi, a.wlo, a.K, C, c, a.nq);
         double xs[NB][DIM];
         gather_coords<DIM>(X, v, xs);
         dfl e[DIM][DIM];
@@ -364,51 +406,27 @@ __global__ void __launch_bounds__(kBlock) adj_df_kernel(const __grid_constant__ 
         for (int j = 0; j < DIM; ++j)
 #pragma unroll
             for (int k = 0; k < DIM; ++k) e[j][k] = df_from_double(xs[j + 1][k] - xs[0][k]);
-        dfl n[DIM][DIM], det;
-        if constexpr (DIM == 2) {
-            n[0][0] = e[1][1], n[0][1] = df_neg(e[1][0]);
-            n[1][0] = df_neg(e[0][1]), n[1][1] = e[0][0];
-            det = df_sub(df_mul(e[0][0], e[1][1]), df_mul(e[0][1], e[1][0]));
-        } else {
-#pragma unroll
-            for (int j = 0; j < 3; ++j) {
-                const dfl *p = e[(j + 1) % 3], *q = e[(j + 2) % 3];
-                n[j][0] = df_sub(df_mul(p[1], q[2]), df_mul(p[2], q[1]));
-                n[j][1] = df_sub(df_mul(p[2], q[0]), df_mul(p[0], q[2]));
-                n[j][2] = df_sub(df_mul(p[0], q[1]), df_mul(p[1], q[0]));
-            }
-            det = df_add(df_add(df_mul(e[0][0], n[0][0]), df_mul(e[0][1], n[0][1])), df_mul(e[0][2], n[0][2]));
-        }
+        dfl n[DIM][DIM];
+        const dfl det = df_adjugate<DIM>(e, n);
         // h_u = sum_j (u_j - u_0) n_j, h_l = sum_j (lambda_j - lambda_0) n_j
-        dfl hu[DIM], hl[DIM];
+        dfl hu[DIM], hl[DIM], du[DIM], dl[DIM];
 #pragma unroll
-        for (int j = 0; j < DIM; ++j) {
-            const dfl du = df_sub(uu[j + 1], uu[0]), dl = df_sub(ll[j + 1], ll[0]);
-#pragma unroll
-            for (int i = 0; i < DIM; ++i) {
-                hu[i] = j == 0 ? df_mul(du, n[0][i]) : df_add(hu[i], df_mul(du, n[j][i]));
-                hl[i] = j == 0 ? df_mul(dl, n[0][i]) : df_add(hl[i], df_mul(dl, n[j][i]));
-            }
-        }
+        for (int j = 0; j < DIM; ++j) du[j] = df_sub(uu[j + 1], uu[0]), dl[j] = df_sub(ll[j + 1], ll[0]);
+        df_combine<DIM>(du, n, hu);
+        df_combine<DIM>(dl, n, hl);
         const dfl inv = df_div(dfl{1.0f, 0.0f}, df_abs(det));
         const dfl s = df_mul(kbar, inv);
         // element residual of lambda_e: r_j = s n_j . h_l, r_0 = -(r_1 + ... + r_d)
         dfl sum;
 #pragma unroll
         for (int j = 0; j < DIM; ++j) {
-            dfl d = df_mul(n[j][0], hl[0]);
-#pragma unroll
-            for (int i = 1; i < DIM; ++i) d = df_add(d, df_mul(n[j][i], hl[i]));
-            const dfl rj = df_mul(s, d);
+            const dfl rj = df_mul(s, df_dotv<DIM>(n[j], hl));
             sum = j == 0 ? rj : df_add(sum, rj);
             __stcs(a.scratch + (j + 1) * C + c, df_to_double(rj));
         }
         __stcs(a.scratch + c, -df_to_double(sum));
         // dK[q] = w_q (h_l . h_u) / |det J|
-        dfl t = df_mul(hl[0], hu[0]);
-#pragma unroll
-        for (int i = 1; i < DIM; ++i) t = df_add(t, df_mul(hl[i], hu[i]));
-        const dfl tf = df_mul(t, inv);
+        const dfl tf = df_mul(df_dotv<DIM>(hl, hu), inv);
         for (int q = 0; q < a.nq; ++q) __stcs(a.dK + q * C + c, df_to_double(df_mul(dfl{a.whi[q], a.wlo[q]}, tf)));
     }
 }
