@@ -453,56 +453,11 @@ __device__ __forceinline__ void lap_pair(const double *const (&X)[DIM], const ui
     if constexpr (P == FEM_FP32_MIXED) shape_ok2<DIM>(e, det, tau2, oka, okb);
 }
 
-// CPT consecutive values of a cell-indexed row in shared memory (one vector load)
-template <int CPT, class T>
-__device__ __forceinline__ void lds_row(const T *p, T (&v)[CPT]) {
-    static_assert(CPT == 2 || CPT == 4, "two or four cells per thread");
-    if constexpr (sizeof(T) * CPT == 8) {
-        const uint2 t = *reinterpret_cast<const uint2 *>(p);
-        memcpy(&v[0], &t.x, 4), memcpy(&v[1], &t.y, 4);
-    } else if constexpr (sizeof(T) * CPT == 16) {
-        const uint4 t = *reinterpret_cast<const uint4 *>(p);
-        memcpy(&v[0], &t, 16);
-    } else {
-        const uint4 t0 = reinterpret_cast<const uint4 *>(p)[0], t1 = reinterpret_cast<const uint4 *>(p)[1];
-        memcpy(&v[0], &t0, 16), memcpy(&v[2], &t1, 16);
-    }
-}
-
-// Staged kernel (fem_pipe.cuh): persistent CTAs walk the chunks of kTile consecutive
-// cells round-robin (chunk blockIdx.x, blockIdx.x + gridDim.x, ...), so that at any time
-// the CTAs of the device work on one contiguous front of the cell arrays (DRAM pages and
-// the L2-resident vertices of neighbouring chunks are shared). The CTA is warp-
-// specialised: one producer warp brings each chunk's connectivity, coefficient (and
-// adjoint-weight) rows into a ring of shared-memory stages with the bulk-copy engine
-// ("full" barriers count the bytes), and kConsumerWarps consumer warps compute. Consumer
-// warps release a stage on its "empty" barrier as soon as they are done with it; there
-// is no CTA-wide barrier per chunk, so the warps drift apart and one warp's vertex
-// gathers overlap other warps' arithmetic. Within a chunk each consumer thread owns kCPT
-// consecutive cells: vector shared-memory reads of every row, vector streaming stores
-// of every output row, and (float32 forms) the cells processed as f32x2 pairs. NQ > 0
-// fixes the quadrature size at compile time; NQ = 0 reads it from the arguments.
-// Tuning (measured on the 1,572,864-tet workload): 4 cells per consumer thread, 8
-// consumer warps, 2 CTAs per SM and a 64 KB stage budget.
-#ifndef FEM_STAGED_MIN_CTAS
-#define FEM_STAGED_MIN_CTAS 2
-#endif
-#ifndef FEM_STAGED_BUDGET_KB
-#define FEM_STAGED_BUDGET_KB 64
-#endif
-#ifndef FEM_STAGED_CPT
-#define FEM_STAGED_CPT 4
-#endif
-#ifndef FEM_STAGED_CWARPS
-#define FEM_STAGED_CWARPS 8
-#endif
-constexpr int kCPT = FEM_STAGED_CPT;
-constexpr int kConsumerWarps = FEM_STAGED_CWARPS;
-constexpr int kTile = kCPT * 32 * kConsumerWarps;
-constexpr int kMaxStages = 4;
-constexpr int kStagedThreads = 32 * kConsumerWarps + 32;  // consumers + one producer warp
-static_assert(kCPT == 2 || kCPT == 4, "two or four cells per thread");
-
+// Staged Laplacian kernel (the chunk loop of fem_pipe.cuh): each consumer thread owns kCPT
+// consecutive cells of a chunk, with vector shared-memory reads of every row, vector
+// streaming stores of every output row, and (float32 forms) the cells processed as f32x2
+// pairs. NQ > 0 fixes the quadrature size at compile time; NQ = 0 reads it from the
+// arguments.
 template <class T>
 __host__ __device__ constexpr uint32_t lap_stage_bytes(int nb, int nq, bool adj) {
     return uint32_t(kTile) * (4u * nb + uint32_t(sizeof(T)) * (nq + (adj ? nb : 0)));
@@ -634,98 +589,40 @@ __global__ void __launch_bounds__(kStagedThreads, FEM_STAGED_MIN_CTAS)
     constexpr int NB = DIM + 1;
     using T = val_t<P>;
     extern __shared__ __align__(128) unsigned char smem[];
-    __shared__ uint64_t full[kMaxStages], empty[kMaxStages];
-    __shared__ volatile int s_abort;
-
     const int64_t C = a.C;
     const int nq = NQ > 0 ? NQ : a.w.nq;
-    const int64_t ntiles = (C + kTile - 1) / kTile;
-    // this CTA's chunks: tiles blockIdx.x + i * gridDim.x, i < nchunks
-    const int64_t nchunks = ntiles > blockIdx.x ? (ntiles - blockIdx.x + gridDim.x - 1) / gridDim.x : 0;
     const uint32_t stage_bytes = lap_stage_bytes<T>(NB, nq, ADJ);
-
     // stage layout: conn[NB][kTile] int32 | K[nq][kTile] T | lambda[NB][kTile] T
     auto stage_conn = [&](int s) { return reinterpret_cast<int32_t *>(smem + size_t(s) * stage_bytes); };
     auto stage_K = [&](int s) { return reinterpret_cast<T *>(stage_conn(s) + NB * kTile); };
     auto stage_lam = [&](int s) { return stage_K(s) + nq * kTile; };
-    auto chunk_start = [&](int64_t i) { return (blockIdx.x + i * gridDim.x) * int64_t(kTile); };
-    auto chunk_cells = [&](int64_t i) {
-        const int64_t c0 = chunk_start(i);
-        return static_cast<uint32_t>(C - c0 < int64_t(kTile) ? C - c0 : int64_t(kTile));
-    };
-
-    if (threadIdx.x == 0) {
-        for (int s = 0; s < stages; ++s) mbar_init(&full[s], 1), mbar_init(&empty[s], kConsumerWarps);
-        fence_barrier_init();
-        s_abort = 0;
-    }
-    __syncthreads();
-
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    if (warp == kConsumerWarps) {
-        // ---------------- producer warp (one elected lane)
-        if (lane != 0) return;
-        const uint64_t pol = l2_evict_first_policy();
-        const T *K = static_cast<const T *>(a.K);
-        const T *L = static_cast<const T *>(a.lam);
-        int64_t issued = 0;
-        for (int64_t i = 0; i < nchunks; ++i, ++issued) {
-            const int s = static_cast<int>(i % stages);
-            if (i >= stages) {
-                // wait until every consumer warp has released the chunk i - stages
-                const uint32_t par = static_cast<uint32_t>(((i / stages) - 1) & 1);
-                if (s_abort || !mbar_wait_bounded(&empty[s], par, kWaitBudgetNs)) {
-                    s_abort = 1;
-                    break;
-                }
-            }
-            const int64_t c0 = chunk_start(i);
-            const uint32_t n = chunk_cells(i);
-            mbar_arrive_expect_tx(&full[s], n * (4u * NB + uint32_t(sizeof(T)) * (nq + (ADJ ? NB : 0))));
-            for (int b = 0; b < NB; ++b)
-                bulk_copy_g2s(stage_conn(s) + b * kTile, a.conn + b * C + c0, n * 4u, &full[s], pol);
-            for (int q = 0; q < nq; ++q)
-                bulk_copy_g2s(stage_K(s) + q * kTile, K + q * C + c0, n * uint32_t(sizeof(T)), &full[s], pol);
-            if constexpr (ADJ) {
-                for (int b = 0; b < NB; ++b)
-                    bulk_copy_g2s(stage_lam(s) + b * kTile, L + b * C + c0, n * uint32_t(sizeof(T)), &full[s], pol);
-            }
-        }
-        // drain: the last copies issued into each stage have landed before this warp leaves
-        for (int64_t k = issued - stages < 0 ? 0 : issued - stages; k < issued; ++k)
-            mbar_wait_bounded(&full[k % stages], static_cast<uint32_t>((k / stages) & 1), kWaitBudgetNs);
-        if (s_abort) record_device_error(err, FEM_DEVERR_TIMEOUT);
-        return;
-    }
-
-    // ---------------- consumer warps
     const double *X[DIM];
 #pragma unroll
     for (int k = 0; k < DIM; ++k) X[k] = a.X[k];
-    const int j0 = kCPT * threadIdx.x;
-    for (int64_t i = 0; i < nchunks; ++i) {
-        const int s = static_cast<int>(i % stages);
-        if (s_abort || !mbar_wait_bounded(&full[s], static_cast<uint32_t>((i / stages) & 1), kWaitBudgetNs)) {
-            s_abort = 1;
-            record_device_error(err, FEM_DEVERR_TIMEOUT);
-            return;
-        }
-        // n is a multiple of 4 (and of kCPT): a thread's cells are all present or all absent
-        if (j0 < static_cast<int>(chunk_cells(i)))
-            lap_chunk<DIM, P, NQ, ADJ>(a, X, nq, stage_conn(s), stage_K(s), stage_lam(s), j0, chunk_start(i));
-        __syncwarp();
-        if (lane == 0) mbar_arrive(&empty[s]);
-    }
+    const uint64_t pol = l2_evict_first_policy();
+    staged_chunks(
+        C, stages, err,
+        [&](int s, int64_t c0, uint32_t n, uint64_t *bar) {
+            const T *K = static_cast<const T *>(a.K);
+            const T *L = static_cast<const T *>(a.lam);
+            mbar_arrive_expect_tx(bar, n * (4u * NB + uint32_t(sizeof(T)) * (nq + (ADJ ? NB : 0))));
+            for (int b = 0; b < NB; ++b) bulk_copy_g2s(stage_conn(s) + b * kTile, a.conn + b * C + c0, n * 4u, bar, pol);
+            for (int q = 0; q < nq; ++q)
+                bulk_copy_g2s(stage_K(s) + q * kTile, K + q * C + c0, n * uint32_t(sizeof(T)), bar, pol);
+            if constexpr (ADJ) {
+                for (int b = 0; b < NB; ++b)
+                    bulk_copy_g2s(stage_lam(s) + b * kTile, L + b * C + c0, n * uint32_t(sizeof(T)), bar, pol);
+            }
+        },
+        [&](int s, int64_t c0, int j0) {
+            lap_chunk<DIM, P, NQ, ADJ>(a, X, nq, stage_conn(s), stage_K(s), stage_lam(s), j0, c0);
+        });
 }
-
-// Shared-memory budget of the staged kernel's ring (per CTA).
-constexpr uint32_t kStageBudget = uint32_t(FEM_STAGED_BUDGET_KB) << 10;
-constexpr uint32_t kStageMax = 200u << 10;
 
 template <int DIM, int P, int NQ, bool ADJ>
 static fem_status launch_staged(const LapArgs &a, uint32_t sb, cudaStream_t s) {
     auto k = lap_staged_kernel<DIM, P, NQ, ADJ>;
-    const int stages = static_cast<int>(std::min<uint32_t>(kMaxStages, std::max<uint32_t>(2u, kStageBudget / sb)));
+    const int stages = ring_stages(sb);
     const size_t smem = size_t(stages) * sb;
     unsigned *err = device_error_word();
     if (!err) return fail(FEM_ERR_CUDA, "device error word unavailable");

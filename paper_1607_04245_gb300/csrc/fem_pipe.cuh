@@ -14,6 +14,7 @@
 #pragma once
 
 #include <stdint.h>
+#include <string.h>
 
 #include "fem_internal.cuh"
 
@@ -97,5 +98,130 @@ __device__ __forceinline__ void bulk_copy_g2s(void *dst, const void *src, uint32
 }
 
 __device__ __forceinline__ void record_device_error(unsigned *err, unsigned bits) { atomicOr(err, bits); }
+
+// ------------------------------------------------------------------ the staged chunk loop
+//
+// Persistent CTAs walk the chunks of kTile consecutive cells round-robin (chunk
+// blockIdx.x, blockIdx.x + gridDim.x, ...), so that at any time the CTAs of the device
+// work on one contiguous front of the cell arrays (DRAM pages and the L2-resident vertices
+// of neighbouring chunks are shared). The CTA is warp-specialised: one producer warp
+// brings each chunk's cell-indexed rows into a ring of shared-memory stages with the
+// bulk-copy engine ("full" barriers count the bytes), and kConsumerWarps consumer warps
+// compute. Consumer warps release a stage on its "empty" barrier as soon as they are done
+// with it; there is no CTA-wide barrier per chunk, so the warps drift apart and one warp's
+// vertex gathers overlap other warps' arithmetic. Within a chunk each consumer thread owns
+// kCPT consecutive cells. Tuning (measured on the 1,572,864-tet Laplacian workload): 4
+// cells per consumer thread, 8 consumer warps, 2 CTAs per SM and a 64 KB stage budget.
+#ifndef FEM_STAGED_MIN_CTAS
+#define FEM_STAGED_MIN_CTAS 2
+#endif
+#ifndef FEM_STAGED_BUDGET_KB
+#define FEM_STAGED_BUDGET_KB 64
+#endif
+#ifndef FEM_STAGED_CPT
+#define FEM_STAGED_CPT 4
+#endif
+#ifndef FEM_STAGED_CWARPS
+#define FEM_STAGED_CWARPS 8
+#endif
+constexpr int kCPT = FEM_STAGED_CPT;
+constexpr int kConsumerWarps = FEM_STAGED_CWARPS;
+constexpr int kTile = kCPT * 32 * kConsumerWarps;
+constexpr int kMaxStages = 4;
+constexpr int kStagedThreads = 32 * kConsumerWarps + 32;  // consumers + one producer warp
+static_assert(kCPT == 2 || kCPT == 4, "two or four cells per thread");
+// shared-memory budget of the ring (per CTA) and the largest stage pair a CTA may hold
+constexpr uint32_t kStageBudget = uint32_t(FEM_STAGED_BUDGET_KB) << 10;
+constexpr uint32_t kStageMax = 200u << 10;
+
+// Stages in the ring for stages of `stage_bytes` each (at least two: copy ahead of use).
+inline int ring_stages(uint32_t stage_bytes) {
+    const uint32_t n = kStageBudget / stage_bytes;
+    return static_cast<int>(n < 2u ? 2u : (n > uint32_t(kMaxStages) ? uint32_t(kMaxStages) : n));
+}
+
+// CPT consecutive values of a cell-indexed row in shared memory (one vector load)
+template <int CPT, class T>
+__device__ __forceinline__ void lds_row(const T *p, T (&v)[CPT]) {
+    static_assert(CPT == 2 || CPT == 4, "two or four cells per thread");
+    if constexpr (sizeof(T) * CPT == 8) {
+        const uint2 t = *reinterpret_cast<const uint2 *>(p);
+        memcpy(&v[0], &t.x, 4), memcpy(&v[1], &t.y, 4);
+    } else if constexpr (sizeof(T) * CPT == 16) {
+        const uint4 t = *reinterpret_cast<const uint4 *>(p);
+        memcpy(&v[0], &t, 16);
+    } else {
+        const uint4 t0 = reinterpret_cast<const uint4 *>(p)[0], t1 = reinterpret_cast<const uint4 *>(p)[1];
+        memcpy(&v[0], &t0, 16), memcpy(&v[2], &t1, 16);
+    }
+}
+
+// The chunk loop of a staged kernel launched with kStagedThreads threads and
+// `stages` * stage-size bytes of dynamic shared memory. The producer lane calls
+// issue(s, c0, n, bar) to start the bulk copies of the chunk of n cells at cell c0 into
+// stage s (announcing their bytes on bar with mbar_arrive_expect_tx); every consumer
+// thread whose cells j0 .. j0 + kCPT - 1 lie in the chunk calls work(s, c0, j0). The cell
+// count C must be a multiple of kCPT, so that a thread's cells are all present or all
+// absent. A wait that runs out sets FEM_DEVERR_TIMEOUT in *err; the producer drains its
+// copies in flight before it leaves.
+template <class Issue, class Work>
+__device__ __forceinline__ void staged_chunks(int64_t C, int stages, unsigned *err, const Issue &issue,
+                                              const Work &work) {
+    __shared__ uint64_t full[kMaxStages], empty[kMaxStages];
+    __shared__ volatile int s_abort;
+    const int64_t ntiles = (C + kTile - 1) / kTile;
+    // this CTA's chunks: tiles blockIdx.x + i * gridDim.x, i < nchunks
+    const int64_t nchunks = ntiles > blockIdx.x ? (ntiles - blockIdx.x + gridDim.x - 1) / gridDim.x : 0;
+    auto chunk_start = [&](int64_t i) { return (blockIdx.x + i * gridDim.x) * int64_t(kTile); };
+    auto chunk_cells = [&](int64_t i) {
+        const int64_t c0 = chunk_start(i);
+        return static_cast<uint32_t>(C - c0 < int64_t(kTile) ? C - c0 : int64_t(kTile));
+    };
+
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < stages; ++s) mbar_init(&full[s], 1), mbar_init(&empty[s], kConsumerWarps);
+        fence_barrier_init();
+        s_abort = 0;
+    }
+    __syncthreads();
+
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (warp == kConsumerWarps) {
+        // ---------------- producer warp (one elected lane)
+        if (lane != 0) return;
+        int64_t issued = 0;
+        for (int64_t i = 0; i < nchunks; ++i, ++issued) {
+            const int s = static_cast<int>(i % stages);
+            if (i >= stages) {
+                // wait until every consumer warp has released the chunk i - stages
+                const uint32_t par = static_cast<uint32_t>(((i / stages) - 1) & 1);
+                if (s_abort || !mbar_wait_bounded(&empty[s], par, kWaitBudgetNs)) {
+                    s_abort = 1;
+                    break;
+                }
+            }
+            issue(s, chunk_start(i), chunk_cells(i), &full[s]);
+        }
+        // drain: the last copies issued into each stage have landed before this warp leaves
+        for (int64_t k = issued - stages < 0 ? 0 : issued - stages; k < issued; ++k)
+            mbar_wait_bounded(&full[k % stages], static_cast<uint32_t>((k / stages) & 1), kWaitBudgetNs);
+        if (s_abort) record_device_error(err, FEM_DEVERR_TIMEOUT);
+        return;
+    }
+
+    // ---------------- consumer warps
+    const int j0 = kCPT * threadIdx.x;
+    for (int64_t i = 0; i < nchunks; ++i) {
+        const int s = static_cast<int>(i % stages);
+        if (s_abort || !mbar_wait_bounded(&full[s], static_cast<uint32_t>((i / stages) & 1), kWaitBudgetNs)) {
+            s_abort = 1;
+            record_device_error(err, FEM_DEVERR_TIMEOUT);
+            return;
+        }
+        if (j0 < static_cast<int>(chunk_cells(i))) work(s, chunk_start(i), j0);
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&empty[s]);
+    }
+}
 
 }  // namespace fem

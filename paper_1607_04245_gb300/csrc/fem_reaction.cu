@@ -120,11 +120,78 @@ __device__ __forceinline__ void rd_element(const RdArgs &a, const T (&n)[DIM][DI
     }
 }
 
+// One cell: its vertex ids (unclamped), the P0 coefficient a0 (unused for a P1 field) and
+// its reaction values ci at the quadrature points give the element vector rr. Float32
+// forms: a cell failing the mixed form's shape test is recomputed in float64.
+template <int DIM, int P, bool A_P1, bool REACT, bool DRIFT, int NQA>
+__device__ __forceinline__ void rd_cell(const RdArgs &a, const double *const (&X)[DIM], const int32_t (&vid)[DIM + 1],
+                                        val_t<P> a0, const val_t<P> (&ci)[NQA], int nq, val_t<P> (&rr)[DIM + 1]) {
+    constexpr int NB = DIM + 1;
+    using T = val_t<P>;
+    const T *__restrict__ u = static_cast<const T *>(a.u);
+    const T *__restrict__ af = static_cast<const T *>(a.a);
+    uint32_t v[NB];
+    T uu[NB], aa[NB];
+#pragma unroll
+    for (int b = 0; b < NB; ++b) {
+        v[b] = clamp_vid(vid[b], a.V);
+        uu[b] = ld_gather(u + v[b]);
+    }
+    // Kbar = sum_q w_q a(xi_q)
+    qsum_t<P> ks;
+    if constexpr (A_P1) {
+#pragma unroll
+        for (int b = 0; b < NB; ++b) aa[b] = ld_gather(af + v[b]);
+        ks.first(tab_m<P>(a.t, 0), aa[0]);
+#pragma unroll
+        for (int b = 1; b < NB; ++b) ks.add(tab_m<P>(a.t, b), aa[b]);
+    } else {
+#pragma unroll
+        for (int b = 0; b < NB; ++b) aa[b] = zero<T>();
+        ks.first(tab_wsum<P>(a.t), a0);
+    }
+    double xs[NB][DIM];
+    gather_coords<DIM>(X, v, xs);
+    if constexpr (P == FEM_FP64) {
+        double ee[DIM][DIM], n[DIM][DIM];
+        columns_f64<DIM>(xs, ee);
+        const double det = adjugate_rows<DIM>(ee, n);
+        rd_element<DIM, P, double, REACT, DRIFT, NQA>(a, n, det, uu, aa, ks.value(), ci, nq, rr);
+    } else {
+        float ee[DIM][DIM], n[DIM][DIM];
+        if constexpr (P == FEM_FP32_MIXED) columns_mixed<DIM>(xs, ee);
+        else columns_f32<DIM>(xs, ee);
+        const float det = adjugate_rows<DIM>(ee, n);
+        bool ok = true;
+        if constexpr (P == FEM_FP32_MIXED) ok = shape_ok<DIM>(ee, det, a.tau2);
+        if (ok) {
+            rd_element<DIM, P, float, REACT, DRIFT, NQA>(a, n, det, uu, aa, ks.value(), ci, nq, rr);
+        } else {
+            // badly shaped cell: float64 geometry and sums, float64 tables
+            double e64[DIM][DIM], n64[DIM][DIM], u64[NB], a64[NB], r64[NB], c64[NQA];
+            columns_f64<DIM>(xs, e64);
+            const double det64 = adjugate_rows<DIM>(e64, n64);
+#pragma unroll
+            for (int b = 0; b < NB; ++b) u64[b] = uu[b], a64[b] = aa[b];
+            if constexpr (REACT) {
+                for (int q = 0; q < nq; ++q) c64[q] = ci[q];
+            }
+            rd_element<DIM, FEM_FP64, double, REACT, DRIFT, NQA>(a, n64, det64, u64, a64, ks.value_f64(), c64, nq,
+                                                                r64);
+#pragma unroll
+            for (int b = 0; b < NB; ++b) rr[b] = static_cast<float>(r64[b]);
+        }
+    }
+}
+
 // Grid-stride over groups of CPT consecutive cells. A_P1: the coefficient field is nodal;
 // DRIFT (P1 only): the grad a term. CPT = 4 with NQ > 0 (the quadrature size fixed at
 // compile time) reads the connectivity, reaction and P0 coefficient rows and writes the
 // element vectors with 16-byte vector accesses; CPT = 1, NQ = 0 is the general form
-// (any n_q, unaligned rows, ragged sizes).
+// (any n_q, unaligned rows, ragged sizes). Staging the rows through shared memory with the
+// bulk-copy loop of the Laplacian kernel was slower here (37.2 against 33.7 us on the
+// 1,572,864-tet workload): at that kernel's 2 CTAs per SM the register cap spills this
+// element's state.
 template <int DIM, int P, bool A_P1, bool REACT, bool DRIFT, int CPT, int NQ>
 __global__ void __launch_bounds__(kBlock) rd_kernel(const __grid_constant__ RdArgs a) {
     static_assert(A_P1 || !DRIFT, "grad a vanishes inside a cell for a P0 field");
@@ -134,7 +201,6 @@ __global__ void __launch_bounds__(kBlock) rd_kernel(const __grid_constant__ RdAr
     using T = val_t<P>;
     const int64_t C = a.C;
     const int nq = NQ > 0 ? NQ : a.w.nq;
-    const T *__restrict__ u = static_cast<const T *>(a.u);
     const T *__restrict__ af = static_cast<const T *>(a.a);
     const T *__restrict__ cf = static_cast<const T *>(a.c);
     T *__restrict__ out = static_cast<T *>(a.out);
@@ -158,64 +224,15 @@ __global__ void __launch_bounds__(kBlock) rd_kernel(const __grid_constant__ RdAr
         T r[NB][CPT];
 #pragma unroll
         for (int i = 0; i < CPT; ++i) {
-            uint32_t v[NB];
-            T uu[NB], aa[NB];
+            int32_t vi[NB];
+            T ci[NQA], rr[NB];
 #pragma unroll
-            for (int b = 0; b < NB; ++b) {
-                v[b] = clamp_vid(vid[b][i], a.V);
-                uu[b] = ld_gather(u + v[b]);
-            }
-            // Kbar = sum_q w_q a(xi_q)
-            qsum_t<P> ks;
-            if constexpr (A_P1) {
-#pragma unroll
-                for (int b = 0; b < NB; ++b) aa[b] = ld_gather(af + v[b]);
-                ks.first(tab_m<P>(a.t, 0), aa[0]);
-#pragma unroll
-                for (int b = 1; b < NB; ++b) ks.add(tab_m<P>(a.t, b), aa[b]);
-            } else {
-#pragma unroll
-                for (int b = 0; b < NB; ++b) aa[b] = zero<T>();
-                ks.first(tab_wsum<P>(a.t), a0[i]);
-            }
-            T ci[NQA];
+            for (int b = 0; b < NB; ++b) vi[b] = vid[b][i];
             if constexpr (REACT) {
 #pragma unroll(NQ > 0 ? NQ : 1)
                 for (int q = 0; q < nq; ++q) ci[q] = cq[q][i];
             }
-            double xs[NB][DIM];
-            gather_coords<DIM>(X, v, xs);
-            T rr[NB];
-            if constexpr (P == FEM_FP64) {
-                double ee[DIM][DIM], n[DIM][DIM];
-                columns_f64<DIM>(xs, ee);
-                const double det = adjugate_rows<DIM>(ee, n);
-                rd_element<DIM, P, double, REACT, DRIFT, NQA>(a, n, det, uu, aa, ks.value(), ci, nq, rr);
-            } else {
-                float ee[DIM][DIM], n[DIM][DIM];
-                if constexpr (P == FEM_FP32_MIXED) columns_mixed<DIM>(xs, ee);
-                else columns_f32<DIM>(xs, ee);
-                const float det = adjugate_rows<DIM>(ee, n);
-                bool ok = true;
-                if constexpr (P == FEM_FP32_MIXED) ok = shape_ok<DIM>(ee, det, a.tau2);
-                if (ok) {
-                    rd_element<DIM, P, float, REACT, DRIFT, NQA>(a, n, det, uu, aa, ks.value(), ci, nq, rr);
-                } else {
-                    // badly shaped cell: float64 geometry and sums, float64 tables
-                    double e64[DIM][DIM], n64[DIM][DIM], u64[NB], a64[NB], r64[NB], c64[NQA];
-                    columns_f64<DIM>(xs, e64);
-                    const double det64 = adjugate_rows<DIM>(e64, n64);
-#pragma unroll
-                    for (int b = 0; b < NB; ++b) u64[b] = uu[b], a64[b] = aa[b];
-                    if constexpr (REACT) {
-                        for (int q = 0; q < nq; ++q) c64[q] = ci[q];
-                    }
-                    rd_element<DIM, FEM_FP64, double, REACT, DRIFT, NQA>(a, n64, det64, u64, a64, ks.value_f64(),
-                                                                        c64, nq, r64);
-#pragma unroll
-                    for (int b = 0; b < NB; ++b) rr[b] = static_cast<float>(r64[b]);
-                }
-            }
+            rd_cell<DIM, P, A_P1, REACT, DRIFT, NQA>(a, X, vi, A_P1 ? zero<T>() : a0[i], ci, nq, rr);
 #pragma unroll
             for (int b = 0; b < NB; ++b) r[b][i] = rr[b];
         }

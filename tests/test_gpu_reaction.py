@@ -10,7 +10,7 @@ import torch
 import oracle
 import paper_1607_04245_gb300 as fem
 import workloads
-from gpu_util import PRECS, TOL, rel_err, to_dev
+from gpu_util import PRECS, TOL, misaligned, rel_err, to_dev
 
 pytestmark = pytest.mark.gpu
 
@@ -64,6 +64,31 @@ def test_reaction_diffusion_ragged_with_drift(n_cells, prec):
     mesh = workloads.first_cells(base.mesh, n_cells)
     case = workloads.Case("laplacian", mesh, base.rule, base.u[: mesh.n_verts], K=base.K[:, :n_cells].copy())
     assert _run(case, a_p1[: mesh.n_verts], 1, c[:, :n_cells].copy(), prec, drift=-0.7) <= TOL[prec]
+
+
+@pytest.mark.parametrize("n_cells", [4, 1020, 1024, 1028, 3076])
+@pytest.mark.parametrize("a_space", [0, 1])
+@pytest.mark.parametrize("prec", ["mixed", "fp32"])
+def test_vector_rows_match_oracle_and_per_cell_path(n_cells, a_space, prec):
+    """Aligned rows and a cell count divisible by 4 take the four-cells-per-thread kernel with
+    16-byte row accesses; misaligned rows take the one-cell-per-thread kernel, whose per-cell
+    arithmetic is the same: the two agree bitwise."""
+    base, a_p1, a_p0, c = _case(3)
+    mesh = workloads.first_cells(base.mesh, n_cells)
+    a = (a_p1[: mesh.n_verts] if a_space == 1 else a_p0[:n_cells]).copy()
+    case = workloads.Case("laplacian", mesh, base.rule, base.u[: mesh.n_verts], K=base.K[:, :n_cells].copy())
+    cc = c[:, :n_cells].copy()
+    drift = 0.6 if a_space == 1 else 0.0
+    assert _run(case, a, a_space, cc, prec, drift) <= TOL[prec]
+    dt = fem.value_dtype(prec)
+    m, q = case.mesh, case.rule
+    coords, conn = to_dev(m.coords, torch.float64), to_dev(m.conn, torch.int32)
+    u, ad, cd = to_dev(case.u, dt), to_dev(a, dt), to_dev(cc, dt)
+    staged = fem.fem_integrate_reaction_diffusion(coords, conn, u, ad, q.points, q.weights, c=cd, a_space=a_space,
+                                                  drift=drift, prec=prec)
+    per_cell = fem.fem_integrate_reaction_diffusion(coords, misaligned(conn), u, ad, q.points, q.weights,
+                                                    c=misaligned(cd), a_space=a_space, drift=drift, prec=prec)
+    assert torch.equal(staged, per_cell)
 
 
 def test_drift_ignored_for_p0_coefficient():
