@@ -318,8 +318,8 @@ fem_status fem_adjoint_laplacian(int dim, int64_t n_cells, int64_t n_verts, cons
  * library until the process exits). Nothing is allocated: no cudaMalloc, no cudaFree.
  *   - Limit: (dim+1) * n_cells * sizeof(value) must not exceed FEM_NOALLOC_SCRATCH_BYTES
  *     (16 MiB: up to 1,048,576 tets or 1,398,101 triangles in the float32 forms,
- *     524,288 tets or 699,050 triangles in float64); larger calls return FEM_ERR_SHAPE
- *     with a message and launch nothing.
+ *     524,288 tets or 699,050 triangles in float64 and FEM_FP64_DF); larger calls
+ *     return FEM_ERR_SHAPE with a message and launch nothing.
  *   - Set-up: the first call on a device looks up the array's device address
  *     (cudaGetSymbolAddress) with that device current; make that first call before
  *     any stream capture.
@@ -392,7 +392,11 @@ int64_t fem_arena_capacity(fem_arena *arena);
  *   fem_build_node2cell then fem_adjoint_laplacian), copy out_bytes[0] from slot OUT
  *   (element vectors, or dK) to host_out[0] and out_bytes[1] from slot DU (du) to
  *   host_out[1], then record `event` (from fem_serve_event_create). Returns after
- *   enqueueing; errors as the entry points it calls.
+ *   enqueueing; errors as the entry points it calls. Before any copy or launch the
+ *   descriptor is checked against the block: every array the request uses (sizes from
+ *   dim, n_q, n_cells, n_verts and prec) must lie inside [0, block_bytes), in_bytes
+ *   must not exceed block_bytes and out_bytes[k] must not exceed its source array;
+ *   otherwise FEM_ERR_ARG and nothing is enqueued.
  * fem_serve_events_query -- done[i] = 1 if events[i] has completed, else 0.
  * ------------------------------------------------------------------------------- */
 enum {
@@ -415,6 +419,7 @@ typedef struct {
     void *host_out[2];
     int64_t out_bytes[2];
     int64_t offset[FEM_SERVE_SLOTS];
+    int64_t block_bytes;    /* size of the device block the offsets point into */
 } fem_serve_request;
 int64_t fem_serve_request_bytes(void); /* sizeof(fem_serve_request), for bindings to check their layout */
 fem_status fem_serve_event_create(void **event);

@@ -55,9 +55,9 @@ extern "C" fem_status fem_adjoint_laplacian_noalloc(int dim, int64_t n_cells, in
                                                     const int32_t *node_idx, fem_precision prec, fem_stream stream) {
     if (dim != 2 && dim != 3) return fail(FEM_ERR_ARG, "dim = %d, must be 2 or 3", dim);
     if (n_cells < 0) return fail(FEM_ERR_ARG, "negative n_cells");
-    if (prec != FEM_FP64 && prec != FEM_FP32_MIXED && prec != FEM_FP32)
+    if (prec != FEM_FP64 && prec != FEM_FP32_MIXED && prec != FEM_FP32 && prec != FEM_FP64_DF)
         return fail(FEM_ERR_ARG, "unknown precision %d", static_cast<int>(prec));
-    const int64_t value_bytes = prec == FEM_FP64 ? 8 : 4;
+    const int64_t value_bytes = (prec == FEM_FP64 || prec == FEM_FP64_DF) ? 8 : 4;
     const int64_t need = int64_t(dim + 1) * n_cells * value_bytes;
     if (need > int64_t(FEM_NOALLOC_SCRATCH_BYTES))
         return fail(FEM_ERR_SHAPE,

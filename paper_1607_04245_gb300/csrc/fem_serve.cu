@@ -38,12 +38,59 @@ extern "C" fem_status fem_serve_events_query(void *const *events, int n, int *do
     return FEM_OK;
 }
 
+// Bytes of every array a request uses (0: slot unused), from its sizes and precision.
+static fem_status slot_bytes(const fem_serve_request *r, int64_t (&bytes)[FEM_SERVE_SLOTS]) {
+    if (r->dim != 2 && r->dim != 3) return fail(FEM_ERR_ARG, "dim = %d, must be 2 or 3", r->dim);
+    if (r->n_q < 1 || r->n_q > FEM_MAX_QPTS) return fail(FEM_ERR_ARG, "n_q = %d", r->n_q);
+    if (r->n_cells < 0 || r->n_cells > INT32_MAX || r->n_verts < 0 || r->n_verts > INT32_MAX)
+        return fail(FEM_ERR_ARG, "n_cells or n_verts out of range");
+    int64_t s;
+    switch (r->prec) {
+        case FEM_FP64: case FEM_FP64_DF: s = 8; break;
+        case FEM_FP32_MIXED: case FEM_FP32: s = 4; break;
+        default: return fail(FEM_ERR_ARG, "unknown precision %d", r->prec);
+    }
+    const int64_t d = r->dim, C = r->n_cells, V = r->n_verts, nq = r->n_q, nc = r->physics == 0 ? 1 : d;
+    for (auto &b : bytes) b = 0;
+    bytes[FEM_SERVE_COORDS] = d * V * 8;
+    bytes[FEM_SERVE_CONN] = (d + 1) * C * 4;
+    bytes[FEM_SERVE_U] = nc * V * s;
+    bytes[FEM_SERVE_K] = nq * C * s;
+    if (r->physics == 1) bytes[FEM_SERVE_MU] = nq * C * s;
+    if (r->kind == 0) {
+        bytes[FEM_SERVE_OUT] = (d + 1) * nc * C * s;
+    } else {
+        bytes[FEM_SERVE_ADJ] = (d + 1) * C * s;
+        bytes[FEM_SERVE_OUT] = nq * C * s;
+        bytes[FEM_SERVE_DU] = V * s;
+        bytes[FEM_SERVE_SCRATCH] = (d + 1) * C * s;
+        bytes[FEM_SERVE_NODE_PTR] = (V + 1) * 4;
+        bytes[FEM_SERVE_NODE_IDX] = (d + 1) * C * 4;
+        bytes[FEM_SERVE_WORK] = fem_node2cell_work_size(V) * 4;
+    }
+    return FEM_OK;
+}
+
 extern "C" fem_status fem_serve_launch(const fem_serve_request *r, void *block, void *event, fem_stream stream) {
     if (!r || !block || !event) return fail(FEM_ERR_ARG, "a NULL argument");
     if (r->kind != 0 && r->kind != 1) return fail(FEM_ERR_ARG, "kind = %d", r->kind);
     if (r->physics != 0 && r->physics != 1) return fail(FEM_ERR_ARG, "physics = %d", r->physics);
     if (r->kind == 1 && r->physics != 0) return fail(FEM_ERR_UNSUPPORTED, "adjoint requests are Laplacian only");
     if (r->in_bytes < 0 || r->out_bytes[0] < 0 || r->out_bytes[1] < 0) return fail(FEM_ERR_ARG, "negative size");
+    // the descriptor against its block: nothing below may touch memory outside it
+    int64_t need[FEM_SERVE_SLOTS];
+    fem_status vs = slot_bytes(r, need);
+    if (vs != FEM_OK) return vs;
+    if (r->block_bytes <= 0 || r->in_bytes > r->block_bytes) return fail(FEM_ERR_ARG, "in_bytes exceeds block_bytes");
+    for (int k = 0; k < FEM_SERVE_SLOTS; ++k) {
+        if (need[k] == 0) continue;
+        if (r->offset[k] < 0 || r->offset[k] > r->block_bytes - need[k])
+            return fail(FEM_ERR_ARG, "array %d (%lld bytes at offset %lld) outside the %lld-byte block", k,
+                        static_cast<long long>(need[k]), static_cast<long long>(r->offset[k]),
+                        static_cast<long long>(r->block_bytes));
+    }
+    if (r->out_bytes[0] > need[FEM_SERVE_OUT] || r->out_bytes[1] > need[FEM_SERVE_DU])
+        return fail(FEM_ERR_ARG, "out_bytes larger than the arrays they copy");
     char *b = static_cast<char *>(block);
     auto at = [&](int slot) { return static_cast<void *>(b + r->offset[slot]); };
     const fem_precision prec = static_cast<fem_precision>(r->prec);

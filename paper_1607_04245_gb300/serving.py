@@ -115,7 +115,7 @@ class ServeRequestDesc(ctypes.Structure):
                 ("qpts", ctypes.c_void_p), ("qw", ctypes.c_void_p),
                 ("host_in", ctypes.c_void_p), ("in_bytes", ctypes.c_int64),
                 ("host_out", ctypes.c_void_p * 2), ("out_bytes", ctypes.c_int64 * 2),
-                ("offset", ctypes.c_int64 * 12)]
+                ("offset", ctypes.c_int64 * 12), ("block_bytes", ctypes.c_int64)]
 
 
 def _serve_lib():
@@ -185,6 +185,7 @@ class Request:
             d.out_bytes[k] = t.numel() * t.element_size()
         for name, off in self.offsets().items():
             d.offset[SERVE_SLOTS[name]] = off
+        d.block_bytes = footprint(self)
         self.desc = d
         return d
 

@@ -145,4 +145,50 @@ def test_serve_launch_validation(lib):
     assert lib.fem_serve_events_query(None, 0, None) == 0
     assert lib.fem_serve_events_query(None, 1, None) == -1
     lib.fem_serve_request_bytes.restype = ctypes.c_int64
-    assert lib.fem_serve_request_bytes() == ctypes.sizeof(ServeRequestDesc) == 200
+    assert lib.fem_serve_request_bytes() == ctypes.sizeof(ServeRequestDesc) == 208
+
+
+def test_serve_launch_checks_the_descriptor_against_its_block(lib):
+    """Arrays outside the block, oversized uploads or downloads are argument errors,
+    found before any copy or launch (the block pointer is never dereferenced)."""
+    from paper_1607_04245_gb300.serving import SERVE_SLOTS, ServeRequestDesc
+
+    P = ctypes.c_void_p
+    lib.fem_serve_launch.argtypes = [ctypes.POINTER(ServeRequestDesc), P, P, P]
+    lib.fem_serve_launch.restype = ctypes.c_int
+    lib.fem_last_error.restype = ctypes.c_char_p
+    fake = P(0x1000)
+
+    def desc(C=8, V=9):
+        d = ServeRequestDesc()
+        d.kind, d.physics, d.dim, d.n_q, d.prec = 0, 0, 2, 3, 1
+        d.n_cells, d.n_verts = C, V
+        sizes = {"coords": 2 * V * 8, "conn": 3 * C * 4, "u": V * 4, "K": 3 * C * 4, "out": 3 * C * 4}
+        off = 0
+        for name, n in sizes.items():
+            d.offset[SERVE_SLOTS[name]] = off
+            off += n
+        d.in_bytes = off - sizes["out"]
+        d.out_bytes[0] = sizes["out"]
+        d.block_bytes = off
+        return d
+
+    d = desc()
+    d.block_bytes -= 1  # the element vectors end one byte past the block
+    assert lib.fem_serve_launch(ctypes.byref(d), fake, fake, None) == -1
+    assert b"outside" in lib.fem_last_error()
+    d = desc()
+    d.offset[SERVE_SLOTS["conn"]] = -16
+    assert lib.fem_serve_launch(ctypes.byref(d), fake, fake, None) == -1
+    d = desc()
+    d.in_bytes = d.block_bytes + 1
+    assert lib.fem_serve_launch(ctypes.byref(d), fake, fake, None) == -1
+    d = desc()
+    d.out_bytes[0] += 4
+    assert lib.fem_serve_launch(ctypes.byref(d), fake, fake, None) == -1
+    d = desc()
+    d.out_bytes[1] = 4  # a residual request has no second result
+    assert lib.fem_serve_launch(ctypes.byref(d), fake, fake, None) == -1
+    d = desc()
+    d.n_q = 0
+    assert lib.fem_serve_launch(ctypes.byref(d), fake, fake, None) == -1

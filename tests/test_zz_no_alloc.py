@@ -60,6 +60,18 @@ def test_noalloc_matches_workspace_entry_point_twice(dim, prec):
         assert rel_err(du, ru) <= TOL[prec], (call, "du")
 
 
+def test_noalloc_double_float_form():
+    """FEM_FP64_DF through the fixed array: float64 values, 8 bytes per workspace entry."""
+    case = workloads.adjoint_case(6 * 24 ** 3)
+    c, d = device_arrays(case, "fp64")
+    ptr, idx = fem.fem_build_node2cell(d["conn"], c.n_verts)
+    lam = torch.from_numpy(np.random.default_rng(7).uniform(-1, 1, (4, c.n_cells))).to("cuda", torch.float64)
+    dK, du = _noalloc(c, d, lam, ptr, idx, "fp64_df")
+    rK, ru = fem.fem_adjoint_laplacian(d["coords"], d["conn"], d["u"], d["K"], c.rule.points, c.rule.weights, lam,
+                                       ptr, idx, prec="fp64_df")
+    assert torch.equal(dK, rK) and torch.equal(du, ru)
+
+
 def test_noalloc_rejects_sizes_beyond_its_array():
     L = binding.lib()
     f = L.fem_adjoint_laplacian_noalloc
