@@ -7,7 +7,7 @@
 #include <cstdarg>
 #include <cstdio>
 #include <mutex>
-#include <unordered_map>
+#include <utility>
 
 #include "fem_pipe.cuh"
 
@@ -111,16 +111,22 @@ int sm_count() {
 
 int grid_for(int64_t n_threads, int block, const void *kernel) {
     static std::mutex mu;
-    static std::unordered_map<const void *, int> occ_cache;
+    static std::map<std::pair<const void *, int>, int> occ_cache[64];  // per device, (kernel, block)
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) dev = 0;
     int occ;
     {
         std::lock_guard<std::mutex> lk(mu);
-        auto it = occ_cache.find(kernel);
-        if (it == occ_cache.end()) {
+        auto &cache = occ_cache[dev];
+        const auto key = std::make_pair(kernel, block);
+        auto it = cache.find(key);
+        if (it == cache.end()) {
             int o = 0;
-            if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, kernel, block, 0) != cudaSuccess || o < 1) o = 1;
-            cudaGetLastError();
-            it = occ_cache.emplace(kernel, o).first;
+            if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, kernel, block, 0) != cudaSuccess) {
+                cudaGetLastError();  // clear the failed query only; the launch reports real errors
+                o = 1;
+            }
+            it = cache.emplace(key, o < 1 ? 1 : o).first;
         }
         occ = it->second;
     }
