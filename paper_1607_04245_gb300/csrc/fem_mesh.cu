@@ -180,18 +180,42 @@ struct NodeSum<float> {  // compensated (TwoSum) sum in float32
     __device__ __forceinline__ float value() const { return s + c; }
 };
 
+constexpr int kGatherBatch = 8;
+
 template <int NB, int NCOMP, class T>
 __global__ void gather_kernel(int64_t C, int64_t V, const T *__restrict__ elem, const int32_t *__restrict__ ptr,
                               const int32_t *__restrict__ idx, T *__restrict__ out) {
     const int64_t stride = int64_t(gridDim.x) * blockDim.x;
+    auto entry = [&](int32_t t, int k) {
+        const int32_t cell = t / NB, a = t - cell * NB;
+        return __ldg(elem + int64_t(a * NCOMP + k) * C + cell);
+    };
     for (int64_t n = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; n < V; n += stride) {
         const int32_t b = ptr[n], e = ptr[n + 1];
         NodeSum<T> acc[NCOMP];
-        for (int32_t j = b; j < e; ++j) {
-            const int32_t t = __ldg(idx + j);
-            const int32_t cell = t / NB, a = t - cell * NB;
+        // kGatherBatch list entries at a time: their loads are independent and in flight
+        // together; the sums still take the entries one by one in list order. (A warp
+        // reading 32 vertices' lists together with coalesced loads and summing from shared
+        // memory was slower: 60.4 against 48.8 us for the adjoint on 1,572,864 tets.)
+        int32_t j = b;
+        for (; j + kGatherBatch <= e; j += kGatherBatch) {
+            int32_t t[kGatherBatch];
+            T val[kGatherBatch][NCOMP];
 #pragma unroll
-            for (int k = 0; k < NCOMP; ++k) acc[k].add(__ldg(elem + int64_t(a * NCOMP + k) * C + cell));
+            for (int i = 0; i < kGatherBatch; ++i) t[i] = __ldg(idx + j + i);
+#pragma unroll
+            for (int i = 0; i < kGatherBatch; ++i)
+#pragma unroll
+                for (int k = 0; k < NCOMP; ++k) val[i][k] = entry(t[i], k);
+#pragma unroll
+            for (int i = 0; i < kGatherBatch; ++i)
+#pragma unroll
+                for (int k = 0; k < NCOMP; ++k) acc[k].add(val[i][k]);
+        }
+        for (; j < e; ++j) {
+            const int32_t t = __ldg(idx + j);
+#pragma unroll
+            for (int k = 0; k < NCOMP; ++k) acc[k].add(entry(t, k));
         }
 #pragma unroll
         for (int k = 0; k < NCOMP; ++k) out[k * V + n] = acc[k].value();
