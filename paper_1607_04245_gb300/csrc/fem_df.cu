@@ -8,14 +8,15 @@
 // significand; Dekker's double-length arithmetic built from TwoSum / TwoProduct):
 //   * the Jacobian columns e_j = x_j - x_0 are formed in float64 (correctly rounded, no
 //     loss to cancellation), then split into pairs with integer operations;
-//   * u_b and K_q are split into pairs the same way; the weights are split on the host;
+//   * u_b and K_q are split into pairs the same way and the weights are split on the host
+//     (the Laplacian forms Kbar = sum_q w_q K_q in float64 and splits that instead);
 //   * adjugate, determinant, field gradient, coefficient sum, the one division and the
 //     contraction run in pair arithmetic, every sum of products as one compensated dot
 //     product with a single renormalisation;
 //   * each element-vector entry is widened back to float64 (integer operations) and
 //     summed with one float64 add.
-// Per cell (3D Laplacian) this issues 13 float64 additions instead of ~71 float64
-// operations (elasticity: 21, the columns and 12 outputs). The
+// Per cell (3D Laplacian) this issues 17 float64 operations instead of ~71 (the columns,
+// the coefficient sum, the 4 outputs; elasticity: 21, the columns and 12 outputs). The
 // relative error against the exact element integral stays near 1e-14 on the workloads
 // (validated against the oracle at the float64 tolerance, 1e-12).
 #include "fem_cell.cuh"
@@ -154,6 +155,15 @@ __device__ __forceinline__ dfl df_weighted(const float *whi, const float *wlo, c
     return acc_value(acc);
 }
 
+// sum_q w_q f_q for a float64 row f[q * C + c], in float64: one rounding per point, and a
+// handful of float64-pipe instructions in place of the ~90 integer and float32 ones of the
+// same sum in pair arithmetic
+__device__ __forceinline__ double weighted64(const double *w, const double *f, int64_t C, int64_t c, int nq) {
+    double s = w[0] * ld_stream(f + c);
+    for (int q = 1; q < nq; ++q) s = fma(w[q], ld_stream(f + q * C + c), s);
+    return s;
+}
+
 // float -> float64 with integer operations (normal numbers; zero and float32 subnormals,
 // below 2^-126, widen to a signed zero)
 __device__ __forceinline__ double widen(float x) {
@@ -174,7 +184,7 @@ struct DfArgs {
     int64_t C;
     uint32_t V;
     int nq;
-    float whi[FEM_MAX_QPTS], wlo[FEM_MAX_QPTS];
+    double wd[FEM_MAX_QPTS];
 };
 
 template <int DIM>
@@ -187,14 +197,18 @@ __global__ void __launch_bounds__(kBlock, 5) lap_df_kernel(const __grid_constant
     const int64_t stride = int64_t(gridDim.x) * blockDim.x;
     for (int64_t c = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; c < C; c += stride) {
         uint32_t v[NB];
-        dfl uu[NB];
 #pragma unroll
-        for (int b = 0; b < NB; ++b) {
-            v[b] = clamp_vid(ld_stream(a.conn + b * C + c), a.V);
-            uu[b] = df_from_double(ld_gather(a.u + v[b]));
+        for (int b = 0; b < NB; ++b) v[b] = clamp_vid(ld_stream(a.conn + b * C + c), a.V);
+        // Kbar = sum_q w_q K_q in float64, then as a pair: 64 against 67 us on the
+        // 1,572,864-tet workload. Forming u_j - u_0 in float64 too, or the elasticity and
+        // adjoint coefficient sums in float64, was slower: the float64 pipe is half busy.
+        const dfl kbar = df_from_double(weighted64(a.wd, a.K, C, c, a.nq));
+        dfl du[DIM];
+        {
+            const dfl u0 = df_from_double(ld_gather(a.u + v[0]));
+#pragma unroll
+            for (int j = 0; j < DIM; ++j) du[j] = df_sub(df_from_double(ld_gather(a.u + v[j + 1])), u0);
         }
-        // Kbar = sum_q w_q K_q
-        const dfl kbar = df_weighted(a.whi, a.wlo, a.K, C, c, a.nq);
         // Jacobian columns in float64, then pairs
         double xs[NB][DIM];
         gather_coords<DIM>(X, v, xs);
@@ -207,9 +221,7 @@ __global__ void __launch_bounds__(kBlock, 5) lap_df_kernel(const __grid_constant
         dfl n[DIM][DIM];
         const dfl det = df_adjugate<DIM>(e, n);
         // h = sum_j (u_j - u_0) n_j
-        dfl du[DIM], h[DIM];
-#pragma unroll
-        for (int j = 0; j < DIM; ++j) du[j] = df_sub(uu[j + 1], uu[0]);
+        dfl h[DIM];
         df_combine<DIM>(du, n, h);
         // r_j = (Kbar / |det J|) n_j . h, r_0 = -(r_1 + ... + r_d)
         const dfl s = df_div(kbar, df_abs(det));
@@ -240,11 +252,7 @@ fem_status launch_lap_df(int dim, int64_t n_cells, int64_t n_verts, const double
     a.C = n_cells;
     a.V = static_cast<uint32_t>(n_verts);
     a.nq = n_q;
-    for (int q = 0; q < FEM_MAX_QPTS; ++q) {
-        const double w = q < n_q ? qw[q] : 0.0;
-        a.whi[q] = static_cast<float>(w);
-        a.wlo[q] = static_cast<float>(w - static_cast<double>(a.whi[q]));
-    }
+    for (int q = 0; q < FEM_MAX_QPTS; ++q) a.wd[q] = q < n_q ? qw[q] : 0.0;
     if (dim == 2) {
         auto k = lap_df_kernel<2>;
         k<<<grid_for(n_cells, kBlock, reinterpret_cast<const void *>(k)), kBlock, 0, stream>>>(a);
