@@ -47,8 +47,8 @@ HEADLINE_KERNEL = ("lap_staged_kernel<3, FP32_MIXED, NQ=4> (persistent; cp.async
                    "coefficient rows; 8 consumer warps x 4 cells/thread + 1 producer warp)")
 FLUSH_BYTES = 512 << 20
 # float64 instructions per cell of the float64 3D Laplacian kernel (ncu sass counters,
-# profiles/lap3d_fp64_1572864.md): DFMA 33, DADD 17, DMUL 21
-FP64_INST_PER_CELL_LAP3D = {"dfma": 33, "dadd": 17, "dmul": 21}
+# profiles/lap3d_fp64_1572864.md): DFMA 30, DADD 16, DMUL 21
+FP64_INST_PER_CELL_LAP3D = {"dfma": 30, "dadd": 16, "dmul": 21}
 # FP64 peak: 1.25 TFLOP/s nominal for GB300 = 0.625 T FMA instructions/s, i.e. 2 float64
 # instructions per clock per SM at 2070 MHz on 152 SMs
 FP64_NOMINAL_TFLOPS = 1.25

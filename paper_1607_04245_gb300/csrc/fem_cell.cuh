@@ -96,8 +96,33 @@ __device__ __forceinline__ double diffprod(double a, double b, double c, double 
 __device__ __forceinline__ float diffprod(float a, float b, float c, float d) { return fmaf(a, b, -(c * d)); }
 __device__ __forceinline__ f2 diffprod(f2 a, f2 b, f2 c, f2 d) { return a * b - c * d; }
 
-// num / |den|: one correctly-rounded division in float64, the fast reciprocal in float32
-__device__ __forceinline__ double quot_abs(double num, double den) { return num / fabs(den); }
+// num / |den| in float64. The IEEE division is about a dozen float64 instructions and the
+// float64 forms are bound by the float64 pipe, so: |den| = m 2^e with m in [1, 2) (integer
+// operations on the exponent field); a float32 reciprocal of m, truncated to 23 bits, as the
+// seed (relative error below 2^-22); two Newton-Raphson steps y <- y + y (1 - m y) in
+// float64, each squaring the relative error, so the second ends at the float64 rounding
+// level; the exponent put back and one product -- five float64 instructions, a result
+// within about two units in the last place of the correctly rounded quotient. |den|
+// outside [2^-1000, 2^1001) (zero, subnormal, infinite, NaN or extreme) takes the IEEE
+// division.
+__device__ __forceinline__ double quot_abs(double num, double den) {
+    const uint32_t hw = static_cast<uint32_t>(__double2hiint(den)) & 0x7fffffffu;
+    const uint32_t lw = static_cast<uint32_t>(__double2loint(den));
+    const int ef = static_cast<int>(hw >> 20);  // biased exponent of |den|
+    if (ef < 23 || ef > 2023) return num / fabs(den);
+    const double m = __hiloint2double(static_cast<int>((hw & 0x000fffffu) | 0x3ff00000u), static_cast<int>(lw));
+    const float yf = __frcp_rn(__uint_as_float(0x3f800000u | ((hw & 0x000fffffu) << 3) | (lw >> 29)));
+    // yf in [0.5, 1]: widen it to float64 exactly with integer operations
+    const uint32_t fb = __float_as_uint(yf);
+    double y = __hiloint2double(static_cast<int>(((((fb >> 23) & 0xffu) + 896u) << 20) | ((fb & 0x7fffffu) >> 3)),
+                                static_cast<int>(fb << 29));
+    y = fma(y, fma(-m, y, 1.0), y);
+    y = fma(y, fma(-m, y, 1.0), y);
+    // 1 / |den| = y 2^-(ef - 1023): y's exponent field stays inside [22, 2023]
+    const uint32_t yh = static_cast<uint32_t>(__double2hiint(y)) - (static_cast<uint32_t>(ef - 1023) << 20);
+    return num * __hiloint2double(static_cast<int>(yh), __double2loint(y));
+}
+// float32: the fast reciprocal (the mixed form's tolerance is far above its error)
 __device__ __forceinline__ float quot_abs(float num, float den) { return __fdividef(num, fabsf(den)); }
 __device__ __forceinline__ f2 quot_abs(f2 num, f2 den) {
     return f2_make(__fdividef(f2_x(num), fabsf(f2_x(den))), __fdividef(f2_y(num), fabsf(f2_y(den))));

@@ -47,7 +47,7 @@ __device__ __forceinline__ void el_element(const T (&n)[DIM][DIM], T det, const 
 #pragma unroll
     for (int k = 1; k < DIM; ++k) tr += H[k][k];
     T s;
-    if constexpr (std::is_same<T, double>::value) s = T(1) / fabs(det);
+    if constexpr (std::is_same<T, double>::value) s = quot_abs(1.0, det);
     else s = __fdividef(1.0f, fabsf(det));
     const T ltr = lbar * tr;
     T Tm[DIM][DIM];
