@@ -153,6 +153,26 @@ def test_mixed_fallback_on_slivers(dim):
         fem.fem_set_mixed_threshold(old)
 
 
+@pytest.mark.parametrize("scale,prec", [(1e-60, "fp64"), (1e-30, "fp64"), (1e30, "fp64"), (1e60, "fp64"),
+                                        (1e-30, "mixed"), (1e30, "mixed")])
+def test_extreme_coordinate_scales(scale, prec):
+    """Coordinates scaled by up to 1e+-60: the float64 division by abs(det J) (a Newton-Raphson
+    reciprocal with the exponent taken apart and put back) sees exponents near +-600, and the
+    residual scales as scale^(d-2). In the mixed form det J leaves float32's range and every
+    cell is recomputed in float64; its float32 outputs bound the scales it can take (the
+    residual itself must be a normal float32). The collapsed P1 form multiplies
+    Kbar / abs(det J) by n_j . h, which scales as scale^4 in 3D, so float64 coordinates must
+    stay well inside 1e+-75."""
+    base = workloads.laplacian_cube_case(6 * 8 ** 3)
+    mesh = workloads.Mesh(3, base.mesh.coords * scale, base.mesh.conn)
+    case = workloads.Case("laplacian", mesh, base.rule, base.u, K=base.K)
+    c, d = device_arrays(case, prec)
+    r = residual(c, d, prec)
+    ref = oracle.residual_for(c)
+    assert np.isfinite(ref).all() and np.abs(ref).max() > 0
+    assert rel_err(r, ref) <= TOL[prec]
+
+
 def test_constant_field_null_space(lap3d):
     for prec in ("fp64", "mixed"):
         c, d = device_arrays(lap3d, prec)
