@@ -85,8 +85,11 @@ __global__ void __launch_bounds__(256) dot_final_kernel(const double *partial, d
     if (threadIdx.x == 0) *result = s[0];
 }
 
-// scalars[] layout: 0 rz, 1 pq, 2 rz_new, 3 rr, 4 (rtol ||r_0||)^2, 5 iterations done, 6 beta
-enum { S_RZ = 0, S_PQ = 1, S_RZNEW = 2, S_RR = 3, S_TOL2 = 4, S_ITER = 5, S_BETA = 6, S_COUNT = 7 };
+// scalars[] layout: 0 rz, 1 pq, 2 rz_new, 3 rr, 4 (rtol ||r_0||)^2, 5 iterations done, 6 beta,
+// 7 two 32-bit block counters of the loop's reductions (see last_block)
+enum { S_RZ = 0, S_PQ = 1, S_RZNEW = 2, S_RR = 3, S_TOL2 = 4, S_ITER = 5, S_BETA = 6, S_TICKETS = 7, S_COUNT = 8 };
+
+__device__ __forceinline__ unsigned *tickets(double *sc) { return reinterpret_cast<unsigned *>(sc + S_TICKETS); }
 
 // Block-level sum of one double per thread (256 threads); thread 0 gets the total.
 __device__ __forceinline__ double block_sum256(double v, double *sh) {
@@ -97,6 +100,20 @@ __device__ __forceinline__ double block_sum256(double v, double *sh) {
         __syncthreads();
     }
     return sh[0];
+}
+
+// True in the block that finishes last: each block's thread 0 publishes the block's partial
+// sums (fence), then takes a ticket; the block holding ticket kDotBlocks - 1 sees every
+// partial and reduces them in place of a separate one-block kernel (the order of the sum
+// does not depend on which block that is), then resets the counter for the next iteration.
+__device__ __forceinline__ bool last_block(unsigned *ticket) {
+    __shared__ bool s_last;
+    if (threadIdx.x == 0) {
+        __threadfence();
+        s_last = atomicAdd(ticket, 1u) == unsigned(kDotBlocks - 1);
+    }
+    __syncthreads();
+    return s_last;
 }
 
 // r = b - Ax (free vertices), 0 on fixed ones; z = r / D; p = z
@@ -117,10 +134,10 @@ __global__ void cg_init_kernel(int64_t V, const T *b, const T *Ax, const T *D, c
 // thread t: i = 256 b + t + k 256 kDotBlocks) and finish like dot_final_kernel, so every
 // sum is reproducible and independent of the device.
 
-// q = 0 on fixed vertices; block partial sums of p . q
+// q = 0 on fixed vertices; block partial sums of p . q; the last block sums them into pq
 template <class T>
 __global__ void __launch_bounds__(256) mask_dot_kernel(int64_t V, const uint8_t *fixed, const T *p, T *q,
-                                                       double *partial) {
+                                                       double *partial, double *sc) {
     __shared__ double sh[256];
     double acc = 0.0;
     for (int64_t i = int64_t(blockIdx.x) * 256 + threadIdx.x; i < V; i += int64_t(kDotBlocks) * 256) {
@@ -130,13 +147,48 @@ __global__ void __launch_bounds__(256) mask_dot_kernel(int64_t V, const uint8_t 
     }
     const double t = block_sum256(acc, sh);
     if (threadIdx.x == 0) partial[blockIdx.x] = t;
+    if (last_block(tickets(sc))) {
+        double a = 0.0;
+        for (int i = threadIdx.x; i < kDotBlocks; i += 256) a += __ldcg(partial + i);
+        const double pq = block_sum256(a, sh);
+        if (threadIdx.x == 0) {
+            sc[S_PQ] = pq;
+            tickets(sc)[0] = 0u;
+        }
+    }
+}
+
+// In one block: rz_new and rr from the partials, beta = rz_new / rz, rz = rz_new, then
+// count the iteration and set the loop condition (not converged, fewer than max_iter; a
+// NaN residual ends the loop: every comparison with it is false).
+__device__ __forceinline__ void finish_iteration(const double *partial, double *sc, int max_iter,
+                                                 cudaGraphConditionalHandle loop, double *sh) {
+    double a = 0.0, b = 0.0;
+    for (int i = threadIdx.x; i < kDotBlocks; i += 256) a += __ldcg(partial + i), b += __ldcg(partial + kDotBlocks + i);
+    const double rz_new = block_sum256(a, sh);
+    __syncthreads();
+    const double rr = block_sum256(b, sh);
+    if (threadIdx.x == 0) {
+        const double rz = sc[S_RZ];
+        sc[S_BETA] = rz != 0.0 ? rz_new / rz : 0.0;
+        sc[S_RZNEW] = rz_new;
+        sc[S_RZ] = rz_new;
+        sc[S_RR] = rr;
+        const double it = sc[S_ITER] + 1.0;
+        sc[S_ITER] = it;
+        const bool more = it < static_cast<double>(max_iter) && rr > sc[S_TOL2] && rr > 0.0;
+        cudaGraphSetConditional(loop, more ? 1u : 0u);
+        tickets(sc)[1] = 0u;
+    }
 }
 
 // alpha = rz / pq; x += alpha p; r -= alpha q; z = r / D; block partial sums of r . z
-// (partial[0 .. kDotBlocks)) and r . r (partial[kDotBlocks .. 2 kDotBlocks))
+// (partial[0 .. kDotBlocks)) and r . r (partial[kDotBlocks .. 2 kDotBlocks)); the last block
+// finishes the iteration (finish_iteration)
 template <class T>
-__global__ void __launch_bounds__(256) step_dots_kernel(int64_t V, const double *sc, const T *p, const T *q,
-                                                        const T *D, T *x, T *r, T *z, double *partial) {
+__global__ void __launch_bounds__(256) step_dots_kernel(int64_t V, double *sc, const T *p, const T *q,
+                                                        const T *D, T *x, T *r, T *z, double *partial, int max_iter,
+                                                        cudaGraphConditionalHandle loop) {
     __shared__ double sh[256];
     const double alpha = sc[S_PQ] != 0.0 ? sc[S_RZ] / sc[S_PQ] : 0.0;
     double rz = 0.0, rr = 0.0;
@@ -154,30 +206,7 @@ __global__ void __launch_bounds__(256) step_dots_kernel(int64_t V, const double 
     __syncthreads();
     const double t2 = block_sum256(rr, sh);
     if (threadIdx.x == 0) partial[kDotBlocks + blockIdx.x] = t2;
-}
-
-// one block: rz_new and rr from the partials, beta = rz_new / rz, rz = rz_new, then count
-// the iteration and set the loop condition (not converged, fewer than max_iter; a NaN
-// residual ends the loop: every comparison with it is false)
-__global__ void __launch_bounds__(256) finish_iteration_kernel(const double *partial, double *sc, int max_iter,
-                                                               cudaGraphConditionalHandle loop) {
-    __shared__ double sh[256];
-    double a = 0.0, b = 0.0;
-    for (int i = threadIdx.x; i < kDotBlocks; i += 256) a += partial[i], b += partial[kDotBlocks + i];
-    const double rz_new = block_sum256(a, sh);
-    __syncthreads();
-    const double rr = block_sum256(b, sh);
-    if (threadIdx.x == 0) {
-        const double rz = sc[S_RZ];
-        sc[S_BETA] = rz != 0.0 ? rz_new / rz : 0.0;
-        sc[S_RZNEW] = rz_new;
-        sc[S_RZ] = rz_new;
-        sc[S_RR] = rr;
-        const double it = sc[S_ITER] + 1.0;
-        sc[S_ITER] = it;
-        const bool more = it < static_cast<double>(max_iter) && rr > sc[S_TOL2] && rr > 0.0;
-        cudaGraphSetConditional(loop, more ? 1u : 0u);
-    }
+    if (last_block(tickets(sc) + 1)) finish_iteration(partial, sc, max_iter, loop, sh);
 }
 
 // p = z + beta p
@@ -192,6 +221,7 @@ __global__ void dir_kernel(int64_t V, const double *sc, const T *z, T *p) {
 __global__ void loop_init_kernel(double *sc, double tol2) {
     sc[S_TOL2] = tol2;
     sc[S_ITER] = 0.0;
+    tickets(sc)[0] = tickets(sc)[1] = 0u;
 }
 
 // a library stream per device to capture the loop body on (capture needs a stream other
@@ -318,14 +348,13 @@ static fem_status pcg_run(int dim, int64_t C, int64_t V, const double *coords, c
             e = cudaStreamBeginCaptureToGraph(cs, np.conditional.phGraph_out[0], nullptr, nullptr, 0,
                                               cudaStreamCaptureModeThreadLocal);
         if (e == cudaSuccess) {
-            // one iteration in 7 kernels: residual, gather, q masked with p.q, pq, the
-            // updates with r.z and r.r, the scalars and the loop condition, the direction
+            // one iteration in 5 kernels: residual, gather, q masked with p.q (and pq), the
+            // updates with r.z and r.r (and the scalars and the loop condition), the direction
             st = matvec(p, q, cs);
             if (st == FEM_OK) {
-                mask_dot_kernel<T><<<kDotBlocks, 256, 0, cs>>>(V, fixed, p, q, w.partial);
-                dot_final_kernel<<<1, 256, 0, cs>>>(w.partial, w.scalars + S_PQ);
-                step_dots_kernel<T><<<kDotBlocks, 256, 0, cs>>>(V, w.scalars, p, q, D, X, r, z, w.partial);
-                finish_iteration_kernel<<<1, 256, 0, cs>>>(w.partial, w.scalars, max_iter, loop);
+                mask_dot_kernel<T><<<kDotBlocks, 256, 0, cs>>>(V, fixed, p, q, w.partial, w.scalars);
+                step_dots_kernel<T><<<kDotBlocks, 256, 0, cs>>>(V, w.scalars, p, q, D, X, r, z, w.partial, max_iter,
+                                                                loop);
                 dir_kernel<T><<<gV, 256, 0, cs>>>(V, w.scalars, z, p);
             }
             cudaGraph_t body = nullptr;
