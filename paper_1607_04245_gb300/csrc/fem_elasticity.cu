@@ -49,12 +49,16 @@ __device__ __forceinline__ void el_element(const T (&n)[DIM][DIM], T det, const 
     T s;
     if constexpr (std::is_same<T, double>::value) s = quot_abs(1.0, det);
     else s = __fdividef(1.0f, fabsf(det));
-    const T ltr = lbar * tr;
+    // T = s (Lbar tr(H) I + Mbar (H + H^T)) is symmetric: the diagonal and the d(d-1)/2
+    // entries above it, with s folded into the two coefficients
+    const T sm = s * mbar, sl = s * lbar * tr, sm2 = sm + sm;
     T Tm[DIM][DIM];
 #pragma unroll
-    for (int k = 0; k < DIM; ++k)
+    for (int k = 0; k < DIM; ++k) {
+        Tm[k][k] = fma(sm2, H[k][k], sl);
 #pragma unroll
-        for (int i = 0; i < DIM; ++i) Tm[k][i] = s * (mbar * (H[k][i] + H[i][k]) + (k == i ? ltr : T(0)));
+        for (int i = k + 1; i < DIM; ++i) Tm[k][i] = Tm[i][k] = sm * (H[k][i] + H[i][k]);
+    }
 #pragma unroll
     for (int k = 0; k < DIM; ++k) r[0][k] = T(0);
 #pragma unroll
