@@ -319,16 +319,16 @@ __global__ void __launch_bounds__(kBlock) el_df_kernel(const __grid_constant__ D
 #pragma unroll
         for (int k = 1; k < DIM; ++k) tr = df_add(tr, H[k][k]);
         const dfl inv = df_div(dfl{1.0f, 0.0f}, df_abs(det));
-        const dfl ltr = df_mul(lbar, tr);
+        // T is symmetric: its diagonal and upper entries, 1/|det J| folded into the Lame sums
+        const dfl sm = df_mul(inv, mbar), sl = df_mul(df_mul(inv, lbar), tr);
+        const dfl sm2{sm.hi + sm.hi, sm.lo + sm.lo};  // 2 sm, exact
         dfl Tm[DIM][DIM];
 #pragma unroll
-        for (int k = 0; k < DIM; ++k)
+        for (int k = 0; k < DIM; ++k) {
+            Tm[k][k] = df_add(df_mul(sm2, H[k][k]), sl);
 #pragma unroll
-            for (int i = 0; i < DIM; ++i) {
-                dfl t = df_mul(mbar, df_add(H[k][i], H[i][k]));
-                if (k == i) t = df_add(t, ltr);
-                Tm[k][i] = df_mul(inv, t);
-            }
+            for (int i = k + 1; i < DIM; ++i) Tm[k][i] = Tm[i][k] = df_mul(sm, df_add(H[k][i], H[i][k]));
+        }
         dfl r0[DIM];
 #pragma unroll
         for (int k = 0; k < DIM; ++k) r0[k] = dfl{0.0f, 0.0f};
