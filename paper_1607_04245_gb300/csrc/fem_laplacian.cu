@@ -65,10 +65,12 @@ __device__ __forceinline__ void lap_element(const T (&n)[DIM][DIM], T det, const
     lap_apply<DIM>(n, quot_abs(kbar, det), uu, r);
 }
 
-// h_lambda . h_u / |det J|
+// The adjoint's element part in one pass: h_lambda and h_u once, one reciprocal of |det J|
+// for both quotients; r_b = (Kbar / |det J|) n_b . h_lambda (the residual of lambda_e),
+// tf = h_lambda . h_u / |det J|.
 template <int DIM, class T>
-__device__ __forceinline__ T lap_dk_factor(const T (&n)[DIM][DIM], T det, const T (&uu)[DIM + 1],
-                                           const T (&ll)[DIM + 1]) {
+__device__ __forceinline__ void lap_adj_element(const T (&n)[DIM][DIM], T det, const T (&uu)[DIM + 1],
+                                                const T (&ll)[DIM + 1], T kbar, T (&r)[DIM + 1], T &tf) {
     T hu[DIM], hl[DIM];
 #pragma unroll
     for (int i = 0; i < DIM; ++i) hu[i] = zero<T>(), hl[i] = zero<T>();
@@ -78,7 +80,18 @@ __device__ __forceinline__ T lap_dk_factor(const T (&n)[DIM][DIM], T det, const 
 #pragma unroll
         for (int i = 0; i < DIM; ++i) hu[i] = fma(du, n[j][i], hu[i]), hl[i] = fma(dl, n[j][i], hl[i]);
     }
-    return quot_abs(dotv<DIM>(hl, hu), det);
+    T one;
+    if constexpr (std::is_same<T, f2>::value) one = f2_splat(1.0f);
+    else one = T(1);
+    const T y = quot_abs(one, det), s = kbar * y;
+    T sum = zero<T>();
+#pragma unroll
+    for (int j = 0; j < DIM; ++j) {
+        r[j + 1] = s * dotv<DIM>(n[j], hl);
+        sum = sum + r[j + 1];
+    }
+    r[0] = neg(sum);
+    tf = dotv<DIM>(hl, hu) * y;
 }
 
 template <int P>
@@ -100,8 +113,7 @@ __device__ __forceinline__ void lap_cell(const double (&xs)[DIM + 1][DIM],
         columns_f64<DIM>(xs, e);
         double det = adjugate_rows<DIM>(e, n);
         if constexpr (ADJ) {
-            lap_element<DIM>(n, det, ll, ks.value(), rr);
-            tf = lap_dk_factor<DIM>(n, det, uu, ll);
+            lap_adj_element<DIM>(n, det, uu, ll, ks.value(), rr, tf);
         } else {
             lap_element<DIM>(n, det, uu, ks.value(), rr);
         }
@@ -114,8 +126,7 @@ __device__ __forceinline__ void lap_cell(const double (&xs)[DIM + 1][DIM],
         if constexpr (P == FEM_FP32_MIXED) ok = shape_ok<DIM>(e, det, tau2);
         if (ok) {
             if constexpr (ADJ) {
-                lap_element<DIM>(n, det, ll, ks.value(), rr);
-                tf = lap_dk_factor<DIM>(n, det, uu, ll);
+                lap_adj_element<DIM>(n, det, uu, ll, ks.value(), rr, tf);
             } else {
                 lap_element<DIM>(n, det, uu, ks.value(), rr);
             }
@@ -131,8 +142,9 @@ __device__ __forceinline__ void lap_cell(const double (&xs)[DIM + 1][DIM],
                 double l64[NB];
 #pragma unroll
                 for (int b = 0; b < NB; ++b) l64[b] = ll[b];
-                lap_element<DIM>(n64, det64, l64, kb64, r64);
-                tf = static_cast<float>(lap_dk_factor<DIM>(n64, det64, u64, l64));
+                double tf64;
+                lap_adj_element<DIM>(n64, det64, u64, l64, kb64, r64, tf64);
+                tf = static_cast<float>(tf64);
             } else {
                 lap_element<DIM>(n64, det64, u64, kb64, r64);
             }
@@ -383,8 +395,7 @@ __device__ __forceinline__ void lap_cell_f64(const double (&xs)[DIM + 1][DIM], c
 #pragma unroll
     for (int b = 0; b < NB; ++b) u64[b] = uf[b], l64[b] = lf[b];
     if constexpr (ADJ) {
-        lap_element<DIM>(n, det, l64, kbar, r);
-        tf = lap_dk_factor<DIM>(n, det, u64, l64);
+        lap_adj_element<DIM>(n, det, u64, l64, kbar, r, tf);
     } else {
         lap_element<DIM>(n, det, u64, kbar, r);
         tf = 0.0;
@@ -444,8 +455,7 @@ __device__ __forceinline__ void lap_pair(const double *const (&X)[DIM], const ui
     }
     const f2 det = adjugate_rows<DIM>(e, n);
     if constexpr (ADJ) {
-        lap_element<DIM>(n, det, ll, ks.value(), rr);
-        tf = lap_dk_factor<DIM>(n, det, uu, ll);
+        lap_adj_element<DIM>(n, det, uu, ll, ks.value(), rr, tf);
     } else {
         lap_element<DIM>(n, det, uu, ks.value(), rr);
     }
