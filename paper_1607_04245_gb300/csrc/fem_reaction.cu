@@ -65,7 +65,17 @@ template <int P> __device__ __forceinline__ val_t<P> rd_weight(const QuadW &w, i
 
 // f1 part (Laplacian with Kbar) and f0 part of one cell from its adjugate rows and det J;
 // DRIFT: the grad a term, from the nodal values aa of a P1 coefficient
-template <int DIM, int P, class T, bool REACT, bool DRIFT, int NQA>
+// num / |den|: quot_abs, or (NEWTON false, float64) the IEEE division
+template <bool NEWTON, class T>
+__device__ __forceinline__ T quot_div(T num, T den) {
+    if constexpr (!NEWTON && std::is_same<T, double>::value) return num / fabs(den);
+    else return quot_abs(num, den);
+}
+
+// NEWTON: the float64 quotients through quot_abs's Newton reciprocal (the float64 form);
+// false in the mixed form's rare float64 recomputation, where the plain division keeps the
+// main path's register allocation as it was
+template <int DIM, int P, class T, bool REACT, bool DRIFT, int NQA, bool NEWTON = true>
 __device__ __forceinline__ void rd_element(const RdArgs &a, const T (&n)[DIM][DIM], T det, const T (&uu)[DIM + 1],
                                            const T (&aa)[DIM + 1], T kbar, const T (&cq)[NQA], int nq,
                                            T (&r)[DIM + 1]) {
@@ -79,7 +89,11 @@ __device__ __forceinline__ void rd_element(const RdArgs &a, const T (&n)[DIM][DI
 #pragma unroll
         for (int i = 0; i < DIM; ++i) h[i] = fma(du, n[j][i], h[i]);
     }
-    const T s = quot_abs(kbar, det);
+    // float64: one reciprocal of |det J| for both quotients (the float64 pipe bounds that
+    // form); float32: two fast divisions (one reciprocal cost the mixed form 10 %)
+    constexpr bool ONE_RCP = std::is_same<T, double>::value && NEWTON;
+    const T y = ONE_RCP ? quot_abs(T(1), det) : T(0);
+    const T s = ONE_RCP ? kbar * y : quot_div<NEWTON>(kbar, det);
     T sum = zero<T>();
 #pragma unroll
     for (int j = 0; j < DIM; ++j) {
@@ -98,7 +112,7 @@ __device__ __forceinline__ void rd_element(const RdArgs &a, const T (&n)[DIM][DI
             for (int i = 0; i < DIM; ++i) ha[i] = fma(da, n[j][i], ha[i]);
         }
         const T g = P == FEM_FP64 ? T(a.gd) : T(a.gf);
-        const T t = quot_abs(g * dotv<DIM>(ha, h), det);
+        const T t = ONE_RCP ? g * dotv<DIM>(ha, h) * y : quot_div<NEWTON>(g * dotv<DIM>(ha, h), det);
 #pragma unroll
         for (int b = 0; b < NB; ++b) r[b] = fma(T(tab_m<P>(a.t, b)), t, r[b]);
     }
@@ -176,7 +190,7 @@ __device__ __forceinline__ void rd_cell(const RdArgs &a, const double *const (&X
             if constexpr (REACT) {
                 for (int q = 0; q < nq; ++q) c64[q] = ci[q];
             }
-            rd_element<DIM, FEM_FP64, double, REACT, DRIFT, NQA>(a, n64, det64, u64, a64, ks.value_f64(), c64, nq,
+            rd_element<DIM, FEM_FP64, double, REACT, DRIFT, NQA, false>(a, n64, det64, u64, a64, ks.value_f64(), c64, nq,
                                                                 r64);
 #pragma unroll
             for (int b = 0; b < NB; ++b) rr[b] = static_cast<float>(r64[b]);
