@@ -192,3 +192,22 @@ def test_serve_launch_checks_the_descriptor_against_its_block(lib):
     d = desc()
     d.n_q = 0
     assert lib.fem_serve_launch(ctypes.byref(d), fake, fake, None) == -1
+
+    # an adjoint request (kind 1): twelve arrays, the vertex lists' workspace last
+    lib.fem_node2cell_work_size.restype = ctypes.c_int64
+    lib.fem_node2cell_work_size.argtypes = [ctypes.c_int64]
+    C, V = 6, 7
+    sizes = {"coords": 3 * V * 8, "conn": 4 * C * 4, "u": V * 8, "K": 4 * C * 8, "adj": 4 * C * 8,
+             "dK": 4 * C * 8, "du": V * 8, "scratch": 4 * C * 8, "node_ptr": (V + 1) * 4, "node_idx": 4 * C * 4,
+             "work": lib.fem_node2cell_work_size(V) * 4}
+    a = ServeRequestDesc()
+    a.kind, a.physics, a.dim, a.n_q, a.prec = 1, 0, 3, 4, 0
+    a.n_cells, a.n_verts = C, V
+    off = 0
+    for name, n in sizes.items():
+        a.offset[SERVE_SLOTS[name]] = off
+        off += n
+    a.block_bytes = off - 4  # the workspace ends 4 bytes past the block
+    a.out_bytes[0], a.out_bytes[1] = sizes["dK"], sizes["du"]
+    assert lib.fem_serve_launch(ctypes.byref(a), fake, fake, None) == -1
+    assert b"outside" in lib.fem_last_error()
