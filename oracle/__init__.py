@@ -60,8 +60,9 @@ def _lib():
         lib.oracle_elasticity.argtypes = [ci, i64, i64, P, P, P, P, P, ci, P, P, P]
         lib.oracle_adjoint_laplacian.argtypes = [ci, i64, i64, P, P, P, P, ci, P, P, P, P, P]
         lib.oracle_reaction_diffusion.argtypes = [ci, i64, i64, P, P, P, P, ci, P, ctypes.c_double, ci, P, P, P]
+        lib.oracle_pointwise.argtypes = [ci, P, ci, ci, ci, i64, i64, P, P, P, P, ci, P, P, P]
         for f in (lib.oracle_laplacian, lib.oracle_elasticity, lib.oracle_adjoint_laplacian,
-                  lib.oracle_reaction_diffusion):
+                  lib.oracle_reaction_diffusion, lib.oracle_pointwise):
             f.restype = ci
         lib.oracle_num_threads.restype = ci
         lib.oracle_set_threads.argtypes = [ci]
@@ -146,6 +147,37 @@ def reaction_diffusion(coords, conn, u, a, a_space, c, qpts, qw, drift=0.0) -> n
     out = np.zeros((dim + 1, C), dtype=np.float64)
     _check(_lib().oracle_reaction_diffusion(dim, C, V, _ptr(coords), _ptr(conn), _ptr(u), _ptr(a), int(a_space),
                                             _ptr(c), float(drift), nq, _ptr(qpts), _ptr(qw), _ptr(out)))
+    return out
+
+
+POINTWISE_PHYSICS = {"laplacian": 0, "nonlinear": 1, "elasticity": 2, "reaction": 3}
+
+
+def pointwise(physics, coords, conn, u, coef, qpts, qw, params=(0.0, 0.0, 0.0, 0.0)) -> np.ndarray:
+    """Element vectors [(dim+1)*n_comp][C] of one of the oracle's pointwise physics
+    (fem_oracle.c, oracle_pointwise): "laplacian" f1 = a0 grad u; "nonlinear" f1 =
+    (p0 + p1 u + p2 u^2)(1 + p3 s(x)) grad u, s(x) = x_0 + 2 x_1 (+ 3 x_2); "elasticity" (Lame,
+    a0 = lambda, a1 = mu);
+    "reaction" f0 = a0 u + p0, f1 = a1 grad u. u is [V] or [n_comp][V], coef
+    [n_coef][n_q][C] (or None)."""
+    pid = POINTWISE_PHYSICS[physics]
+    coords, qpts, qw = map(_f64, (coords, qpts, qw))
+    u = _f64(u)
+    if u.ndim == 1:
+        u = u[None, :]
+    conn = np.ascontiguousarray(conn, dtype=np.int32)
+    dim, V = coords.shape
+    C = conn.shape[1]
+    nq = qw.shape[0]
+    n_comp = u.shape[0]
+    coef = None if coef is None else _f64(coef)
+    n_coef = 0 if coef is None else coef.shape[0]
+    if coef is not None and coef.shape != (n_coef, nq, C):
+        raise ValueError("coef must be [n_coef][n_q][C]")
+    p = _f64(np.asarray(params, dtype=np.float64).reshape(-1)[:4])
+    out = np.zeros(((dim + 1) * n_comp, C), dtype=np.float64)
+    _check(_lib().oracle_pointwise(pid, _ptr(p), dim, n_comp, n_coef, C, V, _ptr(coords), _ptr(conn), _ptr(u),
+                                   _ptr(coef), nq, _ptr(qpts), _ptr(qw), _ptr(out)))
     return out
 
 

@@ -414,3 +414,112 @@ int oracle_reaction_diffusion(int dim, int64_t n_cells, int64_t n_verts, const d
     }
     return bad ? ORA_ERR_BADMESH : ORA_OK;
 }
+
+/* Pointwise physics of the caller's choosing: the general bracket of Eq. 2 for a field of
+ * n_comp components,
+ *     r_{e,b,k} = sum_q w_q |det J| [ phi_b(xi_q) f0_k(q) + sum_i G_{b,i}(q) f1_{k,i}(q) ],
+ * with the pointwise functions evaluated at every quadrature point from
+ *     u_k(q) = sum_b phi_b(xi_q) u_{b,k},   grad u_{k,i}(q) = sum_b u_{b,k} G_{b,i}(q),
+ *     x_i(q) = sum_b phi_b(xi_q) x_{b,i},   a_j(q) = coef[(j*n_q + q)*n_cells + e].
+ * The CUDA library takes f0 and f1 as source strings compiled at run time (Sec. 5); the
+ * oracle has a fixed set of them, chosen by `physics` (params p[0..3]):
+ *   0  f1 = a_0 grad u                                  (the variable-coefficient Laplacian)
+ *   1  f1 = kappa(u, x) grad u,  kappa = (p0 + p1 u + p2 u^2)(1 + p3 s(x)),
+ *      s(x) = x_0 + 2 x_1 (+ 3 x_2)                     (Sec. 2's nonlinear kappa(u, x) grad u)
+ *   2  f1 = a_0 tr(eps) I + 2 a_1 eps, eps = (grad u + grad u^T)/2   (Lame; n_comp = dim)
+ *   3  f0 = a_0 u + p0,  f1 = a_1 grad u                (reaction, source and diffusion)
+ * u is [n_comp][n_verts], out [(dim+1)*n_comp][n_cells] with row b*n_comp + k. */
+static void pointwise_f(int physics, const double *p, int dim, int n_comp, const double *uq, double gu[3][3],
+                        const double *xq, const double *aq, double f0[3], double f1[3][3]) {
+    for (int k = 0; k < n_comp; ++k) {
+        f0[k] = 0.0;
+        for (int i = 0; i < dim; ++i) f1[k][i] = 0.0;
+    }
+    if (physics == 0) {
+        for (int i = 0; i < dim; ++i) f1[0][i] = aq[0] * gu[0][i];
+    } else if (physics == 1) {
+        double sx = 0.0;
+        for (int i = 0; i < dim; ++i) sx += (i + 1) * xq[i];
+        const double kappa = (p[0] + p[1] * uq[0] + p[2] * uq[0] * uq[0]) * (1.0 + p[3] * sx);
+        for (int i = 0; i < dim; ++i) f1[0][i] = kappa * gu[0][i];
+    } else if (physics == 2) {
+        double eps[3][3], tr = 0.0;
+        for (int k = 0; k < dim; ++k)
+            for (int i = 0; i < dim; ++i) eps[k][i] = 0.5 * (gu[k][i] + gu[i][k]);
+        for (int k = 0; k < dim; ++k) tr += eps[k][k];
+        for (int k = 0; k < dim; ++k)
+            for (int i = 0; i < dim; ++i) f1[k][i] = 2.0 * aq[1] * eps[k][i] + (k == i ? aq[0] * tr : 0.0);
+    } else {
+        f0[0] = aq[0] * uq[0] + p[0];
+        for (int i = 0; i < dim; ++i) f1[0][i] = aq[1] * gu[0][i];
+    }
+}
+
+int oracle_pointwise(int physics, const double *params, int dim, int n_comp, int n_coef, int64_t n_cells,
+                     int64_t n_verts, const double *coords, const int32_t *conn, const double *u,
+                     const double *coef, int n_q, const double *qpts, const double *qw, double *out) {
+    int st = check_args(dim, n_cells, n_verts, n_q);
+    if (st) return st;
+    if (physics < 0 || physics > 3 || n_comp < 1 || n_comp > 3 || n_coef < 0) return ORA_ERR_ARG;
+    if ((physics == 2) != (n_comp == dim && n_comp > 1)) return ORA_ERR_ARG;
+    const int need_coef = physics == 1 ? 0 : (physics == 0 ? 1 : 2);
+    if (n_coef < need_coef) return ORA_ERR_ARG;
+    if (n_cells == 0) return ORA_OK;
+    if (!coords || !conn || !u || !qpts || !qw || !out || !params || (n_coef > 0 && !coef)) return ORA_ERR_ARG;
+    if ((st = check_conn(dim, n_cells, n_verts, conn))) return st;
+    const int nb = dim + 1;
+    double phi[ORA_MAX_Q][4], dphi[ORA_MAX_Q][4][3];
+    tabulate_p1(dim, n_q, qpts, phi, dphi);
+    int bad = 0;
+#pragma omp parallel for schedule(static)
+    for (int64_t e = 0; e < n_cells; ++e) {
+        double J[3][3], invJ[3][3];
+        double detJ = cell_geometry(dim, e, n_cells, n_verts, coords, conn, J, invJ);
+        if (detJ == 0.0) {
+#pragma omp atomic write
+            bad = 1;
+            continue;
+        }
+        double ub[4][3], xb[4][3];
+        for (int b = 0; b < nb; ++b) {
+            int64_t v = conn[(int64_t)b * n_cells + e];
+            for (int k = 0; k < n_comp; ++k) ub[b][k] = u[(int64_t)k * n_verts + v];
+            for (int i = 0; i < dim; ++i) xb[b][i] = coords[(int64_t)i * n_verts + v];
+        }
+        /* quadrature phase: f0 and f1 at every point, scaled by w_q |det J| */
+        double f0[ORA_MAX_Q][3], f1[ORA_MAX_Q][3][3];
+        for (int q = 0; q < n_q; ++q) {
+            double uq[3] = {0, 0, 0}, xq[3] = {0, 0, 0}, gu[3][3] = {{0}}, aq[8] = {0};
+            for (int b = 0; b < nb; ++b) {
+                double G[3];
+                phys_grad(dim, invJ, dphi[q][b], G);
+                for (int k = 0; k < n_comp; ++k) {
+                    uq[k] += phi[q][b] * ub[b][k];
+                    for (int i = 0; i < dim; ++i) gu[k][i] += ub[b][k] * G[i];
+                }
+                for (int i = 0; i < dim; ++i) xq[i] += phi[q][b] * xb[b][i];
+            }
+            for (int j = 0; j < n_coef && j < 8; ++j) aq[j] = coef[((int64_t)j * n_q + q) * n_cells + e];
+            double g0[3], g1[3][3];
+            pointwise_f(physics, params, dim, n_comp, uq, gu, xq, aq, g0, g1);
+            const double scale = qw[q] * fabs(detJ);
+            for (int k = 0; k < n_comp; ++k) {
+                f0[q][k] = g0[k] * scale;
+                for (int i = 0; i < dim; ++i) f1[q][k][i] = g1[k][i] * scale;
+            }
+        }
+        /* basis phase: r_{b,k} = sum_q phi_b(q) f0_k(q) + G_b(q) . f1_k(q) */
+        for (int b = 0; b < nb; ++b)
+            for (int k = 0; k < n_comp; ++k) {
+                double r = 0.0;
+                for (int q = 0; q < n_q; ++q) {
+                    double G[3];
+                    phys_grad(dim, invJ, dphi[q][b], G);
+                    r += phi[q][b] * f0[q][k];
+                    for (int i = 0; i < dim; ++i) r += G[i] * f1[q][k][i];
+                }
+                out[(int64_t)(b * n_comp + k) * n_cells + e] = r;
+            }
+    }
+    return bad ? ORA_ERR_BADMESH : ORA_OK;
+}
