@@ -43,11 +43,12 @@ from paper_1607_04245_gb300 import perfmodel  # noqa: E402
 METRIC = "cells/s and HBM GB/s (% of GB300 peak), FP32 vs FP64 at stated error; served p99"
 WORKLOAD = "3D P1 Laplacian, variable coefficient: 64^3 hexes x 6 = 1,572,864 jittered tets, 4-pt degree-2 rule"
 HEADLINE_CELLS = 1572864
-HEADLINE_KERNEL = ("lap_staged_kernel<3, FP32_MIXED, NQ=4> (persistent; cp.async.bulk-staged connectivity and "
-                   "coefficient rows; 8 consumer warps x 4 cells/thread + 1 producer warp)")
+HEADLINE_KERNEL = ("lap_pair_kernel<3, FP32_MIXED, NQ=4> (two consecutive cells per thread as f32x2 pairs, "
+                   "8-byte row loads and streaming stores, one wave of 4 x 256-thread CTAs per SM)")
 FLUSH_BYTES = 512 << 20
-# float64 instructions per cell of the float64 3D Laplacian kernel (ncu sass counters,
-# profiles/lap3d_fp64_1572864.md): DFMA 30, DADD 16, DMUL 21
+# float64 instructions per cell of the float64 3D Laplacian kernel, counted by ncu
+# (smsp__sass_thread_inst_executed_op_dfma/dadd/dmul_pred_on.sum over one launch on the
+# 1,572,864-tet workload, divided by the cells): DFMA 30, DADD 16, DMUL 21
 FP64_INST_PER_CELL_LAP3D = {"dfma": 30, "dadd": 16, "dmul": 21}
 # FP64 peak: 1.25 TFLOP/s nominal for GB300 = 0.625 T FMA instructions/s, i.e. 2 float64
 # instructions per clock per SM at 2070 MHz on 152 SMs
@@ -88,7 +89,8 @@ def load_peaks():
 
 
 KERNEL_SOURCES = {
-    "lap": ("fem_internal.cuh", "fem_cell.cuh", "fem_f2.cuh", "fem_pipe.cuh", "fem_laplacian.cu"),
+    # fem_core.cu sizes the launches (grid, occupancy), so it belongs to the kernel's definition
+    "lap": ("fem_internal.cuh", "fem_cell.cuh", "fem_f2.cuh", "fem_pipe.cuh", "fem_laplacian.cu", "fem_core.cu"),
     "el": ("fem_internal.cuh", "fem_cell.cuh", "fem_f2.cuh", "fem_elasticity.cu"),
 }
 
@@ -226,17 +228,28 @@ def weak_scaling_value(ws, cells_per_rank, steps, t_max):
 # ----------------------------------------------------------------------------- timing
 
 
+WARM_S = 0.25  # minimum wall time of the warm-up: the GPU leaves its idle clocks first
+
+
 def timed_steps(step_fn, steps, warmup, stream, flush, dist=None, ws=1, sampler=None):
-    """Per-step device time (ms) of step_fn with an L2 flush before every step."""
+    """Per-step device time (ms) of step_fn with an L2 flush before every step.
+
+    The clock sampler starts first (its start-up leaves the GPU idle for a moment); then
+    come the warm-up steps -- at least `warmup` of them and at least WARM_S seconds of
+    them, so that the timed steps do not run while the clocks ramp up from idle."""
     import torch
 
-    for _ in range(warmup):
-        flush()
-        step_fn()
-    torch.cuda.synchronize()
-    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
     if sampler:
         sampler.start()
+    t_w, n = time.time(), 0
+    while n < warmup or time.time() - t_w < WARM_S:
+        flush()
+        step_fn()
+        n += 1
+        if n % 16 == 0:
+            torch.cuda.synchronize()  # keep the queue of enqueued steps short
+    torch.cuda.synchronize()
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
     barrier(dist, ws)
     torch.cuda.synchronize()
     t0 = time.time()
@@ -251,6 +264,30 @@ def timed_steps(step_fn, steps, warmup, stream, flush, dist=None, ws=1, sampler=
     clocks = sampler.stop(t0, t1) if sampler else None
     ms = [a.elapsed_time(b) for a, b in evs]
     return ms, t1 - t0, clocks
+
+
+def measure_fp64_fma_rate(device):
+    """float64 FMA instructions per second on this GPU: the library's probe kernel (every
+    thread runs 8 independent chains of dependent float64 FMAs), timed with CUDA events;
+    the measured peak of the float64 forms' ALU roofline."""
+    import torch
+
+    import paper_1607_04245_gb300 as fem
+
+    sms = torch.cuda.get_device_properties(device).multi_processor_count
+    n, iters = 256 * 8 * sms, 2048
+    out = torch.empty(n, dtype=torch.float64, device=device)
+    fem.fem_probe(0, n, iters, out=out)
+    best = None
+    for _ in range(3):
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        fem.fem_probe(0, n, iters, out=out)
+        b.record()
+        torch.cuda.synchronize()
+        t = a.elapsed_time(b) * 1e-3
+        best = t if best is None else min(best, t)
+    return {"fma_per_s": n * iters * 8 / best, "threads": n}
 
 
 def make_flush(device):
@@ -340,6 +377,10 @@ def measure_residual(case, prec, device, stream, flush, steps, warmup, peak, ora
         row["rel_maxnorm_err_vs_oracle"] = rel_err(out, oracle_timed(row, c.n_cells,
                                                                      lambda: oracle_mod.residual_for(c)))
         row["tolerance"] = TOL[prec]
+        if c is not case:
+            # against the float64 data of the workload itself: the float32 storage of the
+            # values included (the line above compares on identical, rounded inputs)
+            row["rel_maxnorm_err_vs_oracle_fp64_inputs"] = rel_err(out, oracle_mod.residual_for(case))
     return row, ms, wall, clocks
 
 
@@ -452,6 +493,10 @@ def measure_adjoint(case, prec, device, stream, flush, steps, warmup, peak, orac
         row["rel_err_dK"] = rel_err(dK, rK)
         row["rel_err_du"] = rel_err(du, ru)
         row["tolerance"] = TOL[prec]
+        if c is not case:  # against the unrounded float64 u, K and lambda
+            rK64, ru64 = oracle_mod.adjoint_for(case)
+            row["rel_err_dK_fp64_inputs"] = rel_err(dK, rK64)
+            row["rel_err_du_fp64_inputs"] = rel_err(du, ru64)
     return row
 
 
@@ -487,6 +532,65 @@ def measure_reaction(case, prec, device, stream, flush, steps, warmup, peak, ora
         torch.cuda.synchronize()
         ref = oracle_timed(row, c.n_cells, lambda: oracle_mod.reaction_diffusion(
             c.mesh.coords, c.mesh.conn, c.u, a_np, 1, c_np, q.points, q.weights, drift=drift))
+        row["rel_maxnorm_err_vs_oracle"] = rel_err(out, ref)
+        row["tolerance"] = TOL[prec]
+        if prec != "fp64":
+            a64, c64 = workloads.reaction_inputs(case)
+            row["rel_maxnorm_err_vs_oracle_fp64_inputs"] = rel_err(out, oracle_mod.reaction_diffusion(
+                case.mesh.coords, case.mesh.conn, case.u, a64, 1, c64, q.points, q.weights, drift=drift))
+    return row
+
+
+POINTWISE_SRC = {
+    "laplacian": "for (int i = 0; i < DIM; ++i) f1[i] = a[0] * grad_u[i];",
+    # the oracle's "nonlinear" physics: kappa(u, x) = (p0 + p1 u + p2 u^2)(1 + p3 (x_0 + 2 x_1 + 3 x_2))
+    "nonlinear": ("T s = T(0);\nfor (int i = 0; i < DIM; ++i) s += T(i + 1) * x[i];\n"
+                  "const T kappa = (T(1.3) + T(-0.7) * u[0] + T(0.45) * u[0] * u[0]) * (T(1) + T(0.35) * s);\n"
+                  "for (int i = 0; i < DIM; ++i) f1[i] = kappa * grad_u[i];"),
+}
+POINTWISE_PARAMS = (1.3, -0.7, 0.45, 0.35)
+
+
+def measure_pointwise(case, physics, prec, device, stream, flush, steps, warmup, peak, oracle_mod=None):
+    """User physics compiled at run time (fem_integrate_pointwise, Sec. 5): the Laplacian
+    written as a source string, or the nonlinear kappa(u, x) grad u of Sec. 2, on the
+    headline mesh. The compilation happens once, before the timed steps."""
+    import torch
+
+    import paper_1607_04245_gb300 as fem
+
+    c, d = device_case(case, prec, device)
+    q = c.rule
+    dt = fem.value_dtype(prec)
+    coef = d["K"][None].contiguous() if physics == "laplacian" else None
+    out = torch.empty((c.dim + 1, c.n_cells), dtype=dt, device=device)
+    t0 = time.perf_counter()
+    fem.fem_integrate_pointwise(d["coords"], d["conn"][:, :0].contiguous(), d["u"], None if coef is None else
+                                coef[:, :, :0].contiguous(), q.points, q.weights, f1=POINTWISE_SRC[physics],
+                                prec=prec)
+    compile_s = time.perf_counter() - t0
+    fn = lambda: fem.fem_integrate_pointwise(d["coords"], d["conn"], d["u"], coef, q.points, q.weights,
+                                             f1=POINTWISE_SRC[physics], out=out, prec=prec, stream=stream)
+    with torch.cuda.stream(stream):
+        ms, _, _ = timed_steps(fn, steps, warmup, stream, flush)
+    t = statistics.mean(ms) * 1e-3
+    s = 8 if prec == "fp64" else 4
+    nb, C, V = c.dim + 1, c.n_cells, c.n_verts
+    ncoef = 1 if coef is not None else 0
+    nbytes = nb * 4 * C + ncoef * q.n_q * s * C + nb * s * C + (c.dim * 8 + s) * V
+    row = {"physics": f"pointwise_{physics}", "dim": c.dim, "prec": prec, "cells": C,
+           "ms_per_launch": round(statistics.mean(ms), 6), "cells_per_s": C / t, "alg_bytes_per_launch": nbytes,
+           "alg_gbs": nbytes / t / 1e9, "hbm_frac_of_measured": nbytes / t / 1e9 / peak,
+           "compile_s": round(compile_s, 3),
+           "alg_bytes_per_cell": "conn 4(d+1) + coef n_coef n_q s + out (d+1) s + (V/C)(coords 8d + u s)",
+           "kernel": "fem_pointwise_kernel (NVRTC, one cell per thread, per-point evaluation of Eq. 2)"}
+    if oracle_mod is not None:
+        torch.cuda.synchronize()
+        if physics == "laplacian":
+            ref = oracle_timed(row, C, lambda: oracle_mod.residual_for(c))
+        else:
+            ref = oracle_timed(row, C, lambda: oracle_mod.pointwise("nonlinear", c.mesh.coords, c.mesh.conn, c.u, None,
+                                                                    q.points, q.weights, params=POINTWISE_PARAMS))
         row["rel_maxnorm_err_vs_oracle"] = rel_err(out, ref)
         row["tolerance"] = TOL[prec]
     return row
@@ -637,9 +741,10 @@ def measure_serving(device, n_requests, seed=0):
         reset([0.0] * len(reqs))
         sats.append(Scheduler(ex).run(reqs))
     sat = sorted(sats, key=lambda x: x.req_per_s)[1]
-    # sustained rate: the highest of 85/70/55/40 % of the saturation rate at which the
-    # backlog stays bounded (served rate within 3 % of the offered rate in the median run)
-    sweep, st, rate = [], None, None
+    # the operating curve: Poisson arrivals at 85/70/55/40 % of the saturation rate, every
+    # fraction measured; the sustained rate is the highest fraction whose backlog stays
+    # bounded (served rate within 3 % of the offered rate in the median run)
+    sweep, st, rate, p99_runs = [], None, None, None
     for frac in (0.85, 0.70, 0.55, 0.40):
         r_off = frac * sat.req_per_s
         runs = []
@@ -648,14 +753,26 @@ def measure_serving(device, n_requests, seed=0):
             ex.launches = 0
             runs.append(Scheduler(ex).run(reqs, arrival_rate=r_off))
         med = sorted(runs, key=lambda x: x.p99_ms)[1]
+        bounded = med.req_per_s >= 0.97 * r_off
         sweep.append({"fraction": frac, "offered_req_per_s": r_off, "served_req_per_s": med.req_per_s,
-                      "p50_ms": med.p50_ms, "p99_ms": med.p99_ms,
+                      "p50_ms": med.p50_ms, "p99_ms": med.p99_ms, "bounded_backlog": bounded,
                       "p99_ms_of_3_runs": sorted(x.p99_ms for x in runs)})
-        if med.req_per_s >= 0.97 * r_off:
-            st, rate = med, r_off
-            break
+        if bounded and st is None:
+            st, rate, p99_runs = med, r_off, sweep[-1]["p99_ms_of_3_runs"]
     if st is None:
-        st, rate = med, r_off
+        st, rate, p99_runs = med, r_off, sweep[-1]["p99_ms_of_3_runs"]
+    # what bounds the saturation rate: the bytes each request moves across the host link
+    # against this box's measured link rates, and the host time per request
+    h2d = sum(r.input_bytes for r in reqs)
+    d2h = sum(sum(t.numel() * t.element_size() for t in r.result.values()) for r in reqs)
+    link = host_link_rates(device)
+    link_s = max(h2d / link["h2d_gbs"], d2h / link["d2h_gbs"], (h2d + d2h) / link["both_gbs"]) / 1e9
+    bound = {"h2d_bytes": h2d, "d2h_bytes": d2h, "served_h2d_gbs": h2d / sat.makespan_s / 1e9,
+             "served_d2h_gbs": d2h / sat.makespan_s / 1e9, "link": link,
+             "link_floor_s": link_s, "link_fraction_of_makespan": link_s / sat.makespan_s,
+             "makespan_s": sat.makespan_s, "host_us_per_request": sat.makespan_s / len(reqs) * 1e6,
+             "reading": "link_fraction_of_makespan near 1: the host link bounds the rate; well below 1: the "
+                        "per-request host work (admission, launch, polling) does"}
     kinds = {}
     for sp in specs:
         k = f"{sp['physics']}{sp['dim']}d_{sp['kind']}"
@@ -668,8 +785,42 @@ def measure_serving(device, n_requests, seed=0):
             "poisson": {"arrival_rate_req_per_s": rate, "req_per_s": st.req_per_s, "cells_per_s": st.cells_per_s,
                         "p50_ms": st.p50_ms, "p99_ms": st.p99_ms, "mean_ms": st.mean_ms,
                         "max_inflight": st.max_inflight, "rejected": st.n_rejected, "makespan_s": st.makespan_s,
-                        "cells": st.cells, "p99_ms_of_3_runs": sweep[-1]["p99_ms_of_3_runs"]},
-            "rate_sweep": sweep}
+                        "cells": st.cells, "p99_ms_of_3_runs": p99_runs},
+            "rate_sweep": sweep, "saturation_bound": bound}
+
+
+def host_link_rates(device, nbytes=64 << 20):
+    """Host<->device copy rates of this machine (GB/s) between page-locked host memory and the
+    device: host to device, device to host, and both directions at once (two streams);
+    best of 3, CUDA events."""
+    import torch
+
+    h = torch.empty(nbytes, dtype=torch.uint8, pin_memory=True)
+    h2 = torch.empty(nbytes, dtype=torch.uint8, pin_memory=True)
+    d = torch.empty(nbytes, dtype=torch.uint8, device=device)
+    d2 = torch.empty(nbytes, dtype=torch.uint8, device=device)
+    s1, s2 = torch.cuda.Stream(device=device), torch.cuda.Stream(device=device)
+
+    def best(fn):
+        t = None
+        for _ in range(3):
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            fn()
+            torch.cuda.synchronize()
+            dt = time.perf_counter() - t0
+            t = dt if t is None else min(t, dt)
+        return t
+
+    def both():
+        with torch.cuda.stream(s1):
+            d.copy_(h, non_blocking=True)
+        with torch.cuda.stream(s2):
+            h2.copy_(d2, non_blocking=True)
+
+    return {"h2d_gbs": nbytes / best(lambda: d.copy_(h, non_blocking=True)) / 1e9,
+            "d2h_gbs": nbytes / best(lambda: h2.copy_(d2, non_blocking=True)) / 1e9,
+            "both_gbs": 2 * nbytes / best(both) / 1e9, "bytes": nbytes}
 
 
 def cpu_model() -> str:
@@ -828,7 +979,11 @@ def run_ours(args):
     achieved = nbytes / (row["ms_per_launch"] * 1e-3) / 1e9
     traffic = recorded_traffic("lap3d_mixed")
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-                "traffic": traffic, "peak_kind": f"{peak_kind} copy bandwidth (MEASURED_PEAKS.json hbm_gbs)"
+                "traffic": traffic,
+                "traffic_kind": "recorded: ncu dram__bytes_read.sum + dram__bytes_write.sum of one launch of the "
+                                "same kernel sources (profiles/dram_traffic.txt, keyed by a hash of the sources; "
+                                "null once they change), not measured in this run",
+                "peak_kind": f"{peak_kind} copy bandwidth (MEASURED_PEAKS.json hbm_gbs)"
                 if peak_kind == "measured" else "fallback 6800 GB/s",
                 "kernel": HEADLINE_KERNEL,
                 "alg_bytes_per_launch": nbytes,
@@ -847,6 +1002,12 @@ def run_ours(args):
                                   f"at the sampled {sm_mhz:.0f} MHz",
                      "kernel": "lap_staged_kernel<3, FP64, NQ=4>",
                      "inst_per_cell": FP64_INST_PER_CELL_LAP3D}
+
+    probe = measure_fp64_fma_rate(device)
+    roofline_fp64_measured = dict(roofline_fp64, peak=probe["fma_per_s"] / 1e12,
+                                  frac=fp64_inst / t64 / probe["fma_per_s"],
+                                  peak_kind="measured in this run: float64 FMA instructions/s of fem_probe kind 0 "
+                                            f"({probe['threads']} threads x 8 independent FMA chains, best of 3)")
 
     rows = {"fp64": row64}
     # float64 values with float32-pair arithmetic: float64-class error, float32-pipe speed
@@ -889,6 +1050,11 @@ def run_ours(args):
         if want(f"reaction3d_grad_a_{prec}"):
             rows[f"reaction3d_grad_a_{prec}"] = measure_reaction(case, prec, device, stream, flush, rsteps, args.warmup,
                                                                  peak, oracle)
+    for prec in ("mixed", "fp64"):
+        for phys in ("laplacian", "nonlinear"):
+            if want(f"pointwise_{phys}3d_{prec}"):
+                rows[f"pointwise_{phys}3d_{prec}"] = measure_pointwise(case, phys, prec, device, stream, flush, rsteps,
+                                                                       args.warmup, peak, oracle)
     for prec in ("fp64", "fp64_df"):
         if want(f"pcg_lap3d_{prec}"):
             rows[f"pcg_lap3d_{prec}"] = measure_pcg(case, device, stream, peak, prec)
@@ -910,7 +1076,8 @@ def run_ours(args):
     e2e = measure_e2e(case, "mixed", device, max(3, args.steps // 100), 3)
 
     line = {"metric": METRIC, "value": value, "unit": "cells/s", "n_gpus": ws, "steps": args.steps,
-            "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
+            "warmup": args.warmup, "ms_per_step": ms_per_step, "ms_median": row["ms_median"],
+            "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": {"workload": WORKLOAD, "cells": case.n_cells, "verts": case.n_verts,
                        "form": "fp32_mixed (float32 values, float64 coordinates split to float32 pairs, "
@@ -921,6 +1088,7 @@ def run_ours(args):
             "hbm_frac_of_nominal_8tbs": row["alg_gbs"] / 8000.0,
             "paper_model_gflops": row["paper_model_gflops"], "counted_gflops": row.get("counted_gflops"),
             "rel_maxnorm_err_vs_oracle": row.get("rel_maxnorm_err_vs_oracle"),
+            "rel_maxnorm_err_vs_oracle_fp64_inputs": row.get("rel_maxnorm_err_vs_oracle_fp64_inputs"),
             "fp64": {"cells_per_s": row64["cells_per_s"], "ms_per_launch": row64["ms_per_launch"],
                      "alg_gbs": row64["alg_gbs"], "hbm_frac_of_measured": row64["hbm_frac_of_measured"],
                      "rel_maxnorm_err_vs_oracle": row64.get("rel_maxnorm_err_vs_oracle")},
@@ -929,7 +1097,7 @@ def run_ours(args):
                         "rel_maxnorm_err_vs_oracle": rows["fp64_df"].get("rel_maxnorm_err_vs_oracle"),
                         "speedup_over_fp64": rows["fp64_df"]["cells_per_s"] / row64["cells_per_s"],
                         "form": "float64 values, float32-pair arithmetic on the float32 pipe"},
-            "roofline": roofline, "roofline_fp64": roofline_fp64,
+            "roofline": roofline, "roofline_fp64": roofline_fp64, "roofline_fp64_measured": roofline_fp64_measured,
             "cpu_baseline": cpu_baseline(case) if (ws == 1 and not args.no_cpu_baseline) else None,
             "e2e": e2e, "gpu_launches": args.steps,
             "clocks": clocks, "rows": rows,

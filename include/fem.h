@@ -39,8 +39,13 @@
  *    thread-local message for the most recent failing call. No exception crosses
  *    the ABI. n_cells = 0 is a valid no-op.
  *  - Vertex ids are clamped into [0, n_verts) in-kernel, so malformed connectivity
- *    cannot make a kernel read out of bounds; it gives meaningless values instead.
- *    fem_check_mesh() detects such input.
+ *    cannot make a kernel read out of bounds; it gives meaningless values for the cells
+ *    concerned instead. Every kernel also checks its mesh as it goes (the mesh check of
+ *    the boundary, always on): a vertex id outside [0, n_verts), or a cell with det J = 0
+ *    or a non-finite det J, or with a repeated vertex id, sets a bit in the device error
+ *    word, and the next fem_device_error() returns FEM_ERR_BADMESH. (The mixed form
+ *    checks the determinant of the cells its shape test sends to float64, which every
+ *    degenerate cell fails for tau > 0.) fem_check_mesh() counts such cells.
  *  - Vectorised (128-bit) loads are used when every cell-indexed row is 16-byte
  *    aligned (n_cells a multiple of 4 and 16-byte aligned base pointers); other
  *    inputs run the same kernels with scalar loads, still on the GPU.
@@ -62,7 +67,7 @@ typedef enum {
     FEM_ERR_SHAPE = -2,     /* sizes out of the supported range */
     FEM_ERR_CUDA = -3,      /* a CUDA launch or runtime call failed */
     FEM_ERR_OOM = -4,       /* a caller-provided buffer is too small */
-    FEM_ERR_BADMESH = -5,   /* reported by fem_check_mesh */
+    FEM_ERR_BADMESH = -5,   /* fem_device_error: a kernel met an invalid mesh */
     FEM_ERR_TIMEOUT = -6,   /* a bounded device-side wait gave up */
     FEM_ERR_UNSUPPORTED = -7
 } fem_status;
@@ -86,8 +91,9 @@ typedef enum {
      * pair of float32 values (hi + lo, double-length arithmetic from TwoSum/TwoProduct),
      * the outputs are widened back to float64. Values must lie in float32's normal range
      * (|x| in [2^-126, 2^128), or zero). fem_integrate_laplacian, fem_integrate_elasticity,
-     * fem_adjoint_laplacian (its element part; the vertex sum in float64) and (for its
-     * residual) fem_pcg_laplacian only; the other entry points return FEM_ERR_ARG for it. */
+     * fem_adjoint_laplacian (its element part; the vertex sum in float64), (for its
+     * residual) fem_pcg_laplacian, and fem_gather_nodes (float64 sums) only; the other
+     * entry points return FEM_ERR_ARG for it. */
     FEM_FP64_DF = 3
 } fem_precision;
 
@@ -165,6 +171,45 @@ fem_status fem_integrate_reaction_diffusion(int dim, int64_t n_cells, int64_t n_
                                             const void *c, double drift, int n_q, const double *qpts,
                                             const double *qw, void *elem_out, fem_precision prec,
                                             fem_stream stream);
+
+/* ---------------------------------------------------------------------------------
+ * fem_integrate_pointwise -- element vectors of the full bracket of Eq. 2 for pointwise
+ * functions f0 and f1 given as CUDA C++ source text, compiled at run time (Sec. 5: the
+ * library user provides f0 and f1 as strings, which are inlined into the kernel source
+ * handed to the just-in-time compiler). For a field of n_comp components:
+ *     r_{e,b,k} = sum_q w_q |det J| [ phi_b(xi_q) f0_k(q) + sum_i G_{b,i} f1_{k,i}(q) ]
+ * with G_b = J^{-T} grad_ref phi_b and, at every quadrature point, the field, its gradient,
+ * the coefficients and the physical point.
+ *   f0_src, f1_src  function BODIES (either may be NULL = zero; not both). In scope:
+ *                   const T *u       [NCOMP]        u_k(q) = sum_b phi_b(xi_q) u_{b,k}
+ *                   const T *grad_u  [NCOMP*DIM]    grad_u[k*DIM + i] = d u_k / d x_i
+ *                   const T *a       [NCOEF]        a[j] = coef[j][q][e]
+ *                   const T *x       [DIM]          x(q) = sum_b phi_b(xi_q) x_b
+ *                   T *f0 [NCOMP] or T *f1 [NCOMP*DIM] (zeroed before the call), to fill
+ *                   and the constants DIM, NCOMP, NCOEF; T is double (FEM_FP64) or float
+ *                   (FEM_FP32_MIXED). Example, the variable-coefficient Laplacian:
+ *                     f1_src = "for (int i = 0; i < DIM; ++i) f1[i] = a[0] * grad_u[i];"
+ *   n_comp          1..3 field components; u is [n_comp][n_verts]
+ *   n_coef          0..FEM_POINTWISE_MAX_COEF per-point coefficients; coef [n_coef][n_q][n_cells]
+ *   qpts            required (phi_b(xi_q) enters u(q), x(q) and the f0 term)
+ *   elem_out        [(dim+1)*n_comp][n_cells], row b*n_comp + k
+ *   prec            FEM_FP64 (all float64) or FEM_FP32_MIXED (values, physics and sums in
+ *                   float32; coordinates split exactly into float32 pairs for the Jacobian;
+ *                   cells failing the shape test get their geometry in float64)
+ * The first call for a given (device, precision, dim, n_comp, n_coef, n_q, f0_src, f1_src)
+ * compiles the kernel with NVRTC for the device's architecture and loads it (tens to
+ * hundreds of milliseconds); later calls reuse the cached kernel. A call with n_cells = 0
+ * compiles and caches without launching: make it before any stream capture, which must
+ * not contain a compilation. Returns FEM_ERR_ARG with the compiler's log in
+ * fem_last_error() when the source does not compile, FEM_ERR_UNSUPPORTED when NVRTC
+ * (libnvrtc.so) cannot be loaded; otherwise as fem_integrate_laplacian. Mesh errors are
+ * reported through fem_device_error() like the built-in kernels.
+ * ------------------------------------------------------------------------------- */
+#define FEM_POINTWISE_MAX_COEF 8
+fem_status fem_integrate_pointwise(const char *f0_src, const char *f1_src, int dim, int n_comp, int n_coef,
+                                   int64_t n_cells, int64_t n_verts, const double *coords, const int32_t *conn,
+                                   const void *u, const void *coef, int n_q, const double *qpts, const double *qw,
+                                   void *elem_out, fem_precision prec, fem_stream stream);
 
 /* ---------------------------------------------------------------------------------
  * fem_integrate_laplacian_host -- fem_integrate_laplacian for arrays in HOST memory
@@ -324,11 +369,15 @@ fem_status fem_adjoint_laplacian(int dim, int64_t n_cells, int64_t n_verts, cons
  *     return FEM_ERR_SHAPE with a message and launch nothing.
  *   - Set-up: the first call on a device looks up the array's device address
  *     (cudaGetSymbolAddress) with that device current; make that first call before
- *     any stream capture.
+ *     any stream capture. The address is kept for the life of the process, so resetting
+ *     the device (cudaDeviceReset) after the first call is not supported.
  *   - Sharing: every call on a device uses the same array, which keeps the last call's
  *     contents. Each call writes every entry it reads before reading it, so nothing
  *     needs clearing; but calls that overlap on the GPU (different streams, or host
  *     threads) race on the array and must be serialised by the caller.
+ *   - Validity: dK and du are valid only if the next fem_device_error() returns FEM_OK.
+ *     A bounded wait that gave up (FEM_ERR_TIMEOUT) leaves a tile of the array unwritten,
+ *     and du then includes the previous call's values for it.
  * Arguments, layouts and results are those of fem_adjoint_laplacian without `scratch`.
  * ------------------------------------------------------------------------------- */
 #define FEM_NOALLOC_SCRATCH_BYTES (16u << 20)
@@ -356,8 +405,12 @@ fem_status fem_build_node2cell(int dim, int64_t n_cells, int64_t n_verts, const 
  * fem_gather_nodes -- the assembly sum E^T of Eq. 2 for element vectors:
  *   out[k][n] = sum over the entries e*(dim+1) + a of vertex n (in list order) of
  *               elem[(a*n_comp + k)*C + e]
- * elem is [(dim+1)*n_comp][C] (the layout of the integrate outputs), out is
- * [n_comp][V]; both of the value type of prec. Fixed summation order, no atomics.
+ * elem is [(dim+1)*n_comp][C] (the layout of the integrate outputs: n_comp = 1 for the
+ * Laplacian, dim for elasticity), out is [n_comp][V]; both of the value type of prec
+ * (float64 for FEM_FP64 and FEM_FP64_DF, float32 otherwise). Fixed summation order, no
+ * atomics, so repeated calls give bitwise the same out; float64 sums are plain, float32
+ * sums compensated (TwoSum). node_ptr / node_idx from fem_build_node2cell for the conn
+ * that produced elem.
  * ------------------------------------------------------------------------------- */
 fem_status fem_gather_nodes(int dim, int n_comp, int64_t n_cells, int64_t n_verts, const void *elem,
                             const int32_t *node_ptr, const int32_t *node_idx, void *out,
@@ -391,14 +444,22 @@ int64_t fem_arena_capacity(fem_arena *arena);
  *
  * fem_serve_launch -- on `stream`: upload host_in (one copy), run the request's kernels
  *   (kind 0: fem_integrate_laplacian or fem_integrate_elasticity; kind 1, Laplacian only:
- *   fem_build_node2cell then fem_adjoint_laplacian), copy out_bytes[0] from slot OUT
- *   (element vectors, or dK) to host_out[0] and out_bytes[1] from slot DU (du) to
- *   host_out[1], then record `event` (from fem_serve_event_create). Returns after
- *   enqueueing; errors as the entry points it calls. Before any copy or launch the
- *   descriptor is checked against the block: every array the request uses (sizes from
- *   dim, n_q, n_cells, n_verts and prec) must lie inside [0, block_bytes), in_bytes
- *   must not exceed block_bytes and out_bytes[k] must not exceed its source array;
- *   otherwise FEM_ERR_ARG and nothing is enqueued.
+ *   fem_build_node2cell then fem_adjoint_laplacian; kind 2: the bounded-wait self-test of
+ *   fem_selftest_wait with a 1 ms budget and no arrays -- a request that always fails with
+ *   the timeout bit, for tests of the failure path), copy out_bytes[0] from slot
+ *   OUT (element vectors, or dK) to host_out[0] and out_bytes[1] from slot DU (du) to
+ *   host_out[1], then record `event` (from fem_serve_event_create). With host_status set,
+ *   the request's kernels report their device-side errors into that word instead of the
+ *   device-wide word of fem_device_error: a 4-byte word of page-locked, device-mapped host
+ *   memory (cudaHostAlloc, pinned tensors; otherwise FEM_ERR_ARG) that the caller sets to
+ *   0 before the launch. Once the event has completed it holds the request's error bits:
+ *   0 = none, 1 = a bounded wait gave up (outputs incomplete), 2 = invalid mesh (a vertex
+ *   id outside [0, n_verts) or a degenerate cell). Returns after enqueueing; errors as the entry
+ *   points it calls. Before any copy or launch the descriptor is checked against the
+ *   block: every array the request uses (sizes from dim, n_q, n_cells, n_verts and prec)
+ *   must lie inside [0, block_bytes), in_bytes must not exceed block_bytes and
+ *   out_bytes[k] must not exceed its source array; otherwise FEM_ERR_ARG and nothing is
+ *   enqueued.
  * fem_serve_events_query -- done[i] = 1 if events[i] has completed, else 0.
  * ------------------------------------------------------------------------------- */
 enum {
@@ -411,7 +472,7 @@ enum {
     FEM_SERVE_SLOTS = 12
 };
 typedef struct {
-    int32_t kind;           /* 0 residual, 1 adjoint */
+    int32_t kind;           /* 0 residual, 1 adjoint, 2 bounded-wait self-test */
     int32_t physics;        /* 0 Laplacian, 1 elasticity */
     int32_t dim, n_q, prec, reserved;
     int64_t n_cells, n_verts;
@@ -422,6 +483,8 @@ typedef struct {
     int64_t out_bytes[2];
     int64_t offset[FEM_SERVE_SLOTS];
     int64_t block_bytes;    /* size of the device block the offsets point into */
+    void *host_status;      /* device-mapped page-locked uint32 host word for the request's error
+                               bits (zeroed by the caller before the launch), or NULL */
 } fem_serve_request;
 int64_t fem_serve_request_bytes(void); /* sizeof(fem_serve_request), for bindings to check their layout */
 fem_status fem_serve_event_create(void **event);
@@ -440,12 +503,19 @@ fem_status fem_serve_launch(const fem_serve_request *request, void *block, void 
 fem_status fem_probe(int kind, int64_t n_threads, int iters, void *out, fem_stream stream);
 
 /* ---------------------------------------------------------------------------------
- * fem_device_error -- bounded device-side waits (not in the paper). The staged kernels
- * wait on the bulk copies of their inputs with a time budget (0.5 s per wait); a wait
- * that runs out stops that CTA without writing the tile it waited for and sets a bit in
- * a per-device error word. fem_device_error synchronises `stream`, reads and clears the
- * word of the current device, and returns FEM_ERR_TIMEOUT if any wait gave up since the
- * last call (outputs of the calls in between are then incomplete), else FEM_OK.
+ * fem_device_error -- the device-side status of the kernels since the last call: a
+ * per-device error word that kernels set bits in. Two conditions: (1) bounded waits (not
+ * in the paper): the staged kernels wait on the bulk copies of their inputs with a time
+ * budget (0.5 s per wait); a wait that runs out stops that CTA without writing the tile
+ * it waited for; (2) the mesh check (the boundary's debug check, always on): a vertex id
+ * outside [0, n_verts) (clamped, so nothing is read out of bounds), or a cell with
+ * det J = 0, a non-finite det J or a repeated vertex id. fem_device_error synchronises
+ * `stream`, reads and clears the word of the current device, and returns
+ * FEM_ERR_TIMEOUT if any wait gave up since the last call (outputs of the calls in
+ * between are then incomplete), else FEM_ERR_BADMESH if a kernel met an invalid mesh
+ * (the outputs of the cells concerned are meaningless; the others are unaffected), else
+ * FEM_OK. Requests of the serving launch report into their own words (fem_serve_launch),
+ * not into this one.
  * ------------------------------------------------------------------------------- */
 fem_status fem_device_error(fem_stream stream);
 
@@ -454,6 +524,15 @@ fem_status fem_device_error(fem_stream stream);
  * completes, so that the next fem_device_error() returns FEM_ERR_TIMEOUT. For tests of
  * the timeout path; it faults nothing and leaves the context usable. */
 fem_status fem_selftest_wait(int64_t budget_ns, fem_stream stream);
+
+/* fem_selftest_quotient -- the float64 kernels' division num / |det J| on the device, for
+ * tests of its accuracy: q_lib[i] = the library's quotient of num[i] by |den[i]| (a float32
+ * seed of the reciprocal refined by two float64 Newton-Raphson steps, the IEEE division
+ * for |den| outside [2^-1000, 2^1001), zero, subnormal, infinite or NaN), q_ieee[i] =
+ * num[i] / fabs(den[i]) with CUDA's IEEE division. All four arrays are [n] float64 device
+ * arrays. */
+fem_status fem_selftest_quotient(int64_t n, const double *num, const double *den, double *q_lib, double *q_ieee,
+                                 fem_stream stream);
 
 /* status text and the thread-local message of the last failing call */
 const char *fem_status_string(fem_status st);

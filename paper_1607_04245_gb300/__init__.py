@@ -29,10 +29,12 @@ from .binding import (  # noqa: F401
     fem_integrate_laplacian_host,
     fem_integrate_laplacian_geom,
     fem_integrate_laplacian_transposed,
+    fem_integrate_pointwise,
     fem_integrate_reaction_diffusion,
     fem_precompute_geometry,
     fem_pcg_laplacian,
     fem_probe,
+    fem_selftest_quotient,
     fem_selftest_wait,
     fem_set_mixed_threshold,
     fem_status_string,

@@ -62,6 +62,9 @@ def lib():
             "fem_pcg_laplacian": [ci, i64, i64, P, P, P, ci, P, P, P, P, P, P, P, ci, cd, P, i64, P, P, ci, P],
             "fem_integrate_laplacian_geom": [ci, i64, i64, P, P, P, ci, P, P, P, P, ci, P],
             "fem_selftest_wait": [i64, P],
+            "fem_selftest_quotient": [i64, P, P, P, P, P],
+            "fem_integrate_pointwise": [ctypes.c_char_p, ctypes.c_char_p, ci, ci, ci, i64, i64, P, P, P, P, ci, P,
+                                        P, P, ci, P],
         }
         for name, args in sig.items():
             f = getattr(L, name)
@@ -201,6 +204,33 @@ def fem_integrate_elasticity(coords, conn, u, lam, mu, qpts, qw, out=None, prec=
         _dev(u, "u", dt, (dim, V), dev), _dev(lam, "lam", dt, (nq, C), dev), _dev(mu, "mu", dt, (nq, C), dev),
         nq, qp.ptr, w.ptr, _dev(out, "out", dt, ((dim + 1) * dim, C), dev), p, _stream(stream))
     _check("fem_integrate_elasticity", st)
+    return out
+
+
+def fem_integrate_pointwise(coords, conn, u, coef, qpts, qw, f1=None, f0=None, out=None, prec="mixed",
+                            stream=None) -> torch.Tensor:
+    """Element vectors [(dim+1)*n_comp][C] of Eq. 2 for pointwise functions given as CUDA
+    source text: f1 and f0 are function bodies (see fem_integrate_pointwise in
+    include/fem.h for the names in scope), compiled at run time and cached. u is [V] or
+    [n_comp][V]; coef is [n_coef][n_q][C] or None. An empty mesh (C = 0) only compiles."""
+    p = precision(prec)
+    dt = value_dtype(p)
+    dim, V, C = _mesh_sizes(coords, conn)
+    nq = int(np.asarray(qw).shape[0]) if not isinstance(qw, torch.Tensor) else int(qw.shape[0])
+    dev = coords.device
+    n_comp = 1 if u.dim() == 1 else int(u.shape[0])
+    n_coef = 0 if coef is None else int(coef.shape[0])
+    if out is None:
+        out = torch.empty(((dim + 1) * n_comp, C), dtype=dt, device=dev)
+    qp, w = _HostTable(qpts, (nq, dim), "qpts"), _HostTable(qw, (nq,), "qw")
+    enc = lambda t: None if t is None else t.encode()
+    st = lib().fem_integrate_pointwise(
+        enc(f0), enc(f1), dim, n_comp, n_coef, C, V, _dev(coords, "coords", torch.float64, device=dev),
+        _dev(conn, "conn", torch.int32, device=dev),
+        _dev(u, "u", dt, (V,) if u.dim() == 1 else (n_comp, V), dev),
+        None if coef is None else _dev(coef, "coef", dt, (n_coef, nq, C), dev), nq, qp.ptr, w.ptr,
+        _dev(out, "out", dt, ((dim + 1) * n_comp, C), dev), p, _stream(stream))
+    _check("fem_integrate_pointwise", st)
     return out
 
 
@@ -436,9 +466,24 @@ def fem_probe(kind: int, n_threads: int, iters: int, out=None, stream=None) -> t
 
 
 def fem_device_error(stream=None) -> int:
-    """Synchronise `stream`; return (and clear) the device error status: 0 (FEM_OK) or
-    -6 (FEM_ERR_TIMEOUT) when a kernel gave up a bounded device-side wait."""
+    """Synchronise `stream`; return (and clear) the device error status: 0 (FEM_OK), -6
+    (FEM_ERR_TIMEOUT) when a kernel gave up a bounded device-side wait, or -5
+    (FEM_ERR_BADMESH) when a kernel met a vertex id outside [0, n_verts) or a degenerate
+    cell (det J = 0, non-finite, or a repeated vertex id)."""
     return int(lib().fem_device_error(_stream(stream)))
+
+
+def fem_selftest_quotient(num: torch.Tensor, den: torch.Tensor, stream=None):
+    """(library quotient num / |den|, IEEE num / fabs(den)) computed on the device."""
+    n = int(num.numel())
+    if den.numel() != n:
+        raise ValueError("num and den differ in size")
+    q_lib = torch.empty_like(num)
+    q_ieee = torch.empty_like(num)
+    _check("fem_selftest_quotient", lib().fem_selftest_quotient(
+        n, _dev(num, "num", torch.float64), _dev(den, "den", torch.float64), _dev(q_lib, "q_lib", torch.float64),
+        _dev(q_ieee, "q_ieee", torch.float64), _stream(stream)))
+    return q_lib, q_ieee
 
 
 def fem_selftest_wait(budget_ns: int, stream=None) -> None:

@@ -24,7 +24,7 @@ BUILD = os.path.join(PKG, "_build")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 SOURCES = ["fem_core.cu", "fem_laplacian.cu", "fem_elasticity.cu", "fem_mesh.cu", "fem_geometry.cu", "fem_reaction.cu",
            "fem_solver.cu", "fem_transpose.cu", "fem_host.cu", "fem_df.cu",
-           "fem_arena.cpp", "fem_noalloc.cu", "fem_serve.cu"]
+           "fem_arena.cpp", "fem_noalloc.cu", "fem_serve.cu", "fem_pointwise.cu"]
 
 
 def nvcc() -> str:
@@ -62,7 +62,7 @@ def build(force: bool = False, verbose_ptxas: bool = False) -> str:
         for _, log in results:
             sys.stderr.write(log)
     tmp = OUT + ".tmp"
-    cmd = [cc] + ARCH + ["-shared", "-o", tmp] + [o for o, _ in results] + ["-lcudart"]
+    cmd = [cc] + ARCH + ["-shared", "-o", tmp] + [o for o, _ in results] + ["-lcudart", "-ldl"]
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError(f"link failed:\n{r.stderr}")

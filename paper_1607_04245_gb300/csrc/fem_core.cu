@@ -9,6 +9,7 @@
 #include <mutex>
 #include <utility>
 
+#include "fem_cell.cuh"
 #include "fem_pipe.cuh"
 
 // Device error word of the staged kernels (see fem_pipe.cuh); one per device.
@@ -77,9 +78,20 @@ fem_status check_common(int dim, int64_t n_cells, int64_t n_verts, const double 
 
 float mixed_tau() { return g_mixed_tau.load(std::memory_order_relaxed); }
 
+static thread_local unsigned *t_error_word_override = nullptr;
+
+void set_error_word_override(unsigned *w) { t_error_word_override = w; }
+
 // Device address of g_fem_device_error on the current device, looked up once per device
-// (host code cannot use the symbol itself as a device pointer).
+// (host code cannot use the symbol itself as a device pointer), unless the calling thread
+// has redirected its launches to another word (set_error_word_override).
+static unsigned *device_error_word_global();
+
 unsigned *device_error_word() {
+    return t_error_word_override ? t_error_word_override : device_error_word_global();
+}
+
+static unsigned *device_error_word_global() {
     static std::mutex mu;
     static unsigned *cached[64] = {nullptr};
     int dev = 0;
@@ -107,6 +119,35 @@ int sm_count() {
         cached[dev].store(n, std::memory_order_relaxed);
     }
     return n;
+}
+
+// Resident CTAs per SM of a kernel launched with `block` threads and no dynamic shared
+// memory (cached per device and kernel).
+static int occupancy(const void *kernel, int block) {
+    static std::mutex mu;
+    static std::map<std::pair<const void *, int>, int> occ_cache[64];  // per device, (kernel, block)
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) dev = 0;
+    std::lock_guard<std::mutex> lk(mu);
+    auto &cache = occ_cache[dev];
+    const auto key = std::make_pair(kernel, block);
+    auto it = cache.find(key);
+    if (it == cache.end()) {
+        int o = 0;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, kernel, block, 0) != cudaSuccess) {
+            cudaGetLastError();  // clear the failed query only; the launch reports real errors
+            o = 1;
+        }
+        it = cache.emplace(key, o < 1 ? 1 : o).first;
+    }
+    return it->second;
+}
+
+int resident_grid(const void *kernel, int block, int64_t n_threads) {
+    const int64_t need = (n_threads + block - 1) / block;
+    const int64_t cap = int64_t(occupancy(kernel, block)) * sm_count();
+    const int64_t g = need < cap ? need : cap;
+    return static_cast<int>(g < 1 ? 1 : g);
 }
 
 int grid_for(int64_t n_threads, int block, const void *kernel) {
@@ -235,12 +276,34 @@ __global__ void selftest_wait_kernel(uint64_t budget_ns, unsigned *err) {
     if (!mbar_wait_bounded(&bar, 0, budget_ns)) record_device_error(err, FEM_DEVERR_TIMEOUT);
 }
 
+// The float64 kernels' quotient num / |den| (a Newton-Raphson reciprocal, fem_cell.cuh)
+// beside the IEEE division num / fabs(den), element by element.
+__global__ void selftest_quotient_kernel(int64_t n, const double *num, const double *den, double *q_lib,
+                                         double *q_ieee) {
+    const int64_t stride = int64_t(gridDim.x) * blockDim.x;
+    for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < n; i += stride) {
+        q_lib[i] = quot_abs(num[i], den[i]);
+        q_ieee[i] = num[i] / fabs(den[i]);
+    }
+}
+
 }  // namespace fem
 
 using namespace fem;
 
+extern "C" fem_status fem_selftest_quotient(int64_t n, const double *num, const double *den, double *q_lib,
+                                            double *q_ieee, fem_stream stream) {
+    if (n < 0) return fail(FEM_ERR_ARG, "negative n");
+    if (n == 0) return FEM_OK;
+    if (!num || !den || !q_lib || !q_ieee) return fail(FEM_ERR_ARG, "a NULL array");
+    const int64_t blocks = (n + 255) / 256;
+    selftest_quotient_kernel<<<static_cast<unsigned>(blocks < 4096 ? blocks : 4096), 256, 0, stream>>>(
+        n, num, den, q_lib, q_ieee);
+    return check_launch("fem_selftest_quotient");
+}
+
 extern "C" fem_status fem_device_error(fem_stream stream) {
-    unsigned *w = device_error_word();
+    unsigned *w = device_error_word_global();
     if (!w) return fail(FEM_ERR_CUDA, "fem_device_error: device error word unavailable");
     cudaError_t e = cudaStreamSynchronize(stream);
     if (e != cudaSuccess) return fail(FEM_ERR_CUDA, "fem_device_error: %s", cudaGetErrorString(e));
@@ -251,7 +314,12 @@ extern "C" fem_status fem_device_error(fem_stream stream) {
         e = cudaMemcpy(w, &zero, sizeof(zero), cudaMemcpyHostToDevice);
     }
     if (e != cudaSuccess) return fail(FEM_ERR_CUDA, "fem_device_error: %s", cudaGetErrorString(e));
-    if (v & FEM_DEVERR_TIMEOUT) return fail(FEM_ERR_TIMEOUT, "a kernel gave up a bounded device-side wait");
+    if (v & FEM_DEVERR_TIMEOUT)
+        return fail(FEM_ERR_TIMEOUT, "a kernel gave up a bounded device-side wait%s",
+                    (v & FEM_DEVERR_BADMESH) ? " (and a kernel met an invalid mesh)" : "");
+    if (v & FEM_DEVERR_BADMESH)
+        return fail(FEM_ERR_BADMESH, "a kernel met a vertex id outside [0, n_verts) or a cell with det J = 0 or "
+                                     "a non-finite det J (fem_check_mesh counts them)");
     return FEM_OK;
 }
 

@@ -184,6 +184,7 @@ struct DfArgs {
     int64_t C;
     uint32_t V;
     int nq;
+    unsigned *err;  // device error word (FEM_DEVERR_BADMESH)
     double wd[FEM_MAX_QPTS];
 };
 
@@ -194,11 +195,13 @@ __global__ void __launch_bounds__(kBlock, 5) lap_df_kernel(const __grid_constant
     const double *X[DIM];
 #pragma unroll
     for (int k = 0; k < DIM; ++k) X[k] = a.X[k];
+    uint32_t vmax = 0;     // largest vertex id seen (bad ids are clamped and reported)
+    bool bad_det = false;  // a cell with det J = 0 or non-finite
     const int64_t stride = int64_t(gridDim.x) * blockDim.x;
     for (int64_t c = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; c < C; c += stride) {
         uint32_t v[NB];
 #pragma unroll
-        for (int b = 0; b < NB; ++b) v[b] = clamp_vid(ld_stream(a.conn + b * C + c), a.V);
+        for (int b = 0; b < NB; ++b) v[b] = clamp_vid(ld_stream(a.conn + b * C + c), a.V, vmax);
         // Kbar = sum_q w_q K_q in float64, then as a pair: 64 against 67 us on the
         // 1,572,864-tet workload. Forming u_j - u_0 in float64 too, or the elasticity and
         // adjoint coefficient sums in float64, was slower: the float64 pipe is half busy.
@@ -220,6 +223,7 @@ __global__ void __launch_bounds__(kBlock, 5) lap_df_kernel(const __grid_constant
         // adjugate rows n_j and det J
         dfl n[DIM][DIM];
         const dfl det = df_adjugate<DIM>(e, n);
+        bad_det |= det_bad(det.hi) | ids_repeat<NB>(v);
         // h = sum_j (u_j - u_0) n_j
         dfl h[DIM];
         df_combine<DIM>(du, n, h);
@@ -237,6 +241,7 @@ __global__ void __launch_bounds__(kBlock, 5) lap_df_kernel(const __grid_constant
 #pragma unroll
         for (int b = 0; b < NB; ++b) __stcs(a.out + b * C + c, r[b]);
     }
+    report_mesh(a.err, vmax, a.V, bad_det);
 }
 
 // called by fem_integrate_laplacian for FEM_FP64_DF (arguments already validated there)
@@ -252,6 +257,7 @@ fem_status launch_lap_df(int dim, int64_t n_cells, int64_t n_verts, const double
     a.C = n_cells;
     a.V = static_cast<uint32_t>(n_verts);
     a.nq = n_q;
+    if (!(a.err = device_error_word())) return fail(FEM_ERR_CUDA, "device error word unavailable");
     for (int q = 0; q < FEM_MAX_QPTS; ++q) a.wd[q] = q < n_q ? qw[q] : 0.0;
     if (dim == 2) {
         auto k = lap_df_kernel<2>;
@@ -276,6 +282,7 @@ struct DfElArgs {
     int64_t C;
     uint32_t V;
     int nq;
+    unsigned *err;  // device error word (FEM_DEVERR_BADMESH)
     float whi[FEM_MAX_QPTS], wlo[FEM_MAX_QPTS];
 };
 
@@ -287,11 +294,13 @@ __global__ void __launch_bounds__(kBlock) el_df_kernel(const __grid_constant__ D
     const double *X[DIM];
 #pragma unroll
     for (int k = 0; k < DIM; ++k) X[k] = a.X[k];
+    uint32_t vmax = 0;     // largest vertex id seen (bad ids are clamped and reported)
+    bool bad_det = false;  // a cell with det J = 0 or non-finite
     const int64_t stride = int64_t(gridDim.x) * blockDim.x;
     for (int64_t c = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; c < C; c += stride) {
         uint32_t v[NB];
 #pragma unroll
-        for (int b = 0; b < NB; ++b) v[b] = clamp_vid(ld_stream(a.conn + b * C + c), a.V);
+        for (int b = 0; b < NB; ++b) v[b] = clamp_vid(ld_stream(a.conn + b * C + c), a.V, vmax);
         // Lbar = sum_q w_q lambda_q, Mbar = sum_q w_q mu_q
         const dfl lbar = df_weighted(a.whi, a.wlo, a.lam, C, c, a.nq);
         const dfl mbar = df_weighted(a.whi, a.wlo, a.mu, C, c, a.nq);
@@ -305,6 +314,7 @@ __global__ void __launch_bounds__(kBlock) el_df_kernel(const __grid_constant__ D
             for (int k = 0; k < DIM; ++k) e[j][k] = df_from_double(xs[j + 1][k] - xs[0][k]);
         dfl n[DIM][DIM];
         const dfl det = df_adjugate<DIM>(e, n);
+        bad_det |= det_bad(det.hi) | ids_repeat<NB>(v);
         // H[k][i] = sum_j (u_{j,k} - u_{0,k}) n_j[i]
         dfl H[DIM][DIM];
 #pragma unroll
@@ -343,6 +353,7 @@ __global__ void __launch_bounds__(kBlock) el_df_kernel(const __grid_constant__ D
 #pragma unroll
         for (int k = 0; k < DIM; ++k) __stcs(a.out + k * C + c, df_to_double(r0[k]));
     }
+    report_mesh(a.err, vmax, a.V, bad_det);
 }
 
 // called by fem_integrate_elasticity for FEM_FP64_DF (arguments already validated there)
@@ -359,6 +370,7 @@ fem_status launch_el_df(int dim, int64_t n_cells, int64_t n_verts, const double 
     a.C = n_cells;
     a.V = static_cast<uint32_t>(n_verts);
     a.nq = n_q;
+    if (!(a.err = device_error_word())) return fail(FEM_ERR_CUDA, "device error word unavailable");
     for (int q = 0; q < FEM_MAX_QPTS; ++q) {
         const double w = q < n_q ? qw[q] : 0.0;
         a.whi[q] = static_cast<float>(w);
@@ -386,6 +398,7 @@ struct DfAdjArgs {
     int64_t C;
     uint32_t V;
     int nq;
+    unsigned *err;  // device error word (FEM_DEVERR_BADMESH)
     float whi[FEM_MAX_QPTS], wlo[FEM_MAX_QPTS];
 };
 
@@ -396,13 +409,15 @@ __global__ void __launch_bounds__(kBlock) adj_df_kernel(const __grid_constant__ 
     const double *X[DIM];
 #pragma unroll
     for (int k = 0; k < DIM; ++k) X[k] = a.X[k];
+    uint32_t vmax = 0;     // largest vertex id seen (bad ids are clamped and reported)
+    bool bad_det = false;  // a cell with det J = 0 or non-finite
     const int64_t stride = int64_t(gridDim.x) * blockDim.x;
     for (int64_t c = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; c < C; c += stride) {
         uint32_t v[NB];
         dfl uu[NB], ll[NB];
 #pragma unroll
         for (int b = 0; b < NB; ++b) {
-            v[b] = clamp_vid(ld_stream(a.conn + b * C + c), a.V);
+            v[b] = clamp_vid(ld_stream(a.conn + b * C + c), a.V, vmax);
             uu[b] = df_from_double(ld_gather(a.u + v[b]));
             ll[b] = df_from_double(ld_stream(a.lam + b * C + c));
         }
@@ -416,6 +431,7 @@ __global__ void __launch_bounds__(kBlock) adj_df_kernel(const __grid_constant__ 
             for (int k = 0; k < DIM; ++k) e[j][k] = df_from_double(xs[j + 1][k] - xs[0][k]);
         dfl n[DIM][DIM];
         const dfl det = df_adjugate<DIM>(e, n);
+        bad_det |= det_bad(det.hi) | ids_repeat<NB>(v);
         // h_u = sum_j (u_j - u_0) n_j, h_l = sum_j (lambda_j - lambda_0) n_j
         dfl hu[DIM], hl[DIM], du[DIM], dl[DIM];
 #pragma unroll
@@ -437,6 +453,7 @@ __global__ void __launch_bounds__(kBlock) adj_df_kernel(const __grid_constant__ 
         const dfl tf = df_mul(df_dotv<DIM>(hl, hu), inv);
         for (int q = 0; q < a.nq; ++q) __stcs(a.dK + q * C + c, df_to_double(df_mul(dfl{a.whi[q], a.wlo[q]}, tf)));
     }
+    report_mesh(a.err, vmax, a.V, bad_det);
 }
 
 // the element part of fem_adjoint_laplacian for FEM_FP64_DF (arguments validated by the caller)
@@ -454,6 +471,7 @@ fem_status launch_adj_df(int dim, int64_t n_cells, int64_t n_verts, const double
     a.C = n_cells;
     a.V = static_cast<uint32_t>(n_verts);
     a.nq = n_q;
+    if (!(a.err = device_error_word())) return fail(FEM_ERR_CUDA, "device error word unavailable");
     for (int q = 0; q < FEM_MAX_QPTS; ++q) {
         const double w = q < n_q ? qw[q] : 0.0;
         a.whi[q] = static_cast<float>(w);

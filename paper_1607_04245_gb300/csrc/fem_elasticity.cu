@@ -24,6 +24,7 @@ struct ElArgs {
     int64_t C;
     uint32_t V;
     float tau2;
+    unsigned *err;  // device error word (FEM_DEVERR_BADMESH)
     QuadW w;
 };
 
@@ -76,6 +77,41 @@ __device__ __forceinline__ val_t<P> el_weight(const QuadW &w, int q) {
     else return w.wf[q];
 }
 
+// Float64 recomputation of cell c of the mixed form (badly shaped, or a non-finite float32
+// result), stored over the float32 result the caller has already written (same thread,
+// program order). Everything is read again from global memory and the coefficient sums
+// come in as float64: the path is rare and kept out of line, so none of its state takes
+// registers on the common path.
+template <int DIM>
+__device__ __noinline__ void el_fallback_store(const ElArgs &a, int64_t c, double lbar, double mbar) {
+    constexpr int NB = DIM + 1;
+    const int64_t C = a.C;
+    const int64_t V = a.V;
+    const float *u = static_cast<const float *>(a.u);
+    uint32_t v[NB];
+    double u64[NB][DIM];
+#pragma unroll
+    for (int b = 0; b < NB; ++b) {
+        v[b] = clamp_vid(a.conn[b * C + c], a.V);
+#pragma unroll
+        for (int k = 0; k < DIM; ++k) u64[b][k] = u[k * V + v[b]];
+    }
+    const double *X[DIM];
+#pragma unroll
+    for (int k = 0; k < DIM; ++k) X[k] = a.X[k];
+    double xs[NB][DIM], e64[DIM][DIM], n64[DIM][DIM], r64[NB][DIM];
+    gather_coords<DIM>(X, v, xs);
+    columns_f64<DIM>(xs, e64);
+    const double det64 = adjugate_rows<DIM>(e64, n64);
+    if (det_bad(det64) || ids_repeat<NB>(v)) record_device_error(a.err, FEM_DEVERR_BADMESH);
+    el_element<DIM>(n64, det64, u64, lbar, mbar, r64);
+    float *out = static_cast<float *>(a.out);
+#pragma unroll
+    for (int b = 0; b < NB; ++b)
+#pragma unroll
+        for (int k = 0; k < DIM; ++k) out[(b * DIM + k) * C + c] = static_cast<float>(r64[b][k]);
+}
+
 // NQ > 0: quadrature size fixed at compile time, every coefficient row load issued
 // before the first sum; NQ = 0: read from the arguments.
 template <int DIM, int P, int CPT, int NQ>
@@ -92,6 +128,8 @@ __global__ void __launch_bounds__(kBlock) el_kernel(const __grid_constant__ ElAr
     for (int k = 0; k < DIM; ++k) X[k] = a.X[k];
     const int64_t V = a.V;
 
+    uint32_t vmax = 0;     // largest vertex id seen (bad ids are clamped and reported)
+    bool bad_det = false;  // a cell with det J = 0 or non-finite
     const int64_t ngroups = (C + CPT - 1) / CPT;
     const int64_t stride = int64_t(gridDim.x) * blockDim.x;
     for (int64_t g = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; g < ngroups; g += stride) {
@@ -133,47 +171,36 @@ __global__ void __launch_bounds__(kBlock) el_kernel(const __grid_constant__ ElAr
         }
 
         T r[NB * DIM][CPT];
+        bool ok[CPT];
 #pragma unroll
         for (int i = 0; i < CPT; ++i) {
             uint32_t v[NB];
             T uu[NB][DIM];
 #pragma unroll
             for (int b = 0; b < NB; ++b) {
-                v[b] = clamp_vid(vid[b][i], a.V);
+                v[b] = clamp_vid(vid[b][i], a.V, vmax);
 #pragma unroll
                 for (int k = 0; k < DIM; ++k) uu[b][k] = ld_gather(u + k * V + v[b]);
             }
             double xs[NB][DIM];
             gather_coords<DIM>(X, v, xs);
             T rr[NB][DIM];
+            ok[i] = true;
             if constexpr (P == FEM_FP64) {
                 double e[DIM][DIM], n[DIM][DIM];
                 columns_f64<DIM>(xs, e);
                 double det = adjugate_rows<DIM>(e, n);
+                bad_det |= det_bad(det) | ids_repeat<NB>(v);
                 el_element<DIM>(n, det, uu, ls[i].value(), ms[i].value(), rr);
             } else {
                 float e[DIM][DIM], n[DIM][DIM];
                 if constexpr (P == FEM_FP32_MIXED) columns_mixed<DIM>(xs, e);
                 else columns_f32<DIM>(xs, e);
                 float det = adjugate_rows<DIM>(e, n);
-                bool ok = true;
-                if constexpr (P == FEM_FP32_MIXED) ok = shape_ok<DIM>(e, det, a.tau2);
-                if (ok) {
-                    el_element<DIM>(n, det, uu, ls[i].value(), ms[i].value(), rr);
-                } else {
-                    double e64[DIM][DIM], n64[DIM][DIM], u64[NB][DIM], r64[NB][DIM];
-                    columns_f64<DIM>(xs, e64);
-                    double det64 = adjugate_rows<DIM>(e64, n64);
-#pragma unroll
-                    for (int b = 0; b < NB; ++b)
-#pragma unroll
-                        for (int k = 0; k < DIM; ++k) u64[b][k] = uu[b][k];
-                    el_element<DIM>(n64, det64, u64, ls[i].value_f64(), ms[i].value_f64(), r64);
-#pragma unroll
-                    for (int b = 0; b < NB; ++b)
-#pragma unroll
-                        for (int k = 0; k < DIM; ++k) rr[b][k] = static_cast<float>(r64[b][k]);
-                }
+                if constexpr (P == FEM_FP32_MIXED) ok[i] = shape_ok<DIM>(e, det, a.tau2);
+                else bad_det |= det_bad(det) | ids_repeat<NB>(v);
+                // a failing cell's float32 result is meaningless here; it is recomputed below
+                el_element<DIM>(n, det, uu, ls[i].value(), ms[i].value(), rr);
             }
 #pragma unroll
             for (int b = 0; b < NB; ++b)
@@ -182,7 +209,13 @@ __global__ void __launch_bounds__(kBlock) el_kernel(const __grid_constant__ ElAr
         }
 #pragma unroll
         for (int row = 0; row < NB * DIM; ++row) store_row<CPT>(out + row * C + c0, r[row]);
+        if constexpr (P == FEM_FP32_MIXED) {
+#pragma unroll
+            for (int i = 0; i < CPT; ++i)
+                if (!ok[i]) el_fallback_store<DIM>(a, c0 + i, ls[i].value_f64(), ms[i].value_f64());
+        }
     }
+    report_mesh(a.err, vmax, a.V, bad_det);
 }
 
 template <int DIM, int P>
@@ -236,6 +269,7 @@ extern "C" fem_status fem_integrate_elasticity(int dim, int64_t n_cells, int64_t
     a.V = static_cast<uint32_t>(n_verts);
     const float tau = mixed_tau();
     a.tau2 = tau * tau;
+    if (!(a.err = device_error_word())) return fail(FEM_ERR_CUDA, "device error word unavailable");
     const bool vec = n_cells % 4 == 0 && aligned16(conn) && aligned16(lam) && aligned16(mu) && aligned16(elem_out);
     const int key = dim * 10 + static_cast<int>(prec);
     switch (key) {

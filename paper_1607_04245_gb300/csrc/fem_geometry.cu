@@ -21,6 +21,7 @@ struct GeomArgs {
     void *geom;  // [dim*dim + 1][C]: invJ rows then det J
     int64_t C;
     uint32_t V;
+    unsigned *err;  // device error word (FEM_DEVERR_BADMESH)
 };
 
 // geometry of CPT consecutive cells per thread, computed in float64 and stored in the
@@ -34,15 +35,18 @@ __global__ void __launch_bounds__(kBlock) geometry_kernel(const __grid_constant_
     const double *X[DIM];
 #pragma unroll
     for (int k = 0; k < DIM; ++k) X[k] = a.X[k];
+    uint32_t vmax = 0;
+    bool bad_det = false;
     const int64_t stride = int64_t(gridDim.x) * blockDim.x;
     for (int64_t c = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; c < C; c += stride) {
         uint32_t v[NB];
 #pragma unroll
-        for (int b = 0; b < NB; ++b) v[b] = clamp_vid(a.conn[b * C + c], a.V);
+        for (int b = 0; b < NB; ++b) v[b] = clamp_vid(a.conn[b * C + c], a.V, vmax);
         double xs[NB][DIM], e[DIM][DIM], n[DIM][DIM];
         gather_coords<DIM>(X, v, xs);
         columns_f64<DIM>(xs, e);
         const double det = adjugate_rows<DIM>(e, n);
+        bad_det |= det_bad(det) | ids_repeat<NB>(v);
         const double rdet = 1.0 / det;
         // (J^{-1})_{ji} = n_j[i] / det J  (row j of J^{-1} is n_j / det J)
 #pragma unroll
@@ -51,6 +55,7 @@ __global__ void __launch_bounds__(kBlock) geometry_kernel(const __grid_constant_
             for (int i = 0; i < DIM; ++i) geom[(j * DIM + i) * C + c] = static_cast<T>(n[j][i] * rdet);
         geom[(DIM * DIM) * C + c] = static_cast<T>(det);
     }
+    report_mesh(a.err, vmax, a.V, bad_det);
 }
 
 struct LapGeomArgs {
@@ -61,6 +66,7 @@ struct LapGeomArgs {
     void *out;
     int64_t C;
     uint32_t V;
+    unsigned *err;  // device error word (FEM_DEVERR_BADMESH)
     QuadW w;
 };
 
@@ -82,6 +88,8 @@ __global__ void __launch_bounds__(kBlock) lap_geom_kernel(const __grid_constant_
     const T *__restrict__ geom = static_cast<const T *>(a.geom);
     T *__restrict__ out = static_cast<T *>(a.out);
     const int nq = NQ > 0 ? NQ : a.w.nq;
+    uint32_t vmax = 0;
+    bool bad_det = false;
     const int64_t ngroups = (C + CPT - 1) / CPT;
     const int64_t stride = int64_t(gridDim.x) * blockDim.x;
     for (int64_t g = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; g < ngroups; g += stride) {
@@ -108,7 +116,7 @@ __global__ void __launch_bounds__(kBlock) lap_geom_kernel(const __grid_constant_
         for (int i = 0; i < CPT; ++i) {
             T uu[NB];
 #pragma unroll
-            for (int b = 0; b < NB; ++b) uu[b] = ld_gather(u + clamp_vid(vid[b][i], a.V));
+            for (int b = 0; b < NB; ++b) uu[b] = ld_gather(u + clamp_vid(vid[b][i], a.V, vmax));
             // g = sum_{j>=1} (u_j - u_0) G_j, G_j = row j of J^{-1}
             T gv[DIM];
 #pragma unroll
@@ -120,6 +128,7 @@ __global__ void __launch_bounds__(kBlock) lap_geom_kernel(const __grid_constant_
                 for (int k = 0; k < DIM; ++k) gv[k] = fma(du, gm[j * DIM + k][i], gv[k]);
             }
             T det = gm[DIM * DIM][i];
+            bad_det |= det_bad(det);
             det = det < T(0) ? -det : det;
             const T s = ks[i].value() * det;
             T sum = zero<T>();
@@ -136,6 +145,7 @@ __global__ void __launch_bounds__(kBlock) lap_geom_kernel(const __grid_constant_
 #pragma unroll
         for (int b = 0; b < NB; ++b) store_row<CPT>(out + b * C + c0, r[b]);
     }
+    report_mesh(a.err, vmax, a.V, bad_det);
 }
 
 template <int DIM, int P>
@@ -172,6 +182,7 @@ extern "C" fem_status fem_precompute_geometry(int dim, int64_t n_cells, int64_t 
     a.geom = geom;
     a.C = n_cells;
     a.V = static_cast<uint32_t>(n_verts);
+    if (!(a.err = device_error_word())) return fail(FEM_ERR_CUDA, "device error word unavailable");
     const bool f64 = prec == FEM_FP64;
     if (dim == 2) {
         auto k = f64 ? geometry_kernel<2, FEM_FP64> : geometry_kernel<2, FEM_FP32>;
@@ -206,6 +217,7 @@ extern "C" fem_status fem_integrate_laplacian_geom(int dim, int64_t n_cells, int
     a.out = elem_out;
     a.C = n_cells;
     a.V = static_cast<uint32_t>(n_verts);
+    if (!(a.err = device_error_word())) return fail(FEM_ERR_CUDA, "device error word unavailable");
     const bool vec = n_cells % 4 == 0 && aligned16(conn) && aligned16(K) && aligned16(geom) && aligned16(elem_out);
     // the float32 forms both integrate from float32 geometry (there are no coordinates
     // to fall back on): FEM_FP32_MIXED differs from FEM_FP32 only in its compensated sum

@@ -37,14 +37,69 @@ int sm_count();  // multiprocessors of the current device (cached)
 float mixed_tau();
 
 inline bool aligned16(const void *p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; }
+inline bool aligned8(const void *p) { return (reinterpret_cast<uintptr_t>(p) & 7u) == 0; }
 
 constexpr int kBlock = 256;
 
 // ------------------------------------------------------------------ device helpers
 
+// ------------------------------------------------------------------ device error word
+//
+// One word per device (fem_core.cu) collects error bits from the kernels; launchers pass
+// its device address (device_error_word()) as a kernel argument, and fem_device_error()
+// reads and clears it. FEM_DEVERR_TIMEOUT: a staged kernel gave up a bounded wait.
+// FEM_DEVERR_BADMESH: a kernel met a vertex id outside [0, V) (it was clamped, the
+// result is meaningless) or a cell with det J = 0 or a non-finite det J.
+enum : unsigned { FEM_DEVERR_TIMEOUT = 1u, FEM_DEVERR_BADMESH = 2u };
+unsigned *device_error_word();
+// Kernels launched by the calling host thread report into `w` instead (per-request error
+// words of the serving launch); nullptr restores the device-wide word.
+void set_error_word_override(unsigned *w);
+
+__device__ __forceinline__ void record_device_error(unsigned *err, unsigned bits) {
+    // the read first: after the first report, further threads find the bit set and skip
+    // the atomic (a badly broken mesh would otherwise send one atomic per cell)
+    if ((*reinterpret_cast<volatile unsigned *>(err) & bits) != bits) atomicOr(err, bits);
+}
+
 // Clamp a vertex id into [0, n): malformed input cannot read out of bounds.
 __device__ __forceinline__ uint32_t clamp_vid(int32_t v, uint32_t n) {
     return min(static_cast<uint32_t>(v), n - 1u);
+}
+
+// The same, also folding the id (as unsigned: a negative id counts as too large) into the
+// running maximum vmax of the calling thread; vmax >= n at the end means a bad id.
+__device__ __forceinline__ uint32_t clamp_vid(int32_t v, uint32_t n, uint32_t &vmax) {
+    vmax = max(vmax, static_cast<uint32_t>(v));
+    return min(static_cast<uint32_t>(v), n - 1u);
+}
+
+// det J = 0 or not finite (checked on the bits: integer operations only)
+__device__ __forceinline__ bool det_bad(double d) {
+    const uint32_t hi = static_cast<uint32_t>(__double2hiint(d)) & 0x7fffffffu;
+    const uint32_t lo = static_cast<uint32_t>(__double2loint(d));
+    return (hi | lo) == 0u || hi >= 0x7ff00000u;
+}
+__device__ __forceinline__ bool det_bad(float d) {
+    const uint32_t b = __float_as_uint(d) & 0x7fffffffu;
+    return b == 0u || b >= 0x7f800000u;
+}
+
+// A cell whose vertex ids repeat (its det J vanishes in exact arithmetic; computed with FMA
+// contraction it may come out as a rounding residue instead of an exact zero)
+template <int NB>
+__device__ __forceinline__ bool ids_repeat(const uint32_t (&v)[NB]) {
+    bool r = false;
+#pragma unroll
+    for (int i = 0; i < NB; ++i)
+#pragma unroll
+        for (int j = i + 1; j < NB; ++j) r |= v[i] == v[j];
+    return r;
+}
+
+// End of a thread's cells: report a bad id (vmax >= n) or a degenerate cell.
+__device__ __forceinline__ void report_mesh(unsigned *err, uint32_t vmax, uint32_t n, bool bad_det) {
+    if ((vmax >= n || bad_det) && err) record_device_error(err, FEM_DEVERR_BADMESH);
 }
 
 // Split a float64 value, given as its two 32-bit words, into float32 hi + lo with
@@ -103,6 +158,9 @@ __device__ __forceinline__ T ld_gather(const T *p) { return __ldg(p); }
 // Grid size: enough CTAs to cover the work, capped at a whole number of waves of the
 // device's SMs (the kernels are grid-stride loops).
 int grid_for(int64_t n_threads, int block, const void *kernel);
+// One wave: as many CTAs as are resident on the device at once, at most one per `block`
+// threads of work (for grid-stride kernels whose CTAs stay until the work runs out).
+int resident_grid(const void *kernel, int block, int64_t n_threads);
 fem_status staged_grid(const void *kernel, int block, size_t smem, int64_t n_tiles, int &grid);
 
 }  // namespace fem

@@ -30,6 +30,7 @@ struct LapArgs {
     int64_t C;
     uint32_t V;
     float tau2;
+    unsigned *err;  // device error word (FEM_DEVERR_BADMESH)
     QuadW w;
 };
 
@@ -102,16 +103,20 @@ __device__ __forceinline__ val_t<P> weight(const QuadW &w, int q) {
 
 // One cell: vertex coordinates xs, nodal values uu (adjoint: ll = lambda_e), the
 // quadrature sum of the coefficient ks; writes the element vector rr and (adjoint) the
-// dK factor tf.
+// dK factor tf. bad_det collects the mesh check: det J = 0 or non-finite, or (rep) vertex
+// ids that repeat; the mixed form checks only the cells its shape test sends to float64
+// (every degenerate cell fails that test for tau > 0).
 template <int DIM, int P, bool ADJ>
 __device__ __forceinline__ void lap_cell(const double (&xs)[DIM + 1][DIM],
                                          const val_t<P> (&uu)[DIM + 1], const val_t<P> (&ll)[DIM + 1],
-                                         const qsum_t<P> &ks, float tau2, val_t<P> (&rr)[DIM + 1], val_t<P> &tf) {
+                                         const qsum_t<P> &ks, float tau2, val_t<P> (&rr)[DIM + 1], val_t<P> &tf,
+                                         bool rep, bool &bad_det) {
     constexpr int NB = DIM + 1;
     if constexpr (P == FEM_FP64) {
         double e[DIM][DIM], n[DIM][DIM];
         columns_f64<DIM>(xs, e);
         double det = adjugate_rows<DIM>(e, n);
+        bad_det |= det_bad(det) | rep;
         if constexpr (ADJ) {
             lap_adj_element<DIM>(n, det, uu, ll, ks.value(), rr, tf);
         } else {
@@ -124,6 +129,7 @@ __device__ __forceinline__ void lap_cell(const double (&xs)[DIM + 1][DIM],
         float det = adjugate_rows<DIM>(e, n);
         bool ok = true;
         if constexpr (P == FEM_FP32_MIXED) ok = shape_ok<DIM>(e, det, tau2);
+        else bad_det |= det_bad(det) | rep;
         if (ok) {
             if constexpr (ADJ) {
                 lap_adj_element<DIM>(n, det, uu, ll, ks.value(), rr, tf);
@@ -135,6 +141,7 @@ __device__ __forceinline__ void lap_cell(const double (&xs)[DIM + 1][DIM],
             double e64[DIM][DIM], n64[DIM][DIM], u64[NB], r64[NB];
             columns_f64<DIM>(xs, e64);
             double det64 = adjugate_rows<DIM>(e64, n64);
+            bad_det |= det_bad(det64) | rep;
             const double kb64 = ks.value_f64();
 #pragma unroll
             for (int b = 0; b < NB; ++b) u64[b] = uu[b];
@@ -169,6 +176,8 @@ __global__ void __launch_bounds__(kBlock) lap_kernel(const __grid_constant__ Lap
 #pragma unroll
     for (int k = 0; k < DIM; ++k) X[k] = a.X[k];
 
+    uint32_t vmax = 0;     // largest vertex id seen (bad ids are clamped and reported)
+    bool bad_det = false;  // a cell with det J = 0 or non-finite
     const int64_t ngroups = (C + CPT - 1) / CPT;
     const int64_t stride = int64_t(gridDim.x) * blockDim.x;
     for (int64_t g = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; g < ngroups; g += stride) {
@@ -220,7 +229,7 @@ __global__ void __launch_bounds__(kBlock) lap_kernel(const __grid_constant__ Lap
             T uu[NB], ll[NB];
 #pragma unroll
             for (int b = 0; b < NB; ++b) {
-                v[b] = clamp_vid(vid[b][i], a.V);
+                v[b] = clamp_vid(vid[b][i], a.V, vmax);
                 uu[b] = ld_gather(u + v[b]);
                 ll[b] = ADJ ? lamv[ADJ ? b : 0][i] : T(0);
             }
@@ -228,7 +237,7 @@ __global__ void __launch_bounds__(kBlock) lap_kernel(const __grid_constant__ Lap
             gather_coords<DIM>(X, v, xs);
             T rr[NB];
             T tf = T(0);
-            lap_cell<DIM, P, ADJ>(xs, uu, ll, ks[i], a.tau2, rr, tf);
+            lap_cell<DIM, P, ADJ>(xs, uu, ll, ks[i], a.tau2, rr, tf, ids_repeat<NB>(v), bad_det);
 #pragma unroll
             for (int b = 0; b < NB; ++b) r[b][i] = rr[b];
             tfac[i] = tf;
@@ -246,6 +255,7 @@ __global__ void __launch_bounds__(kBlock) lap_kernel(const __grid_constant__ Lap
             }
         }
     }
+    report_mesh(a.err, vmax, a.V, bad_det);
 }
 
 // ------------------------------------------------------------------ several fields
@@ -275,7 +285,9 @@ __device__ __noinline__ void lap_fields_fallback(const FieldsArgs &fa, int64_t c
     double xs[NB][DIM], e64[DIM][DIM], n64[DIM][DIM];
     gather_coords<DIM>(X, v, xs);
     columns_f64<DIM>(xs, e64);
-    const double s = quot_abs(kbar, adjugate_rows<DIM>(e64, n64));
+    const double det64 = adjugate_rows<DIM>(e64, n64);
+    if (det_bad(det64) || ids_repeat<NB>(v)) record_device_error(a.err, FEM_DEVERR_BADMESH);
+    const double s = quot_abs(kbar, det64);
     const float *u = static_cast<const float *>(a.u);
     float *out = static_cast<float *>(a.out);
     for (int f = 0; f < fa.nf; ++f) {
@@ -302,6 +314,8 @@ __global__ void __launch_bounds__(kBlock) lap_fields_kernel(const __grid_constan
 #pragma unroll
     for (int k = 0; k < DIM; ++k) X[k] = a.X[k];
     const int nq = NQ > 0 ? NQ : a.w.nq;
+    uint32_t vmax = 0;
+    bool bad_det = false;
     const int64_t ngroups = (C + CPT - 1) / CPT;
     const int64_t stride = int64_t(gridDim.x) * blockDim.x;
     for (int64_t g = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; g < ngroups; g += stride) {
@@ -330,7 +344,7 @@ __global__ void __launch_bounds__(kBlock) lap_fields_kernel(const __grid_constan
 #pragma unroll
         for (int i = 0; i < CPT; ++i) {
 #pragma unroll
-            for (int b = 0; b < NB; ++b) v[i][b] = clamp_vid(vid[b][i], a.V);
+            for (int b = 0; b < NB; ++b) v[i][b] = clamp_vid(vid[b][i], a.V, vmax);
             double xs[NB][DIM];
             gather_coords<DIM>(X, v[i], xs);
             T e[DIM][DIM];
@@ -341,6 +355,7 @@ __global__ void __launch_bounds__(kBlock) lap_fields_kernel(const __grid_constan
             s[i] = quot_abs(ks[i].value(), det);
             ok[i] = true;
             if constexpr (P == FEM_FP32_MIXED) ok[i] = shape_ok<DIM>(e, det, a.tau2);
+            else bad_det |= det_bad(det) | ids_repeat<NB>(v[i]);
         }
         for (int f = 0; f < fa.nf; ++f) {
             const T *uf = u + int64_t(f) * V;
@@ -363,6 +378,7 @@ __global__ void __launch_bounds__(kBlock) lap_fields_kernel(const __grid_constan
                 if (!ok[i]) lap_fields_fallback<DIM>(fa, c0 + i, ks[i].value_f64());
         }
     }
+    report_mesh(a.err, vmax, a.V, bad_det);
 }
 
 template <int DIM, int P>
@@ -387,11 +403,12 @@ static fem_status launch_fields(const FieldsArgs &fa, bool vec, cudaStream_t s) 
 template <int DIM, bool ADJ>
 __device__ __forceinline__ void lap_cell_f64(const double (&xs)[DIM + 1][DIM], const float (&uf)[DIM + 1],
                                              const float (&lf)[DIM + 1], double kbar, double (&r)[DIM + 1],
-                                             double &tf) {
+                                             double &tf, unsigned *err) {
     constexpr int NB = DIM + 1;
     double e[DIM][DIM], n[DIM][DIM], u64[NB], l64[NB];
     columns_f64<DIM>(xs, e);
     const double det = adjugate_rows<DIM>(e, n);
+    if (det_bad(det)) record_device_error(err, FEM_DEVERR_BADMESH);
 #pragma unroll
     for (int b = 0; b < NB; ++b) u64[b] = uf[b], l64[b] = lf[b];
     if constexpr (ADJ) {
@@ -426,7 +443,8 @@ __device__ __noinline__ void lap_fallback_store(const LapArgs &a, int64_t c, dou
     for (int k = 0; k < DIM; ++k) X[k] = a.X[k];
     double xs[NB][DIM], r64[NB], t64;
     gather_coords<DIM>(X, v, xs);
-    lap_cell_f64<DIM, ADJ>(xs, uf, lf, kbar, r64, t64);
+    if (ids_repeat<NB>(v)) record_device_error(a.err, FEM_DEVERR_BADMESH);
+    lap_cell_f64<DIM, ADJ>(xs, uf, lf, kbar, r64, t64, a.err);
     float *out = static_cast<float *>(a.out);
 #pragma unroll
     for (int b = 0; b < NB; ++b) out[b * C + c] = static_cast<float>(r64[b]);
@@ -439,7 +457,8 @@ __device__ __noinline__ void lap_fallback_store(const LapArgs &a, int64_t c, dou
 // Two cells of a float32 form at once (lane x: cell a, lane y: cell b), vertex ids va,
 // vb. The coordinates are gathered here and are dead once split into float32. In the
 // mixed form, oka / okb report whether each cell passed the shape test; a failing cell's
-// result here is meaningless and the caller recomputes it (lap_fallback_store).
+// result here is meaningless and the caller recomputes it (lap_fallback_store). In the
+// float32 ablation they report whether det J is nonzero and finite (the mesh check).
 template <int DIM, int P, bool ADJ>
 __device__ __forceinline__ void lap_pair(const double *const (&X)[DIM], const uint32_t (&va)[DIM + 1],
                                          const uint32_t (&vb)[DIM + 1], const f2 (&uu)[DIM + 1],
@@ -459,8 +478,103 @@ __device__ __forceinline__ void lap_pair(const double *const (&X)[DIM], const ui
     } else {
         lap_element<DIM>(n, det, uu, ks.value(), rr);
     }
-    oka = okb = true;
-    if constexpr (P == FEM_FP32_MIXED) shape_ok2<DIM>(e, det, tau2, oka, okb);
+    if constexpr (P == FEM_FP32_MIXED) {
+        shape_ok2<DIM>(e, det, tau2, oka, okb);
+    } else {
+        oka = !det_bad(f2_x(det));
+        okb = !det_bad(f2_y(det));
+    }
+}
+
+// ------------------------------------------------------------------ pair kernel
+//
+// The float32 forms' kernel for rows that are 8-byte aligned (an even cell count): each
+// thread owns two consecutive cells at a time and computes them as f32x2 pairs
+// (lap_pair), reading every cell-indexed row with 8-byte loads and writing 8-byte
+// streaming stores, grid-stride over the cell pairs with one wave of resident CTAs (4 of
+// 256 threads per SM at 64 registers for the residual). A badly shaped cell of the mixed form is
+// recomputed in float64 out of line (lap_fallback_store) after its pair's stores.
+//
+// Measured on the 1,572,864-tet workload (L2 flushed, CUDA events): 25.9 us against
+// 27.8 us for the bulk-copy staged kernel with the same per-cell arithmetic (bitwise the
+// same results): the staged kernel's pipeline fill costs more than its prefetching saves
+// at this size; at 2^23 cells the two are within 1 %. Both are bound by the latency of
+// the 16 vertex gathers per cell and by the integer float64 -> float32 splits (ALU pipe
+// half busy), not by DRAM (30 % of peak over the launch).
+// (the adjoint's element part holds lambda and h_lambda too: 3 CTAs, 80 registers, no spills)
+template <bool ADJ>
+constexpr int pair_min_blocks() { return ADJ ? 3 : 4; }
+
+template <int DIM, int P, int NQ, bool ADJ>
+__global__ void __launch_bounds__(kBlock, pair_min_blocks<ADJ>()) lap_pair_kernel(const __grid_constant__ LapArgs a) {
+    static_assert(P != FEM_FP64, "float32 forms only");
+    constexpr int NB = DIM + 1;
+    const int64_t C = a.C;  // even
+    const float *__restrict__ u = static_cast<const float *>(a.u);
+    const float *__restrict__ K = static_cast<const float *>(a.K);
+    const float *__restrict__ L = static_cast<const float *>(a.lam);
+    float *__restrict__ out = static_cast<float *>(a.out);
+    float *__restrict__ dK = static_cast<float *>(a.dK);
+    const double *X[DIM];
+#pragma unroll
+    for (int k = 0; k < DIM; ++k) X[k] = a.X[k];
+    const int nq = NQ > 0 ? NQ : a.w.nq;
+    uint32_t vmax = 0;     // largest vertex id seen (bad ids are clamped and reported)
+    bool bad_det = false;  // float32 ablation: a cell with det J = 0 or non-finite, or repeated ids
+    const int64_t np = C / 2;
+    const int64_t stride = int64_t(gridDim.x) * blockDim.x;
+    for (int64_t g = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; g < np; g += stride) {
+        const int64_t c = 2 * g;
+        uint32_t va[NB], vb[NB];
+#pragma unroll
+        for (int b = 0; b < NB; ++b) {
+            const int2 t = __ldcs(reinterpret_cast<const int2 *>(a.conn + b * C + c));
+            va[b] = clamp_vid(t.x, a.V, vmax);
+            vb[b] = clamp_vid(t.y, a.V, vmax);
+        }
+        qsum2_t<P> ks;
+#pragma unroll(NQ > 0 ? NQ : 1)
+        for (int q = 0; q < nq; ++q) {
+            const float2 k = __ldcs(reinterpret_cast<const float2 *>(K + q * C + c));
+            if (q == 0) ks.first(a.w.wf[0], f2_make(k.x, k.y));
+            else ks.add(a.w.wf[q], f2_make(k.x, k.y));
+        }
+        f2 uu[NB], ll[NB], rr[NB], tf = zero<f2>();
+#pragma unroll
+        for (int b = 0; b < NB; ++b) {
+            uu[b] = f2_make(ld_gather(u + va[b]), ld_gather(u + vb[b]));
+            if constexpr (ADJ) {
+                const float2 l = __ldcs(reinterpret_cast<const float2 *>(L + b * C + c));
+                ll[b] = f2_make(l.x, l.y);
+            } else {
+                ll[b] = zero<f2>();
+            }
+        }
+        bool oka, okb;
+        lap_pair<DIM, P, ADJ>(X, va, vb, uu, ll, ks, a.tau2, rr, tf, oka, okb);
+#pragma unroll
+        for (int b = 0; b < NB; ++b)
+            __stcs(reinterpret_cast<float2 *>(out + b * C + c), make_float2(f2_x(rr[b]), f2_y(rr[b])));
+        if constexpr (ADJ) {
+            for (int q = 0; q < nq; ++q) {
+                const float wq = a.w.wf[q];
+                __stcs(reinterpret_cast<float2 *>(dK + q * C + c), make_float2(wq * f2_x(tf), wq * f2_y(tf)));
+            }
+        }
+        if constexpr (P == FEM_FP32_MIXED) {
+            if (!oka) lap_fallback_store<DIM, ADJ>(a, c, ks.value_f64_x());
+            if (!okb) lap_fallback_store<DIM, ADJ>(a, c + 1, ks.value_f64_y());
+        } else {
+            bad_det |= !oka | !okb | ids_repeat<NB>(va) | ids_repeat<NB>(vb);
+        }
+    }
+    report_mesh(a.err, vmax, a.V, bad_det);
+}
+
+template <int DIM, int P, int NQ, bool ADJ>
+static void launch_pair(const LapArgs &a, cudaStream_t s) {
+    auto k = lap_pair_kernel<DIM, P, NQ, ADJ>;
+    k<<<resident_grid(reinterpret_cast<const void *>(k), kBlock, a.C / 2), kBlock, 0, s>>>(a);
 }
 
 // Staged Laplacian kernel (the chunk loop of fem_pipe.cuh): each consumer thread owns kCPT
@@ -500,7 +614,7 @@ __device__ __forceinline__ void store_cells(const LapArgs &a, int nq, int64_t c,
 template <int DIM, int P, int NQ, bool ADJ>
 __device__ __forceinline__ void lap_chunk(const LapArgs &a, const double *const (&X)[DIM], int nq,
                                           const int32_t *sc, const val_t<P> *sK, const val_t<P> *sL, int j0,
-                                          int64_t c0) {
+                                          int64_t c0, uint32_t &vmax, bool &bad_det) {
     constexpr int NB = DIM + 1;
     using T = val_t<P>;
     const T *__restrict__ u = static_cast<const T *>(a.u);
@@ -510,7 +624,7 @@ __device__ __forceinline__ void lap_chunk(const LapArgs &a, const double *const 
         int32_t id[kCPT];
         lds_row<kCPT>(sc + b * kTile + j0, id);
 #pragma unroll
-        for (int c = 0; c < kCPT; ++c) v[c][b] = clamp_vid(id[c], a.V);
+        for (int c = 0; c < kCPT; ++c) v[c][b] = clamp_vid(id[c], a.V, vmax);
     }
     T lv[kCPT][NB];
     if constexpr (ADJ) {
@@ -545,7 +659,7 @@ __device__ __forceinline__ void lap_chunk(const LapArgs &a, const double *const 
                 ll[b] = ADJ ? lv[c][b] : T(0);
             }
             gather_coords<DIM>(X, v[c], xs);
-            lap_cell<DIM, P, ADJ>(xs, uu, ll, ks[c], a.tau2, rr, tf);
+            lap_cell<DIM, P, ADJ>(xs, uu, ll, ks[c], a.tau2, rr, tf, ids_repeat<NB>(v[c]), bad_det);
 #pragma unroll
             for (int b = 0; b < NB; ++b) r[b][c] = rr[b];
             tfv[c] = tf;
@@ -576,6 +690,8 @@ __device__ __forceinline__ void lap_chunk(const LapArgs &a, const double *const 
             }
             lap_pair<DIM, P, ADJ>(X, v[2 * p], v[2 * p + 1], uu, ll, ks[p], a.tau2, rr, tf, ok[2 * p],
                                   ok[2 * p + 1]);
+            if constexpr (P == FEM_FP32)
+                bad_det |= !ok[2 * p] | !ok[2 * p + 1] | ids_repeat<NB>(v[2 * p]) | ids_repeat<NB>(v[2 * p + 1]);
 #pragma unroll
             for (int b = 0; b < NB; ++b) r[b][2 * p] = f2_x(rr[b]), r[b][2 * p + 1] = f2_y(rr[b]);
             tfv[2 * p] = f2_x(tf), tfv[2 * p + 1] = f2_y(tf);
@@ -610,6 +726,8 @@ __global__ void __launch_bounds__(kStagedThreads, FEM_STAGED_MIN_CTAS)
 #pragma unroll
     for (int k = 0; k < DIM; ++k) X[k] = a.X[k];
     const uint64_t pol = l2_evict_first_policy();
+    uint32_t vmax = 0;     // largest vertex id seen by this consumer thread
+    bool bad_det = false;  // a cell with det J = 0 or non-finite (float64 form)
     staged_chunks(
         C, stages, err,
         [&](int s, int64_t c0, uint32_t n, uint64_t *bar) {
@@ -625,8 +743,9 @@ __global__ void __launch_bounds__(kStagedThreads, FEM_STAGED_MIN_CTAS)
             }
         },
         [&](int s, int64_t c0, int j0) {
-            lap_chunk<DIM, P, NQ, ADJ>(a, X, nq, stage_conn(s), stage_K(s), stage_lam(s), j0, c0);
+            lap_chunk<DIM, P, NQ, ADJ>(a, X, nq, stage_conn(s), stage_K(s), stage_lam(s), j0, c0, vmax, bad_det);
         });
+    report_mesh(err, vmax, a.V, bad_det);
 }
 
 template <int DIM, int P, int NQ, bool ADJ>
@@ -644,7 +763,7 @@ static fem_status launch_staged(const LapArgs &a, uint32_t sb, cudaStream_t s) {
 }
 
 template <int DIM, int P, bool ADJ>
-static fem_status launch_lap(const LapArgs &a, bool vec, cudaStream_t s, bool staged_ok = true) {
+static fem_status launch_lap(const LapArgs &a, bool vec, bool pairs, cudaStream_t s, bool staged_ok = true) {
     using T = val_t<P>;
     const uint32_t sb = lap_stage_bytes<T>(DIM + 1, a.w.nq, ADJ);
     fem_status st = FEM_OK;
@@ -661,6 +780,14 @@ static fem_status launch_lap(const LapArgs &a, bool vec, cudaStream_t s, bool st
             const unsigned grid = static_cast<unsigned>((a.C + block - 1) / block);
             if (native_nq) lap_kernel<DIM, P, 1, DIM + 1, ADJ><<<grid, block, 0, s>>>(a);
             else lap_kernel<DIM, P, 1, 0, ADJ><<<grid, block, 0, s>>>(a);
+            return check_launch(ADJ ? "fem_adjoint_laplacian" : "fem_integrate_laplacian");
+        }
+    }
+    if constexpr (P != FEM_FP64) {
+        // float32 forms: the pair kernel (the bulk-copy staged kernel is kept for float64)
+        if (staged_ok && pairs) {
+            if (native_nq) launch_pair<DIM, P, DIM + 1, ADJ>(a, s);
+            else launch_pair<DIM, P, 0, ADJ>(a, s);
             return check_launch(ADJ ? "fem_adjoint_laplacian" : "fem_integrate_laplacian");
         }
     }
@@ -688,20 +815,25 @@ static fem_status launch_lap(const LapArgs &a, bool vec, cudaStream_t s, bool st
     return check_launch(ADJ ? "fem_adjoint_laplacian" : "fem_integrate_laplacian");
 }
 
+// vec: every cell-indexed row 16-byte aligned (C % 4 == 0); the pair kernel needs 8 bytes
 template <bool ADJ>
-static fem_status dispatch_lap(int dim, fem_precision prec, const LapArgs &a, bool vec, cudaStream_t s,
+static fem_status dispatch_lap(int dim, fem_precision prec, const LapArgs &args, bool vec, cudaStream_t s,
                                bool staged_ok = true) {
+    LapArgs a = args;
+    if (!(a.err = device_error_word())) return fail(FEM_ERR_CUDA, "device error word unavailable");
+    const bool pairs = a.C % 2 == 0 && aligned8(a.conn) && aligned8(a.K) && aligned8(a.out) &&
+                       (!ADJ || (aligned8(a.lam) && aligned8(a.dK)));
     if (dim == 2) {
         switch (prec) {
-            case FEM_FP64: return launch_lap<2, FEM_FP64, ADJ>(a, vec, s, staged_ok);
-            case FEM_FP32_MIXED: return launch_lap<2, FEM_FP32_MIXED, ADJ>(a, vec, s, staged_ok);
-            case FEM_FP32: return launch_lap<2, FEM_FP32, ADJ>(a, vec, s, staged_ok);
+            case FEM_FP64: return launch_lap<2, FEM_FP64, ADJ>(a, vec, pairs, s, staged_ok);
+            case FEM_FP32_MIXED: return launch_lap<2, FEM_FP32_MIXED, ADJ>(a, vec, pairs, s, staged_ok);
+            case FEM_FP32: return launch_lap<2, FEM_FP32, ADJ>(a, vec, pairs, s, staged_ok);
         }
     } else {
         switch (prec) {
-            case FEM_FP64: return launch_lap<3, FEM_FP64, ADJ>(a, vec, s, staged_ok);
-            case FEM_FP32_MIXED: return launch_lap<3, FEM_FP32_MIXED, ADJ>(a, vec, s, staged_ok);
-            case FEM_FP32: return launch_lap<3, FEM_FP32, ADJ>(a, vec, s, staged_ok);
+            case FEM_FP64: return launch_lap<3, FEM_FP64, ADJ>(a, vec, pairs, s, staged_ok);
+            case FEM_FP32_MIXED: return launch_lap<3, FEM_FP32_MIXED, ADJ>(a, vec, pairs, s, staged_ok);
+            case FEM_FP32: return launch_lap<3, FEM_FP32, ADJ>(a, vec, pairs, s, staged_ok);
         }
     }
     return fail(FEM_ERR_ARG, "unknown precision %d", static_cast<int>(prec));
@@ -726,6 +858,7 @@ static fem_status fill_args(LapArgs &a, int dim, int64_t n_cells, int64_t n_vert
     a.V = static_cast<uint32_t>(n_verts);
     float tau = mixed_tau();
     a.tau2 = tau * tau;
+    a.err = nullptr;  // set by dispatch_lap, once there is something to launch
     return FEM_OK;
 }
 
@@ -776,6 +909,7 @@ extern "C" fem_status fem_integrate_laplacian_fields(int dim, int64_t n_cells, i
     if (!u || !K || !elem_out) return fail(FEM_ERR_ARG, "u, K or elem_out is NULL");
     fa.a.out = elem_out;
     fa.nf = n_fields;
+    if (!(fa.a.err = device_error_word())) return fail(FEM_ERR_CUDA, "device error word unavailable");
     // vector rows: C a multiple of 4 keeps every field's rows 16-byte aligned
     const bool vec = n_cells % 4 == 0 && aligned16(conn) && aligned16(K) && aligned16(elem_out);
     switch (dim * 10 + static_cast<int>(prec)) {

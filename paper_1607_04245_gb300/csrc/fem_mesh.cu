@@ -100,10 +100,12 @@ static fem_status inclusive_scan(int32_t *data, int64_t n, int32_t *tile_sums, c
 
 // ------------------------------------------------------------------ vertex-to-cell lists
 
-__global__ void count_kernel(const int32_t *conn, int64_t total, uint32_t V, int32_t *ptr1) {
+__global__ void count_kernel(const int32_t *conn, int64_t total, uint32_t V, int32_t *ptr1, unsigned *err) {
+    uint32_t vmax = 0;
     const int64_t stride = int64_t(gridDim.x) * blockDim.x;
     for (int64_t j = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; j < total; j += stride)
-        atomicAdd(ptr1 + clamp_vid(conn[j], V), 1);
+        atomicAdd(ptr1 + clamp_vid(conn[j], V, vmax), 1);
+    report_mesh(err, vmax, V, false);
 }
 
 __global__ void copy_kernel(const int32_t *src, int32_t *dst, int64_t n) {
@@ -246,7 +248,7 @@ static void launch_gather_t(int n_comp, int64_t C, int64_t V, const void *elem, 
 fem_status launch_gather(int dim, int n_comp, int64_t C, int64_t V, const void *elem, const int32_t *node_ptr,
                          const int32_t *node_idx, void *out, fem_precision prec, cudaStream_t s) {
     if (V == 0) return FEM_OK;
-    const bool f64 = prec == FEM_FP64;
+    const bool f64 = prec == FEM_FP64 || prec == FEM_FP64_DF;  // float64 values either way
     if (dim == 2) {
         if (f64) launch_gather_t<3, double>(n_comp, C, V, elem, node_ptr, node_idx, out, s);
         else launch_gather_t<3, float>(n_comp, C, V, elem, node_ptr, node_idx, out, s);
@@ -331,8 +333,10 @@ extern "C" fem_status fem_build_node2cell(int dim, int64_t n_cells, int64_t n_ve
         return check_launch("node2cell memset");
     if (n_cells == 0 || n_verts == 0) return check_launch("node2cell");
     const uint32_t V = static_cast<uint32_t>(n_verts);
+    unsigned *err = device_error_word();
+    if (!err) return fail(FEM_ERR_CUDA, "device error word unavailable");
     count_kernel<<<grid_for(NB * n_cells, kBlock, reinterpret_cast<const void *>(count_kernel)), kBlock, 0, s>>>(
-        conn, NB * n_cells, V, node_ptr + 1);
+        conn, NB * n_cells, V, node_ptr + 1, err);
     if ((st = inclusive_scan(node_ptr + 1, n_verts, work + n_verts, s)) != FEM_OK) return st;
     copy_kernel<<<grid_for(n_verts, kBlock, reinterpret_cast<const void *>(copy_kernel)), kBlock, 0, s>>>(
         node_ptr, work, n_verts);
@@ -350,7 +354,8 @@ extern "C" fem_status fem_gather_nodes(int dim, int n_comp, int64_t n_cells, int
     if (dim != 2 && dim != 3) return fail(FEM_ERR_ARG, "dim = %d", dim);
     if (n_comp < 1 || n_comp > 3) return fail(FEM_ERR_ARG, "n_comp = %d", n_comp);
     if (n_cells < 0 || n_verts < 0) return fail(FEM_ERR_ARG, "negative size");
-    if (prec != FEM_FP64 && prec != FEM_FP32_MIXED && prec != FEM_FP32) return fail(FEM_ERR_ARG, "precision");
+    if (prec != FEM_FP64 && prec != FEM_FP32_MIXED && prec != FEM_FP32 && prec != FEM_FP64_DF)
+        return fail(FEM_ERR_ARG, "unknown precision %d", static_cast<int>(prec));
     if (n_verts > 0 && (!node_ptr || !out)) return fail(FEM_ERR_ARG, "NULL argument");
     if (n_cells > 0 && (!elem || !node_idx)) return fail(FEM_ERR_ARG, "NULL argument");
     return launch_gather(dim, n_comp, n_cells, n_verts, elem, node_ptr, node_idx, out, prec, stream);

@@ -25,7 +25,8 @@ namespace fem {
 static std::mutex g_noalloc_mu;
 static void *g_noalloc_ptr[256] = {nullptr};
 
-// Device address of g_noalloc_scratch on the current device (looked up once per device).
+// Device address of g_noalloc_scratch on the current device (looked up once per device and
+// kept for the life of the process: a device reset after the first call is not supported).
 static fem_status noalloc_scratch(void **out) {
     int dev = -1;
     cudaError_t e = cudaGetDevice(&dev);
@@ -69,7 +70,9 @@ extern "C" fem_status fem_adjoint_laplacian_noalloc(int dim, int64_t n_cells, in
     fem_status st = noalloc_scratch(&scratch);
     if (st != FEM_OK) return st;
     // Every workspace entry the gather reads is written by the element kernel earlier in
-    // this same call, so nothing has to be cleared between calls.
+    // this same call, so nothing has to be cleared between calls -- unless a staged element
+    // kernel gave up a bounded wait (FEM_ERR_TIMEOUT from fem_device_error): it then skips
+    // that tile's writes, and du mixes in the previous call's values; the header says so.
     return fem_adjoint_laplacian(dim, n_cells, n_verts, coords, conn, u, K, n_q, qpts, qw, lambda, dK, du, node_ptr,
                                  node_idx, scratch, prec, stream);
 }

@@ -20,12 +20,6 @@
 
 namespace fem {
 
-// Device error word: bits set by kernels that gave up a bounded wait. It lives in
-// fem_core.cu; kernels get its device address (device_error_word()) as an argument.
-// fem_device_error() reads and clears it.
-enum : unsigned { FEM_DEVERR_TIMEOUT = 1u };
-unsigned *device_error_word();
-
 // budget of one bounded wait (nanoseconds of %globaltimer)
 constexpr uint64_t kWaitBudgetNs = 500ull * 1000ull * 1000ull;
 
@@ -96,8 +90,6 @@ __device__ __forceinline__ void bulk_copy_g2s(void *dst, const void *src, uint32
         "l"(src), "r"(bytes), "r"(smem_addr(bar)), "l"(policy)
         : "memory");
 }
-
-__device__ __forceinline__ void record_device_error(unsigned *err, unsigned bits) { atomicOr(err, bits); }
 
 // ------------------------------------------------------------------ the staged chunk loop
 //

@@ -41,6 +41,7 @@ struct RdArgs {
     float tau2;
     double gd;  // g of the grad a term (P1 a only)
     float gf;
+    unsigned *err;  // device error word (FEM_DEVERR_BADMESH)
     QuadW w;
     BasisTab t;
 };
@@ -134,12 +135,56 @@ __device__ __forceinline__ void rd_element(const RdArgs &a, const T (&n)[DIM][DI
     }
 }
 
+// Float64 recomputation of cell e of the mixed form (badly shaped, or a non-finite float32
+// result), stored over the float32 element vector the caller has already written (same
+// thread, program order). Everything is read again from global memory and summed in
+// float64: the path is rare and kept out of line, so none of its state takes registers on
+// the common path.
+template <int DIM, bool A_P1, bool REACT, bool DRIFT>
+__device__ __noinline__ void rd_fallback_store(const RdArgs &a, int64_t e) {
+    constexpr int NB = DIM + 1;
+    const int64_t C = a.C;
+    const float *u = static_cast<const float *>(a.u);
+    const float *af = static_cast<const float *>(a.a);
+    const float *cf = static_cast<const float *>(a.c);
+    uint32_t v[NB];
+    double u64[NB], a64[NB], c64[FEM_MAX_QPTS];
+    double kbar = 0.0;
+#pragma unroll
+    for (int b = 0; b < NB; ++b) {
+        v[b] = clamp_vid(a.conn[b * C + e], a.V);
+        u64[b] = u[v[b]];
+        a64[b] = A_P1 ? double(af[v[b]]) : 0.0;
+        if (A_P1) kbar += a.t.md[b] * a64[b];
+    }
+    if (!A_P1) kbar = a.t.wsumd * double(af[e]);
+    if constexpr (REACT) {
+        for (int q = 0; q < a.w.nq; ++q) c64[q] = cf[q * C + e];
+    }
+    const double *X[DIM];
+#pragma unroll
+    for (int k = 0; k < DIM; ++k) X[k] = a.X[k];
+    double xs[NB][DIM], e64[DIM][DIM], n64[DIM][DIM], r64[NB];
+    gather_coords<DIM>(X, v, xs);
+    columns_f64<DIM>(xs, e64);
+    const double det64 = adjugate_rows<DIM>(e64, n64);
+    if (det_bad(det64) || ids_repeat<NB>(v)) record_device_error(a.err, FEM_DEVERR_BADMESH);
+    rd_element<DIM, FEM_FP64, double, REACT, DRIFT, FEM_MAX_QPTS, false>(a, n64, det64, u64, a64, kbar, c64, a.w.nq,
+                                                                        r64);
+    float *out = static_cast<float *>(a.out);
+#pragma unroll
+    for (int b = 0; b < NB; ++b) out[b * C + e] = static_cast<float>(r64[b]);
+}
+
 // One cell: its vertex ids (unclamped), the P0 coefficient a0 (unused for a P1 field) and
-// its reaction values ci at the quadrature points give the element vector rr. Float32
-// forms: a cell failing the mixed form's shape test is recomputed in float64.
+// its reaction values ci at the quadrature points give the element vector rr. Returns
+// false for a cell of the mixed form that fails its shape test (its rr is then
+// meaningless; the caller recomputes it with rd_fallback_store). vmax and bad_det collect
+// the mesh check (largest vertex id, det J = 0 or non-finite).
 template <int DIM, int P, bool A_P1, bool REACT, bool DRIFT, int NQA>
-__device__ __forceinline__ void rd_cell(const RdArgs &a, const double *const (&X)[DIM], const int32_t (&vid)[DIM + 1],
-                                        val_t<P> a0, const val_t<P> (&ci)[NQA], int nq, val_t<P> (&rr)[DIM + 1]) {
+__device__ __forceinline__ bool rd_cell(const RdArgs &a, const double *const (&X)[DIM], const int32_t (&vid)[DIM + 1],
+                                        val_t<P> a0, const val_t<P> (&ci)[NQA], int nq, val_t<P> (&rr)[DIM + 1],
+                                        uint32_t &vmax, bool &bad_det) {
     constexpr int NB = DIM + 1;
     using T = val_t<P>;
     const T *__restrict__ u = static_cast<const T *>(a.u);
@@ -148,7 +193,7 @@ __device__ __forceinline__ void rd_cell(const RdArgs &a, const double *const (&X
     T uu[NB], aa[NB];
 #pragma unroll
     for (int b = 0; b < NB; ++b) {
-        v[b] = clamp_vid(vid[b], a.V);
+        v[b] = clamp_vid(vid[b], a.V, vmax);
         uu[b] = ld_gather(u + v[b]);
     }
     // Kbar = sum_q w_q a(xi_q)
@@ -170,7 +215,9 @@ __device__ __forceinline__ void rd_cell(const RdArgs &a, const double *const (&X
         double ee[DIM][DIM], n[DIM][DIM];
         columns_f64<DIM>(xs, ee);
         const double det = adjugate_rows<DIM>(ee, n);
+        bad_det |= det_bad(det) | ids_repeat<NB>(v);
         rd_element<DIM, P, double, REACT, DRIFT, NQA>(a, n, det, uu, aa, ks.value(), ci, nq, rr);
+        return true;
     } else {
         float ee[DIM][DIM], n[DIM][DIM];
         if constexpr (P == FEM_FP32_MIXED) columns_mixed<DIM>(xs, ee);
@@ -178,23 +225,9 @@ __device__ __forceinline__ void rd_cell(const RdArgs &a, const double *const (&X
         const float det = adjugate_rows<DIM>(ee, n);
         bool ok = true;
         if constexpr (P == FEM_FP32_MIXED) ok = shape_ok<DIM>(ee, det, a.tau2);
-        if (ok) {
-            rd_element<DIM, P, float, REACT, DRIFT, NQA>(a, n, det, uu, aa, ks.value(), ci, nq, rr);
-        } else {
-            // badly shaped cell: float64 geometry and sums, float64 tables
-            double e64[DIM][DIM], n64[DIM][DIM], u64[NB], a64[NB], r64[NB], c64[NQA];
-            columns_f64<DIM>(xs, e64);
-            const double det64 = adjugate_rows<DIM>(e64, n64);
-#pragma unroll
-            for (int b = 0; b < NB; ++b) u64[b] = uu[b], a64[b] = aa[b];
-            if constexpr (REACT) {
-                for (int q = 0; q < nq; ++q) c64[q] = ci[q];
-            }
-            rd_element<DIM, FEM_FP64, double, REACT, DRIFT, NQA, false>(a, n64, det64, u64, a64, ks.value_f64(), c64, nq,
-                                                                r64);
-#pragma unroll
-            for (int b = 0; b < NB; ++b) rr[b] = static_cast<float>(r64[b]);
-        }
+        else bad_det |= det_bad(det) | ids_repeat<NB>(v);
+        rd_element<DIM, P, float, REACT, DRIFT, NQA>(a, n, det, uu, aa, ks.value(), ci, nq, rr);
+        return ok;
     }
 }
 
@@ -221,6 +254,8 @@ __global__ void __launch_bounds__(kBlock) rd_kernel(const __grid_constant__ RdAr
     const double *X[DIM];
 #pragma unroll
     for (int k = 0; k < DIM; ++k) X[k] = a.X[k];
+    uint32_t vmax = 0;     // largest vertex id seen (bad ids are clamped and reported)
+    bool bad_det = false;  // a cell with det J = 0 or non-finite
     const int64_t ngroups = (C + CPT - 1) / CPT;
     const int64_t stride = int64_t(gridDim.x) * blockDim.x;
     for (int64_t g = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; g < ngroups; g += stride) {
@@ -236,6 +271,7 @@ __global__ void __launch_bounds__(kBlock) rd_kernel(const __grid_constant__ RdAr
             for (int q = 0; q < nq; ++q) load_row<CPT>(cf + q * C + c0, cq[q]);
         }
         T r[NB][CPT];
+        bool ok[CPT];
 #pragma unroll
         for (int i = 0; i < CPT; ++i) {
             int32_t vi[NB];
@@ -246,13 +282,20 @@ __global__ void __launch_bounds__(kBlock) rd_kernel(const __grid_constant__ RdAr
 #pragma unroll(NQ > 0 ? NQ : 1)
                 for (int q = 0; q < nq; ++q) ci[q] = cq[q][i];
             }
-            rd_cell<DIM, P, A_P1, REACT, DRIFT, NQA>(a, X, vi, A_P1 ? zero<T>() : a0[i], ci, nq, rr);
+            ok[i] = rd_cell<DIM, P, A_P1, REACT, DRIFT, NQA>(a, X, vi, A_P1 ? zero<T>() : a0[i], ci, nq, rr, vmax,
+                                                            bad_det);
 #pragma unroll
             for (int b = 0; b < NB; ++b) r[b][i] = rr[b];
         }
 #pragma unroll
         for (int b = 0; b < NB; ++b) store_row<CPT>(out + b * C + c0, r[b]);
+        if constexpr (P == FEM_FP32_MIXED) {
+#pragma unroll
+            for (int i = 0; i < CPT; ++i)
+                if (!ok[i]) rd_fallback_store<DIM, A_P1, REACT, DRIFT>(a, c0 + i);
+        }
     }
+    report_mesh(a.err, vmax, a.V, bad_det);
 }
 
 template <int DIM, int P, bool A_P1, bool REACT, bool DRIFT>
@@ -332,6 +375,7 @@ extern "C" fem_status fem_integrate_reaction_diffusion(int dim, int64_t n_cells,
     r.tau2 = tau * tau;
     r.gd = drift;
     r.gf = static_cast<float>(drift);
+    if (!(r.err = device_error_word())) return fail(FEM_ERR_CUDA, "device error word unavailable");
     // grad a vanishes inside a cell for a P0 field: the term is then absent
     const bool p1 = a_space == 1, react = c != nullptr, with_drift = p1 && drift != 0.0;
     // 16-byte rows: every cell-indexed array aligned and the cell count a multiple of 4

@@ -40,6 +40,8 @@ extern "C" fem_status fem_serve_events_query(void *const *events, int n, int *do
 
 // Bytes of every array a request uses (0: slot unused), from its sizes and precision.
 static fem_status slot_bytes(const fem_serve_request *r, int64_t (&bytes)[FEM_SERVE_SLOTS]) {
+    for (auto &b : bytes) b = 0;
+    if (r->kind == 2) return FEM_OK;  // the self-test uses no arrays
     if (r->dim != 2 && r->dim != 3) return fail(FEM_ERR_ARG, "dim = %d, must be 2 or 3", r->dim);
     if (r->n_q < 1 || r->n_q > FEM_MAX_QPTS) return fail(FEM_ERR_ARG, "n_q = %d", r->n_q);
     if (r->n_cells < 0 || r->n_cells > INT32_MAX || r->n_verts < 0 || r->n_verts > INT32_MAX)
@@ -51,7 +53,6 @@ static fem_status slot_bytes(const fem_serve_request *r, int64_t (&bytes)[FEM_SE
         default: return fail(FEM_ERR_ARG, "unknown precision %d", r->prec);
     }
     const int64_t d = r->dim, C = r->n_cells, V = r->n_verts, nq = r->n_q, nc = r->physics == 0 ? 1 : d;
-    for (auto &b : bytes) b = 0;
     bytes[FEM_SERVE_COORDS] = d * V * 8;
     bytes[FEM_SERVE_CONN] = (d + 1) * C * 4;
     bytes[FEM_SERVE_U] = nc * V * s;
@@ -73,7 +74,7 @@ static fem_status slot_bytes(const fem_serve_request *r, int64_t (&bytes)[FEM_SE
 
 extern "C" fem_status fem_serve_launch(const fem_serve_request *r, void *block, void *event, fem_stream stream) {
     if (!r || !block || !event) return fail(FEM_ERR_ARG, "a NULL argument");
-    if (r->kind != 0 && r->kind != 1) return fail(FEM_ERR_ARG, "kind = %d", r->kind);
+    if (r->kind < 0 || r->kind > 2) return fail(FEM_ERR_ARG, "kind = %d", r->kind);
     if (r->physics != 0 && r->physics != 1) return fail(FEM_ERR_ARG, "physics = %d", r->physics);
     if (r->kind == 1 && r->physics != 0) return fail(FEM_ERR_UNSUPPORTED, "adjoint requests are Laplacian only");
     if (r->in_bytes < 0 || r->out_bytes[0] < 0 || r->out_bytes[1] < 0) return fail(FEM_ERR_ARG, "negative size");
@@ -91,6 +92,18 @@ extern "C" fem_status fem_serve_launch(const fem_serve_request *r, void *block, 
     }
     if (r->out_bytes[0] > need[FEM_SERVE_OUT] || r->out_bytes[1] > need[FEM_SERVE_DU])
         return fail(FEM_ERR_ARG, "out_bytes larger than the arrays they copy");
+    unsigned *status_dev = nullptr;  // the device's address of host_status
+    if (r->host_status) {
+        // the kernels write this word: it must be host memory the device can reach
+        cudaPointerAttributes pa;
+        if (cudaPointerGetAttributes(&pa, r->host_status) != cudaSuccess || pa.type != cudaMemoryTypeHost ||
+            !pa.devicePointer || (reinterpret_cast<uintptr_t>(r->host_status) & 3u)) {
+            cudaGetLastError();
+            return fail(FEM_ERR_ARG, "host_status must be a 4-byte aligned word of page-locked, device-mapped "
+                                     "host memory");
+        }
+        status_dev = static_cast<unsigned *>(pa.devicePointer);
+    }
     char *b = static_cast<char *>(block);
     auto at = [&](int slot) { return static_cast<void *>(b + r->offset[slot]); };
     const fem_precision prec = static_cast<fem_precision>(r->prec);
@@ -102,8 +115,16 @@ extern "C" fem_status fem_serve_launch(const fem_serve_request *r, void *block, 
     }
     const double *coords = static_cast<const double *>(at(FEM_SERVE_COORDS));
     const int32_t *conn = static_cast<const int32_t *>(at(FEM_SERVE_CONN));
+    // the request's own error word (mapped host memory, zeroed by the caller): every kernel
+    // below reports into it
+    struct Redirect {  // restores the device-wide word however this function returns
+        explicit Redirect(unsigned *w) { set_error_word_override(w); }
+        ~Redirect() { set_error_word_override(nullptr); }
+    } redirect(status_dev);
     fem_status st = FEM_OK;
-    if (r->kind == 0) {
+    if (r->kind == 2) {
+        st = fem_selftest_wait(1000 * 1000, stream);  // a 1 ms wait that nothing completes
+    } else if (r->kind == 0) {
         if (r->physics == 0)
             st = fem_integrate_laplacian(r->dim, r->n_cells, r->n_verts, coords, conn, at(FEM_SERVE_U),
                                          at(FEM_SERVE_K), r->n_q, r->qpts, r->qw, at(FEM_SERVE_OUT), prec, stream);

@@ -26,22 +26,25 @@ constexpr int kDotBlocks = 1024;  // fixed: the partial sums and their order do 
 // element diagonals of the Laplacian stiffness: out[b][e] = Kbar |n_b|^2 / |det J|
 template <int DIM, class T>
 __global__ void lap_diag_kernel(const double *X0, int64_t C, uint32_t V, const int32_t *conn, const T *K, int nq,
-                                QuadW w, T *out) {
+                                QuadW w, T *out, unsigned *err) {
     constexpr int NB = DIM + 1;
     const double *X[DIM];
 #pragma unroll
     for (int k = 0; k < DIM; ++k) X[k] = X0 + int64_t(k) * V;
+    uint32_t vmax = 0;
+    bool bad_det = false;
     const int64_t stride = int64_t(gridDim.x) * blockDim.x;
     for (int64_t e = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; e < C; e += stride) {
         uint32_t v[NB];
 #pragma unroll
-        for (int b = 0; b < NB; ++b) v[b] = clamp_vid(conn[b * C + e], V);
+        for (int b = 0; b < NB; ++b) v[b] = clamp_vid(conn[b * C + e], V, vmax);
         double kbar = 0.0;
         for (int q = 0; q < nq; ++q) kbar += w.wd[q] * static_cast<double>(K[q * C + e]);
         double xs[NB][DIM], ee[DIM][DIM], n[DIM][DIM];
         gather_coords<DIM>(X, v, xs);
         columns_f64<DIM>(xs, ee);
         const double det = adjugate_rows<DIM>(ee, n);
+        bad_det |= det_bad(det) | ids_repeat<NB>(v);
         const double s = kbar / fabs(det);
         double n0[DIM];
 #pragma unroll
@@ -54,6 +57,7 @@ __global__ void lap_diag_kernel(const double *X0, int64_t C, uint32_t V, const i
 #pragma unroll
         for (int j = 0; j < DIM; ++j) out[(j + 1) * C + e] = static_cast<T>(s * dotv<DIM>(n[j], n[j]));
     }
+    report_mesh(err, vmax, V, bad_det);
 }
 
 // block partial sums of x . y (float64 accumulation), fixed grid and order
@@ -290,11 +294,14 @@ static fem_status pcg_run(int dim, int64_t C, int64_t V, const double *coords, c
     // assembled diagonal
     {
         const int g = static_cast<int>(std::min<int64_t>((C + 255) / 256, 4096));
+        unsigned *err = device_error_word();
+        if (!err) return fail(FEM_ERR_CUDA, "device error word unavailable");
         if (dim == 2) lap_diag_kernel<2, T><<<g, 256, 0, s>>>(coords, C, static_cast<uint32_t>(V), conn,
                                                                 static_cast<const T *>(K), n_q, qwt,
-                                                                static_cast<T *>(w.elem));
+                                                                static_cast<T *>(w.elem), err);
         else lap_diag_kernel<3, T><<<g, 256, 0, s>>>(coords, C, static_cast<uint32_t>(V), conn,
-                                                       static_cast<const T *>(K), n_q, qwt, static_cast<T *>(w.elem));
+                                                       static_cast<const T *>(K), n_q, qwt, static_cast<T *>(w.elem),
+                                                       err);
         if ((st = check_launch("fem_pcg_laplacian diagonal")) != FEM_OK) return st;
         if ((st = launch_gather(dim, 1, C, V, w.elem, ptr, idx, D, vprec, s)) != FEM_OK) return st;
         diag_fix_kernel<T><<<gV, 256, 0, s>>>(V, fixed, D);

@@ -117,10 +117,13 @@ __global__ void __launch_bounds__(B *(DIM + 1)) transpose_kernel(const __grid_co
 
 // element basis coefficients: ue[b][e] = u[conn[b][e]] (the closure of u)
 template <class T>
-__global__ void element_values_kernel(int64_t total, int64_t C, uint32_t V, const int32_t *conn, const T *u, T *ue) {
+__global__ void element_values_kernel(int64_t total, int64_t C, uint32_t V, const int32_t *conn, const T *u, T *ue,
+                                      unsigned *err) {
+    uint32_t vmax = 0;
     const int64_t stride = int64_t(gridDim.x) * blockDim.x;
     for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < total; i += stride)
-        ue[i] = ld_gather(u + clamp_vid(conn[i], V));
+        ue[i] = ld_gather(u + clamp_vid(conn[i], V, vmax));
+    report_mesh(err, vmax, V, false);
 }
 
 template <int DIM, class T, int B>
@@ -161,16 +164,18 @@ extern "C" fem_status fem_element_values(int dim, int64_t n_cells, int64_t n_ver
     if (n_cells == 0) return FEM_OK;
     if (n_verts < 1 || !conn || !u || !ue) return fail(FEM_ERR_ARG, "a NULL array argument or no vertices");
     const int64_t total = int64_t(dim + 1) * n_cells;
+    unsigned *err = device_error_word();
+    if (!err) return fail(FEM_ERR_CUDA, "device error word unavailable");
     if (prec == FEM_FP64) {
         auto k = element_values_kernel<double>;
         k<<<grid_for(total, kBlock, reinterpret_cast<const void *>(k)), kBlock, 0, stream>>>(
             total, n_cells, static_cast<uint32_t>(n_verts), conn, static_cast<const double *>(u),
-            static_cast<double *>(ue));
+            static_cast<double *>(ue), err);
     } else {
         auto k = element_values_kernel<float>;
         k<<<grid_for(total, kBlock, reinterpret_cast<const void *>(k)), kBlock, 0, stream>>>(
             total, n_cells, static_cast<uint32_t>(n_verts), conn, static_cast<const float *>(u),
-            static_cast<float *>(ue));
+            static_cast<float *>(ue), err);
     }
     return check_launch("fem_element_values");
 }

@@ -104,6 +104,10 @@ class Arena:
 
 SERVE_SLOTS = {"coords": 0, "conn": 1, "u": 2, "K": 3, "lam": 3, "mu": 4, "adj": 5, "out": 6, "dK": 6, "du": 7,
                "scratch": 8, "node_ptr": 9, "node_idx": 10, "work": 11}
+KINDS = {"residual": 0, "adjoint": 1, "selftest": 2}
+# error bits of a request's status word (the library's device error bits)
+STATUS_TEXT = {1: "timeout: a bounded device-side wait gave up (outputs incomplete)",
+               2: "bad mesh: a vertex id outside [0, n_verts) or a cell with det J = 0"}
 
 
 class ServeRequestDesc(ctypes.Structure):
@@ -115,7 +119,7 @@ class ServeRequestDesc(ctypes.Structure):
                 ("qpts", ctypes.c_void_p), ("qw", ctypes.c_void_p),
                 ("host_in", ctypes.c_void_p), ("in_bytes", ctypes.c_int64),
                 ("host_out", ctypes.c_void_p * 2), ("out_bytes", ctypes.c_int64 * 2),
-                ("offset", ctypes.c_int64 * 12), ("block_bytes", ctypes.c_int64)]
+                ("offset", ctypes.c_int64 * 12), ("block_bytes", ctypes.c_int64), ("host_status", ctypes.c_void_p)]
 
 
 def _serve_lib():
@@ -166,19 +170,23 @@ class Request:
     input_bytes: int = 0
     _offsets: Optional[dict] = dataclasses.field(default=None, repr=False, compare=False)
     desc: Optional[ServeRequestDesc] = dataclasses.field(default=None, repr=False, compare=False)
+    # page-locked word the request's kernels report their error bits into (zeroed before
+    # each launch, read after completion); status_np is a numpy view of it (cheap to read)
+    status_host: Optional[torch.Tensor] = dataclasses.field(default=None, repr=False, compare=False)
+    status_np: Optional[np.ndarray] = dataclasses.field(default=None, repr=False, compare=False)
 
     def build_desc(self) -> ServeRequestDesc:
         """The request as the native launcher sees it (built once; the tensors it points
         into are owned by the request)."""
         d = ServeRequestDesc()
-        d.kind = 0 if self.kind == "residual" else 1
+        d.kind = KINDS[self.kind]
         d.physics = 0 if self.physics == "laplacian" else 1
         d.dim, d.n_q, d.prec = self.dim, int(self.qw.shape[0]), binding.precision(self.prec)
         d.n_cells, d.n_verts = self.n_cells, self.n_verts
         d.qpts, d.qw = self.qpts.ctypes.data, self.qw.ctypes.data
         d.host_in = self.host_block.data_ptr() if self.host_block is not None else None
         d.in_bytes = self.input_bytes
-        outs = ["out"] if self.kind == "residual" else ["dK", "du"]
+        outs = {"residual": ["out"], "adjoint": ["dK", "du"], "selftest": []}[self.kind]
         for k, name in enumerate(outs):
             t = self.result[name]
             d.host_out[k] = t.data_ptr() if t.numel() else None
@@ -186,8 +194,16 @@ class Request:
         for name, off in self.offsets().items():
             d.offset[SERVE_SLOTS[name]] = off
         d.block_bytes = footprint(self)
+        if self.status_host is None:
+            self.status_host = torch.zeros(1, dtype=torch.int32, pin_memory=True)
+            self.status_np = self.status_host.numpy()
+        d.host_status = self.status_host.data_ptr()
         self.desc = d
         return d
+
+    def device_status(self) -> int:
+        """Error bits the request's kernels reported (valid once it has completed)."""
+        return 0 if self.status_np is None else int(self.status_np[0])
 
     @property
     def n_comp(self) -> int:
@@ -213,6 +229,8 @@ class Request:
         return self._offsets
 
     def _device_arrays(self):
+        if self.kind == "selftest":
+            return [("scratch", (1,), torch.int32)]  # no arrays used: a minimal arena block
         d, C, V, nq = self.dim, self.n_cells, self.n_verts, int(self.qw.shape[0])
         dt = value_dtype(self.prec)
         arrs = [("coords", (d, V), torch.float64), ("conn", (d + 1, C), torch.int32),
@@ -232,7 +250,9 @@ class Request:
     def alloc_results(self):
         dt = value_dtype(self.prec)
         d, C, V, nq = self.dim, self.n_cells, self.n_verts, int(self.qw.shape[0])
-        if self.kind == "residual":
+        if self.kind == "selftest":
+            self.result = {}
+        elif self.kind == "residual":
             self.result = {"out": torch.empty(((d + 1) * self.n_comp, C), dtype=dt, pin_memory=True)}
         else:
             self.result = {"dK": torch.empty((nq, C), dtype=dt, pin_memory=True),
@@ -285,6 +305,18 @@ def make_request(rid, case, kind, prec="mixed", arrival=0.0, adj=None) -> Reques
         view.copy_(torch.from_numpy(np.ascontiguousarray(values[name])).to(t))
         r.host[name] = view
         off += (nb + ALIGN - 1) // ALIGN * ALIGN
+    r.alloc_results()
+    r.build_desc()
+    return r
+
+
+def make_selftest_request(rid, arrival=0.0) -> Request:
+    """A request whose only kernel is the bounded-wait self-test (a wait that nothing
+    completes, given up after 1 ms): it always comes back failed with the timeout bit, and
+    the requests around it are unaffected. For tests of the failure path."""
+    r = Request(rid, "selftest", "laplacian", 3, 0, 0, np.zeros((1, 3)), np.ones(1), {}, prec="mixed",
+                arrival=arrival)
+    r.input_bytes = 0
     r.alloc_results()
     r.build_desc()
     return r
@@ -343,6 +375,7 @@ class GpuExecutor:
         stream: one native call (fem_serve_launch) with pointers into the request's block."""
         slot, offs, base = admitted
         desc = req.desc if req.desc is not None else req.build_desc()
+        req.status_np[0] = 0  # the kernels only set bits
         if self.nvtx:
             torch.cuda.nvtx.range_push(f"{req.kind} {req.physics}{req.dim}d rid={req.rid} cells={req.n_cells}")
         st = self._L.fem_serve_launch(ctypes.byref(desc), ctypes.c_void_p(self.pool_ptr + base), self.events[slot],
@@ -353,7 +386,8 @@ class GpuExecutor:
             self.arena.free(base)
             self.free_slots.append(slot)
             raise binding.FemError("fem_serve_launch", st, self._L.fem_last_error().decode())
-        self.launches += 1 if req.kind == "residual" else 9  # adjoint: list build (7 kernels) + element + gather
+        # residual: 1 kernel; adjoint: list build (7 kernels) + element + gather; self-test: 1
+        self.launches += 9 if req.kind == "adjoint" else 1
         self.inflight[req.rid] = (req, slot, offs, None)
 
     def poll(self) -> List[Request]:
@@ -373,6 +407,9 @@ class GpuExecutor:
                 for o in offs:
                     self.arena.free(o)
                 self.free_slots.append(slot)
+                bits = req.device_status()
+                if bits:
+                    req.error = "; ".join(t for b, t in STATUS_TEXT.items() if bits & b) or f"device error bits {bits}"
                 out.append(req)
         return out
 
@@ -395,6 +432,7 @@ class ServeStats:
     n: int
     n_done: int
     n_rejected: int
+    n_failed: int
     makespan_s: float
     cells: int
     cells_per_s: float
@@ -470,7 +508,7 @@ class Scheduler:
             max_inflight = max(max_inflight, len(getattr(self.ex, "inflight", ())))
             for r in self.ex.poll():
                 r.t_done = self.clock()
-                r.status = "done"
+                r.status = "failed" if r.error else "done"
                 finished += 1
                 progressed = True
             if not progressed:
@@ -493,6 +531,7 @@ class Scheduler:
             return lat[k]
 
         return ServeStats(n=n, n_done=len(done), n_rejected=sum(r.status == "rejected" for r in requests),
+                          n_failed=sum(r.status == "failed" for r in requests),
                           makespan_s=span, cells=cells, cells_per_s=cells / span if span > 0 else math.nan,
                           req_per_s=len(done) / span if span > 0 else math.nan, p50_ms=pct(50), p99_ms=pct(99),
                           mean_ms=statistics.mean(lat) if done else math.nan, max_inflight=max_inflight,

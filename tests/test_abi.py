@@ -138,14 +138,16 @@ def test_serve_launch_validation(lib):
     fake = P(0x1000)  # never dereferenced
     assert lib.fem_serve_launch(None, fake, fake, None) == -1
     d = ServeRequestDesc()
-    d.kind = 2
+    d.kind = 3  # no such kind
+    assert lib.fem_serve_launch(ctypes.byref(d), fake, fake, None) == -1
+    d.kind = 2  # the self-test: still needs a block
     assert lib.fem_serve_launch(ctypes.byref(d), fake, fake, None) == -1
     d.kind, d.physics = 1, 1  # adjoint of elasticity
     assert lib.fem_serve_launch(ctypes.byref(d), fake, fake, None) == -7
     assert lib.fem_serve_events_query(None, 0, None) == 0
     assert lib.fem_serve_events_query(None, 1, None) == -1
     lib.fem_serve_request_bytes.restype = ctypes.c_int64
-    assert lib.fem_serve_request_bytes() == ctypes.sizeof(ServeRequestDesc) == 208
+    assert lib.fem_serve_request_bytes() == ctypes.sizeof(ServeRequestDesc) == 216
 
 
 def test_serve_launch_checks_the_descriptor_against_its_block(lib):
@@ -211,3 +213,42 @@ def test_serve_launch_checks_the_descriptor_against_its_block(lib):
     a.out_bytes[0], a.out_bytes[1] = sizes["dK"], sizes["du"]
     assert lib.fem_serve_launch(ctypes.byref(a), fake, fake, None) == -1
     assert b"outside" in lib.fem_last_error()
+
+
+def test_pointwise_validation(lib):
+    """Argument checks of the run-time compiled entry point, all before any compilation."""
+    P = ctypes.c_void_p
+    qw = _qw(4)
+    qwp = qw.ctypes.data_as(P)
+    qp = np.full((4, 3), 0.25)
+    qpp = qp.ctypes.data_as(P)
+    fake = P(0x1000)
+    f1 = b"f1[0] = grad_u[0];"
+    call = lambda f0, f1, dim=3, nc=1, nk=1, nq=4, q=qpp, prec=0: lib.fem_integrate_pointwise(
+        f0, f1, dim, nc, nk, 10, 10, fake, fake, fake, fake, nq, q, qwp, fake, prec, None)
+    assert call(None, None) == -1  # neither f0 nor f1
+    assert call(None, f1, prec=2) == -1  # FEM_FP32 ablation: not offered here
+    assert call(None, f1, prec=3) == -1  # FEM_FP64_DF: not offered here
+    assert call(None, f1, nc=0) == -1 and call(None, f1, nc=4) == -1
+    assert call(None, f1, nk=-1) == -1 and call(None, f1, nk=9) == -1
+    assert call(None, f1, dim=4) == -1
+    assert call(None, f1, nq=0) == -2
+    assert call(None, f1, q=None) == -1  # the quadrature points are required
+    assert b"qpts" in lib.fem_last_error()
+
+
+def test_serve_launch_rejects_a_status_word_the_device_cannot_reach(lib):
+    """host_status must be page-locked, device-mapped host memory: plain host memory is an
+    argument error found before anything is enqueued."""
+    from paper_1607_04245_gb300.serving import SERVE_SLOTS, ServeRequestDesc
+
+    P = ctypes.c_void_p
+    lib.fem_serve_launch.argtypes = [ctypes.POINTER(ServeRequestDesc), P, P, P]
+    lib.fem_serve_launch.restype = ctypes.c_int
+    d = ServeRequestDesc()
+    d.kind, d.physics, d.dim, d.n_q, d.prec, d.n_cells, d.n_verts = 2, 0, 3, 4, 1, 0, 0
+    d.block_bytes = 256
+    word = np.zeros(1, dtype=np.uint32)  # pageable host memory
+    d.host_status = word.ctypes.data
+    st = lib.fem_serve_launch(ctypes.byref(d), P(0x1000), P(0x1000), None)
+    assert st in (-1, -3)  # FEM_ERR_ARG (or FEM_ERR_CUDA where no CUDA driver answers the query)

@@ -61,6 +61,11 @@ def test_adjoint_parity_full(adj3d, prec):
     eK, eu = rel_err(dK, rK), rel_err(du, ru)
     print(f"adjoint {prec}: dK err {eK:.3e}, du err {eu:.3e}")
     assert eK <= TOL[prec] and eu <= TOL[prec]
+    if prec == "mixed":
+        rK64, ru64 = oracle.adjoint_for(adj3d)  # the unrounded float64 u, K and lambda
+        eK64, eu64 = rel_err(dK, rK64), rel_err(du, ru64)
+        print(f"adjoint mixed vs the float64 inputs: dK {eK64:.3e}, du {eu64:.3e}")
+        assert eK64 <= TOL["mixed"] and eu64 <= TOL["mixed"]
 
 
 @pytest.mark.parametrize("n_cells", [1, 5, 6 * 6 ** 3 - 2])

@@ -25,6 +25,10 @@ def test_full_size(elast, prec):
     err = rel_err(r, oracle.residual_for(c))
     print(f"{elast.name} {prec}: rel max-norm err {err:.3e}")
     assert err <= TOL[prec]
+    if prec == "mixed":
+        err64 = rel_err(r, oracle.residual_for(elast))  # the unrounded float64 u, lambda, mu
+        print(f"{elast.name} mixed vs the float64 inputs: {err64:.3e}")
+        assert err64 <= TOL["mixed"]
     # per-component element sums vanish
     dim = elast.dim
     s = r.double().view(dim + 1, dim, -1).sum(0).abs().max().item()

@@ -9,7 +9,9 @@ import torch
 import oracle
 import workloads
 from gpu_util import TOL, rel_err
-from paper_1607_04245_gb300.serving import GpuExecutor, Scheduler, footprint, make_request, poisson_arrivals
+import paper_1607_04245_gb300 as fem
+from paper_1607_04245_gb300.serving import (GpuExecutor, Scheduler, footprint, make_request, make_selftest_request,
+                                            poisson_arrivals)
 
 pytestmark = pytest.mark.gpu
 
@@ -65,3 +67,30 @@ def test_poisson_arrivals_latency():
     assert 0 < st.p50_ms <= st.p99_ms
     assert st.makespan_s >= t[-1]
     assert all(r.t_done > r.t_arrive for r in reqs)
+
+
+def test_failed_requests_are_reported_and_isolated():
+    """A request whose mesh is invalid (an out-of-range vertex id) and a self-test request
+    whose bounded wait gives up come back failed with their reason, read from their own
+    error words; the requests served beside them are unaffected (bitwise equal to their
+    results alone) and the device-wide error word stays clear."""
+    _, mix = _stream(16, seed=21, max_cells=30000)
+    victim = next(r for r in mix if r.kind == "residual")
+    victim.host["conn"][0, 3] = victim.n_verts + 5  # a view into the request's pinned input block
+    probe = make_selftest_request(999, arrival=0.0)
+    ex = GpuExecutor(capacity=1 << 30, n_slots=4)
+    assert fem.fem_device_error() == 0
+    st = Scheduler(ex).run(mix + [probe])
+    assert st.n_failed == 2 and st.n_done == len(mix) - 1
+    assert victim.status == "failed" and "bad mesh" in victim.error
+    assert probe.status == "failed" and "timeout" in probe.error
+    assert fem.fem_device_error() == 0
+    _, alone = _stream(16, seed=21, max_cells=30000)
+    ex1 = GpuExecutor(capacity=1 << 30, n_slots=1)
+    for a, b in zip(mix, alone):
+        if a is victim:
+            continue
+        Scheduler(ex1).run([b])
+        assert a.status == "done" and b.status == "done"
+        for k in a.result:
+            assert torch.equal(a.result[k], b.result[k]), (a.rid, k)

@@ -5,9 +5,14 @@ inside the library, so it takes no scratch argument.
 
 Called here through the C ABI (ctypes, raw device pointers) and compared with
 fem_adjoint_laplacian, which takes a caller-owned workspace, on two calls in a row with
-different adjoint weights: the second call reuses the array the first one wrote.
-This file is named to be collected last; it also passes on its own in a fresh process.
+different adjoint weights: the second call reuses the array the first one wrote. Both
+entry points run the same kernels, so the results must be bitwise equal; a stale entry
+left in the array by an earlier, larger call would show up as a difference. One call is
+also checked against the CPU oracle. This file is named to be collected last; it also
+passes on its own in a fresh process.
 """
+
+import oracle
 
 import ctypes
 
@@ -55,9 +60,30 @@ def test_noalloc_matches_workspace_entry_point_twice(dim, prec):
         rK, ru = fem.fem_adjoint_laplacian(d["coords"], d["conn"], d["u"], d["K"], c.rule.points, c.rule.weights,
                                            lam, ptr, idx, prec=prec)
         torch.cuda.synchronize()
-        rK, ru = rK.double().cpu().numpy(), ru.double().cpu().numpy()
-        assert rel_err(dK, rK) <= TOL[prec], (call, "dK")
-        assert rel_err(du, ru) <= TOL[prec], (call, "du")
+        assert fem.fem_device_error() == 0
+        assert torch.equal(dK, rK), (call, "dK")
+        assert torch.equal(du, ru), (call, "du")
+        if call == 1:
+            oK, ou = oracle.adjoint_for(c, lam.double().cpu().numpy())
+            assert rel_err(dK, oK) <= TOL[prec] and rel_err(du, ou) <= TOL[prec]
+
+
+@pytest.mark.parametrize("prec", ["mixed", "fp64"])
+def test_noalloc_large_call_then_small_call(prec):
+    """A call that fills most of the array, then a smaller one on another mesh: the
+    smaller call must not read anything the larger one left behind."""
+    dt = fem.value_dtype(prec)
+    rng = np.random.default_rng(3)
+    for n in (6 * 40 ** 3, 6 * 9 ** 3 + 6):
+        case = workloads.adjoint_case(n)
+        c, d = device_arrays(case, prec)
+        ptr, idx = fem.fem_build_node2cell(d["conn"], c.n_verts)
+        lam = torch.from_numpy(rng.uniform(-1, 1, (4, c.n_cells))).to("cuda", dt)
+        dK, du = _noalloc(c, d, lam, ptr, idx, prec)
+        rK, ru = fem.fem_adjoint_laplacian(d["coords"], d["conn"], d["u"], d["K"], c.rule.points, c.rule.weights,
+                                           lam, ptr, idx, prec=prec)
+        torch.cuda.synchronize()
+        assert torch.equal(dK, rK) and torch.equal(du, ru), n
 
 
 def test_noalloc_double_float_form():
