@@ -541,6 +541,41 @@ def measure_reaction(case, prec, device, stream, flush, steps, warmup, peak, ora
     return row
 
 
+def measure_prepared(case, device, stream, flush, steps, warmup, peak, oracle_mod=None):
+    """The mixed-form Laplacian from prepared vertex records (fem_prepare_vertices once per
+    mesh, timed separately; fem_integrate_laplacian_prepared timed like the headline): one
+    32-byte record load per vertex instead of three coordinate gathers and three splits."""
+    import torch
+
+    import paper_1607_04245_gb300 as fem
+
+    c, d = device_case(case, "mixed", device)
+    q = c.rule
+    with torch.cuda.stream(stream):
+        rec = fem.fem_prepare_vertices(d["coords"], stream=stream)
+        ms_prep, _, _ = timed_steps(lambda: fem.fem_prepare_vertices(d["coords"], rec=rec, stream=stream), steps,
+                                    warmup, stream, flush)
+        out = torch.empty((c.dim + 1, c.n_cells), dtype=torch.float32, device=device)
+        fn = lambda: fem.fem_integrate_laplacian_prepared(d["coords"], rec, d["conn"], d["u"], d["K"], q.points,
+                                                          q.weights, out=out, stream=stream)
+        ms, _, _ = timed_steps(fn, steps, warmup, stream, flush)
+    t = statistics.mean(ms) * 1e-3
+    C, V, nb = c.n_cells, c.n_verts, c.dim + 1
+    R = 8 if c.dim == 3 else 4
+    nbytes = nb * 4 * C + q.n_q * 4 * C + nb * 4 * C + (R * 4 + 4) * V
+    row = {"physics": "laplacian_prepared_vertex_records", "dim": c.dim, "prec": "mixed", "cells": C,
+           "ms_per_launch": round(statistics.mean(ms), 6), "ms_median": round(statistics.median(ms), 6),
+           "cells_per_s": C / t, "alg_bytes_per_launch": nbytes, "alg_gbs": nbytes / t / 1e9,
+           "hbm_frac_of_measured": nbytes / t / 1e9 / peak,
+           "prepare_ms_per_mesh": round(statistics.mean(ms_prep), 6),
+           "alg_bytes_per_cell": "conn 4(d+1) + K 4 n_q + out 4(d+1) + (V/C)(record 4R + u 4), R = 8 (3D) or 4 (2D)",
+           "kernel": "lap_rec_kernel (the pair kernel with one 32-byte record load per vertex, no splits)"}
+    if oracle_mod is not None:
+        torch.cuda.synchronize()
+        row["rel_maxnorm_err_vs_oracle"] = rel_err(out, oracle_timed(row, C, lambda: oracle_mod.residual_for(c)))
+    return row
+
+
 POINTWISE_SRC = {
     "laplacian": "for (int i = 0; i < DIM; ++i) f1[i] = a[0] * grad_u[i];",
     # the oracle's "nonlinear" physics: kappa(u, x) = (p0 + p1 u + p2 u^2)(1 + p3 (x_0 + 2 x_1 + 3 x_2))
@@ -1050,6 +1085,8 @@ def run_ours(args):
         if want(f"reaction3d_grad_a_{prec}"):
             rows[f"reaction3d_grad_a_{prec}"] = measure_reaction(case, prec, device, stream, flush, rsteps, args.warmup,
                                                                  peak, oracle)
+    if want("lap3d_prepared_mixed"):
+        rows["lap3d_prepared_mixed"] = measure_prepared(case, device, stream, flush, rsteps, args.warmup, peak, oracle)
     for prec in ("mixed", "fp64"):
         for phys in ("laplacian", "nonlinear"):
             if want(f"pointwise_{phys}3d_{prec}"):

@@ -308,6 +308,29 @@ fem_status fem_integrate_laplacian_geom(int dim, int64_t n_cells, int64_t n_vert
                                         fem_precision prec, fem_stream stream);
 
 /* ---------------------------------------------------------------------------------
+ * Prepared vertex records for the mixed-form Laplacian (not in the paper; the per-mesh
+ * counterpart of the paper's precomputed geometry, for meshes evaluated many times):
+ *
+ * fem_prepare_vertices -- once per mesh: every float64 coordinate split into the float32
+ *   (hi, lo) pair the mixed form differences its Jacobian columns from, written to rec,
+ *   fem_prepared_record_floats(dim) floats per vertex (3D: 8 = hi_x hi_y hi_z lo_x lo_y lo_z
+ *   and two unused; 2D: 4 = hi_x hi_y lo_x lo_y). rec is a caller-owned float32 device
+ *   array of n_verts * fem_prepared_record_floats(dim) entries, 32-byte aligned.
+ * fem_integrate_laplacian_prepared -- fem_integrate_laplacian in FEM_FP32_MIXED with the
+ *   coordinate gathers and splits replaced by one record load per vertex; the element
+ *   vectors are bitwise those of fem_integrate_laplacian (same operations on the same
+ *   pairs). coords is still read, for the float64 recomputation of badly shaped cells.
+ *   Needs an even n_cells and 8-byte aligned conn, K and elem_out (FEM_ERR_SHAPE
+ *   otherwise). Other arguments as fem_integrate_laplacian (values float32).
+ * ------------------------------------------------------------------------------- */
+int64_t fem_prepared_record_floats(int dim);
+fem_status fem_prepare_vertices(int dim, int64_t n_verts, const double *coords, float *rec, fem_stream stream);
+fem_status fem_integrate_laplacian_prepared(int dim, int64_t n_cells, int64_t n_verts, const double *coords,
+                                            const float *rec, const int32_t *conn, const void *u, const void *K,
+                                            int n_q, const double *qpts, const double *qw, void *elem_out,
+                                            fem_stream stream);
+
+/* ---------------------------------------------------------------------------------
  * fem_set_mixed_threshold / fem_get_mixed_threshold -- the shape-test threshold tau of
  * FEM_FP32_MIXED (default 0.05). tau = 0 sends no cell to the float64 path, tau > 1
  * sends every cell. Process-wide; set it between calls, not during them.

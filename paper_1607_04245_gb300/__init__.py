@@ -30,6 +30,8 @@ from .binding import (  # noqa: F401
     fem_integrate_laplacian_geom,
     fem_integrate_laplacian_transposed,
     fem_integrate_pointwise,
+    fem_integrate_laplacian_prepared,
+    fem_prepare_vertices,
     fem_integrate_reaction_diffusion,
     fem_precompute_geometry,
     fem_pcg_laplacian,

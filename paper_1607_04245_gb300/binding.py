@@ -63,6 +63,8 @@ def lib():
             "fem_integrate_laplacian_geom": [ci, i64, i64, P, P, P, ci, P, P, P, P, ci, P],
             "fem_selftest_wait": [i64, P],
             "fem_selftest_quotient": [i64, P, P, P, P, P],
+            "fem_prepare_vertices": [ci, i64, P, P, P],
+            "fem_integrate_laplacian_prepared": [ci, i64, i64, P, P, P, P, P, ci, P, P, P, P],
             "fem_integrate_pointwise": [ctypes.c_char_p, ctypes.c_char_p, ci, ci, ci, i64, i64, P, P, P, P, ci, P,
                                         P, P, ci, P],
         }
@@ -76,6 +78,8 @@ def lib():
         L.fem_host_work_bytes.restype = i64
         L.fem_pcg_work_bytes.argtypes = [ci, i64, i64, ci]
         L.fem_pcg_work_bytes.restype = i64
+        L.fem_prepared_record_floats.argtypes = [ci]
+        L.fem_prepared_record_floats.restype = i64
         L.fem_node2cell_work_size.argtypes = [i64]
         L.fem_node2cell_work_size.restype = i64
         for name in ("fem_last_error", "fem_version"):
@@ -204,6 +208,40 @@ def fem_integrate_elasticity(coords, conn, u, lam, mu, qpts, qw, out=None, prec=
         _dev(u, "u", dt, (dim, V), dev), _dev(lam, "lam", dt, (nq, C), dev), _dev(mu, "mu", dt, (nq, C), dev),
         nq, qp.ptr, w.ptr, _dev(out, "out", dt, ((dim + 1) * dim, C), dev), p, _stream(stream))
     _check("fem_integrate_elasticity", st)
+    return out
+
+
+def fem_prepare_vertices(coords, rec=None, stream=None) -> torch.Tensor:
+    """Per-mesh vertex records [V][8] (3D) or [V][4] (2D), float32: each coordinate's
+    (hi, lo) split, for fem_integrate_laplacian_prepared."""
+    dim, V = int(coords.shape[0]), int(coords.shape[1])
+    R = int(lib().fem_prepared_record_floats(dim))
+    if R < 0:
+        raise ValueError("coords must be (2, V) or (3, V)")
+    dev = coords.device
+    rec = torch.empty((V, R), dtype=torch.float32, device=dev) if rec is None else rec
+    _check("fem_prepare_vertices", lib().fem_prepare_vertices(
+        dim, V, _dev(coords, "coords", torch.float64, device=dev), _dev(rec, "rec", torch.float32, (V, R), dev),
+        _stream(stream)))
+    return rec
+
+
+def fem_integrate_laplacian_prepared(coords, rec, conn, u, K, qpts, qw, out=None, stream=None) -> torch.Tensor:
+    """fem_integrate_laplacian (FP32-mixed) from the prepared vertex records: bitwise the same
+    element vectors [dim+1][C]."""
+    dim, V, C = _mesh_sizes(coords, conn)
+    nq = int(np.asarray(qw).shape[0]) if not isinstance(qw, torch.Tensor) else int(qw.shape[0])
+    dev = coords.device
+    R = int(lib().fem_prepared_record_floats(dim))
+    if out is None:
+        out = torch.empty((dim + 1, C), dtype=torch.float32, device=dev)
+    qp, w = _HostTable(qpts, (nq, dim), "qpts"), _HostTable(qw, (nq,), "qw")
+    st = lib().fem_integrate_laplacian_prepared(
+        dim, C, V, _dev(coords, "coords", torch.float64, device=dev), _dev(rec, "rec", torch.float32, (V, R), dev),
+        _dev(conn, "conn", torch.int32, device=dev), _dev(u, "u", torch.float32, (V,), dev),
+        _dev(K, "K", torch.float32, (nq, C), dev), nq, qp.ptr, w.ptr,
+        _dev(out, "out", torch.float32, (dim + 1, C), dev), _stream(stream))
+    _check("fem_integrate_laplacian_prepared", st)
     return out
 
 

@@ -29,6 +29,9 @@ __device__ __forceinline__ void load_row(const int32_t *p, int32_t (&v)[CPT]) {
     if constexpr (CPT == 4) {
         int4 t = ld_stream(reinterpret_cast<const int4 *>(p));
         v[0] = t.x, v[1] = t.y, v[2] = t.z, v[3] = t.w;
+    } else if constexpr (CPT == 2) {
+        int2 t = __ldcs(reinterpret_cast<const int2 *>(p));
+        v[0] = t.x, v[1] = t.y;
     } else {
 #pragma unroll
         for (int i = 0; i < CPT; ++i) v[i] = ld_stream(p + i);
@@ -40,6 +43,9 @@ __device__ __forceinline__ void load_row(const float *p, float (&v)[CPT]) {
     if constexpr (CPT == 4) {
         float4 t = ld_stream(reinterpret_cast<const float4 *>(p));
         v[0] = t.x, v[1] = t.y, v[2] = t.z, v[3] = t.w;
+    } else if constexpr (CPT == 2) {
+        float2 t = __ldcs(reinterpret_cast<const float2 *>(p));
+        v[0] = t.x, v[1] = t.y;
     } else {
 #pragma unroll
         for (int i = 0; i < CPT; ++i) v[i] = ld_stream(p + i);
@@ -52,6 +58,9 @@ __device__ __forceinline__ void load_row(const double *p, double (&v)[CPT]) {
         double2 a = ld_stream(reinterpret_cast<const double2 *>(p));
         double2 b = ld_stream(reinterpret_cast<const double2 *>(p) + 1);
         v[0] = a.x, v[1] = a.y, v[2] = b.x, v[3] = b.y;
+    } else if constexpr (CPT == 2) {
+        double2 a = ld_stream(reinterpret_cast<const double2 *>(p));
+        v[0] = a.x, v[1] = a.y;
     } else {
 #pragma unroll
         for (int i = 0; i < CPT; ++i) v[i] = ld_stream(p + i);

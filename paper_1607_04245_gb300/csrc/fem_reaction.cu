@@ -239,8 +239,16 @@ __device__ __forceinline__ bool rd_cell(const RdArgs &a, const double *const (&X
 // bulk-copy loop of the Laplacian kernel was slower here (37.2 against 33.7 us on the
 // 1,572,864-tet workload): at that kernel's 2 CTAs per SM the register cap spills this
 // element's state.
+// 3D float32 forms take two cells per thread at 80 registers (3 CTAs of 256 threads per SM):
+// 31.2 us on the 1,572,864-tet workload with reaction and drift, against 33.0 us with four
+// cells at 128 registers (2 CTAs); 64 registers spill, and 2 CTAs of two cells run 39 us.
+template <int DIM, int P, int CPT>
+constexpr int rd_min_blocks() {
+    return (P != FEM_FP64 && DIM == 3 && CPT == 2) ? 3 : 1;
+}
+
 template <int DIM, int P, bool A_P1, bool REACT, bool DRIFT, int CPT, int NQ>
-__global__ void __launch_bounds__(kBlock) rd_kernel(const __grid_constant__ RdArgs a) {
+__global__ void __launch_bounds__(kBlock, rd_min_blocks<DIM, P, CPT>()) rd_kernel(const __grid_constant__ RdArgs a) {
     static_assert(A_P1 || !DRIFT, "grad a vanishes inside a cell for a P0 field");
     static_assert(CPT == 1 || NQ > 0, "vector rows need a compile-time quadrature size");
     constexpr int NB = DIM + 1;
@@ -299,13 +307,16 @@ __global__ void __launch_bounds__(kBlock) rd_kernel(const __grid_constant__ RdAr
 }
 
 template <int DIM, int P, bool A_P1, bool REACT, bool DRIFT>
-static void launch_rd_one(const RdArgs &a, bool vec, cudaStream_t s) {
+static void launch_rd_one(const RdArgs &a, bool vec4, bool vec2, cudaStream_t s) {
     constexpr int NQN = DIM + 1 == 4 ? 4 : 3;  // the workloads' rules: 3 points in 2D, 4 in 3D
-    // the float64 form is bound by the float64 pipe; four cells per thread only cost it
-    // occupancy (457 against 416 us on the 1,572,864-tet workload)
+    // float32 forms: two cells per thread in 3D, four in 2D (rd_min_blocks); the float64 form
+    // is bound by the float64 pipe and keeps one cell per thread (four cost it occupancy: 457
+    // against 416 us on the 1,572,864-tet workload)
+    constexpr int CPTV = DIM == 3 ? 2 : 4;
+    const bool vec = CPTV == 2 ? vec2 : vec4;
     if (P != FEM_FP64 && vec && a.w.nq == NQN) {
-        auto k = rd_kernel<DIM, P, A_P1, REACT, DRIFT, 4, NQN>;
-        k<<<grid_for((a.C + 3) / 4, kBlock, reinterpret_cast<const void *>(k)), kBlock, 0, s>>>(a);
+        auto k = rd_kernel<DIM, P, A_P1, REACT, DRIFT, CPTV, NQN>;
+        k<<<grid_for((a.C + CPTV - 1) / CPTV, kBlock, reinterpret_cast<const void *>(k)), kBlock, 0, s>>>(a);
     } else {
         auto k = rd_kernel<DIM, P, A_P1, REACT, DRIFT, 1, 0>;
         k<<<grid_for(a.C, kBlock, reinterpret_cast<const void *>(k)), kBlock, 0, s>>>(a);
@@ -313,14 +324,15 @@ static void launch_rd_one(const RdArgs &a, bool vec, cudaStream_t s) {
 }
 
 template <int DIM, int P>
-static fem_status launch_rd(const RdArgs &a, bool a_p1, bool react, bool drift, bool vec, cudaStream_t s) {
+static fem_status launch_rd(const RdArgs &a, bool a_p1, bool react, bool drift, bool vec4, bool vec2,
+                            cudaStream_t s) {
     if (a_p1) {
-        if (drift) react ? launch_rd_one<DIM, P, true, true, true>(a, vec, s)
-                         : launch_rd_one<DIM, P, true, false, true>(a, vec, s);
-        else react ? launch_rd_one<DIM, P, true, true, false>(a, vec, s)
-                   : launch_rd_one<DIM, P, true, false, false>(a, vec, s);
+        if (drift) react ? launch_rd_one<DIM, P, true, true, true>(a, vec4, vec2, s)
+                         : launch_rd_one<DIM, P, true, false, true>(a, vec4, vec2, s);
+        else react ? launch_rd_one<DIM, P, true, true, false>(a, vec4, vec2, s)
+                   : launch_rd_one<DIM, P, true, false, false>(a, vec4, vec2, s);
     } else {
-        react ? launch_rd_one<DIM, P, false, true, false>(a, vec, s) : launch_rd_one<DIM, P, false, false, false>(a, vec, s);
+        react ? launch_rd_one<DIM, P, false, true, false>(a, vec4, vec2, s) : launch_rd_one<DIM, P, false, false, false>(a, vec4, vec2, s);
     }
     return check_launch("fem_integrate_reaction_diffusion");
 }
@@ -379,15 +391,17 @@ extern "C" fem_status fem_integrate_reaction_diffusion(int dim, int64_t n_cells,
     // grad a vanishes inside a cell for a P0 field: the term is then absent
     const bool p1 = a_space == 1, react = c != nullptr, with_drift = p1 && drift != 0.0;
     // 16-byte rows: every cell-indexed array aligned and the cell count a multiple of 4
-    const bool vec = n_cells % 4 == 0 && aligned16(conn) && aligned16(elem_out) && (!react || aligned16(c)) &&
-                     (p1 || aligned16(a));
+    const bool vec4 = n_cells % 4 == 0 && aligned16(conn) && aligned16(elem_out) && (!react || aligned16(c)) &&
+                      (p1 || aligned16(a));
+    const bool vec2 = n_cells % 2 == 0 && aligned8(conn) && aligned8(elem_out) && (!react || aligned8(c)) &&
+                      (p1 || aligned8(a));
     switch (dim * 10 + static_cast<int>(prec)) {
-        case 20: return launch_rd<2, FEM_FP64>(r, p1, react, with_drift, vec, stream);
-        case 21: return launch_rd<2, FEM_FP32_MIXED>(r, p1, react, with_drift, vec, stream);
-        case 22: return launch_rd<2, FEM_FP32>(r, p1, react, with_drift, vec, stream);
-        case 30: return launch_rd<3, FEM_FP64>(r, p1, react, with_drift, vec, stream);
-        case 31: return launch_rd<3, FEM_FP32_MIXED>(r, p1, react, with_drift, vec, stream);
-        case 32: return launch_rd<3, FEM_FP32>(r, p1, react, with_drift, vec, stream);
+        case 20: return launch_rd<2, FEM_FP64>(r, p1, react, with_drift, vec4, vec2, stream);
+        case 21: return launch_rd<2, FEM_FP32_MIXED>(r, p1, react, with_drift, vec4, vec2, stream);
+        case 22: return launch_rd<2, FEM_FP32>(r, p1, react, with_drift, vec4, vec2, stream);
+        case 30: return launch_rd<3, FEM_FP64>(r, p1, react, with_drift, vec4, vec2, stream);
+        case 31: return launch_rd<3, FEM_FP32_MIXED>(r, p1, react, with_drift, vec4, vec2, stream);
+        case 32: return launch_rd<3, FEM_FP32>(r, p1, react, with_drift, vec4, vec2, stream);
     }
     return fail(FEM_ERR_ARG, "unsupported dim/precision");
 }
