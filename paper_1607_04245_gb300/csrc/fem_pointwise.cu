@@ -4,8 +4,9 @@
 // Sec. 5 of the paper builds its kernel source from run-time parameters and hands it to
 // the OpenCL just-in-time compiler, with the user's f0 and f1 inlined into it; this file
 // does the same with NVRTC for the GPU the call runs on. The generated kernel evaluates
-// the bracket of Eq. 2 the direct way, one cell per thread, without the P1 collapse of the
-// built-in kernels (the user's physics may be nonlinear in u and depend on x):
+// the bracket of Eq. 2 one cell per thread, the pointwise functions at every quadrature point
+// (the user's physics may be nonlinear in u and depend on x; the built-in kernels collapse
+// the point loop further, which only a linear f1 allows):
 //
 //     r_{e,b,k} = sum_q w_q |det J| [ phi_b(xi_q) f0_k(q) + sum_i G_{b,i} f1_{k,i}(q) ]
 //
@@ -188,9 +189,13 @@ extern "C" __global__ void __launch_bounds__(256) fem_pointwise_kernel(const PwA
                 for (int b = 1; b < NB; ++b) s += ub[b][k] * G[b][i];
                 gu[k * FEM_DIM + i] = s;
             }
-        T r[NB][FEM_NCOMP];
+        // For P1 the basis gradients G_b do not depend on the point, so the f1 part of the
+        // quadrature sum is G_b . (sum_q w_q f1(q)): the point loop accumulates F1 = sum_q
+        // w_q f1(q) and F0_b = sum_q w_q phi_b(q) f0(q), and the basis phase runs once.
+        T F1[FEM_NCOMP * FEM_DIM], F0[NB][FEM_NCOMP];
+        for (int k = 0; k < FEM_NCOMP * FEM_DIM; ++k) F1[k] = (T)0;
         for (int b = 0; b < NB; ++b)
-            for (int k = 0; k < FEM_NCOMP; ++k) r[b][k] = (T)0;
+            for (int k = 0; k < FEM_NCOMP; ++k) F0[b][k] = (T)0;
         for (int q = 0; q < FEM_NQ; ++q) {
             T ph[NB], uq[FEM_NCOMP], xq[FEM_DIM], aq[FEM_NCOEF > 0 ? FEM_NCOEF : 1];
             for (int b = 0; b < NB; ++b) ph[b] = (T)a.phi[q][b];
@@ -206,25 +211,28 @@ extern "C" __global__ void __launch_bounds__(256) fem_pointwise_kernel(const PwA
                 xq[i] = s;
             }
             for (int c = 0; c < FEM_NCOEF; ++c) aq[c] = coef[((i64)c * FEM_NQ + q) * C + e];
-            T f0[FEM_NCOMP], f1[FEM_NCOMP * FEM_DIM];
-            for (int k = 0; k < FEM_NCOMP; ++k) f0[k] = (T)0;
-            for (int k = 0; k < FEM_NCOMP * FEM_DIM; ++k) f1[k] = (T)0;
+            const T wq = (T)a.w[q];
 #if FEM_HAS_F0
+            T f0[FEM_NCOMP];
+            for (int k = 0; k < FEM_NCOMP; ++k) f0[k] = (T)0;
             fem_f0(uq, gu, aq, xq, f0);
+            for (int b = 0; b < NB; ++b)
+                for (int k = 0; k < FEM_NCOMP; ++k) F0[b][k] += (wq * ph[b]) * f0[k];
 #endif
 #if FEM_HAS_F1
+            T f1[FEM_NCOMP * FEM_DIM];
+            for (int k = 0; k < FEM_NCOMP * FEM_DIM; ++k) f1[k] = (T)0;
             fem_f1(uq, gu, aq, xq, f1);
+            for (int k = 0; k < FEM_NCOMP * FEM_DIM; ++k) F1[k] += wq * f1[k];
 #endif
-            const T wd = (T)a.w[q] * adet;
-            for (int b = 0; b < NB; ++b)
-                for (int k = 0; k < FEM_NCOMP; ++k) {
-                    T s = ph[b] * f0[k];
-                    for (int i = 0; i < FEM_DIM; ++i) s += G[b][i] * f1[k * FEM_DIM + i];
-                    r[b][k] += wd * s;
-                }
         }
+        // basis phase: r_{b,k} = |det J| (F0_{b,k} + G_b . F1_k)
         for (int b = 0; b < NB; ++b)
-            for (int k = 0; k < FEM_NCOMP; ++k) out[(i64)(b * FEM_NCOMP + k) * C + e] = r[b][k];
+            for (int k = 0; k < FEM_NCOMP; ++k) {
+                T s = F0[b][k];
+                for (int i = 0; i < FEM_DIM; ++i) s += G[b][i] * F1[k * FEM_DIM + i];
+                out[(i64)(b * FEM_NCOMP + k) * C + e] = adet * s;
+            }
     }
     if (vmax >= a.V || bad) record_err(a.err);
 }
