@@ -515,6 +515,35 @@ void fem_serve_event_destroy(void *event);
 fem_status fem_serve_events_query(void *const *events, int n, int *done);
 fem_status fem_serve_launch(const fem_serve_request *request, void *block, void *event, fem_stream stream);
 
+/* fem_serve_run -- a whole request stream served in native code, with the scheduling of
+ * the serving loop (continuous batching; not in the paper). Request r arrives arrival[r]
+ * seconds (0 <= arrival < 1e9) after the call starts and joins a FIFO queue. A queued request
+ * is admitted as soon as one of n_slots (1..FEM_SERVE_MAX_SLOTS) slots -- a stream and a
+ * completion event, created and destroyed by the call -- is free and a first-fit arena over
+ * `pool` (device memory, pool_bytes bytes, aligned to `alignment`: a power of two >= 256)
+ * holds footprint[r] bytes rounded up to `alignment`; with backfill != 0 a later request that
+ * fits overtakes a head that does not. Admission zeroes *host_status (if set) and launches
+ * reqs[r] with fem_serve_launch into its block (block_bytes taken from footprint[r]);
+ * completion is observed by polling the events, and the call returns when every request has
+ * finished. results[r] (caller-owned, n entries) receives t_arrive, t_admit, t_done in
+ * seconds from the start of the loop (-1 where the request did not get that far), status
+ * (FEM_SERVE_DONE; FEM_SERVE_REJECTED: its footprint exceeds the arena, on arrival;
+ * FEM_SERVE_FAILED: its kernels set device error bits, in `bits`, see fem_serve_launch;
+ * FEM_SERVE_REFUSED: fem_serve_launch refused its descriptor, an argument error, and the
+ * stream went on). Returns FEM_ERR_ARG for bad arguments (before anything runs) and
+ * FEM_ERR_CUDA when the runtime fails (an event query or enqueue error; the requests in
+ * flight are waited for before it returns). */
+#define FEM_SERVE_MAX_SLOTS 64
+enum { FEM_SERVE_DONE = 0, FEM_SERVE_REJECTED = 1, FEM_SERVE_FAILED = 2, FEM_SERVE_REFUSED = 3 };
+typedef struct {
+    double t_arrive, t_admit, t_done;
+    int32_t status;
+    uint32_t bits;
+} fem_serve_result;
+fem_status fem_serve_run(const fem_serve_request *reqs, const int64_t *footprint, const double *arrival, int n,
+                         void *pool, int64_t pool_bytes, int64_t alignment, int n_slots, int backfill,
+                         fem_serve_result *results);
+
 /* ---------------------------------------------------------------------------------
  * Throughput probes for the roofline (not part of the method): each thread runs
  * `iters` iterations of 8 independent dependent chains of the chosen operation and

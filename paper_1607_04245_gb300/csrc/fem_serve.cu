@@ -2,8 +2,9 @@
 // uploads a request's inputs (one pinned host block laid out like the leading part of its
 // device block), runs its kernels, downloads its results and records its completion
 // event, all on the request's stream; a second call tests many completion events at
-// once. The host-side scheduler (arrival, admission by arena footprint, statistics) stays
-// above the C ABI; what it calls per request is these two functions.
+// once. A host-side scheduler above the C ABI (arrival, admission by arena footprint,
+// statistics) calls these two per request; fem_serve_run, at the end of this file, is the
+// same scheduling as one native call over a whole stream.
 #include "fem_internal.cuh"
 
 using namespace fem;
@@ -152,5 +153,160 @@ extern "C" fem_status fem_serve_launch(const fem_serve_request *r, void *block, 
     }
     if (e == cudaSuccess) e = cudaEventRecord(static_cast<cudaEvent_t>(event), stream);
     if (e != cudaSuccess) return fail(FEM_ERR_CUDA, "fem_serve_launch: %s", cudaGetErrorString(e));
+    return FEM_OK;
+}
+
+// ------------------------------------------------------------------ the whole loop in native code
+//
+// fem_serve_run runs a stream of requests the way the host scheduler of serving.py does --
+// a FIFO of arrived requests, admission as soon as a slot (a stream and its completion
+// event) is free and the arena holds the request's footprint, backfill past a head that
+// does not fit, completion by event -- without returning to the caller per request: the
+// per-request host work is the launch call itself plus a few container operations.
+
+#include <algorithm>
+#include <chrono>
+#include <deque>
+#include <thread>
+#include <vector>
+
+namespace {
+
+struct ServeRun {
+    int n_slots;
+    std::vector<cudaStream_t> streams;
+    std::vector<cudaEvent_t> events;
+    fem_arena *arena = nullptr;
+    explicit ServeRun(int n) : n_slots(n), streams(n, nullptr), events(n, nullptr) {}
+    ~ServeRun() {
+        for (int s = 0; s < n_slots; ++s) {
+            if (streams[s]) cudaStreamSynchronize(streams[s]);  // nothing of ours stays in flight
+            if (events[s]) cudaEventDestroy(events[s]);
+            if (streams[s]) cudaStreamDestroy(streams[s]);
+        }
+        if (arena) fem_arena_destroy(arena);
+    }
+};
+
+}  // namespace
+
+extern "C" fem_status fem_serve_run(const fem_serve_request *reqs, const int64_t *footprint, const double *arrival,
+                                    int n, void *pool, int64_t pool_bytes, int64_t alignment, int n_slots,
+                                    int backfill, fem_serve_result *results) {
+    if (n < 0 || n_slots < 1 || n_slots > FEM_SERVE_MAX_SLOTS)
+        return fail(FEM_ERR_ARG, "n = %d, n_slots = %d (1..%d)", n, n_slots, FEM_SERVE_MAX_SLOTS);
+    if (n == 0) return FEM_OK;
+    if (!reqs || !footprint || !arrival || !results || !pool) return fail(FEM_ERR_ARG, "a NULL argument");
+    if (pool_bytes <= 0) return fail(FEM_ERR_ARG, "pool_bytes must be positive");
+    if (alignment < 256 || (alignment & (alignment - 1)) != 0)
+        return fail(FEM_ERR_ARG, "alignment = %lld, must be a power of two >= 256", static_cast<long long>(alignment));
+    if (reinterpret_cast<uintptr_t>(pool) % static_cast<uintptr_t>(alignment) != 0)
+        return fail(FEM_ERR_ARG, "pool is not aligned to %lld bytes", static_cast<long long>(alignment));
+    for (int i = 0; i < n; ++i)
+        if (!(arrival[i] >= 0.0 && arrival[i] < 1e9) || footprint[i] < 0)
+            return fail(FEM_ERR_ARG, "request %d: arrival %g or footprint %lld", i, arrival[i],
+                        static_cast<long long>(footprint[i]));
+    ServeRun run(n_slots);
+    fem_status st = fem_arena_create(pool_bytes, alignment, &run.arena);
+    if (st != FEM_OK) return st;
+    for (int s = 0; s < n_slots; ++s) {
+        cudaError_t e = cudaStreamCreateWithFlags(&run.streams[s], cudaStreamNonBlocking);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&run.events[s], cudaEventDisableTiming);
+        if (e != cudaSuccess) return fail(FEM_ERR_CUDA, "fem_serve_run: %s", cudaGetErrorString(e));
+    }
+    const int64_t capacity = fem_arena_capacity(run.arena);
+    auto rounded = [&](int64_t b) { return b == 0 ? alignment : (b + alignment - 1) / alignment * alignment; };
+    std::vector<int> order(n);
+    for (int i = 0; i < n; ++i) order[i] = i;
+    std::stable_sort(order.begin(), order.end(), [&](int x, int y) { return arrival[x] < arrival[y]; });
+    for (int i = 0; i < n; ++i) results[i] = fem_serve_result{-1.0, -1.0, -1.0, -1, 0u};
+    struct Slot {
+        int req = -1;
+        int64_t offset = 0;
+        bool refused = false;  // its launch was refused: nothing but (maybe) its upload ran
+    };
+    std::vector<Slot> slots(n_slots);
+    std::vector<int> free_slots;
+    for (int s = n_slots - 1; s >= 0; --s) free_slots.push_back(s);
+    std::deque<int> queue;
+    const auto t0 = std::chrono::steady_clock::now();
+    auto now_s = [&]() { return std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count(); };
+    int next = 0, finished = 0, inflight = 0;
+    while (finished < n) {
+        const double t = now_s();
+        while (next < n && arrival[order[next]] <= t) {
+            const int r = order[next++];
+            results[r].t_arrive = arrival[r];
+            if (rounded(footprint[r]) > capacity) {  // can never run: rejected on arrival
+                results[r].t_done = now_s();
+                results[r].status = FEM_SERVE_REJECTED;
+                ++finished;
+            } else {
+                queue.push_back(r);
+            }
+        }
+        bool progressed = false;
+        if (!free_slots.empty() && !queue.empty()) {
+            int64_t largest = fem_arena_largest_free(run.arena);
+            for (size_t i = 0; i < queue.size() && !free_slots.empty();) {
+                const int r = queue[i];
+                int64_t off = 0;
+                if (rounded(footprint[r]) > largest || fem_arena_alloc(run.arena, footprint[r], &off) != FEM_OK) {
+                    if (!backfill) break;
+                    ++i;
+                    continue;
+                }
+                const int s = free_slots.back();
+                free_slots.pop_back();
+                if (reqs[r].host_status) *static_cast<volatile unsigned *>(reqs[r].host_status) = 0u;
+                fem_serve_request rq = reqs[r];
+                rq.block_bytes = footprint[r];
+                results[r].t_admit = now_s();
+                st = fem_serve_launch(&rq, static_cast<char *>(pool) + off, run.events[s], run.streams[s]);
+                bool refused = false;
+                if (st == FEM_ERR_CUDA) return st;  // the device or the runtime failed: stop
+                if (st != FEM_OK) {
+                    // a descriptor the launcher refused: the request fails, the stream goes on; its
+                    // block stays held until whatever it enqueued has drained
+                    refused = true;
+                    const cudaError_t e = cudaEventRecord(run.events[s], run.streams[s]);
+                    if (e != cudaSuccess) return fail(FEM_ERR_CUDA, "fem_serve_run: %s", cudaGetErrorString(e));
+                }
+                slots[s] = Slot{r, off, refused};
+                queue.erase(queue.begin() + static_cast<std::ptrdiff_t>(i));
+                ++inflight;
+                progressed = true;
+                largest = fem_arena_largest_free(run.arena);
+            }
+        }
+        for (int s = 0; s < n_slots && inflight > 0; ++s) {
+            if (slots[s].req < 0) continue;
+            const cudaError_t q = cudaEventQuery(run.events[s]);
+            if (q == cudaErrorNotReady) continue;
+            const int r = slots[s].req;
+            if (q != cudaSuccess)
+                return fail(FEM_ERR_CUDA, "fem_serve_run: request %d: %s", r, cudaGetErrorString(q));
+            results[r].t_done = now_s();
+            if (slots[s].refused) {
+                results[r].status = FEM_SERVE_REFUSED;
+            } else {
+                const unsigned bits =
+                    reqs[r].host_status ? *static_cast<volatile unsigned *>(reqs[r].host_status) : 0u;
+                results[r].bits = bits;
+                results[r].status = bits ? FEM_SERVE_FAILED : FEM_SERVE_DONE;
+            }
+            fem_arena_free(run.arena, slots[s].offset);
+            slots[s] = Slot{};
+            free_slots.push_back(s);
+            --inflight;
+            ++finished;
+            progressed = true;
+        }
+        if (!progressed && inflight == 0 && queue.empty() && next < n) {
+            // idle until the next arrival: sleeps of at most 1 ms, the last 0.2 ms spun
+            const double wait = arrival[order[next]] - now_s();
+            if (wait > 2e-4) std::this_thread::sleep_for(std::chrono::duration<double>(std::min(wait - 2e-4, 1e-3)));
+        }
+    }
     return FEM_OK;
 }

@@ -122,6 +122,17 @@ class ServeRequestDesc(ctypes.Structure):
                 ("offset", ctypes.c_int64 * 12), ("block_bytes", ctypes.c_int64), ("host_status", ctypes.c_void_p)]
 
 
+class ServeResult(ctypes.Structure):
+    """ctypes mirror of fem_serve_result (include/fem.h)."""
+
+    _fields_ = [("t_arrive", ctypes.c_double), ("t_admit", ctypes.c_double), ("t_done", ctypes.c_double),
+                ("status", ctypes.c_int32), ("bits", ctypes.c_uint32)]
+
+
+# fem_serve_result.status
+NATIVE_STATUS = {0: "done", 1: "rejected", 2: "failed", 3: "failed"}
+
+
 def _serve_lib():
     L = binding.lib()
     if not getattr(L, "_serve_ready", False):
@@ -134,6 +145,10 @@ def _serve_lib():
         L.fem_serve_events_query.restype = ctypes.c_int
         L.fem_serve_launch.argtypes = [ctypes.POINTER(ServeRequestDesc), P, P, P]
         L.fem_serve_launch.restype = ctypes.c_int
+        L.fem_serve_run.argtypes = [ctypes.POINTER(ServeRequestDesc), ctypes.POINTER(ctypes.c_int64),
+                                    ctypes.POINTER(ctypes.c_double), ctypes.c_int, P, ctypes.c_int64, ctypes.c_int64,
+                                    ctypes.c_int, ctypes.c_int, ctypes.POINTER(ServeResult)]
+        L.fem_serve_run.restype = ctypes.c_int
         L.fem_serve_request_bytes.argtypes = []
         L.fem_serve_request_bytes.restype = ctypes.c_int64
         if L.fem_serve_request_bytes() != ctypes.sizeof(ServeRequestDesc):
@@ -520,22 +535,79 @@ class Scheduler:
                     time.sleep(self.idle_sleep)
                 # idle_sleep = 0: poll again at once (a short sleep costs the timer slack,
                 # ~50 us on Linux, on every completion)
-        t1 = self.clock()
-        done = [r for r in requests if r.status == "done"]
-        lat = sorted(r.latency * 1e3 for r in done) or [math.nan]
-        cells = sum(r.n_cells for r in done)
-        span = t1 - t0
+        return _stats(requests, self.clock() - t0, arrival_rate, max_inflight)
 
-        def pct(p):
-            k = max(0, min(len(lat) - 1, int(math.ceil(p / 100.0 * len(lat))) - 1))
-            return lat[k]
 
-        return ServeStats(n=n, n_done=len(done), n_rejected=sum(r.status == "rejected" for r in requests),
-                          n_failed=sum(r.status == "failed" for r in requests),
-                          makespan_s=span, cells=cells, cells_per_s=cells / span if span > 0 else math.nan,
-                          req_per_s=len(done) / span if span > 0 else math.nan, p50_ms=pct(50), p99_ms=pct(99),
-                          mean_ms=statistics.mean(lat) if done else math.nan, max_inflight=max_inflight,
-                          arrival_rate=arrival_rate)
+class NativeScheduler:
+    """The same scheduling as Scheduler (FIFO by arrival, admission when a slot and arena
+    memory are free, optional backfill), run as one native call (fem_serve_run) over the
+    whole stream: the host does no per-request work in Python. Uses the executor's device
+    pool and slot count; the call creates its own streams and events and its own arena over
+    the pool, so the executor must have nothing in flight."""
+
+    def __init__(self, executor, backfill: bool = True):
+        self.ex = executor
+        self.backfill = backfill
+        self._L = _serve_lib()
+
+    def run(self, requests: List[Request], arrival_rate: float = math.nan) -> ServeStats:
+        if getattr(self.ex, "inflight", None):
+            raise RuntimeError("the executor has requests in flight")
+        n = len(requests)
+        descs = (ServeRequestDesc * max(1, n))()
+        foot = (ctypes.c_int64 * max(1, n))()
+        arr = (ctypes.c_double * max(1, n))()
+        for k, r in enumerate(requests):
+            descs[k] = r.desc if r.desc is not None else r.build_desc()
+            foot[k] = footprint(r)
+            arr[k] = float(r.arrival)
+        res = (ServeResult * max(1, n))()
+        st = self._L.fem_serve_run(descs, foot, arr, n, ctypes.c_void_p(self.ex.pool_ptr), self.ex.capacity, ALIGN,
+                                   self.ex.n_slots, 1 if self.backfill else 0, res)
+        if st != 0:
+            raise binding.FemError("fem_serve_run", st, self._L.fem_last_error().decode())
+        # the loop's own clock starts after its streams are made: place it at the end of the call
+        span = max((res[k].t_done for k in range(n)), default=0.0)
+        base = time.perf_counter() - span
+        at = lambda x: math.nan if x < 0 else base + x
+        for k, r in enumerate(requests):
+            x = res[k]
+            r.t_arrive, r.t_admit, r.t_done = at(x.t_arrive), at(x.t_admit), at(x.t_done)
+            r.status = NATIVE_STATUS.get(x.status, "failed")
+            r.error = ""
+            if x.status == 1:
+                r.error = "footprint exceeds the device arena"
+            elif x.status == 2:
+                bits = int(x.bits)
+                r.error = "; ".join(t for b, t in STATUS_TEXT.items() if bits & b) or f"device error bits {bits}"
+            elif x.status == 3:
+                r.error = "launch refused (argument error)"
+        # most requests in flight at once, from the admission and completion times
+        ev = sorted([(x.t_admit, 1) for x in res[:n] if x.t_admit >= 0] +
+                    [(x.t_done, -1) for x in res[:n] if x.t_admit >= 0])
+        cur = peak = 0
+        for _, d in ev:
+            cur += d
+            peak = max(peak, cur)
+        return _stats(requests, span, arrival_rate, max_inflight=peak)
+
+
+def _stats(requests, span, arrival_rate, max_inflight) -> ServeStats:
+    n = len(requests)
+    done = [r for r in requests if r.status == "done"]
+    lat = sorted(r.latency * 1e3 for r in done) or [math.nan]
+    cells = sum(r.n_cells for r in done)
+
+    def pct(p):
+        k = max(0, min(len(lat) - 1, int(math.ceil(p / 100.0 * len(lat))) - 1))
+        return lat[k]
+
+    return ServeStats(n=n, n_done=len(done), n_rejected=sum(r.status == "rejected" for r in requests),
+                      n_failed=sum(r.status == "failed" for r in requests),
+                      makespan_s=span, cells=cells, cells_per_s=cells / span if span > 0 else math.nan,
+                      req_per_s=len(done) / span if span > 0 else math.nan, p50_ms=pct(50), p99_ms=pct(99),
+                      mean_ms=statistics.mean(lat) if done else math.nan, max_inflight=max_inflight,
+                      arrival_rate=arrival_rate)
 
 
 def request_log(requests, t0: float = None) -> List[dict]:

@@ -252,3 +252,32 @@ def test_serve_launch_rejects_a_status_word_the_device_cannot_reach(lib):
     d.host_status = word.ctypes.data
     st = lib.fem_serve_launch(ctypes.byref(d), P(0x1000), P(0x1000), None)
     assert st in (-1, -3)  # FEM_ERR_ARG (or FEM_ERR_CUDA where no CUDA driver answers the query)
+
+
+def test_serve_run_validation(lib):
+    """Argument checks of the native serving loop, all made before any CUDA call."""
+    from paper_1607_04245_gb300.serving import ServeRequestDesc, ServeResult
+
+    P, i64, f64 = ctypes.c_void_p, ctypes.c_int64, ctypes.c_double
+    lib.fem_serve_run.argtypes = [ctypes.POINTER(ServeRequestDesc), ctypes.POINTER(i64), ctypes.POINTER(f64),
+                                  ctypes.c_int, P, i64, i64, ctypes.c_int, ctypes.c_int, ctypes.POINTER(ServeResult)]
+    lib.fem_serve_run.restype = ctypes.c_int
+    d = (ServeRequestDesc * 2)()
+    foot = (i64 * 2)(4096, 8192)
+    arr = (f64 * 2)(0.0, 0.001)
+    res = (ServeResult * 2)()
+    pool = P(1 << 20)  # never dereferenced on the host
+    run = lambda n=2, pool=pool, nbytes=1 << 20, align=256, slots=4, foot=foot, arr=arr, res=res: lib.fem_serve_run(
+        d, foot, arr, n, pool, nbytes, align, slots, 1, res)
+    assert run(n=0) == 0  # nothing to serve: returns at once
+    assert run(slots=0) == -1 and run(slots=65) == -1
+    assert run(n=-1) == -1
+    assert run(pool=None) == -1 and run(res=None) == -1
+    assert run(nbytes=0) == -1
+    assert run(align=100) == -1 and run(align=128) == -1
+    assert run(pool=P((1 << 20) + 16)) == -1  # not aligned to the arena's alignment
+    assert b"aligned" in lib.fem_last_error()
+    assert run(arr=(f64 * 2)(0.0, -1.0)) == -1
+    assert run(arr=(f64 * 2)(0.0, float("nan"))) == -1
+    assert run(foot=(i64 * 2)(4096, -1)) == -1
+    assert ctypes.sizeof(ServeResult) == 32
