@@ -1123,6 +1123,11 @@ def run_ours(args):
         rows["serving"] = measure_serving(device, args.serving_requests)
 
     e2e = measure_e2e(case, "mixed", device, max(3, args.steps // 100), 3)
+    # every measured launch's device-side status: a bounded wait that gave up or a mesh error
+    # would make the timed work incomplete (0 = FEM_OK)
+    device_status = fem.fem_device_error()
+    if device_status != 0:
+        print(f"bench: fem_device_error() = {device_status} after the measured launches", file=sys.stderr)
 
     line = {"metric": METRIC, "value": value, "unit": "cells/s", "n_gpus": ws, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_per_step, "ms_median": row["ms_median"],
@@ -1150,7 +1155,8 @@ def run_ours(args):
             "cpu_baseline": cpu_baseline(case) if (ws == 1 and not args.no_cpu_baseline) else None,
             "e2e": e2e, "gpu_launches": args.steps,
             "clocks": clocks, "rows": rows,
-            "served_p99_ms": rows.get("serving", {}).get("poisson", {}).get("p99_ms")}
+            "served_p99_ms": rows.get("serving", {}).get("poisson", {}).get("p99_ms"),
+            "device_status": device_status}
     print(json.dumps(line))
     barrier(dist, ws)
     return 0

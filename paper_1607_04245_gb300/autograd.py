@@ -4,6 +4,10 @@ forward  : r = fem_integrate_laplacian(u, K)            (element vectors [dim+1]
 backward : for an incoming gradient lambda = dL/dr, the hand-written adjoint kernels
            of fem_adjoint_laplacian return dL/dK (per quadrature point) and dL/du
            (per vertex, summed over the vertex-to-cell lists in a fixed order).
+
+Like every call of the library, the kernels report a bounded device-side wait that gave up,
+or a bad mesh, through the device error word rather than an exception: a training loop that
+needs the guarantee calls fem_device_error() (one synchronisation) after its steps.
 """
 
 from __future__ import annotations
