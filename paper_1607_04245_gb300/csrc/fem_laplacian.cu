@@ -162,8 +162,10 @@ __device__ __forceinline__ void lap_cell(const double (&xs)[DIM + 1][DIM],
 }
 
 // Direct kernel: one thread owns CPT consecutive cells and reads the cell-indexed rows
-// with (vector) loads from global memory. Used for any quadrature size, for inputs whose
-// rows are not 16-byte aligned, and where the staged kernel's stages do not fit.
+// with (vector) loads from global memory. Used where neither the pair kernel (float32
+// forms: an even cell count, 8-byte aligned rows) nor the staged kernel (float64 form:
+// 16-byte aligned rows, stages that fit in shared memory) applies, and by the host-buffer
+// path, which reads page-locked host memory.
 template <int DIM, int P, int CPT, int NQ, bool ADJ>
 __global__ void __launch_bounds__(kBlock) lap_kernel(const __grid_constant__ LapArgs a) {
     constexpr int NB = DIM + 1;
@@ -396,7 +398,7 @@ static fem_status launch_fields(const FieldsArgs &fa, bool vec, cudaStream_t s) 
     return check_launch("fem_integrate_laplacian_fields");
 }
 
-// ------------------------------------------------------------------ staged kernel
+// ------------------------------------------------------------------ mixed-form fallback and cell pairs
 
 // Float64 recomputation of one cell of the mixed form (badly shaped or non-finite):
 // float64 geometry and sums from the gathered coordinates and the float32 values.
@@ -717,12 +719,13 @@ __device__ __forceinline__ void store_cells(const LapArgs &a, int nq, int64_t c,
     }
 }
 
-// The consumer work of one chunk: thread j0/kCPT's cells j0 .. j0+kCPT-1 of the chunk
-// starting at cell c0, rows read from one shared-memory stage.
+// The consumer work of one chunk (float64 form): thread j0/kCPT's cells j0 .. j0+kCPT-1 of
+// the chunk starting at cell c0, rows read from one shared-memory stage.
 template <int DIM, int P, int NQ, bool ADJ>
 __device__ __forceinline__ void lap_chunk(const LapArgs &a, const double *const (&X)[DIM], int nq,
                                           const int32_t *sc, const val_t<P> *sK, const val_t<P> *sL, int j0,
                                           int64_t c0, uint32_t &vmax, bool &bad_det) {
+    static_assert(P == FEM_FP64, "the float32 forms take the pair kernel");
     constexpr int NB = DIM + 1;
     using T = val_t<P>;
     const T *__restrict__ u = static_cast<const T *>(a.u);
@@ -745,74 +748,31 @@ __device__ __forceinline__ void lap_chunk(const LapArgs &a, const double *const 
         }
     }
     T r[NB][kCPT], tfv[kCPT];
-    if constexpr (P == FEM_FP64) {
-        qsum_t<P> ks[kCPT];
+    qsum_t<P> ks[kCPT];
 #pragma unroll(NQ > 0 ? NQ : 1)
-        for (int q = 0; q < nq; ++q) {
-            T kr[kCPT];
-            lds_row<kCPT>(sK + q * kTile + j0, kr);
-#pragma unroll
-            for (int c = 0; c < kCPT; ++c) {
-                if (q == 0) ks[c].first(weight<P>(a.w, 0), kr[c]);
-                else ks[c].add(weight<P>(a.w, q), kr[c]);
-            }
-        }
+    for (int q = 0; q < nq; ++q) {
+        T kr[kCPT];
+        lds_row<kCPT>(sK + q * kTile + j0, kr);
 #pragma unroll
         for (int c = 0; c < kCPT; ++c) {
-            double xs[NB][DIM];
-            T uu[NB], rr[NB], tf = T(0), ll[NB];
-#pragma unroll
-            for (int b = 0; b < NB; ++b) {
-                uu[b] = ld_gather(u + v[c][b]);
-                ll[b] = ADJ ? lv[c][b] : T(0);
-            }
-            gather_coords<DIM>(X, v[c], xs);
-            lap_cell<DIM, P, ADJ>(xs, uu, ll, ks[c], a.tau2, rr, tf, ids_repeat<NB>(v[c]), bad_det);
-#pragma unroll
-            for (int b = 0; b < NB; ++b) r[b][c] = rr[b];
-            tfv[c] = tf;
+            if (q == 0) ks[c].first(weight<P>(a.w, 0), kr[c]);
+            else ks[c].add(weight<P>(a.w, q), kr[c]);
         }
-    } else {
-        constexpr int NP = kCPT / 2;
-        qsum2_t<P> ks[NP];
-#pragma unroll(NQ > 0 ? NQ : 1)
-        for (int q = 0; q < nq; ++q) {
-            T kr[kCPT];
-            lds_row<kCPT>(sK + q * kTile + j0, kr);
-            const float wq = a.w.wf[q];
+    }
 #pragma unroll
-            for (int p = 0; p < NP; ++p) {
-                const f2 kp = f2_make(kr[2 * p], kr[2 * p + 1]);
-                if (q == 0) ks[p].first(wq, kp);
-                else ks[p].add(wq, kp);
-            }
+    for (int c = 0; c < kCPT; ++c) {
+        double xs[NB][DIM];
+        T uu[NB], rr[NB], tf = T(0), ll[NB];
+#pragma unroll
+        for (int b = 0; b < NB; ++b) {
+            uu[b] = ld_gather(u + v[c][b]);
+            ll[b] = ADJ ? lv[c][b] : T(0);
         }
-        bool ok[kCPT];
+        gather_coords<DIM>(X, v[c], xs);
+        lap_cell<DIM, P, ADJ>(xs, uu, ll, ks[c], a.tau2, rr, tf, ids_repeat<NB>(v[c]), bad_det);
 #pragma unroll
-        for (int p = 0; p < NP; ++p) {
-            f2 uu[NB], ll[NB], rr[NB], tf = zero<f2>();
-#pragma unroll
-            for (int b = 0; b < NB; ++b) {
-                uu[b] = f2_make(ld_gather(u + v[2 * p][b]), ld_gather(u + v[2 * p + 1][b]));
-                ll[b] = ADJ ? f2_make(lv[2 * p][b], lv[2 * p + 1][b]) : zero<f2>();
-            }
-            lap_pair<DIM, P, ADJ>(X, v[2 * p], v[2 * p + 1], uu, ll, ks[p], a.tau2, rr, tf, ok[2 * p],
-                                  ok[2 * p + 1]);
-            if constexpr (P == FEM_FP32)
-                bad_det |= !ok[2 * p] | !ok[2 * p + 1] | ids_repeat<NB>(v[2 * p]) | ids_repeat<NB>(v[2 * p + 1]);
-#pragma unroll
-            for (int b = 0; b < NB; ++b) r[b][2 * p] = f2_x(rr[b]), r[b][2 * p + 1] = f2_y(rr[b]);
-            tfv[2 * p] = f2_x(tf), tfv[2 * p + 1] = f2_y(tf);
-        }
-        store_cells<DIM, P, ADJ>(a, nq, c0 + j0, r, tfv);
-        if constexpr (P == FEM_FP32_MIXED) {
-#pragma unroll
-            for (int c = 0; c < kCPT; ++c)
-                if (!ok[c])
-                    lap_fallback_store<DIM, ADJ>(a, c0 + j0 + c,
-                                                 (c & 1) ? ks[c / 2].value_f64_y() : ks[c / 2].value_f64_x());
-        }
-        return;
+        for (int b = 0; b < NB; ++b) r[b][c] = rr[b];
+        tfv[c] = tf;
     }
     store_cells<DIM, P, ADJ>(a, nq, c0 + j0, r, tfv);
 }
@@ -892,20 +852,22 @@ static fem_status launch_lap(const LapArgs &a, bool vec, bool pairs, cudaStream_
         }
     }
     if constexpr (P != FEM_FP64) {
-        // float32 forms: the pair kernel (the bulk-copy staged kernel is kept for float64)
+        // float32 forms: the pair kernel (the bulk-copy staged kernel is the float64 form's)
         if (staged_ok && pairs) {
             if (native_nq) launch_pair<DIM, P, DIM + 1, ADJ>(a, s);
             else launch_pair<DIM, P, 0, ADJ>(a, s);
             return check_launch(ADJ ? "fem_adjoint_laplacian" : "fem_integrate_laplacian");
         }
     }
-#ifndef FEM_LAP_DIRECT
-    if (staged_ok && vec && 2u * sb <= kStageMax) {
-        if (a.w.nq == DIM + 1 && DIM == 3) st = launch_staged<DIM, P, 4, ADJ>(a, sb, s);
-        else if (a.w.nq == 3 && DIM == 2) st = launch_staged<DIM, P, 3, ADJ>(a, sb, s);
-        else st = launch_staged<DIM, P, 0, ADJ>(a, sb, s);
-    } else
-#endif
+    if constexpr (P == FEM_FP64) {
+        if (staged_ok && vec && 2u * sb <= kStageMax) {
+            if (a.w.nq == DIM + 1 && DIM == 3) st = launch_staged<DIM, P, 4, ADJ>(a, sb, s);
+            else if (a.w.nq == 3 && DIM == 2) st = launch_staged<DIM, P, 3, ADJ>(a, sb, s);
+            else st = launch_staged<DIM, P, 0, ADJ>(a, sb, s);
+            if (st != FEM_OK) return st;
+            return check_launch(ADJ ? "fem_adjoint_laplacian" : "fem_integrate_laplacian");
+        }
+    }
     if (vec && native_nq) {
         auto k = lap_kernel<DIM, P, 4, DIM + 1, ADJ>;
         int grid = grid_for((a.C + 3) / 4, kBlock, reinterpret_cast<const void *>(k));
@@ -919,7 +881,6 @@ static fem_status launch_lap(const LapArgs &a, bool vec, bool pairs, cudaStream_
         int grid = grid_for(a.C, kBlock, reinterpret_cast<const void *>(k));
         k<<<grid, kBlock, 0, s>>>(a);
     }
-    if (st != FEM_OK) return st;
     return check_launch(ADJ ? "fem_adjoint_laplacian" : "fem_integrate_laplacian");
 }
 

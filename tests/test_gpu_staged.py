@@ -1,9 +1,10 @@
-"""Parity of the staged (bulk-copy pipelined) kernels at the edges of their tiling.
+"""Parity at the edges of the kernels' tilings, in every precision form.
 
-Inputs whose cell-indexed rows are 16-byte aligned (n_cells a multiple of 4) run the
-persistent staged kernel: tiles of 1024 cells, a partial last tile, and quadrature
-rules of any size (large rules whose stages do not fit shared memory take the direct
-kernel). Also covered: the bounded device-side wait and its error status.
+Float64 inputs whose cell-indexed rows are 16-byte aligned (n_cells a multiple of 4) run
+the persistent bulk-copy staged kernel: tiles of 1024 cells, a partial last tile, and
+quadrature rules of any size (large rules whose stages do not fit shared memory take the
+direct kernel); the float32 forms run the pair kernel on the same sizes. Also covered: the
+bounded device-side wait and its error status.
 """
 
 import numpy as np
