@@ -52,7 +52,17 @@ struct PwArgs {
     u32 *err;
     double w[32];
     double phi[32][4];
+    float wf[32];       // the same tables rounded to float32 (the mixed form reads these: a
+    float phif[32][4];  // float64 -> float32 conversion per point would run on the float64 pipe)
 };
+
+#if FEM_MIXED
+#define FEM_W(q) a.wf[q]
+#define FEM_PHI(q, b) a.phif[q][b]
+#else
+#define FEM_W(q) a.w[q]
+#define FEM_PHI(q, b) a.phi[q][b]
+#endif
 
 __device__ __forceinline__ void record_err(u32 *err) {
     if ((*(volatile u32 *)err & 2u) == 0u) atomicOr(err, 2u);
@@ -198,7 +208,7 @@ extern "C" __global__ void __launch_bounds__(256) fem_pointwise_kernel(const PwA
             for (int k = 0; k < FEM_NCOMP; ++k) F0[b][k] = (T)0;
         for (int q = 0; q < FEM_NQ; ++q) {
             T ph[NB], uq[FEM_NCOMP], xq[FEM_DIM], aq[FEM_NCOEF > 0 ? FEM_NCOEF : 1];
-            for (int b = 0; b < NB; ++b) ph[b] = (T)a.phi[q][b];
+            for (int b = 0; b < NB; ++b) ph[b] = (T)FEM_PHI(q, b);
             for (int k = 0; k < FEM_NCOMP; ++k) {
                 T s = ph[0] * ub[0][k];
                 for (int b = 1; b < NB; ++b) s += ph[b] * ub[b][k];
@@ -211,7 +221,7 @@ extern "C" __global__ void __launch_bounds__(256) fem_pointwise_kernel(const PwA
                 xq[i] = s;
             }
             for (int c = 0; c < FEM_NCOEF; ++c) aq[c] = coef[((i64)c * FEM_NQ + q) * C + e];
-            const T wq = (T)a.w[q];
+            const T wq = (T)FEM_W(q);
 #if FEM_HAS_F0
             T f0[FEM_NCOMP];
             for (int k = 0; k < FEM_NCOMP; ++k) f0[k] = (T)0;
@@ -251,6 +261,8 @@ struct PwArgs {
     unsigned *err;
     double w[32];
     double phi[32][4];
+    float wf[32];
+    float phif[32][4];
 };
 static_assert(FEM_MAX_QPTS == 32, "the generated argument block holds 32 quadrature points");
 
@@ -453,6 +465,8 @@ extern "C" fem_status fem_integrate_pointwise(const char *f0_src, const char *f1
             a.phi[q][0] = 1.0 - s;
             for (int b = 1; b <= dim; ++b) a.phi[q][b] = qpts[q * dim + b - 1];
         }
+        a.wf[q] = static_cast<float>(a.w[q]);
+        for (int b = 0; b < 4; ++b) a.phif[q][b] = static_cast<float>(a.phi[q][b]);
     }
     const int64_t need = (n_cells + 255) / 256, cap = int64_t(m.grid_per_sm) * sm_count();
     const unsigned grid = static_cast<unsigned>(need < cap ? need : cap);
