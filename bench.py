@@ -676,6 +676,48 @@ def measure_pcg(case, device, stream, peak, prec="fp64", rtol=1e-8, max_iter=500
                       "flushed between iterations"}
 
 
+def measure_pcg_refined(case, device, stream, residual_prec="fp64", rtol=1e-8, inner_rtol=1e-4, reps=2):
+    """The same solve by mixed-precision iterative refinement: float64 iterate, residuals
+    in residual_prec, corrections by the FP32-mixed PCG (the headline kernel as its
+    operator). Reported beside the float64 PCG on the same problem: time, outer and inner
+    iterations, the final relative residual (float64) and the difference to the float64
+    PCG's solution."""
+    import torch
+
+    import paper_1607_04245_gb300 as fem
+
+    c, d = device_case(case, "fp64", device)
+    q = c.rule
+    fixed_np, x0_np = workloads.dirichlet_problem(c)
+    ptr, idx = fem.fem_build_node2cell(d["conn"], c.n_verts)
+    fixed = torch.from_numpy(fixed_np).to(device)
+    x0 = torch.from_numpy(x0_np).to(device)
+    work = torch.empty(max(1, int(fem.binding.lib().fem_pcg_refined_work_bytes(c.dim, c.n_cells, c.n_verts,
+                                                                                 q.n_q))),
+                       dtype=torch.uint8, device=device)
+    times, outer, inner, resid, x = [], 0, 0, 0.0, None
+    for _ in range(reps + 1):
+        x = x0.clone()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        _, outer, inner, resid = fem.fem_pcg_laplacian_refined(
+            d["coords"], d["conn"], d["K"], q.points, q.weights, ptr, idx, fixed, x, max_outer=30, max_inner=5000,
+            inner_rtol=inner_rtol, rtol=rtol, work=work, residual_prec=residual_prec, stream=stream)
+        torch.cuda.synchronize()
+        times.append(time.perf_counter() - t0)
+    t = statistics.median(times[1:])
+    x64 = x0.clone()
+    fem.fem_pcg_laplacian(d["coords"], d["conn"], d["K"], q.points, q.weights, ptr, idx, fixed, x64, max_iter=5000,
+                          rtol=rtol, prec="fp64", stream=stream)
+    torch.cuda.synchronize()
+    diff = ((x - x64).abs().max() / x64.abs().max()).item()
+    return {"physics": "pcg_laplacian_refined", "dim": c.dim, "residual_prec": residual_prec, "cells": c.n_cells,
+            "verts": c.n_verts, "rtol": rtol, "inner_rtol": inner_rtol, "outer_steps": outer,
+            "inner_iterations": inner, "rel_residual": resid, "ms_per_solve": t * 1e3,
+            "rel_maxnorm_diff_vs_fp64_pcg": diff,
+            "timing": "host wall clock around the whole solve; median of 2 solves after one warm-up"}
+
+
 def measure_fields(case, prec, device, stream, flush, steps, warmup, peak, oracle_mod=None, n_fields=8):
     """n_fields nodal fields on one mesh and coefficient in one launch (the cell geometry
     computed once per cell and reused for every field)."""
@@ -1107,6 +1149,9 @@ def run_ours(args):
     for prec in ("fp64", "fp64_df"):
         if want(f"pcg_lap3d_{prec}"):
             rows[f"pcg_lap3d_{prec}"] = measure_pcg(case, device, stream, peak, prec)
+    for rprec in ("fp64", "fp64_df"):
+        if want(f"pcg_refined_lap3d_{rprec}"):
+            rows[f"pcg_refined_lap3d_{rprec}"] = measure_pcg_refined(case, device, stream, rprec)
     for prec in ("mixed", "fp64"):
         if want(f"lap3d_fields8_{prec}"):
             rows[f"lap3d_fields8_{prec}"] = measure_fields(case, prec, device, stream, flush, rsteps, args.warmup, peak,

@@ -287,6 +287,32 @@ fem_status fem_pcg_laplacian(int dim, int64_t n_cells, int64_t n_verts, const do
                              int *iters_out, double *resid_out, fem_precision prec, fem_stream stream);
 
 /* ---------------------------------------------------------------------------------
+ * fem_pcg_laplacian_refined -- the same system solved by mixed-precision iterative
+ * refinement (not in the paper): each outer step forms the true residual r = b - A x of
+ * the float64 iterate with the residual kernel in residual_prec (FEM_FP64 or FEM_FP64_DF),
+ * solves A d = r with fem_pcg_laplacian's Jacobi-PCG in FEM_FP32_MIXED (float32 values,
+ * K rounded to float32 once, to relative residual inner_rtol or max_inner iterations) and
+ * sets x += d in float64 on the free vertices. It stops when ||r|| <= rtol ||r_0|| (r_0 the
+ * residual of the initial x, both in float64) or after max_outer corrections.
+ *   K, b, x    float64 ([n_q][C], [V] or NULL, [V]: initial guess and Dirichlet values in,
+ *              solution out); the other arguments as fem_pcg_laplacian
+ *   work       caller-owned device workspace of fem_pcg_refined_work_bytes() bytes, 256-byte
+ *              aligned (holds the float32 solve's workspace, K in float32, the float64 residual)
+ *   outer_out, inner_out, resid_out (host, may be NULL): corrections made, float32 PCG
+ *              iterations in all, ||r|| / ||r_0|| of the returned x
+ * Synchronises `stream` once per outer step (the residual norm) and as fem_pcg_laplacian
+ * does inside each correction; returns when the solve has finished.
+ * ------------------------------------------------------------------------------- */
+int64_t fem_pcg_refined_work_bytes(int dim, int64_t n_cells, int64_t n_verts, int n_q);
+fem_status fem_pcg_laplacian_refined(int dim, int64_t n_cells, int64_t n_verts, const double *coords,
+                                     const int32_t *conn, const double *K, int n_q, const double *qpts,
+                                     const double *qw, const int32_t *node_ptr, const int32_t *node_idx,
+                                     const uint8_t *fixed, const double *b, double *x, int max_outer, int max_inner,
+                                     double inner_rtol, double rtol, void *work, int64_t work_bytes, int *outer_out,
+                                     int *inner_out, double *resid_out, fem_precision residual_prec,
+                                     fem_stream stream);
+
+/* ---------------------------------------------------------------------------------
  * The paper's precomputed-geometry layout (Sec. 3 and the Appendix load J^{-1} and det J
  * per cell rather than computing them), as an alternate entry for the Laplacian:
  *

@@ -138,6 +138,15 @@ __global__ void cg_init_kernel(int64_t V, const T *b, const T *Ax, const T *D, c
 // thread t: i = 256 b + t + k 256 kDotBlocks) and finish like dot_final_kernel, so every
 // sum is reproducible and independent of the device.
 
+// the product of two vector entries as a float64 term of a dot product: float32 entries are
+// multiplied in float32 and widened once (one conversion on the float64 pipe instead of
+// two and a float64 multiply); float64 entries multiply in float64
+template <class T>
+__device__ __forceinline__ double dot_term(T a, T b) {
+    if constexpr (std::is_same<T, float>::value) return static_cast<double>(a * b);
+    else return a * b;
+}
+
 // q = 0 on fixed vertices; block partial sums of p . q; the last block sums them into pq
 template <class T>
 __global__ void __launch_bounds__(256) mask_dot_kernel(int64_t V, const uint8_t *fixed, const T *p, T *q,
@@ -147,7 +156,7 @@ __global__ void __launch_bounds__(256) mask_dot_kernel(int64_t V, const uint8_t 
     for (int64_t i = int64_t(blockIdx.x) * 256 + threadIdx.x; i < V; i += int64_t(kDotBlocks) * 256) {
         T qi = q[i];
         if (fixed[i]) q[i] = qi = T(0);
-        acc += static_cast<double>(p[i]) * static_cast<double>(qi);
+        acc += dot_term(p[i], qi);
     }
     const double t = block_sum256(acc, sh);
     if (threadIdx.x == 0) partial[blockIdx.x] = t;
@@ -194,16 +203,17 @@ __global__ void __launch_bounds__(256) step_dots_kernel(int64_t V, double *sc, c
                                                         const T *D, T *x, T *r, T *z, double *partial, int max_iter,
                                                         cudaGraphConditionalHandle loop) {
     __shared__ double sh[256];
-    const double alpha = sc[S_PQ] != 0.0 ? sc[S_RZ] / sc[S_PQ] : 0.0;
+    // the updates run in the vectors' own type (float32 vectors: no float64 conversions)
+    const T alpha = static_cast<T>(sc[S_PQ] != 0.0 ? sc[S_RZ] / sc[S_PQ] : 0.0);
     double rz = 0.0, rr = 0.0;
     for (int64_t i = int64_t(blockIdx.x) * 256 + threadIdx.x; i < V; i += int64_t(kDotBlocks) * 256) {
-        x[i] = static_cast<T>(x[i] + alpha * p[i]);
-        const T ri = static_cast<T>(r[i] - alpha * q[i]);
+        x[i] = x[i] + alpha * p[i];
+        const T ri = r[i] - alpha * q[i];
         const T zi = ri / D[i];
         r[i] = ri;
         z[i] = zi;
-        rz += static_cast<double>(ri) * static_cast<double>(zi);
-        rr += static_cast<double>(ri) * static_cast<double>(ri);
+        rz += dot_term(ri, zi);
+        rr += dot_term(ri, ri);
     }
     const double t1 = block_sum256(rz, sh);
     if (threadIdx.x == 0) partial[blockIdx.x] = t1;
@@ -216,10 +226,9 @@ __global__ void __launch_bounds__(256) step_dots_kernel(int64_t V, double *sc, c
 // p = z + beta p
 template <class T>
 __global__ void dir_kernel(int64_t V, const double *sc, const T *z, T *p) {
-    const double beta = sc[S_BETA];
+    const T beta = static_cast<T>(sc[S_BETA]);
     const int64_t stride = int64_t(gridDim.x) * blockDim.x;
-    for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < V; i += stride)
-        p[i] = static_cast<T>(z[i] + beta * p[i]);
+    for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < V; i += stride) p[i] = z[i] + beta * p[i];
 }
 
 __global__ void loop_init_kernel(double *sc, double tol2) {
@@ -279,9 +288,11 @@ template <class T>
 static fem_status pcg_run(int dim, int64_t C, int64_t V, const double *coords, const int32_t *conn, const void *K,
                           int n_q, const double *qpts, const double *qw, const int32_t *ptr, const int32_t *idx,
                           const uint8_t *fixed, const void *b, void *x, int max_iter, double rtol, const Workspace &w,
-                          int *iters_out, double *resid_out, fem_precision prec, cudaStream_t s) {
+                          int *iters_out, double *resid_out, fem_precision prec, cudaStream_t s,
+                          bool diag_ready = false) {
     // the residual runs in `prec`; every other kernel sees the value type (FEM_FP64_DF
-    // values are float64)
+    // values are float64). diag_ready: w.D already holds this operator's diagonal (a
+    // repeated solve with the same workspace).
     const fem_precision vprec = prec == FEM_FP64_DF ? FEM_FP64 : prec;
     T *X = static_cast<T *>(x);
     T *D = static_cast<T *>(w.D), *r = static_cast<T *>(w.r), *z = static_cast<T *>(w.z);
@@ -292,7 +303,7 @@ static fem_status pcg_run(int dim, int64_t C, int64_t V, const double *coords, c
     fem_status st = load_quadrature(dim, n_q, qpts, qw, qwt);
     if (st != FEM_OK) return st;
     // assembled diagonal
-    {
+    if (!diag_ready) {
         const int g = static_cast<int>(std::min<int64_t>((C + 255) / 256, 4096));
         unsigned *err = device_error_word();
         if (!err) return fail(FEM_ERR_CUDA, "device error word unavailable");
@@ -430,4 +441,141 @@ extern "C" fem_status fem_pcg_laplacian(int dim, int64_t n_cells, int64_t n_vert
                                max_iter, rtol, w, iters_out, resid_out, prec, stream);
     return pcg_run<float>(dim, n_cells, n_verts, coords, conn, K, n_q, qpts, qw, node_ptr, node_idx, fixed, b, x,
                           max_iter, rtol, w, iters_out, resid_out, prec, stream);
+}
+
+// ------------------------------------------------------------------ mixed-precision refinement
+//
+// fem_pcg_laplacian_refined: iterative refinement around the float32-mixed solve. Each
+// outer step forms the true residual r = b - A x of the float64 iterate with the float64
+// (or double-float) residual kernel, solves A d = r approximately with the PCG above in the
+// FP32-mixed form (float32 values, the headline kernel as its operator), and adds d to x in
+// float64. The float32 operator differs from the float64 one by ~1e-7 relative, so each
+// outer step gains several digits and the iterate converges to the float64 solution; most
+// of the work runs at float32 speed.
+
+namespace fem {
+
+__global__ void to_f32_kernel(int64_t n, const double *a, float *b) {
+    const int64_t stride = int64_t(gridDim.x) * blockDim.x;
+    for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < n; i += stride) b[i] = static_cast<float>(a[i]);
+}
+
+// r = b - q on the free vertices, 0 on fixed ones; r32 = r rounded to float32; d32 = 0
+__global__ void refine_residual_kernel(int64_t V, const double *b, const double *q, const uint8_t *fixed, double *r,
+                                       float *r32, float *d32) {
+    const int64_t stride = int64_t(gridDim.x) * blockDim.x;
+    for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < V; i += stride) {
+        const double ri = fixed[i] ? 0.0 : (b ? b[i] : 0.0) - q[i];
+        r[i] = ri;
+        r32[i] = static_cast<float>(ri);
+        d32[i] = 0.0f;
+    }
+}
+
+// x += d on the free vertices
+__global__ void refine_update_kernel(int64_t V, const uint8_t *fixed, const float *d, double *x) {
+    const int64_t stride = int64_t(gridDim.x) * blockDim.x;
+    for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < V; i += stride)
+        if (!fixed[i]) x[i] += static_cast<double>(d[i]);
+}
+
+struct RefineWork {
+    Workspace inner;  // the float32 PCG's
+    float *K32, *r32, *d32;
+    double *elem, *q, *r, *partial, *scalars;
+};
+
+static size_t carve_refined(int64_t C, int64_t V, int dim, int n_q, void *base, RefineWork *w) {
+    Workspace inner;
+    size_t off = carve(C, V, dim, sizeof(float), base, &inner);
+    char *b = static_cast<char *>(base);
+    auto take = [&](size_t bytes) {
+        void *p = b ? b + off : nullptr;
+        off += align256(bytes);
+        return p;
+    };
+    float *K32 = static_cast<float *>(take(size_t(n_q) * size_t(C) * sizeof(float)));
+    float *r32 = static_cast<float *>(take(size_t(V) * sizeof(float)));
+    float *d32 = static_cast<float *>(take(size_t(V) * sizeof(float)));
+    double *elem = static_cast<double *>(take(size_t(dim + 1) * size_t(C) * sizeof(double)));
+    double *q = static_cast<double *>(take(size_t(V) * sizeof(double)));
+    double *r = static_cast<double *>(take(size_t(V) * sizeof(double)));
+    double *partial = static_cast<double *>(take(sizeof(double) * kDotBlocks));
+    double *scalars = static_cast<double *>(take(sizeof(double) * 2));
+    if (w) *w = RefineWork{inner, K32, r32, d32, elem, q, r, partial, scalars};
+    return off;
+}
+
+}  // namespace fem
+
+extern "C" int64_t fem_pcg_refined_work_bytes(int dim, int64_t n_cells, int64_t n_verts, int n_q) {
+    if ((dim != 2 && dim != 3) || n_cells < 0 || n_verts < 0 || n_q < 1 || n_q > FEM_MAX_QPTS) return -1;
+    return static_cast<int64_t>(carve_refined(n_cells, n_verts, dim, n_q, nullptr, nullptr));
+}
+
+extern "C" fem_status fem_pcg_laplacian_refined(int dim, int64_t n_cells, int64_t n_verts, const double *coords,
+                                                const int32_t *conn, const double *K, int n_q, const double *qpts,
+                                                const double *qw, const int32_t *node_ptr, const int32_t *node_idx,
+                                                const uint8_t *fixed, const double *b, double *x, int max_outer,
+                                                int max_inner, double inner_rtol, double rtol, void *work,
+                                                int64_t work_bytes, int *outer_out, int *inner_out,
+                                                double *resid_out, fem_precision residual_prec, fem_stream stream) {
+    fem_status st = check_common(dim, n_cells, n_verts, coords, conn);
+    if (st != FEM_OK) return st;
+    if (residual_prec != FEM_FP64 && residual_prec != FEM_FP64_DF)
+        return fail(FEM_ERR_ARG, "residual_prec must be FEM_FP64 or FEM_FP64_DF");
+    if (max_outer < 0 || max_inner < 0 || !(rtol >= 0.0) || !(inner_rtol > 0.0 && inner_rtol < 1.0))
+        return fail(FEM_ERR_ARG, "max_outer, max_inner must be >= 0, rtol >= 0 and 0 < inner_rtol < 1");
+    if (n_q < 1 || n_q > FEM_MAX_QPTS) return fail(FEM_ERR_SHAPE, "n_q = %d outside [1, %d]", n_q, FEM_MAX_QPTS);
+    if (outer_out) *outer_out = 0;
+    if (inner_out) *inner_out = 0;
+    if (resid_out) *resid_out = 0.0;
+    if (n_verts == 0) return FEM_OK;
+    if (!K || !node_ptr || !node_idx || !fixed || !x || !work) return fail(FEM_ERR_ARG, "a NULL array argument");
+    const int64_t need = fem_pcg_refined_work_bytes(dim, n_cells, n_verts, n_q);
+    if (work_bytes < need)
+        return fail(FEM_ERR_OOM, "fem_pcg_laplacian_refined: workspace of %lld bytes, %lld needed",
+                    static_cast<long long>(work_bytes), static_cast<long long>(need));
+    if (reinterpret_cast<uintptr_t>(work) & 255u) return fail(FEM_ERR_ARG, "work must be 256-byte aligned");
+    RefineWork w;
+    carve_refined(n_cells, n_verts, dim, n_q, work, &w);
+    const int gV = static_cast<int>(std::min<int64_t>((n_verts + 255) / 256, 4096));
+    const int gK = static_cast<int>(std::min<int64_t>((int64_t(n_q) * n_cells + 255) / 256, 4096));
+    to_f32_kernel<<<gK, 256, 0, stream>>>(int64_t(n_q) * n_cells, K, w.K32);
+    if ((st = check_launch("fem_pcg_laplacian_refined")) != FEM_OK) return st;
+    double rn0 = 0.0, rn = 0.0;
+    int outer = 0, inner_total = 0;
+    for (;;) {
+        // the true residual of the float64 iterate
+        if ((st = fem_integrate_laplacian(dim, n_cells, n_verts, coords, conn, x, K, n_q, qpts, qw, w.elem,
+                                          residual_prec, stream)) != FEM_OK)
+            return st;
+        if ((st = launch_gather(dim, 1, n_cells, n_verts, w.elem, node_ptr, node_idx, w.q, FEM_FP64, stream)) != FEM_OK)
+            return st;
+        refine_residual_kernel<<<gV, 256, 0, stream>>>(n_verts, b, w.q, fixed, w.r, w.r32, w.d32);
+        dot_partial_kernel<double><<<kDotBlocks, 256, 0, stream>>>(n_verts, w.r, w.r, w.partial);
+        dot_final_kernel<<<1, 256, 0, stream>>>(w.partial, w.scalars);
+        double rr = 0.0;
+        cudaError_t e = cudaMemcpyAsync(&rr, w.scalars, sizeof(double), cudaMemcpyDeviceToHost, stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(stream);
+        if (e != cudaSuccess) return fail(FEM_ERR_CUDA, "fem_pcg_laplacian_refined: %s", cudaGetErrorString(e));
+        rn = std::sqrt(rr);
+        if (outer == 0) rn0 = rn;
+        if (rn <= rtol * rn0 || rn == 0.0 || outer >= max_outer) break;
+        // the correction in the FP32-mixed form: A d = r, d = 0 on the fixed vertices
+        int it = 0;
+        double res = 0.0;
+        st = pcg_run<float>(dim, n_cells, n_verts, coords, conn, w.K32, n_q, qpts, qw, node_ptr, node_idx, fixed,
+                            w.r32, w.d32, max_inner, inner_rtol, w.inner, &it, &res, FEM_FP32_MIXED, stream,
+                            outer > 0);
+        if (st != FEM_OK) return st;
+        inner_total += it;
+        refine_update_kernel<<<gV, 256, 0, stream>>>(n_verts, fixed, w.d32, x);
+        if ((st = check_launch("fem_pcg_laplacian_refined")) != FEM_OK) return st;
+        ++outer;
+    }
+    if (outer_out) *outer_out = outer;
+    if (inner_out) *inner_out = inner_total;
+    if (resid_out) *resid_out = rn0 > 0.0 ? rn / rn0 : 0.0;
+    return check_launch("fem_pcg_laplacian_refined");
 }

@@ -281,3 +281,27 @@ def test_serve_run_validation(lib):
     assert run(arr=(f64 * 2)(0.0, float("nan"))) == -1
     assert run(foot=(i64 * 2)(4096, -1)) == -1
     assert ctypes.sizeof(ServeResult) == 32
+
+
+def test_pcg_refined_validation(lib):
+    """Argument checks of the refined solve, made before any CUDA call."""
+    P, i64, cd, ci = ctypes.c_void_p, ctypes.c_int64, ctypes.c_double, ctypes.c_int
+    f = lib.fem_pcg_laplacian_refined
+    f.argtypes = [ci, i64, i64, P, P, P, ci, P, P, P, P, P, P, P, ci, ci, cd, cd, P, i64, P, P, P, ci, P]
+    f.restype = ci
+    lib.fem_pcg_refined_work_bytes.argtypes = [ci, i64, i64, ci]
+    lib.fem_pcg_refined_work_bytes.restype = i64
+    fake = P(1 << 20)
+    outer, inner, resid = ctypes.c_int(-1), ctypes.c_int(-1), ctypes.c_double(-1.0)
+    call = lambda V=0, prec=0, rtol=1e-8, inner_rtol=1e-3, mo=5, mi=100, nq=4: f(
+        3, 0, V, fake, fake, fake, nq, fake, fake, fake, fake, fake, None, fake, mo, mi, inner_rtol, rtol, fake,
+        1 << 30, ctypes.byref(outer), ctypes.byref(inner), ctypes.byref(resid), prec, None)
+    assert call(prec=1) == -1 and call(prec=2) == -1  # the residual runs in float64 or double-float
+    assert call(inner_rtol=0.0) == -1 and call(inner_rtol=1.0) == -1
+    assert call(rtol=-1.0) == -1 and call(mo=-1) == -1 and call(mi=-1) == -1
+    assert call(nq=0) == -2
+    assert call(V=0) == 0 and outer.value == 0 and inner.value == 0 and resid.value == 0.0
+    assert call(V=0, prec=3) == 0  # FEM_FP64_DF residuals
+    w = lib.fem_pcg_refined_work_bytes(3, 1000, 300, 4)
+    assert w >= lib.fem_pcg_work_bytes(3, 1000, 300, 1) + 4 * 1000 * 4 + 4 * 1000 * 8
+    assert lib.fem_pcg_refined_work_bytes(4, 1000, 300, 4) == -1
