@@ -353,6 +353,30 @@ struct PlainSum2 {
     __device__ __forceinline__ double value_f64_y() const { return double(f2_y(s)); }
 };
 
+// fixed-order sum of a vertex's list entries (the nodal gather E^T): plain in float64,
+// compensated (TwoSum) in float32
+template <class T>
+struct NodeSum {
+    T s = T(0);
+    __device__ __forceinline__ void add(T x) { s += x; }
+    __device__ __forceinline__ T value() const { return s; }
+};
+
+template <>
+struct NodeSum<float> {
+    float s = 0.0f, c = 0.0f;
+    __device__ __forceinline__ void add(float x) {
+        float t, e;
+        two_sum(s, x, t, e);
+        s = t;
+        c += e;
+    }
+    __device__ __forceinline__ float value() const { return s + c; }
+};
+
+// list entries whose loads a gather keeps in flight at once
+constexpr int kGatherBatch = 8;
+
 template <int P>
 using qsum_t = typename std::conditional<P == FEM_FP64, PlainSum<double>,
                                          typename std::conditional<P == FEM_FP32_MIXED, Dot2Sum, PlainSum<float>>::type>::type;

@@ -163,26 +163,6 @@ __global__ void sort_segments_kernel(const int32_t *ptr, int32_t *idx, int64_t V
 
 // ------------------------------------------------------------------ nodal gather
 
-template <class T>
-struct NodeSum {
-    T s = T(0);
-    __device__ __forceinline__ void add(T x) { s += x; }
-    __device__ __forceinline__ T value() const { return s; }
-};
-
-template <>
-struct NodeSum<float> {  // compensated (TwoSum) sum in float32
-    float s = 0.0f, c = 0.0f;
-    __device__ __forceinline__ void add(float x) {
-        float t, e;
-        two_sum(s, x, t, e);
-        s = t;
-        c += e;
-    }
-    __device__ __forceinline__ float value() const { return s + c; }
-};
-
-constexpr int kGatherBatch = 8;
 
 template <int NB, int NCOMP, class T>
 __global__ void gather_kernel(int64_t C, int64_t V, const T *__restrict__ elem, const int32_t *__restrict__ ptr,

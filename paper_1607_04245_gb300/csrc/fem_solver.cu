@@ -89,9 +89,10 @@ __global__ void __launch_bounds__(256) dot_final_kernel(const double *partial, d
     if (threadIdx.x == 0) *result = s[0];
 }
 
-// scalars[] layout: 0 rz, 1 pq, 2 rz_new, 3 rr, 4 (rtol ||r_0||)^2, 5 iterations done, 6 beta,
-// 7 two 32-bit block counters of the loop's reductions (see last_block)
-enum { S_RZ = 0, S_PQ = 1, S_RZNEW = 2, S_RR = 3, S_TOL2 = 4, S_ITER = 5, S_BETA = 6, S_TICKETS = 7, S_COUNT = 8 };
+// scalars[] layout: 0 gamma = r.u, 1 delta = w.u, 2 alpha, 3 beta, 4 rr = r.r,
+// 5 (rtol ||r_0||)^2, 6 iterations done, 7 the 32-bit block counter of the reduction (last_block)
+enum { S_GAMMA = 0, S_DELTA = 1, S_ALPHA = 2, S_BETA = 3, S_RR = 4, S_TOL2 = 5, S_ITER = 6, S_TICKETS = 7,
+       S_COUNT = 8 };
 
 __device__ __forceinline__ unsigned *tickets(double *sc) { return reinterpret_cast<unsigned *>(sc + S_TICKETS); }
 
@@ -120,23 +121,27 @@ __device__ __forceinline__ bool last_block(unsigned *ticket) {
     return s_last;
 }
 
-// r = b - Ax (free vertices), 0 on fixed ones; z = r / D; p = z
+// The loop is the conjugate gradient method in Chronopoulos and Gear's form (s-step CG with
+// s = 1): with u = D^-1 r, w = A u and s = A p carried as vectors, both inner products of an
+// iteration, gamma = r.u and delta = w.u, come from the same vectors at the same time, so an
+// iteration is one vector update, one operator application and one reduction:
+//     p = u + beta p,  s = w + beta s,  x += alpha p,  r -= alpha s,  u = r / D,
+//     w = A u,  gamma' = r.u,  delta = w.u,
+//     beta = gamma' / gamma,  alpha = gamma' / (delta - beta gamma' / alpha).
+// The reductions visit the vertices with dot_partial_kernel's fixed grid and order (block b,
+// thread t: i = 256 b + t + k 256 kDotBlocks) and are finished by the block that completes
+// last, so every sum is reproducible and independent of the device.
+
+// r = b - Ax on the free vertices (0 on fixed ones), u = r / D, p = s = 0
 template <class T>
-__global__ void cg_init_kernel(int64_t V, const T *b, const T *Ax, const T *D, const uint8_t *fixed, T *r, T *z,
-                               T *p) {
+__global__ void cg_init_kernel(int64_t V, const T *b, const T *Ax, const T *D, const uint8_t *fixed, T *r, T *u,
+                               T *p, T *sv) {
     const int64_t stride = int64_t(gridDim.x) * blockDim.x;
     for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < V; i += stride) {
         const T ri = fixed[i] ? T(0) : (b ? b[i] : T(0)) - Ax[i];
-        const T zi = ri / D[i];
-        r[i] = ri, z[i] = zi, p[i] = zi;
+        r[i] = ri, u[i] = ri / D[i], p[i] = T(0), sv[i] = T(0);
     }
 }
-
-
-// ---- the kernels of the device-side loop (q is restricted to the free vertices). The
-// reductions visit the vertices with dot_partial_kernel's fixed grid and order (block b,
-// thread t: i = 256 b + t + k 256 kDotBlocks) and finish like dot_final_kernel, so every
-// sum is reproducible and independent of the device.
 
 // the product of two vector entries as a float64 term of a dot product: float32 entries are
 // multiplied in float32 and widened once (one conversion on the float64 pipe instead of
@@ -147,94 +152,107 @@ __device__ __forceinline__ double dot_term(T a, T b) {
     else return a * b;
 }
 
-// q = 0 on fixed vertices; block partial sums of p . q; the last block sums them into pq
+// p = u + beta p, s = w + beta s, x += alpha p, r -= alpha s, u = r / D (in the vectors'
+// own type). On fixed vertices r, u, w and so p and s stay 0, and x keeps its value.
 template <class T>
-__global__ void __launch_bounds__(256) mask_dot_kernel(int64_t V, const uint8_t *fixed, const T *p, T *q,
-                                                       double *partial, double *sc) {
-    __shared__ double sh[256];
-    double acc = 0.0;
-    for (int64_t i = int64_t(blockIdx.x) * 256 + threadIdx.x; i < V; i += int64_t(kDotBlocks) * 256) {
-        T qi = q[i];
-        if (fixed[i]) q[i] = qi = T(0);
-        acc += dot_term(p[i], qi);
-    }
-    const double t = block_sum256(acc, sh);
-    if (threadIdx.x == 0) partial[blockIdx.x] = t;
-    if (last_block(tickets(sc))) {
-        double a = 0.0;
-        for (int i = threadIdx.x; i < kDotBlocks; i += 256) a += __ldcg(partial + i);
-        const double pq = block_sum256(a, sh);
-        if (threadIdx.x == 0) {
-            sc[S_PQ] = pq;
-            tickets(sc)[0] = 0u;
-        }
-    }
-}
-
-// In one block: rz_new and rr from the partials, beta = rz_new / rz, rz = rz_new, then
-// count the iteration and set the loop condition (not converged, fewer than max_iter; a
-// NaN residual ends the loop: every comparison with it is false).
-__device__ __forceinline__ void finish_iteration(const double *partial, double *sc, int max_iter,
-                                                 cudaGraphConditionalHandle loop, double *sh) {
-    double a = 0.0, b = 0.0;
-    for (int i = threadIdx.x; i < kDotBlocks; i += 256) a += __ldcg(partial + i), b += __ldcg(partial + kDotBlocks + i);
-    const double rz_new = block_sum256(a, sh);
-    __syncthreads();
-    const double rr = block_sum256(b, sh);
-    if (threadIdx.x == 0) {
-        const double rz = sc[S_RZ];
-        sc[S_BETA] = rz != 0.0 ? rz_new / rz : 0.0;
-        sc[S_RZNEW] = rz_new;
-        sc[S_RZ] = rz_new;
-        sc[S_RR] = rr;
-        const double it = sc[S_ITER] + 1.0;
-        sc[S_ITER] = it;
-        const bool more = it < static_cast<double>(max_iter) && rr > sc[S_TOL2] && rr > 0.0;
-        cudaGraphSetConditional(loop, more ? 1u : 0u);
-        tickets(sc)[1] = 0u;
-    }
-}
-
-// alpha = rz / pq; x += alpha p; r -= alpha q; z = r / D; block partial sums of r . z
-// (partial[0 .. kDotBlocks)) and r . r (partial[kDotBlocks .. 2 kDotBlocks)); the last block
-// finishes the iteration (finish_iteration)
-template <class T>
-__global__ void __launch_bounds__(256) step_dots_kernel(int64_t V, double *sc, const T *p, const T *q,
-                                                        const T *D, T *x, T *r, T *z, double *partial, int max_iter,
-                                                        cudaGraphConditionalHandle loop) {
-    __shared__ double sh[256];
-    // the updates run in the vectors' own type (float32 vectors: no float64 conversions)
-    const T alpha = static_cast<T>(sc[S_PQ] != 0.0 ? sc[S_RZ] / sc[S_PQ] : 0.0);
-    double rz = 0.0, rr = 0.0;
-    for (int64_t i = int64_t(blockIdx.x) * 256 + threadIdx.x; i < V; i += int64_t(kDotBlocks) * 256) {
-        x[i] = x[i] + alpha * p[i];
-        const T ri = r[i] - alpha * q[i];
-        const T zi = ri / D[i];
-        r[i] = ri;
-        z[i] = zi;
-        rz += dot_term(ri, zi);
-        rr += dot_term(ri, ri);
-    }
-    const double t1 = block_sum256(rz, sh);
-    if (threadIdx.x == 0) partial[blockIdx.x] = t1;
-    __syncthreads();
-    const double t2 = block_sum256(rr, sh);
-    if (threadIdx.x == 0) partial[kDotBlocks + blockIdx.x] = t2;
-    if (last_block(tickets(sc) + 1)) finish_iteration(partial, sc, max_iter, loop, sh);
-}
-
-// p = z + beta p
-template <class T>
-__global__ void dir_kernel(int64_t V, const double *sc, const T *z, T *p) {
-    const T beta = static_cast<T>(sc[S_BETA]);
+__global__ void cg_update_kernel(int64_t V, const double *sc, const T *w, const T *D, T *x, T *r, T *u, T *p,
+                                 T *sv) {
+    const T alpha = static_cast<T>(sc[S_ALPHA]), beta = static_cast<T>(sc[S_BETA]);
     const int64_t stride = int64_t(gridDim.x) * blockDim.x;
-    for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < V; i += stride) p[i] = z[i] + beta * p[i];
+    for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < V; i += stride) {
+        const T pi = u[i] + beta * p[i];
+        const T si = w[i] + beta * sv[i];
+        p[i] = pi;
+        sv[i] = si;
+        x[i] = x[i] + alpha * pi;
+        const T ri = r[i] - alpha * si;
+        r[i] = ri;
+        u[i] = ri / D[i];
+    }
+}
+
+// w = A u: the element vectors of u summed per vertex in list order (as the nodal gather
+// does), 0 on fixed vertices; with the block partial sums of r.u, w.u and r.r. The block
+// that finishes last forms gamma, delta and rr and the next alpha and beta; INIT (before
+// the loop): alpha = gamma / delta, beta = 0; otherwise it also counts the iteration and
+// sets the loop condition (not converged, fewer than max_iter; a NaN residual ends the loop:
+// every comparison with it is false).
+template <int NB, class T, bool INIT>
+__global__ void __launch_bounds__(256) cg_apply_dots_kernel(int64_t C, int64_t V, const T *__restrict__ elem,
+                                                            const int32_t *__restrict__ ptr,
+                                                            const int32_t *__restrict__ idx, const uint8_t *fixed,
+                                                            const T *r, const T *u, T *w, double *partial, double *sc,
+                                                            int max_iter, cudaGraphConditionalHandle loop) {
+    __shared__ double sh[256];
+    auto entry = [&](int32_t t) {
+        const int32_t cell = t / NB, a = t - cell * NB;
+        return __ldg(elem + int64_t(a) * C + cell);
+    };
+    double ru = 0.0, wu = 0.0, rr = 0.0;
+    for (int64_t n = int64_t(blockIdx.x) * 256 + threadIdx.x; n < V; n += int64_t(kDotBlocks) * 256) {
+        const int32_t b = ptr[n], e = ptr[n + 1];
+        NodeSum<T> acc;
+        int32_t j = b;
+        for (; j + kGatherBatch <= e; j += kGatherBatch) {
+            int32_t t[kGatherBatch];
+            T val[kGatherBatch];
+#pragma unroll
+            for (int i = 0; i < kGatherBatch; ++i) t[i] = __ldg(idx + j + i);
+#pragma unroll
+            for (int i = 0; i < kGatherBatch; ++i) val[i] = entry(t[i]);
+#pragma unroll
+            for (int i = 0; i < kGatherBatch; ++i) acc.add(val[i]);
+        }
+        for (; j < e; ++j) acc.add(entry(__ldg(idx + j)));
+        const T wn = fixed[n] ? T(0) : acc.value();
+        w[n] = wn;
+        const T rn = r[n], un = u[n];
+        ru += dot_term(rn, un);
+        wu += dot_term(wn, un);
+        rr += dot_term(rn, rn);
+    }
+    double t = block_sum256(ru, sh);
+    if (threadIdx.x == 0) partial[blockIdx.x] = t;
+    __syncthreads();
+    t = block_sum256(wu, sh);
+    if (threadIdx.x == 0) partial[kDotBlocks + blockIdx.x] = t;
+    __syncthreads();
+    t = block_sum256(rr, sh);
+    if (threadIdx.x == 0) partial[2 * kDotBlocks + blockIdx.x] = t;
+    if (!last_block(tickets(sc))) return;
+    double a0 = 0.0, a1 = 0.0, a2 = 0.0;
+    for (int i = threadIdx.x; i < kDotBlocks; i += 256)
+        a0 += __ldcg(partial + i), a1 += __ldcg(partial + kDotBlocks + i), a2 += __ldcg(partial + 2 * kDotBlocks + i);
+    const double gamma = block_sum256(a0, sh);
+    __syncthreads();
+    const double delta = block_sum256(a1, sh);
+    __syncthreads();
+    const double rrs = block_sum256(a2, sh);
+    if (threadIdx.x == 0) {
+        if constexpr (INIT) {
+            sc[S_ALPHA] = delta != 0.0 ? gamma / delta : 0.0;
+            sc[S_BETA] = 0.0;
+        } else {
+            const double g0 = sc[S_GAMMA], a_old = sc[S_ALPHA];
+            const double beta = g0 != 0.0 ? gamma / g0 : 0.0;
+            const double den = a_old != 0.0 ? delta - beta * gamma / a_old : delta;
+            sc[S_BETA] = beta;
+            sc[S_ALPHA] = den != 0.0 ? gamma / den : 0.0;
+            const double it = sc[S_ITER] + 1.0;
+            sc[S_ITER] = it;
+            const bool more = it < static_cast<double>(max_iter) && rrs > sc[S_TOL2] && rrs > 0.0;
+            cudaGraphSetConditional(loop, more ? 1u : 0u);
+        }
+        sc[S_GAMMA] = gamma;
+        sc[S_DELTA] = delta;
+        sc[S_RR] = rrs;
+        tickets(sc)[0] = 0u;
+    }
 }
 
 __global__ void loop_init_kernel(double *sc, double tol2) {
     sc[S_TOL2] = tol2;
     sc[S_ITER] = 0.0;
-    tickets(sc)[0] = tickets(sc)[1] = 0u;
 }
 
 // a library stream per device to capture the loop body on (capture needs a stream other
@@ -263,7 +281,7 @@ __global__ void diag_fix_kernel(int64_t V, const uint8_t *fixed, T *D) {
 static size_t align256(size_t n) { return (n + 255) & ~size_t(255); }
 
 struct Workspace {
-    void *elem, *D, *r, *z, *p, *q;
+    void *elem, *D, *r, *z, *p, *q, *sv;  // z holds u = D^-1 r, q holds w = A u, sv holds s = A p
     double *partial, *scalars;
 };
 
@@ -277,10 +295,10 @@ static size_t carve(int64_t C, int64_t V, int dim, size_t vs, void *base, Worksp
     };
     void *elem = take(size_t(dim + 1) * size_t(C) * vs);
     void *D = take(size_t(V) * vs), *r = take(size_t(V) * vs), *z = take(size_t(V) * vs);
-    void *p = take(size_t(V) * vs), *q = take(size_t(V) * vs);
-    double *partial = static_cast<double *>(take(sizeof(double) * 2 * kDotBlocks));
+    void *p = take(size_t(V) * vs), *q = take(size_t(V) * vs), *sv = take(size_t(V) * vs);
+    double *partial = static_cast<double *>(take(sizeof(double) * 3 * kDotBlocks));
     double *scalars = static_cast<double *>(take(sizeof(double) * S_COUNT));
-    if (w) *w = Workspace{elem, D, r, z, p, q, partial, scalars};
+    if (w) *w = Workspace{elem, D, r, z, p, q, sv, partial, scalars};
     return off;
 }
 
@@ -296,7 +314,7 @@ static fem_status pcg_run(int dim, int64_t C, int64_t V, const double *coords, c
     const fem_precision vprec = prec == FEM_FP64_DF ? FEM_FP64 : prec;
     T *X = static_cast<T *>(x);
     T *D = static_cast<T *>(w.D), *r = static_cast<T *>(w.r), *z = static_cast<T *>(w.z);
-    T *p = static_cast<T *>(w.p), *q = static_cast<T *>(w.q);
+    T *p = static_cast<T *>(w.p), *q = static_cast<T *>(w.q), *sv = static_cast<T *>(w.sv);
     const T *B = static_cast<const T *>(b);
     const int gV = static_cast<int>(std::min<int64_t>((V + 255) / 256, 4096));
     QuadW qwt;
@@ -322,9 +340,23 @@ static fem_status pcg_run(int dim, int64_t C, int64_t V, const double *coords, c
         if (e != FEM_OK) return e;
         return launch_gather(dim, 1, C, V, w.elem, ptr, idx, out, vprec, cs);
     };
-    auto dot = [&](const T *a, const T *c, int slot, cudaStream_t cs) {
-        dot_partial_kernel<T><<<kDotBlocks, 256, 0, cs>>>(V, a, c, w.partial);
-        dot_final_kernel<<<1, 256, 0, cs>>>(w.partial, w.scalars + slot);
+    // w = A u (0 on fixed vertices) with the iteration's inner products and scalars
+    auto apply_dots = [&](bool init, cudaGraphConditionalHandle loop, cudaStream_t cs) -> fem_status {
+        fem_status e = fem_integrate_laplacian(dim, C, V, coords, conn, z, K, n_q, qpts, qw, w.elem, prec, cs);
+        if (e != FEM_OK) return e;
+        const T *el = static_cast<const T *>(w.elem);
+        if (dim == 2) {
+            if (init) cg_apply_dots_kernel<3, T, true><<<kDotBlocks, 256, 0, cs>>>(C, V, el, ptr, idx, fixed, r, z, q,
+                                                                                    w.partial, w.scalars, 0, loop);
+            else cg_apply_dots_kernel<3, T, false><<<kDotBlocks, 256, 0, cs>>>(C, V, el, ptr, idx, fixed, r, z, q,
+                                                                                w.partial, w.scalars, max_iter, loop);
+        } else {
+            if (init) cg_apply_dots_kernel<4, T, true><<<kDotBlocks, 256, 0, cs>>>(C, V, el, ptr, idx, fixed, r, z, q,
+                                                                                    w.partial, w.scalars, 0, loop);
+            else cg_apply_dots_kernel<4, T, false><<<kDotBlocks, 256, 0, cs>>>(C, V, el, ptr, idx, fixed, r, z, q,
+                                                                                w.partial, w.scalars, max_iter, loop);
+        }
+        return FEM_OK;
     };
     auto read = [&](int slot, int n, double *v) -> fem_status {
         cudaError_t e = cudaMemcpyAsync(v, w.scalars + slot, n * sizeof(double), cudaMemcpyDeviceToHost, s);
@@ -332,11 +364,14 @@ static fem_status pcg_run(int dim, int64_t C, int64_t V, const double *coords, c
         if (e != cudaSuccess) return fail(FEM_ERR_CUDA, "fem_pcg_laplacian: %s", cudaGetErrorString(e));
         return FEM_OK;
     };
-    // r0 = b - A x0 on the free vertices
+    // r0 = b - A x0 on the free vertices, u0 = D^-1 r0, w0 = A u0, gamma0, delta0, alpha0
+    {
+        const cudaError_t e = cudaMemsetAsync(w.scalars, 0, sizeof(double) * S_COUNT, s);
+        if (e != cudaSuccess) return fail(FEM_ERR_CUDA, "fem_pcg_laplacian: %s", cudaGetErrorString(e));
+    }
     if ((st = matvec(X, q, s)) != FEM_OK) return st;
-    cg_init_kernel<T><<<gV, 256, 0, s>>>(V, B, q, D, fixed, r, z, p);
-    dot(r, z, S_RZ, s);
-    dot(r, r, S_RR, s);
+    cg_init_kernel<T><<<gV, 256, 0, s>>>(V, B, q, D, fixed, r, z, p, sv);
+    if ((st = apply_dots(true, 0, s)) != FEM_OK) return st;
     double rr0 = 0.0;
     if ((st = read(S_RR, 1, &rr0)) != FEM_OK) return st;
     const double r0 = std::sqrt(rr0);
@@ -366,15 +401,10 @@ static fem_status pcg_run(int dim, int64_t C, int64_t V, const double *coords, c
             e = cudaStreamBeginCaptureToGraph(cs, np.conditional.phGraph_out[0], nullptr, nullptr, 0,
                                               cudaStreamCaptureModeThreadLocal);
         if (e == cudaSuccess) {
-            // one iteration in 5 kernels: residual, gather, q masked with p.q (and pq), the
-            // updates with r.z and r.r (and the scalars and the loop condition), the direction
-            st = matvec(p, q, cs);
-            if (st == FEM_OK) {
-                mask_dot_kernel<T><<<kDotBlocks, 256, 0, cs>>>(V, fixed, p, q, w.partial, w.scalars);
-                step_dots_kernel<T><<<kDotBlocks, 256, 0, cs>>>(V, w.scalars, p, q, D, X, r, z, w.partial, max_iter,
-                                                                loop);
-                dir_kernel<T><<<gV, 256, 0, cs>>>(V, w.scalars, z, p);
-            }
+            // one iteration in 3 kernels: the vector updates; the residual of u; w = A u with
+            // the inner products, the scalars and the loop condition
+            cg_update_kernel<T><<<gV, 256, 0, cs>>>(V, w.scalars, q, D, X, r, z, p, sv);
+            st = apply_dots(false, loop, cs);
             cudaGraph_t body = nullptr;
             const cudaError_t e2 = cudaStreamEndCapture(cs, &body);
             if (e2 != cudaSuccess) e = e2;
