@@ -287,6 +287,21 @@ fem_status fem_pcg_laplacian(int dim, int64_t n_cells, int64_t n_verts, const do
                              int *iters_out, double *resid_out, fem_precision prec, fem_stream stream);
 
 /* ---------------------------------------------------------------------------------
+ * fem_pcg_elasticity -- the same Jacobi-PCG for linear elasticity (not in the paper): A the
+ * assembled operator of fem_integrate_elasticity (element residuals summed per vertex and
+ * component), unknowns u [dim][V] (component-major, as fem_integrate_elasticity's u), the
+ * Jacobi diagonal from the element stiffness diagonals. A vertex with fixed[v] != 0 keeps
+ * all dim components of x. lam, mu [n_q][C]; b, x [dim][V]; the rest as fem_pcg_laplacian,
+ * with a workspace of fem_pcg_elasticity_work_bytes() bytes.
+ * ------------------------------------------------------------------------------- */
+int64_t fem_pcg_elasticity_work_bytes(int dim, int64_t n_cells, int64_t n_verts, fem_precision prec);
+fem_status fem_pcg_elasticity(int dim, int64_t n_cells, int64_t n_verts, const double *coords, const int32_t *conn,
+                              const void *lam, const void *mu, int n_q, const double *qpts, const double *qw,
+                              const int32_t *node_ptr, const int32_t *node_idx, const uint8_t *fixed, const void *b,
+                              void *x, int max_iter, double rtol, void *work, int64_t work_bytes, int *iters_out,
+                              double *resid_out, fem_precision prec, fem_stream stream);
+
+/* ---------------------------------------------------------------------------------
  * fem_pcg_laplacian_refined -- the same system solved by mixed-precision iterative
  * refinement (not in the paper): each outer step forms the true residual r = b - A x of
  * the float64 iterate with the residual kernel in residual_prec (FEM_FP64 or FEM_FP64_DF),

@@ -60,6 +60,7 @@ def lib():
             "fem_integrate_laplacian_host": [ci, i64, i64, P, P, P, P, ci, P, P, P, P, i64, ci, ci, P],
             "fem_integrate_laplacian_transposed": [ci, i64, P, P, ci, P, P, P, P, ci, ci, ci, P],
             "fem_pcg_laplacian": [ci, i64, i64, P, P, P, ci, P, P, P, P, P, P, P, ci, cd, P, i64, P, P, ci, P],
+            "fem_pcg_elasticity": [ci, i64, i64, P, P, P, P, ci, P, P, P, P, P, P, P, ci, cd, P, i64, P, P, ci, P],
             "fem_pcg_laplacian_refined": [ci, i64, i64, P, P, P, ci, P, P, P, P, P, P, P, ci, ci, cd, cd, P, i64, P,
                                           P, P, ci, P],
             "fem_integrate_laplacian_geom": [ci, i64, i64, P, P, P, ci, P, P, P, P, ci, P],
@@ -80,6 +81,8 @@ def lib():
         L.fem_host_work_bytes.restype = i64
         L.fem_pcg_work_bytes.argtypes = [ci, i64, i64, ci]
         L.fem_pcg_work_bytes.restype = i64
+        L.fem_pcg_elasticity_work_bytes.argtypes = [ci, i64, i64, ci]
+        L.fem_pcg_elasticity_work_bytes.restype = i64
         L.fem_pcg_refined_work_bytes.argtypes = [ci, i64, i64, ci]
         L.fem_pcg_refined_work_bytes.restype = i64
         L.fem_prepared_record_floats.argtypes = [ci]
@@ -321,6 +324,32 @@ def fem_pcg_laplacian(coords, conn, K, qpts, qw, node_ptr, node_idx, fixed, x, b
         _dev(work, "work", torch.uint8, None, dev), int(work.numel()), ctypes.byref(iters), ctypes.byref(resid), p,
         _stream(stream))
     _check("fem_pcg_laplacian", st)
+    return x, int(iters.value), float(resid.value)
+
+
+def fem_pcg_elasticity(coords, conn, lam, mu, qpts, qw, node_ptr, node_idx, fixed, x, b=None, max_iter=1000,
+                       rtol=1e-8, work=None, prec="fp64", stream=None):
+    """Solve the assembled linear-elasticity system (x, b: [dim][V]) on the free vertices
+    (Dirichlet values of all components in x). Returns (x, iterations, relative residual)."""
+    p = precision(prec)
+    dt = value_dtype(p)
+    dim, V, C = _mesh_sizes(coords, conn)
+    nq = int(np.asarray(qw).shape[0]) if not isinstance(qw, torch.Tensor) else int(qw.shape[0])
+    dev = coords.device
+    need = int(lib().fem_pcg_elasticity_work_bytes(dim, C, V, p))
+    if work is None:
+        work = torch.empty(max(need, 1), dtype=torch.uint8, device=dev)
+    qp, w = _HostTable(qpts, (nq, dim), "qpts"), _HostTable(qw, (nq,), "qw")
+    iters, resid = ctypes.c_int(0), ctypes.c_double(0.0)
+    st = lib().fem_pcg_elasticity(
+        dim, C, V, _dev(coords, "coords", torch.float64, device=dev), _dev(conn, "conn", torch.int32, device=dev),
+        _dev(lam, "lam", dt, (nq, C), dev), _dev(mu, "mu", dt, (nq, C), dev), nq, qp.ptr, w.ptr,
+        _dev(node_ptr, "node_ptr", torch.int32, (V + 1,), dev),
+        _dev(node_idx, "node_idx", torch.int32, ((dim + 1) * C,), dev), _dev(fixed, "fixed", torch.uint8, (V,), dev),
+        None if b is None else _dev(b, "b", dt, (dim, V), dev), _dev(x, "x", dt, (dim, V), dev), int(max_iter),
+        float(rtol), _dev(work, "work", torch.uint8, None, dev), int(work.numel()), ctypes.byref(iters),
+        ctypes.byref(resid), p, _stream(stream))
+    _check("fem_pcg_elasticity", st)
     return x, int(iters.value), float(resid.value)
 
 

@@ -60,6 +60,56 @@ __global__ void lap_diag_kernel(const double *X0, int64_t C, uint32_t V, const i
     report_mesh(err, vmax, V, bad_det);
 }
 
+// element diagonals of the elasticity stiffness: for the unit displacement of component k at
+// vertex b, H = e_k g^T with g = n_b (n_0 = -(n_1 + ... + n_d)), so
+//     out[b*DIM + k][e] = (Lbar g_k^2 + Mbar (|g|^2 + g_k^2)) / |det J|
+template <int DIM, class T>
+__global__ void el_diag_kernel(const double *X0, int64_t C, uint32_t V, const int32_t *conn, const T *lam,
+                               const T *mu, int nq, QuadW w, T *out, unsigned *err) {
+    constexpr int NB = DIM + 1;
+    const double *X[DIM];
+#pragma unroll
+    for (int k = 0; k < DIM; ++k) X[k] = X0 + int64_t(k) * V;
+    uint32_t vmax = 0;
+    bool bad_det = false;
+    const int64_t stride = int64_t(gridDim.x) * blockDim.x;
+    for (int64_t e = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; e < C; e += stride) {
+        uint32_t v[NB];
+#pragma unroll
+        for (int b = 0; b < NB; ++b) v[b] = clamp_vid(conn[b * C + e], V, vmax);
+        double lbar = 0.0, mbar = 0.0;
+        for (int q = 0; q < nq; ++q) {
+            lbar += w.wd[q] * static_cast<double>(lam[q * C + e]);
+            mbar += w.wd[q] * static_cast<double>(mu[q * C + e]);
+        }
+        double xs[NB][DIM], ee[DIM][DIM], n[DIM][DIM];
+        gather_coords<DIM>(X, v, xs);
+        columns_f64<DIM>(xs, ee);
+        const double det = adjugate_rows<DIM>(ee, n);
+        bad_det |= det_bad(det) | ids_repeat<NB>(v);
+        const double s = 1.0 / fabs(det);
+#pragma unroll
+        for (int b = 0; b < NB; ++b) {
+            double g[DIM];
+#pragma unroll
+            for (int i = 0; i < DIM; ++i) {
+                if (b == 0) {
+                    g[i] = 0.0;
+#pragma unroll
+                    for (int j = 0; j < DIM; ++j) g[i] -= n[j][i];
+                } else {
+                    g[i] = n[b - 1][i];
+                }
+            }
+            const double gg = dotv<DIM>(g, g);
+#pragma unroll
+            for (int k = 0; k < DIM; ++k)
+                out[(b * DIM + k) * C + e] = static_cast<T>(s * (lbar * g[k] * g[k] + mbar * (gg + g[k] * g[k])));
+        }
+    }
+    report_mesh(err, vmax, V, bad_det);
+}
+
 // block partial sums of x . y (float64 accumulation), fixed grid and order
 template <class T>
 __global__ void __launch_bounds__(256) dot_partial_kernel(int64_t n, const T *x, const T *y, double *partial) {
@@ -132,13 +182,16 @@ __device__ __forceinline__ bool last_block(unsigned *ticket) {
 // thread t: i = 256 b + t + k 256 kDotBlocks) and are finished by the block that completes
 // last, so every sum is reproducible and independent of the device.
 
+// The vectors hold n_comp components per vertex, component-major ([n_comp][V]): entry i
+// belongs to vertex i mod V, whose Dirichlet flag covers all its components.
+
 // r = b - Ax on the free vertices (0 on fixed ones), u = r / D, p = s = 0
 template <class T>
-__global__ void cg_init_kernel(int64_t V, const T *b, const T *Ax, const T *D, const uint8_t *fixed, T *r, T *u,
-                               T *p, T *sv) {
+__global__ void cg_init_kernel(int64_t N, int64_t V, const T *b, const T *Ax, const T *D, const uint8_t *fixed,
+                               T *r, T *u, T *p, T *sv) {
     const int64_t stride = int64_t(gridDim.x) * blockDim.x;
-    for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < V; i += stride) {
-        const T ri = fixed[i] ? T(0) : (b ? b[i] : T(0)) - Ax[i];
+    for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < N; i += stride) {
+        const T ri = fixed[i % V] ? T(0) : (b ? b[i] : T(0)) - Ax[i];
         r[i] = ri, u[i] = ri / D[i], p[i] = T(0), sv[i] = T(0);
     }
 }
@@ -155,11 +208,11 @@ __device__ __forceinline__ double dot_term(T a, T b) {
 // p = u + beta p, s = w + beta s, x += alpha p, r -= alpha s, u = r / D (in the vectors'
 // own type). On fixed vertices r, u, w and so p and s stay 0, and x keeps its value.
 template <class T>
-__global__ void cg_update_kernel(int64_t V, const double *sc, const T *w, const T *D, T *x, T *r, T *u, T *p,
+__global__ void cg_update_kernel(int64_t N, const double *sc, const T *w, const T *D, T *x, T *r, T *u, T *p,
                                  T *sv) {
     const T alpha = static_cast<T>(sc[S_ALPHA]), beta = static_cast<T>(sc[S_BETA]);
     const int64_t stride = int64_t(gridDim.x) * blockDim.x;
-    for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < V; i += stride) {
+    for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < N; i += stride) {
         const T pi = u[i] + beta * p[i];
         const T si = w[i] + beta * sv[i];
         p[i] = pi;
@@ -177,39 +230,53 @@ __global__ void cg_update_kernel(int64_t V, const double *sc, const T *w, const 
 // the loop): alpha = gamma / delta, beta = 0; otherwise it also counts the iteration and
 // sets the loop condition (not converged, fewer than max_iter; a NaN residual ends the loop:
 // every comparison with it is false).
-template <int NB, class T, bool INIT>
+template <int NB, int NCOMP, class T, bool INIT>
 __global__ void __launch_bounds__(256) cg_apply_dots_kernel(int64_t C, int64_t V, const T *__restrict__ elem,
                                                             const int32_t *__restrict__ ptr,
                                                             const int32_t *__restrict__ idx, const uint8_t *fixed,
                                                             const T *r, const T *u, T *w, double *partial, double *sc,
                                                             int max_iter, cudaGraphConditionalHandle loop) {
     __shared__ double sh[256];
-    auto entry = [&](int32_t t) {
+    // list entry t = NB cell + a: element row (a, component k)
+    auto entry = [&](int32_t t, int k) {
         const int32_t cell = t / NB, a = t - cell * NB;
-        return __ldg(elem + int64_t(a) * C + cell);
+        return __ldg(elem + int64_t(a * NCOMP + k) * C + cell);
     };
     double ru = 0.0, wu = 0.0, rr = 0.0;
     for (int64_t n = int64_t(blockIdx.x) * 256 + threadIdx.x; n < V; n += int64_t(kDotBlocks) * 256) {
         const int32_t b = ptr[n], e = ptr[n + 1];
-        NodeSum<T> acc;
+        NodeSum<T> acc[NCOMP];
         int32_t j = b;
         for (; j + kGatherBatch <= e; j += kGatherBatch) {
             int32_t t[kGatherBatch];
-            T val[kGatherBatch];
+            T val[kGatherBatch][NCOMP];
 #pragma unroll
             for (int i = 0; i < kGatherBatch; ++i) t[i] = __ldg(idx + j + i);
 #pragma unroll
-            for (int i = 0; i < kGatherBatch; ++i) val[i] = entry(t[i]);
+            for (int i = 0; i < kGatherBatch; ++i)
 #pragma unroll
-            for (int i = 0; i < kGatherBatch; ++i) acc.add(val[i]);
+                for (int k = 0; k < NCOMP; ++k) val[i][k] = entry(t[i], k);
+#pragma unroll
+            for (int i = 0; i < kGatherBatch; ++i)
+#pragma unroll
+                for (int k = 0; k < NCOMP; ++k) acc[k].add(val[i][k]);
         }
-        for (; j < e; ++j) acc.add(entry(__ldg(idx + j)));
-        const T wn = fixed[n] ? T(0) : acc.value();
-        w[n] = wn;
-        const T rn = r[n], un = u[n];
-        ru += dot_term(rn, un);
-        wu += dot_term(wn, un);
-        rr += dot_term(rn, rn);
+        for (; j < e; ++j) {
+            const int32_t t = __ldg(idx + j);
+#pragma unroll
+            for (int k = 0; k < NCOMP; ++k) acc[k].add(entry(t, k));
+        }
+        const bool fx = fixed[n] != 0;
+#pragma unroll
+        for (int k = 0; k < NCOMP; ++k) {
+            const int64_t i = int64_t(k) * V + n;
+            const T wn = fx ? T(0) : acc[k].value();
+            w[i] = wn;
+            const T rn = r[i], un = u[i];
+            ru += dot_term(rn, un);
+            wu += dot_term(wn, un);
+            rr += dot_term(rn, rn);
+        }
     }
     double t = block_sum256(ru, sh);
     if (threadIdx.x == 0) partial[blockIdx.x] = t;
@@ -272,10 +339,10 @@ static cudaStream_t capture_stream() {
 
 // fixed vertices get D = 1 (their rows are the identity)
 template <class T>
-__global__ void diag_fix_kernel(int64_t V, const uint8_t *fixed, T *D) {
+__global__ void diag_fix_kernel(int64_t N, int64_t V, const uint8_t *fixed, T *D) {
     const int64_t stride = int64_t(gridDim.x) * blockDim.x;
-    for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < V; i += stride)
-        if (fixed[i] || !(D[i] > T(0))) D[i] = T(1);
+    for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < N; i += stride)
+        if (fixed[i % V] || !(D[i] > T(0))) D[i] = T(1);
 }
 
 static size_t align256(size_t n) { return (n + 255) & ~size_t(255); }
@@ -285,7 +352,7 @@ struct Workspace {
     double *partial, *scalars;
 };
 
-static size_t carve(int64_t C, int64_t V, int dim, size_t vs, void *base, Workspace *w) {
+static size_t carve(int64_t C, int64_t V, int dim, size_t vs, void *base, Workspace *w, int ncomp = 1) {
     size_t off = 0;
     char *b = static_cast<char *>(base);
     auto take = [&](size_t bytes) {
@@ -293,21 +360,29 @@ static size_t carve(int64_t C, int64_t V, int dim, size_t vs, void *base, Worksp
         off += align256(bytes);
         return p;
     };
-    void *elem = take(size_t(dim + 1) * size_t(C) * vs);
-    void *D = take(size_t(V) * vs), *r = take(size_t(V) * vs), *z = take(size_t(V) * vs);
-    void *p = take(size_t(V) * vs), *q = take(size_t(V) * vs), *sv = take(size_t(V) * vs);
+    const size_t N = size_t(ncomp) * size_t(V);
+    void *elem = take(size_t(dim + 1) * size_t(ncomp) * size_t(C) * vs);
+    void *D = take(N * vs), *r = take(N * vs), *z = take(N * vs);
+    void *p = take(N * vs), *q = take(N * vs), *sv = take(N * vs);
     double *partial = static_cast<double *>(take(sizeof(double) * 3 * kDotBlocks));
     double *scalars = static_cast<double *>(take(sizeof(double) * S_COUNT));
     if (w) *w = Workspace{elem, D, r, z, p, q, sv, partial, scalars};
     return off;
 }
 
+// the assembled operator of a solve: the Laplacian with K, or elasticity with lambda, mu
+struct Operator {
+    int physics;  // 0 Laplacian, 1 elasticity
+    const void *K, *lam, *mu;
+    int ncomp(int dim) const { return physics == 0 ? 1 : dim; }
+};
+
 template <class T>
-static fem_status pcg_run(int dim, int64_t C, int64_t V, const double *coords, const int32_t *conn, const void *K,
-                          int n_q, const double *qpts, const double *qw, const int32_t *ptr, const int32_t *idx,
-                          const uint8_t *fixed, const void *b, void *x, int max_iter, double rtol, const Workspace &w,
-                          int *iters_out, double *resid_out, fem_precision prec, cudaStream_t s,
-                          bool diag_ready = false) {
+static fem_status pcg_run(int dim, int64_t C, int64_t V, const double *coords, const int32_t *conn,
+                          const Operator &op, int n_q, const double *qpts, const double *qw, const int32_t *ptr,
+                          const int32_t *idx, const uint8_t *fixed, const void *b, void *x, int max_iter,
+                          double rtol, const Workspace &w, int *iters_out, double *resid_out, fem_precision prec,
+                          cudaStream_t s, bool diag_ready = false) {
     // the residual runs in `prec`; every other kernel sees the value type (FEM_FP64_DF
     // values are float64). diag_ready: w.D already holds this operator's diagonal (a
     // repeated solve with the same workspace).
@@ -316,7 +391,9 @@ static fem_status pcg_run(int dim, int64_t C, int64_t V, const double *coords, c
     T *D = static_cast<T *>(w.D), *r = static_cast<T *>(w.r), *z = static_cast<T *>(w.z);
     T *p = static_cast<T *>(w.p), *q = static_cast<T *>(w.q), *sv = static_cast<T *>(w.sv);
     const T *B = static_cast<const T *>(b);
-    const int gV = static_cast<int>(std::min<int64_t>((V + 255) / 256, 4096));
+    const int nc = op.ncomp(dim);
+    const int64_t N = int64_t(nc) * V;  // unknowns
+    const int gV = static_cast<int>(std::min<int64_t>((N + 255) / 256, 4096));
     QuadW qwt;
     fem_status st = load_quadrature(dim, n_q, qpts, qw, qwt);
     if (st != FEM_OK) return st;
@@ -325,36 +402,52 @@ static fem_status pcg_run(int dim, int64_t C, int64_t V, const double *coords, c
         const int g = static_cast<int>(std::min<int64_t>((C + 255) / 256, 4096));
         unsigned *err = device_error_word();
         if (!err) return fail(FEM_ERR_CUDA, "device error word unavailable");
-        if (dim == 2) lap_diag_kernel<2, T><<<g, 256, 0, s>>>(coords, C, static_cast<uint32_t>(V), conn,
-                                                                static_cast<const T *>(K), n_q, qwt,
-                                                                static_cast<T *>(w.elem), err);
-        else lap_diag_kernel<3, T><<<g, 256, 0, s>>>(coords, C, static_cast<uint32_t>(V), conn,
-                                                       static_cast<const T *>(K), n_q, qwt, static_cast<T *>(w.elem),
-                                                       err);
-        if ((st = check_launch("fem_pcg_laplacian diagonal")) != FEM_OK) return st;
-        if ((st = launch_gather(dim, 1, C, V, w.elem, ptr, idx, D, vprec, s)) != FEM_OK) return st;
-        diag_fix_kernel<T><<<gV, 256, 0, s>>>(V, fixed, D);
+        const uint32_t V32 = static_cast<uint32_t>(V);
+        T *el = static_cast<T *>(w.elem);
+        if (op.physics == 0) {
+            const T *K = static_cast<const T *>(op.K);
+            if (dim == 2) lap_diag_kernel<2, T><<<g, 256, 0, s>>>(coords, C, V32, conn, K, n_q, qwt, el, err);
+            else lap_diag_kernel<3, T><<<g, 256, 0, s>>>(coords, C, V32, conn, K, n_q, qwt, el, err);
+        } else {
+            const T *lam = static_cast<const T *>(op.lam), *mu = static_cast<const T *>(op.mu);
+            if (dim == 2) el_diag_kernel<2, T><<<g, 256, 0, s>>>(coords, C, V32, conn, lam, mu, n_q, qwt, el, err);
+            else el_diag_kernel<3, T><<<g, 256, 0, s>>>(coords, C, V32, conn, lam, mu, n_q, qwt, el, err);
+        }
+        if ((st = check_launch("fem_pcg diagonal")) != FEM_OK) return st;
+        if ((st = launch_gather(dim, nc, C, V, w.elem, ptr, idx, D, vprec, s)) != FEM_OK) return st;
+        diag_fix_kernel<T><<<gV, 256, 0, s>>>(N, V, fixed, D);
     }
+    // the element vectors of v in w.elem
+    auto residual = [&](const T *v, cudaStream_t cs) -> fem_status {
+        if (op.physics == 0)
+            return fem_integrate_laplacian(dim, C, V, coords, conn, v, op.K, n_q, qpts, qw, w.elem, prec, cs);
+        return fem_integrate_elasticity(dim, C, V, coords, conn, v, op.lam, op.mu, n_q, qpts, qw, w.elem, prec, cs);
+    };
     auto matvec = [&](const T *v, T *out, cudaStream_t cs) -> fem_status {
-        fem_status e = fem_integrate_laplacian(dim, C, V, coords, conn, v, K, n_q, qpts, qw, w.elem, prec, cs);
+        fem_status e = residual(v, cs);
         if (e != FEM_OK) return e;
-        return launch_gather(dim, 1, C, V, w.elem, ptr, idx, out, vprec, cs);
+        return launch_gather(dim, nc, C, V, w.elem, ptr, idx, out, vprec, cs);
     };
     // w = A u (0 on fixed vertices) with the iteration's inner products and scalars
     auto apply_dots = [&](bool init, cudaGraphConditionalHandle loop, cudaStream_t cs) -> fem_status {
-        fem_status e = fem_integrate_laplacian(dim, C, V, coords, conn, z, K, n_q, qpts, qw, w.elem, prec, cs);
+        fem_status e = residual(z, cs);
         if (e != FEM_OK) return e;
         const T *el = static_cast<const T *>(w.elem);
-        if (dim == 2) {
-            if (init) cg_apply_dots_kernel<3, T, true><<<kDotBlocks, 256, 0, cs>>>(C, V, el, ptr, idx, fixed, r, z, q,
-                                                                                    w.partial, w.scalars, 0, loop);
-            else cg_apply_dots_kernel<3, T, false><<<kDotBlocks, 256, 0, cs>>>(C, V, el, ptr, idx, fixed, r, z, q,
-                                                                                w.partial, w.scalars, max_iter, loop);
+        const int mi = init ? 0 : max_iter;
+        auto go = [&](auto kern) {
+            kern<<<kDotBlocks, 256, 0, cs>>>(C, V, el, ptr, idx, fixed, r, z, q, w.partial, w.scalars, mi, loop);
+        };
+        const int key = dim * 10 + nc;  // 21 22 31 33
+        if (init) {
+            if (key == 21) go(cg_apply_dots_kernel<3, 1, T, true>);
+            else if (key == 22) go(cg_apply_dots_kernel<3, 2, T, true>);
+            else if (key == 31) go(cg_apply_dots_kernel<4, 1, T, true>);
+            else go(cg_apply_dots_kernel<4, 3, T, true>);
         } else {
-            if (init) cg_apply_dots_kernel<4, T, true><<<kDotBlocks, 256, 0, cs>>>(C, V, el, ptr, idx, fixed, r, z, q,
-                                                                                    w.partial, w.scalars, 0, loop);
-            else cg_apply_dots_kernel<4, T, false><<<kDotBlocks, 256, 0, cs>>>(C, V, el, ptr, idx, fixed, r, z, q,
-                                                                                w.partial, w.scalars, max_iter, loop);
+            if (key == 21) go(cg_apply_dots_kernel<3, 1, T, false>);
+            else if (key == 22) go(cg_apply_dots_kernel<3, 2, T, false>);
+            else if (key == 31) go(cg_apply_dots_kernel<4, 1, T, false>);
+            else go(cg_apply_dots_kernel<4, 3, T, false>);
         }
         return FEM_OK;
     };
@@ -370,7 +463,7 @@ static fem_status pcg_run(int dim, int64_t C, int64_t V, const double *coords, c
         if (e != cudaSuccess) return fail(FEM_ERR_CUDA, "fem_pcg_laplacian: %s", cudaGetErrorString(e));
     }
     if ((st = matvec(X, q, s)) != FEM_OK) return st;
-    cg_init_kernel<T><<<gV, 256, 0, s>>>(V, B, q, D, fixed, r, z, p, sv);
+    cg_init_kernel<T><<<gV, 256, 0, s>>>(N, V, B, q, D, fixed, r, z, p, sv);
     if ((st = apply_dots(true, 0, s)) != FEM_OK) return st;
     double rr0 = 0.0;
     if ((st = read(S_RR, 1, &rr0)) != FEM_OK) return st;
@@ -403,7 +496,7 @@ static fem_status pcg_run(int dim, int64_t C, int64_t V, const double *coords, c
         if (e == cudaSuccess) {
             // one iteration in 3 kernels: the vector updates; the residual of u; w = A u with
             // the inner products, the scalars and the loop condition
-            cg_update_kernel<T><<<gV, 256, 0, cs>>>(V, w.scalars, q, D, X, r, z, p, sv);
+            cg_update_kernel<T><<<gV, 256, 0, cs>>>(N, w.scalars, q, D, X, r, z, p, sv);
             st = apply_dots(false, loop, cs);
             cudaGraph_t body = nullptr;
             const cudaError_t e2 = cudaStreamEndCapture(cs, &body);
@@ -467,9 +560,52 @@ extern "C" fem_status fem_pcg_laplacian(int dim, int64_t n_cells, int64_t n_vert
     const bool f64 = prec == FEM_FP64 || prec == FEM_FP64_DF;
     carve(n_cells, n_verts, dim, f64 ? 8 : 4, work, &w);
     if (f64)
-        return pcg_run<double>(dim, n_cells, n_verts, coords, conn, K, n_q, qpts, qw, node_ptr, node_idx, fixed, b, x,
+        return pcg_run<double>(dim, n_cells, n_verts, coords, conn, Operator{0, K, nullptr, nullptr}, n_q, qpts, qw,
+                               node_ptr, node_idx, fixed, b, x,
                                max_iter, rtol, w, iters_out, resid_out, prec, stream);
-    return pcg_run<float>(dim, n_cells, n_verts, coords, conn, K, n_q, qpts, qw, node_ptr, node_idx, fixed, b, x,
+    return pcg_run<float>(dim, n_cells, n_verts, coords, conn, Operator{0, K, nullptr, nullptr}, n_q, qpts, qw,
+                          node_ptr, node_idx, fixed, b, x,
+                          max_iter, rtol, w, iters_out, resid_out, prec, stream);
+}
+
+extern "C" int64_t fem_pcg_elasticity_work_bytes(int dim, int64_t n_cells, int64_t n_verts, fem_precision prec) {
+    if ((dim != 2 && dim != 3) || n_cells < 0 || n_verts < 0) return -1;
+    const size_t vs = prec == FEM_FP64 || prec == FEM_FP64_DF ? 8 : 4;
+    return static_cast<int64_t>(carve(n_cells, n_verts, dim, vs, nullptr, nullptr, dim));
+}
+
+extern "C" fem_status fem_pcg_elasticity(int dim, int64_t n_cells, int64_t n_verts, const double *coords,
+                                         const int32_t *conn, const void *lam, const void *mu, int n_q,
+                                         const double *qpts, const double *qw, const int32_t *node_ptr,
+                                         const int32_t *node_idx, const uint8_t *fixed, const void *b, void *x,
+                                         int max_iter, double rtol, void *work, int64_t work_bytes, int *iters_out,
+                                         double *resid_out, fem_precision prec, fem_stream stream) {
+    fem_status st = check_common(dim, n_cells, n_verts, coords, conn);
+    if (st != FEM_OK) return st;
+    if (prec != FEM_FP64 && prec != FEM_FP32_MIXED && prec != FEM_FP32 && prec != FEM_FP64_DF)
+        return fail(FEM_ERR_ARG, "unknown precision %d", static_cast<int>(prec));
+    if (max_iter < 0 || !(rtol >= 0.0)) return fail(FEM_ERR_ARG, "max_iter must be >= 0 and rtol >= 0");
+    if (int64_t(dim) * n_verts >= (int64_t(1) << 31)) return fail(FEM_ERR_SHAPE, "too many vertices");
+    if (n_verts == 0) {
+        if (iters_out) *iters_out = 0;
+        if (resid_out) *resid_out = 0.0;
+        return FEM_OK;
+    }
+    if (!lam || !mu || !node_ptr || !node_idx || !fixed || !x || !work)
+        return fail(FEM_ERR_ARG, "a NULL array argument");
+    const int64_t need = fem_pcg_elasticity_work_bytes(dim, n_cells, n_verts, prec);
+    if (work_bytes < need)
+        return fail(FEM_ERR_OOM, "fem_pcg_elasticity: workspace of %lld bytes, %lld needed",
+                    static_cast<long long>(work_bytes), static_cast<long long>(need));
+    if (reinterpret_cast<uintptr_t>(work) & 255u) return fail(FEM_ERR_ARG, "work must be 256-byte aligned");
+    Workspace w;
+    const bool f64 = prec == FEM_FP64 || prec == FEM_FP64_DF;
+    carve(n_cells, n_verts, dim, f64 ? 8 : 4, work, &w, dim);
+    const Operator op{1, nullptr, lam, mu};
+    if (f64)
+        return pcg_run<double>(dim, n_cells, n_verts, coords, conn, op, n_q, qpts, qw, node_ptr, node_idx, fixed, b, x,
+                               max_iter, rtol, w, iters_out, resid_out, prec, stream);
+    return pcg_run<float>(dim, n_cells, n_verts, coords, conn, op, n_q, qpts, qw, node_ptr, node_idx, fixed, b, x,
                           max_iter, rtol, w, iters_out, resid_out, prec, stream);
 }
 
@@ -595,7 +731,8 @@ extern "C" fem_status fem_pcg_laplacian_refined(int dim, int64_t n_cells, int64_
         // the correction in the FP32-mixed form: A d = r, d = 0 on the fixed vertices
         int it = 0;
         double res = 0.0;
-        st = pcg_run<float>(dim, n_cells, n_verts, coords, conn, w.K32, n_q, qpts, qw, node_ptr, node_idx, fixed,
+        st = pcg_run<float>(dim, n_cells, n_verts, coords, conn, Operator{0, w.K32, nullptr, nullptr}, n_q, qpts, qw,
+                            node_ptr, node_idx, fixed,
                             w.r32, w.d32, max_inner, inner_rtol, w.inner, &it, &res, FEM_FP32_MIXED, stream,
                             outer > 0);
         if (st != FEM_OK) return st;

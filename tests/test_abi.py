@@ -305,3 +305,25 @@ def test_pcg_refined_validation(lib):
     w = lib.fem_pcg_refined_work_bytes(3, 1000, 300, 4)
     assert w >= lib.fem_pcg_work_bytes(3, 1000, 300, 1) + 4 * 1000 * 4 + 4 * 1000 * 8
     assert lib.fem_pcg_refined_work_bytes(4, 1000, 300, 4) == -1
+
+
+def test_pcg_elasticity_validation(lib):
+    """Argument checks of the elasticity solve, made before any CUDA call."""
+    P, i64, cd, ci = ctypes.c_void_p, ctypes.c_int64, ctypes.c_double, ctypes.c_int
+    f = lib.fem_pcg_elasticity
+    f.argtypes = [ci, i64, i64, P, P, P, P, ci, P, P, P, P, P, P, P, ci, cd, P, i64, P, P, ci, P]
+    f.restype = ci
+    lib.fem_pcg_elasticity_work_bytes.argtypes = [ci, i64, i64, ci]
+    lib.fem_pcg_elasticity_work_bytes.restype = i64
+    lib.fem_pcg_work_bytes.argtypes = [ci, i64, i64, ci]
+    lib.fem_pcg_work_bytes.restype = i64
+    fake = P(1 << 20)
+    it, res = ctypes.c_int(-1), ctypes.c_double(-1.0)
+    call = lambda V=0, prec=0, rtol=1e-8, mi=100: f(3, 0, V, fake, fake, fake, fake, 4, fake, fake, fake, fake, fake,
+                                                  None, fake, mi, rtol, fake, 1 << 30, ctypes.byref(it),
+                                                  ctypes.byref(res), prec, None)
+    assert call(prec=7) == -1 and call(rtol=-1.0) == -1 and call(mi=-1) == -1
+    assert call(V=0) == 0 and it.value == 0 and res.value == 0.0
+    # three components per vertex: the vectors are three times the Laplacian solve's
+    assert lib.fem_pcg_elasticity_work_bytes(3, 1000, 300, 0) > lib.fem_pcg_work_bytes(3, 1000, 300, 0)
+    assert lib.fem_pcg_elasticity_work_bytes(4, 1000, 300, 0) == -1

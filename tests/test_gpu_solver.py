@@ -265,3 +265,76 @@ def test_iterations_match_textbook_pcg_on_oracle_operator(dim, n):
     assert abs(iters - k) <= 2, (iters, k)
     assert resid <= rtol
     assert np.abs(x.cpu().numpy() - ref).max() <= 1e-8 * np.abs(ref).max()
+
+
+def _oracle_elasticity_operator(mesh, lam, mu, rule):
+    """Dense assembled elasticity operator ([dim][V] unknowns, component-major) by probing
+    the oracle's element residuals with unit displacements."""
+    dim, V = mesh.dim, mesh.n_verts
+    N = dim * V
+    A = np.zeros((N, N))
+    for j in range(N):
+        u = np.zeros((dim, V))
+        u[j // V, j % V] = 1.0
+        r = oracle.elasticity(mesh.coords, mesh.conn, u, lam, mu, rule.points, rule.weights)
+        for a in range(dim + 1):
+            for k in range(dim):
+                np.add.at(A[k * V:(k + 1) * V, j], mesh.conn[a], r[a * dim + k])
+    return A
+
+
+def _solve_el(mesh, lam, mu, rule, fixed, x0, b, prec, rtol):
+    dt = fem.value_dtype(prec)
+    coords, conn = to_dev(mesh.coords, torch.float64), to_dev(mesh.conn, torch.int32)
+    ptr, idx = fem.fem_build_node2cell(conn, mesh.n_verts)
+    x = to_dev(x0, dt)
+    return fem.fem_pcg_elasticity(coords, conn, to_dev(lam, dt), to_dev(mu, dt), rule.points, rule.weights, ptr, idx,
+                                  to_dev(fixed.astype(np.uint8), torch.uint8), x,
+                                  b=None if b is None else to_dev(b, dt), max_iter=20000, rtol=rtol, prec=prec)
+
+
+@pytest.mark.parametrize("dim,n", [(2, 16), (3, 5)])
+def test_elasticity_patch_test_linear_solution(dim, n):
+    """Constant Lame parameters and a linear displacement held on the boundary: the linear
+    field is the exact discrete solution (patch test)."""
+    mesh = _mesh(dim, n)
+    rule = workloads.rule_for_dim(dim)
+    lam = np.full((rule.n_q, mesh.n_cells), 1.3)
+    mu = np.full((rule.n_q, mesh.n_cells), 0.7)
+    Amat = np.arange(1, dim * dim + 1, dtype=np.float64).reshape(dim, dim) / 10.0
+    g = Amat @ mesh.coords + 0.25
+    fixed = _boundary(mesh)
+    x0 = np.where(fixed[None, :], g, 0.0)
+    x, iters, resid = _solve_el(mesh, lam, mu, rule, fixed, x0, None, "fp64", 1e-13)
+    err = np.abs(x.cpu().numpy() - g).max() / np.abs(g).max()
+    assert resid <= 1e-13 and iters > 0
+    assert err <= 1e-10, err
+
+
+@pytest.mark.parametrize("dim,n", [(2, 8), (3, 3)])
+@pytest.mark.parametrize("prec,rtol,tol", [("fp64", 1e-12, 1e-9), ("fp64_df", 1e-12, 1e-9), ("mixed", 1e-5, 1e-4)])
+def test_elasticity_matches_dense_solve_of_oracle_operator(dim, n, prec, rtol, tol):
+    mesh = _mesh(dim, n)
+    rule = workloads.rule_for_dim(dim)
+    rng = np.random.default_rng(dim + 30)
+    E = rng.lognormal(0.0, 0.5, (rule.n_q, mesh.n_cells))
+    nu = rng.uniform(0.2, 0.45, (rule.n_q, mesh.n_cells))
+    lam, mu = workloads.cases.lame_from_young_poisson(E, nu)
+    V = mesh.n_verts
+    fixed = _boundary(mesh)
+    g = np.stack([np.sin(mesh.coords[0] * 2.0), mesh.coords[1] - 0.5 * mesh.coords[0]] +
+                 ([0.3 * mesh.coords[2]] if dim == 3 else []))
+    b = np.where(fixed[None, :], 0.0, rng.uniform(-1, 1, (dim, V)) / V)
+    if prec == "mixed":
+        lam, mu = (a.astype(np.float32).astype(np.float64) for a in (lam, mu))
+        b, g = (a.astype(np.float32).astype(np.float64) for a in (b, g))
+    x0 = np.where(fixed[None, :], g, 0.0)
+    x, iters, resid = _solve_el(mesh, lam, mu, rule, fixed, x0, b, prec, rtol)
+    A = _oracle_elasticity_operator(mesh, lam, mu, rule)
+    free = np.tile(~fixed, dim)
+    fx = ~free
+    ref = x0.ravel().copy()
+    ref[free] = np.linalg.solve(A[np.ix_(free, free)], b.ravel()[free] - A[np.ix_(free, fx)] @ ref[fx])
+    err = np.abs(x.cpu().numpy().astype(np.float64).ravel() - ref).max() / np.abs(ref).max()
+    assert resid <= rtol
+    assert err <= tol, (err, iters, resid)
