@@ -676,6 +676,42 @@ def measure_pcg(case, device, stream, peak, prec="fp64", rtol=1e-8, max_iter=500
                       "flushed between iterations"}
 
 
+def measure_pcg_elasticity(device, stream, prec="fp64_df", rtol=1e-8, max_iter=20000, reps=2):
+    """The device-loop Jacobi-PCG for linear elasticity on the 3D elasticity workload mesh
+    (2^21 tets), boundary held at a linear displacement, zero load."""
+    import torch
+
+    import paper_1607_04245_gb300 as fem
+
+    case = workloads.elasticity_case(3)
+    c, d = device_case(case, prec, device)
+    q = c.rule
+    x = c.mesh.coords
+    fixed_np = np.any((np.abs(x) < 1e-14) | (np.abs(x - x.max(axis=1, keepdims=True)) < 1e-14), axis=0)
+    g = np.stack([0.1 * x[0] + 0.2 * x[1], -0.1 * x[2], 0.05 * x[0] + 0.3 * x[1]])
+    x0_np = np.where(fixed_np[None, :], g, 0.0)
+    ptr, idx = fem.fem_build_node2cell(d["conn"], c.n_verts)
+    fixed = torch.from_numpy(fixed_np.astype(np.uint8)).to(device)
+    x0 = torch.from_numpy(x0_np).to(device=device, dtype=fem.value_dtype(prec))
+    work = torch.empty(max(1, int(fem.binding.lib().fem_pcg_elasticity_work_bytes(
+        c.dim, c.n_cells, c.n_verts, fem.binding.precision(prec)))), dtype=torch.uint8, device=device)
+    times, iters, resid = [], 0, 0.0
+    for _ in range(reps + 1):
+        xs = x0.clone()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        _, iters, resid = fem.fem_pcg_elasticity(d["coords"], d["conn"], d["lam"], d["mu"], q.points, q.weights,
+                                                 ptr, idx, fixed, xs, max_iter=max_iter, rtol=rtol, work=work,
+                                                 prec=prec, stream=stream)
+        torch.cuda.synchronize()
+        times.append(time.perf_counter() - t0)
+    t = statistics.median(times[1:])
+    return {"physics": "pcg_elasticity", "dim": c.dim, "prec": prec, "cells": c.n_cells, "verts": c.n_verts,
+            "unknowns": c.dim * c.n_verts, "rtol": rtol, "iterations": iters, "rel_residual": resid,
+            "ms_per_solve": t * 1e3, "us_per_iteration": t / max(iters, 1) * 1e6,
+            "timing": "host wall clock around the whole solve; median of 2 solves after one warm-up"}
+
+
 def measure_pcg_refined(case, device, stream, residual_prec="fp64", rtol=1e-8, inner_rtol=1e-4, reps=2):
     """The same solve by mixed-precision iterative refinement: float64 iterate, residuals
     in residual_prec, corrections by the FP32-mixed PCG (the headline kernel as its
@@ -1149,6 +1185,9 @@ def run_ours(args):
     for prec in ("fp64", "fp64_df"):
         if want(f"pcg_lap3d_{prec}"):
             rows[f"pcg_lap3d_{prec}"] = measure_pcg(case, device, stream, peak, prec)
+    for prec in ("fp64_df", "mixed"):
+        if want(f"pcg_elast3d_{prec}"):
+            rows[f"pcg_elast3d_{prec}"] = measure_pcg_elasticity(device, stream, prec)
     for rprec in ("fp64", "fp64_df"):
         if want(f"pcg_refined_lap3d_{rprec}"):
             rows[f"pcg_refined_lap3d_{rprec}"] = measure_pcg_refined(case, device, stream, rprec)
