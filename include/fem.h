@@ -271,9 +271,11 @@ fem_status fem_integrate_laplacian_transposed(int dim, int64_t n_cells, const vo
  *   iters_out, resid_out (host, may be NULL) iterations taken and ||r|| / ||r_0||
  * Value arrays are float64 for FEM_FP64 and FEM_FP64_DF (the residual then runs in the
  * double-float form: float64-class accuracy at float32-pipe speed) and float32 otherwise;
- * dot products accumulate in float64 in a fixed order (reproducible). The iterations run
- * on the device as a CUDA graph with a WHILE node (one iteration captured as its body,
- * the condition set by the body's last kernel), so the host does not wait per iteration;
+ * dot products accumulate in float64 in a fixed order (reproducible). The iteration is CG
+ * in Chronopoulos and Gear's form (both inner products of an iteration from one reduction:
+ * 3 kernels per iteration). The iterations run on the device as a CUDA graph with a WHILE
+ * node (one iteration captured as its body, the condition set by the body's last kernel),
+ * so the host does not wait per iteration;
  * unlike the other entry points this one returns only after the solve: it synchronises
  * `stream` twice (initial residual norm, final iteration count). The loop body is
  * captured on a library-owned stream per device, one capture at a time (a lock), so
