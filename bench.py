@@ -676,7 +676,7 @@ def measure_pcg(case, device, stream, peak, prec="fp64", rtol=1e-8, max_iter=500
                       "flushed between iterations"}
 
 
-def measure_pcg_elasticity(device, stream, prec="fp64_df", rtol=1e-8, max_iter=20000, reps=2):
+def measure_pcg_elasticity(device, stream, prec="fp64_df", rtol=1e-8, max_iter=20000, reps=2, refined=False):
     """The device-loop Jacobi-PCG for linear elasticity on the 3D elasticity workload mesh
     (2^21 tets), boundary held at a linear displacement, zero load."""
     import torch
@@ -695,6 +695,25 @@ def measure_pcg_elasticity(device, stream, prec="fp64_df", rtol=1e-8, max_iter=2
     x0 = torch.from_numpy(x0_np).to(device=device, dtype=fem.value_dtype(prec))
     work = torch.empty(max(1, int(fem.binding.lib().fem_pcg_elasticity_work_bytes(
         c.dim, c.n_cells, c.n_verts, fem.binding.precision(prec)))), dtype=torch.uint8, device=device)
+    if refined:
+        K64 = lambda a: torch.from_numpy(np.ascontiguousarray(getattr(case, a))).to(device=device, dtype=torch.float64)
+        lam64, mu64 = K64("lam"), K64("mu")
+        x064 = torch.from_numpy(x0_np).to(device)
+        times, res = [], None
+        for _ in range(reps + 1):
+            xs = x064.clone()
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            res = fem.fem_pcg_elasticity_refined(d["coords"], d["conn"], lam64, mu64, q.points, q.weights, ptr, idx,
+                                                 fixed, xs, max_outer=30, max_inner=20000, inner_rtol=1e-4,
+                                                 rtol=rtol, residual_prec="fp64_df", stream=stream)
+            torch.cuda.synchronize()
+            times.append(time.perf_counter() - t0)
+        t = statistics.median(times[1:])
+        return {"physics": "pcg_elasticity_refined", "dim": c.dim, "residual_prec": "fp64_df", "cells": c.n_cells,
+                "verts": c.n_verts, "unknowns": c.dim * c.n_verts, "rtol": rtol, "outer_steps": res[1],
+                "inner_iterations": res[2], "rel_residual": res[3], "ms_per_solve": t * 1e3,
+                "timing": "host wall clock around the whole solve; median of 2 solves after one warm-up"}
     times, iters, resid = [], 0, 0.0
     for _ in range(reps + 1):
         xs = x0.clone()
@@ -1188,6 +1207,8 @@ def run_ours(args):
     for prec in ("fp64_df", "mixed"):
         if want(f"pcg_elast3d_{prec}"):
             rows[f"pcg_elast3d_{prec}"] = measure_pcg_elasticity(device, stream, prec)
+    if want("pcg_elast3d_refined"):
+        rows["pcg_elast3d_refined"] = measure_pcg_elasticity(device, stream, "fp64", refined=True)
     for rprec in ("fp64", "fp64_df"):
         if want(f"pcg_refined_lap3d_{rprec}"):
             rows[f"pcg_refined_lap3d_{rprec}"] = measure_pcg_refined(case, device, stream, rprec)

@@ -321,6 +321,7 @@ fem_status fem_pcg_elasticity(int dim, int64_t n_cells, int64_t n_verts, const d
  * does inside each correction; returns when the solve has finished.
  * ------------------------------------------------------------------------------- */
 int64_t fem_pcg_refined_work_bytes(int dim, int64_t n_cells, int64_t n_verts, int n_q);
+int64_t fem_pcg_elasticity_refined_work_bytes(int dim, int64_t n_cells, int64_t n_verts, int n_q);
 fem_status fem_pcg_laplacian_refined(int dim, int64_t n_cells, int64_t n_verts, const double *coords,
                                      const int32_t *conn, const double *K, int n_q, const double *qpts,
                                      const double *qw, const int32_t *node_ptr, const int32_t *node_idx,
@@ -328,6 +329,16 @@ fem_status fem_pcg_laplacian_refined(int dim, int64_t n_cells, int64_t n_verts, 
                                      double inner_rtol, double rtol, void *work, int64_t work_bytes, int *outer_out,
                                      int *inner_out, double *resid_out, fem_precision residual_prec,
                                      fem_stream stream);
+/* fem_pcg_elasticity_refined -- the same refinement for linear elasticity (fem_pcg_elasticity's
+ * operator): lam, mu [n_q][C], b, x [dim][V] in float64, both rounded to float32 once for the
+ * corrections; workspace of fem_pcg_elasticity_refined_work_bytes() bytes. */
+fem_status fem_pcg_elasticity_refined(int dim, int64_t n_cells, int64_t n_verts, const double *coords,
+                                      const int32_t *conn, const double *lam, const double *mu, int n_q,
+                                      const double *qpts, const double *qw, const int32_t *node_ptr,
+                                      const int32_t *node_idx, const uint8_t *fixed, const double *b, double *x,
+                                      int max_outer, int max_inner, double inner_rtol, double rtol, void *work,
+                                      int64_t work_bytes, int *outer_out, int *inner_out, double *resid_out,
+                                      fem_precision residual_prec, fem_stream stream);
 
 /* ---------------------------------------------------------------------------------
  * The paper's precomputed-geometry layout (Sec. 3 and the Appendix load J^{-1} and det J

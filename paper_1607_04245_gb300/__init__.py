@@ -35,6 +35,7 @@ from .binding import (  # noqa: F401
     fem_integrate_reaction_diffusion,
     fem_precompute_geometry,
     fem_pcg_elasticity,
+    fem_pcg_elasticity_refined,
     fem_pcg_laplacian,
     fem_pcg_laplacian_refined,
     fem_probe,

@@ -61,6 +61,8 @@ def lib():
             "fem_integrate_laplacian_transposed": [ci, i64, P, P, ci, P, P, P, P, ci, ci, ci, P],
             "fem_pcg_laplacian": [ci, i64, i64, P, P, P, ci, P, P, P, P, P, P, P, ci, cd, P, i64, P, P, ci, P],
             "fem_pcg_elasticity": [ci, i64, i64, P, P, P, P, ci, P, P, P, P, P, P, P, ci, cd, P, i64, P, P, ci, P],
+            "fem_pcg_elasticity_refined": [ci, i64, i64, P, P, P, P, ci, P, P, P, P, P, P, P, ci, ci, cd, cd, P, i64,
+                                           P, P, P, ci, P],
             "fem_pcg_laplacian_refined": [ci, i64, i64, P, P, P, ci, P, P, P, P, P, P, P, ci, ci, cd, cd, P, i64, P,
                                           P, P, ci, P],
             "fem_integrate_laplacian_geom": [ci, i64, i64, P, P, P, ci, P, P, P, P, ci, P],
@@ -83,6 +85,8 @@ def lib():
         L.fem_pcg_work_bytes.restype = i64
         L.fem_pcg_elasticity_work_bytes.argtypes = [ci, i64, i64, ci]
         L.fem_pcg_elasticity_work_bytes.restype = i64
+        L.fem_pcg_elasticity_refined_work_bytes.argtypes = [ci, i64, i64, ci]
+        L.fem_pcg_elasticity_refined_work_bytes.restype = i64
         L.fem_pcg_refined_work_bytes.argtypes = [ci, i64, i64, ci]
         L.fem_pcg_refined_work_bytes.restype = i64
         L.fem_prepared_record_floats.argtypes = [ci]
@@ -378,6 +382,34 @@ def fem_pcg_laplacian_refined(coords, conn, K, qpts, qw, node_ptr, node_idx, fix
         int(max_inner), float(inner_rtol), float(rtol), _dev(work, "work", torch.uint8, None, dev), int(work.numel()),
         ctypes.byref(outer), ctypes.byref(inner), ctypes.byref(resid), precision(residual_prec), _stream(stream))
     _check("fem_pcg_laplacian_refined", st)
+    return x, int(outer.value), int(inner.value), float(resid.value)
+
+
+def fem_pcg_elasticity_refined(coords, conn, lam, mu, qpts, qw, node_ptr, node_idx, fixed, x, b=None, max_outer=20,
+                               max_inner=5000, inner_rtol=1e-4, rtol=1e-8, work=None, residual_prec="fp64",
+                               stream=None):
+    """Mixed-precision iterative refinement of the assembled elasticity solve (float64
+    lam, mu, b, x [dim][V]). Returns (x, outer steps, float32 PCG iterations, relative residual)."""
+    dim, V, C = _mesh_sizes(coords, conn)
+    nq = int(np.asarray(qw).shape[0]) if not isinstance(qw, torch.Tensor) else int(qw.shape[0])
+    dev = coords.device
+    need = int(lib().fem_pcg_elasticity_refined_work_bytes(dim, C, V, nq))
+    if need < 0:
+        raise ValueError("bad sizes")
+    if work is None:
+        work = torch.empty(max(need, 1), dtype=torch.uint8, device=dev)
+    qp, w = _HostTable(qpts, (nq, dim), "qpts"), _HostTable(qw, (nq,), "qw")
+    outer, inner, resid = ctypes.c_int(0), ctypes.c_int(0), ctypes.c_double(0.0)
+    f64 = torch.float64
+    st = lib().fem_pcg_elasticity_refined(
+        dim, C, V, _dev(coords, "coords", f64, device=dev), _dev(conn, "conn", torch.int32, device=dev),
+        _dev(lam, "lam", f64, (nq, C), dev), _dev(mu, "mu", f64, (nq, C), dev), nq, qp.ptr, w.ptr,
+        _dev(node_ptr, "node_ptr", torch.int32, (V + 1,), dev),
+        _dev(node_idx, "node_idx", torch.int32, ((dim + 1) * C,), dev), _dev(fixed, "fixed", torch.uint8, (V,), dev),
+        None if b is None else _dev(b, "b", f64, (dim, V), dev), _dev(x, "x", f64, (dim, V), dev), int(max_outer),
+        int(max_inner), float(inner_rtol), float(rtol), _dev(work, "work", torch.uint8, None, dev), int(work.numel()),
+        ctypes.byref(outer), ctypes.byref(inner), ctypes.byref(resid), precision(residual_prec), _stream(stream))
+    _check("fem_pcg_elasticity_refined", st)
     return x, int(outer.value), int(inner.value), float(resid.value)
 
 

@@ -627,11 +627,12 @@ __global__ void to_f32_kernel(int64_t n, const double *a, float *b) {
 }
 
 // r = b - q on the free vertices, 0 on fixed ones; r32 = r rounded to float32; d32 = 0
-__global__ void refine_residual_kernel(int64_t V, const double *b, const double *q, const uint8_t *fixed, double *r,
-                                       float *r32, float *d32) {
+// (N = n_comp V entries, component-major)
+__global__ void refine_residual_kernel(int64_t N, int64_t V, const double *b, const double *q, const uint8_t *fixed,
+                                       double *r, float *r32, float *d32) {
     const int64_t stride = int64_t(gridDim.x) * blockDim.x;
-    for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < V; i += stride) {
-        const double ri = fixed[i] ? 0.0 : (b ? b[i] : 0.0) - q[i];
+    for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < N; i += stride) {
+        const double ri = fixed[i % V] ? 0.0 : (b ? b[i] : 0.0) - q[i];
         r[i] = ri;
         r32[i] = static_cast<float>(ri);
         d32[i] = 0.0f;
@@ -639,54 +640,103 @@ __global__ void refine_residual_kernel(int64_t V, const double *b, const double 
 }
 
 // x += d on the free vertices
-__global__ void refine_update_kernel(int64_t V, const uint8_t *fixed, const float *d, double *x) {
+__global__ void refine_update_kernel(int64_t N, int64_t V, const uint8_t *fixed, const float *d, double *x) {
     const int64_t stride = int64_t(gridDim.x) * blockDim.x;
-    for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < V; i += stride)
-        if (!fixed[i]) x[i] += static_cast<double>(d[i]);
+    for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < N; i += stride)
+        if (!fixed[i % V]) x[i] += static_cast<double>(d[i]);
 }
 
 struct RefineWork {
-    Workspace inner;  // the float32 PCG's
-    float *K32, *r32, *d32;
+    Workspace inner;    // the float32 PCG's
+    float *coef32[2];   // K (Laplacian) or lambda, mu (elasticity) rounded to float32
+    float *r32, *d32;
     double *elem, *q, *r, *partial, *scalars;
 };
 
-static size_t carve_refined(int64_t C, int64_t V, int dim, int n_q, void *base, RefineWork *w) {
+// physics 0: Laplacian (one coefficient, one component), 1: elasticity (two, dim)
+static size_t carve_refined(int64_t C, int64_t V, int dim, int n_q, int physics, void *base, RefineWork *w) {
+    const int nc = physics == 0 ? 1 : dim, ncoef = physics == 0 ? 1 : 2;
     Workspace inner;
-    size_t off = carve(C, V, dim, sizeof(float), base, &inner);
+    size_t off = carve(C, V, dim, sizeof(float), base, &inner, nc);
     char *b = static_cast<char *>(base);
     auto take = [&](size_t bytes) {
         void *p = b ? b + off : nullptr;
         off += align256(bytes);
         return p;
     };
-    float *K32 = static_cast<float *>(take(size_t(n_q) * size_t(C) * sizeof(float)));
-    float *r32 = static_cast<float *>(take(size_t(V) * sizeof(float)));
-    float *d32 = static_cast<float *>(take(size_t(V) * sizeof(float)));
-    double *elem = static_cast<double *>(take(size_t(dim + 1) * size_t(C) * sizeof(double)));
-    double *q = static_cast<double *>(take(size_t(V) * sizeof(double)));
-    double *r = static_cast<double *>(take(size_t(V) * sizeof(double)));
+    const size_t N = size_t(nc) * size_t(V);
+    float *coef32[2] = {nullptr, nullptr};
+    for (int c = 0; c < ncoef; ++c) coef32[c] = static_cast<float *>(take(size_t(n_q) * size_t(C) * sizeof(float)));
+    float *r32 = static_cast<float *>(take(N * sizeof(float)));
+    float *d32 = static_cast<float *>(take(N * sizeof(float)));
+    double *elem = static_cast<double *>(take(size_t(dim + 1) * size_t(nc) * size_t(C) * sizeof(double)));
+    double *q = static_cast<double *>(take(N * sizeof(double)));
+    double *r = static_cast<double *>(take(N * sizeof(double)));
     double *partial = static_cast<double *>(take(sizeof(double) * kDotBlocks));
     double *scalars = static_cast<double *>(take(sizeof(double) * 2));
-    if (w) *w = RefineWork{inner, K32, r32, d32, elem, q, r, partial, scalars};
+    if (w) *w = RefineWork{inner, {coef32[0], coef32[1]}, r32, d32, elem, q, r, partial, scalars};
     return off;
 }
 
-}  // namespace fem
-
-extern "C" int64_t fem_pcg_refined_work_bytes(int dim, int64_t n_cells, int64_t n_verts, int n_q) {
-    if ((dim != 2 && dim != 3) || n_cells < 0 || n_verts < 0 || n_q < 1 || n_q > FEM_MAX_QPTS) return -1;
-    return static_cast<int64_t>(carve_refined(n_cells, n_verts, dim, n_q, nullptr, nullptr));
+// the refinement loop of both entry points (arguments validated by the caller); coef64:
+// K, or lambda and mu, in float64
+static fem_status refined_run(int physics, int dim, int64_t C, int64_t V, const double *coords, const int32_t *conn,
+                              const double *const *coef64, int n_q, const double *qpts, const double *qw,
+                              const int32_t *ptr, const int32_t *idx, const uint8_t *fixed, const double *b,
+                              double *x, int max_outer, int max_inner, double inner_rtol, double rtol,
+                              const RefineWork &w, int *outer_out, int *inner_out, double *resid_out,
+                              fem_precision residual_prec, cudaStream_t stream) {
+    const int nc = physics == 0 ? 1 : dim, ncoef = physics == 0 ? 1 : 2;
+    const int64_t N = int64_t(nc) * V;
+    const int gV = static_cast<int>(std::min<int64_t>((N + 255) / 256, 4096));
+    const int gK = static_cast<int>(std::min<int64_t>((int64_t(n_q) * C + 255) / 256, 4096));
+    for (int c = 0; c < ncoef; ++c) to_f32_kernel<<<gK, 256, 0, stream>>>(int64_t(n_q) * C, coef64[c], w.coef32[c]);
+    fem_status st = check_launch("refined solve");
+    if (st != FEM_OK) return st;
+    const Operator op32 = physics == 0 ? Operator{0, w.coef32[0], nullptr, nullptr}
+                                       : Operator{1, nullptr, w.coef32[0], w.coef32[1]};
+    double rn0 = 0.0, rn = 0.0;
+    int outer = 0, inner_total = 0;
+    for (;;) {
+        // the true residual of the float64 iterate
+        st = physics == 0 ? fem_integrate_laplacian(dim, C, V, coords, conn, x, coef64[0], n_q, qpts, qw, w.elem,
+                                                    residual_prec, stream)
+                          : fem_integrate_elasticity(dim, C, V, coords, conn, x, coef64[0], coef64[1], n_q, qpts, qw,
+                                                     w.elem, residual_prec, stream);
+        if (st != FEM_OK) return st;
+        if ((st = launch_gather(dim, nc, C, V, w.elem, ptr, idx, w.q, FEM_FP64, stream)) != FEM_OK) return st;
+        refine_residual_kernel<<<gV, 256, 0, stream>>>(N, V, b, w.q, fixed, w.r, w.r32, w.d32);
+        dot_partial_kernel<double><<<kDotBlocks, 256, 0, stream>>>(N, w.r, w.r, w.partial);
+        dot_final_kernel<<<1, 256, 0, stream>>>(w.partial, w.scalars);
+        double rr = 0.0;
+        cudaError_t e = cudaMemcpyAsync(&rr, w.scalars, sizeof(double), cudaMemcpyDeviceToHost, stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(stream);
+        if (e != cudaSuccess) return fail(FEM_ERR_CUDA, "refined solve: %s", cudaGetErrorString(e));
+        rn = std::sqrt(rr);
+        if (outer == 0) rn0 = rn;
+        if (rn <= rtol * rn0 || rn == 0.0 || outer >= max_outer) break;
+        // the correction in the FP32-mixed form: A d = r, d = 0 on the fixed vertices
+        int it = 0;
+        double res = 0.0;
+        st = pcg_run<float>(dim, C, V, coords, conn, op32, n_q, qpts, qw, ptr, idx, fixed, w.r32, w.d32, max_inner,
+                            inner_rtol, w.inner, &it, &res, FEM_FP32_MIXED, stream, outer > 0);
+        if (st != FEM_OK) return st;
+        inner_total += it;
+        refine_update_kernel<<<gV, 256, 0, stream>>>(N, V, fixed, w.d32, x);
+        if ((st = check_launch("refined solve")) != FEM_OK) return st;
+        ++outer;
+    }
+    if (outer_out) *outer_out = outer;
+    if (inner_out) *inner_out = inner_total;
+    if (resid_out) *resid_out = rn0 > 0.0 ? rn / rn0 : 0.0;
+    return check_launch("refined solve");
 }
 
-extern "C" fem_status fem_pcg_laplacian_refined(int dim, int64_t n_cells, int64_t n_verts, const double *coords,
-                                                const int32_t *conn, const double *K, int n_q, const double *qpts,
-                                                const double *qw, const int32_t *node_ptr, const int32_t *node_idx,
-                                                const uint8_t *fixed, const double *b, double *x, int max_outer,
-                                                int max_inner, double inner_rtol, double rtol, void *work,
-                                                int64_t work_bytes, int *outer_out, int *inner_out,
-                                                double *resid_out, fem_precision residual_prec, fem_stream stream) {
-    fem_status st = check_common(dim, n_cells, n_verts, coords, conn);
+// the argument checks both entry points share
+static fem_status refined_check(int dim, int64_t C, int64_t V, const double *coords, const int32_t *conn, int n_q,
+                                int max_outer, int max_inner, double inner_rtol, double rtol,
+                                fem_precision residual_prec, int *outer_out, int *inner_out, double *resid_out) {
+    fem_status st = check_common(dim, C, V, coords, conn);
     if (st != FEM_OK) return st;
     if (residual_prec != FEM_FP64 && residual_prec != FEM_FP64_DF)
         return fail(FEM_ERR_ARG, "residual_prec must be FEM_FP64 or FEM_FP64_DF");
@@ -696,7 +746,31 @@ extern "C" fem_status fem_pcg_laplacian_refined(int dim, int64_t n_cells, int64_
     if (outer_out) *outer_out = 0;
     if (inner_out) *inner_out = 0;
     if (resid_out) *resid_out = 0.0;
-    if (n_verts == 0) return FEM_OK;
+    return FEM_OK;
+}
+
+}  // namespace fem
+
+extern "C" int64_t fem_pcg_refined_work_bytes(int dim, int64_t n_cells, int64_t n_verts, int n_q) {
+    if ((dim != 2 && dim != 3) || n_cells < 0 || n_verts < 0 || n_q < 1 || n_q > FEM_MAX_QPTS) return -1;
+    return static_cast<int64_t>(carve_refined(n_cells, n_verts, dim, n_q, 0, nullptr, nullptr));
+}
+
+extern "C" int64_t fem_pcg_elasticity_refined_work_bytes(int dim, int64_t n_cells, int64_t n_verts, int n_q) {
+    if ((dim != 2 && dim != 3) || n_cells < 0 || n_verts < 0 || n_q < 1 || n_q > FEM_MAX_QPTS) return -1;
+    return static_cast<int64_t>(carve_refined(n_cells, n_verts, dim, n_q, 1, nullptr, nullptr));
+}
+
+extern "C" fem_status fem_pcg_laplacian_refined(int dim, int64_t n_cells, int64_t n_verts, const double *coords,
+                                                const int32_t *conn, const double *K, int n_q, const double *qpts,
+                                                const double *qw, const int32_t *node_ptr, const int32_t *node_idx,
+                                                const uint8_t *fixed, const double *b, double *x, int max_outer,
+                                                int max_inner, double inner_rtol, double rtol, void *work,
+                                                int64_t work_bytes, int *outer_out, int *inner_out,
+                                                double *resid_out, fem_precision residual_prec, fem_stream stream) {
+    fem_status st = refined_check(dim, n_cells, n_verts, coords, conn, n_q, max_outer, max_inner, inner_rtol, rtol,
+                                  residual_prec, outer_out, inner_out, resid_out);
+    if (st != FEM_OK || n_verts == 0) return st;
     if (!K || !node_ptr || !node_idx || !fixed || !x || !work) return fail(FEM_ERR_ARG, "a NULL array argument");
     const int64_t need = fem_pcg_refined_work_bytes(dim, n_cells, n_verts, n_q);
     if (work_bytes < need)
@@ -704,45 +778,36 @@ extern "C" fem_status fem_pcg_laplacian_refined(int dim, int64_t n_cells, int64_
                     static_cast<long long>(work_bytes), static_cast<long long>(need));
     if (reinterpret_cast<uintptr_t>(work) & 255u) return fail(FEM_ERR_ARG, "work must be 256-byte aligned");
     RefineWork w;
-    carve_refined(n_cells, n_verts, dim, n_q, work, &w);
-    const int gV = static_cast<int>(std::min<int64_t>((n_verts + 255) / 256, 4096));
-    const int gK = static_cast<int>(std::min<int64_t>((int64_t(n_q) * n_cells + 255) / 256, 4096));
-    to_f32_kernel<<<gK, 256, 0, stream>>>(int64_t(n_q) * n_cells, K, w.K32);
-    if ((st = check_launch("fem_pcg_laplacian_refined")) != FEM_OK) return st;
-    double rn0 = 0.0, rn = 0.0;
-    int outer = 0, inner_total = 0;
-    for (;;) {
-        // the true residual of the float64 iterate
-        if ((st = fem_integrate_laplacian(dim, n_cells, n_verts, coords, conn, x, K, n_q, qpts, qw, w.elem,
-                                          residual_prec, stream)) != FEM_OK)
-            return st;
-        if ((st = launch_gather(dim, 1, n_cells, n_verts, w.elem, node_ptr, node_idx, w.q, FEM_FP64, stream)) != FEM_OK)
-            return st;
-        refine_residual_kernel<<<gV, 256, 0, stream>>>(n_verts, b, w.q, fixed, w.r, w.r32, w.d32);
-        dot_partial_kernel<double><<<kDotBlocks, 256, 0, stream>>>(n_verts, w.r, w.r, w.partial);
-        dot_final_kernel<<<1, 256, 0, stream>>>(w.partial, w.scalars);
-        double rr = 0.0;
-        cudaError_t e = cudaMemcpyAsync(&rr, w.scalars, sizeof(double), cudaMemcpyDeviceToHost, stream);
-        if (e == cudaSuccess) e = cudaStreamSynchronize(stream);
-        if (e != cudaSuccess) return fail(FEM_ERR_CUDA, "fem_pcg_laplacian_refined: %s", cudaGetErrorString(e));
-        rn = std::sqrt(rr);
-        if (outer == 0) rn0 = rn;
-        if (rn <= rtol * rn0 || rn == 0.0 || outer >= max_outer) break;
-        // the correction in the FP32-mixed form: A d = r, d = 0 on the fixed vertices
-        int it = 0;
-        double res = 0.0;
-        st = pcg_run<float>(dim, n_cells, n_verts, coords, conn, Operator{0, w.K32, nullptr, nullptr}, n_q, qpts, qw,
-                            node_ptr, node_idx, fixed,
-                            w.r32, w.d32, max_inner, inner_rtol, w.inner, &it, &res, FEM_FP32_MIXED, stream,
-                            outer > 0);
-        if (st != FEM_OK) return st;
-        inner_total += it;
-        refine_update_kernel<<<gV, 256, 0, stream>>>(n_verts, fixed, w.d32, x);
-        if ((st = check_launch("fem_pcg_laplacian_refined")) != FEM_OK) return st;
-        ++outer;
-    }
-    if (outer_out) *outer_out = outer;
-    if (inner_out) *inner_out = inner_total;
-    if (resid_out) *resid_out = rn0 > 0.0 ? rn / rn0 : 0.0;
-    return check_launch("fem_pcg_laplacian_refined");
+    carve_refined(n_cells, n_verts, dim, n_q, 0, work, &w);
+    const double *coef[1] = {K};
+    return refined_run(0, dim, n_cells, n_verts, coords, conn, coef, n_q, qpts, qw, node_ptr, node_idx, fixed, b, x,
+                       max_outer, max_inner, inner_rtol, rtol, w, outer_out, inner_out, resid_out, residual_prec,
+                       stream);
+}
+
+extern "C" fem_status fem_pcg_elasticity_refined(int dim, int64_t n_cells, int64_t n_verts, const double *coords,
+                                                 const int32_t *conn, const double *lam, const double *mu, int n_q,
+                                                 const double *qpts, const double *qw, const int32_t *node_ptr,
+                                                 const int32_t *node_idx, const uint8_t *fixed, const double *b,
+                                                 double *x, int max_outer, int max_inner, double inner_rtol,
+                                                 double rtol, void *work, int64_t work_bytes, int *outer_out,
+                                                 int *inner_out, double *resid_out, fem_precision residual_prec,
+                                                 fem_stream stream) {
+    fem_status st = refined_check(dim, n_cells, n_verts, coords, conn, n_q, max_outer, max_inner, inner_rtol, rtol,
+                                  residual_prec, outer_out, inner_out, resid_out);
+    if (st != FEM_OK || n_verts == 0) return st;
+    if (int64_t(dim) * n_verts >= (int64_t(1) << 31)) return fail(FEM_ERR_SHAPE, "too many vertices");
+    if (!lam || !mu || !node_ptr || !node_idx || !fixed || !x || !work)
+        return fail(FEM_ERR_ARG, "a NULL array argument");
+    const int64_t need = fem_pcg_elasticity_refined_work_bytes(dim, n_cells, n_verts, n_q);
+    if (work_bytes < need)
+        return fail(FEM_ERR_OOM, "fem_pcg_elasticity_refined: workspace of %lld bytes, %lld needed",
+                    static_cast<long long>(work_bytes), static_cast<long long>(need));
+    if (reinterpret_cast<uintptr_t>(work) & 255u) return fail(FEM_ERR_ARG, "work must be 256-byte aligned");
+    RefineWork w;
+    carve_refined(n_cells, n_verts, dim, n_q, 1, work, &w);
+    const double *coef[2] = {lam, mu};
+    return refined_run(1, dim, n_cells, n_verts, coords, conn, coef, n_q, qpts, qw, node_ptr, node_idx, fixed, b, x,
+                       max_outer, max_inner, inner_rtol, rtol, w, outer_out, inner_out, resid_out, residual_prec,
+                       stream);
 }

@@ -338,3 +338,36 @@ def test_elasticity_matches_dense_solve_of_oracle_operator(dim, n, prec, rtol, t
     err = np.abs(x.cpu().numpy().astype(np.float64).ravel() - ref).max() / np.abs(ref).max()
     assert resid <= rtol
     assert err <= tol, (err, iters, resid)
+
+
+@pytest.mark.parametrize("dim,n", [(2, 8), (3, 3)])
+@pytest.mark.parametrize("residual_prec", ["fp64", "fp64_df"])
+def test_elasticity_refined_matches_dense_solve_of_oracle_operator(dim, n, residual_prec):
+    """Mixed-precision refinement of the elasticity solve reaches the float64 solution of the
+    oracle's assembled operator."""
+    mesh = _mesh(dim, n)
+    rule = workloads.rule_for_dim(dim)
+    rng = np.random.default_rng(dim + 40)
+    E = rng.lognormal(0.0, 0.5, (rule.n_q, mesh.n_cells))
+    nu = rng.uniform(0.2, 0.45, (rule.n_q, mesh.n_cells))
+    lam, mu = workloads.cases.lame_from_young_poisson(E, nu)
+    V = mesh.n_verts
+    fixed = _boundary(mesh)
+    g = np.stack([mesh.coords[1] - 0.5 * mesh.coords[0]] + [np.cos(mesh.coords[0])] * (dim - 1))
+    b = np.where(fixed[None, :], 0.0, rng.uniform(-1, 1, (dim, V)) / V)
+    x0 = np.where(fixed[None, :], g, 0.0)
+    coords, conn = to_dev(mesh.coords, torch.float64), to_dev(mesh.conn, torch.int32)
+    ptr, idx = fem.fem_build_node2cell(conn, V)
+    x = to_dev(x0, torch.float64)
+    x, outer, inner, resid = fem.fem_pcg_elasticity_refined(
+        coords, conn, to_dev(lam, torch.float64), to_dev(mu, torch.float64), rule.points, rule.weights, ptr, idx,
+        to_dev(fixed.astype(np.uint8), torch.uint8), x, b=to_dev(b, torch.float64), max_outer=30, max_inner=20000,
+        inner_rtol=1e-4, rtol=1e-12, residual_prec=residual_prec)
+    A = _oracle_elasticity_operator(mesh, lam, mu, rule)
+    free = np.tile(~fixed, dim)
+    fx = ~free
+    ref = x0.ravel().copy()
+    ref[free] = np.linalg.solve(A[np.ix_(free, free)], b.ravel()[free] - A[np.ix_(free, fx)] @ ref[fx])
+    err = np.abs(x.cpu().numpy().ravel() - ref).max() / np.abs(ref).max()
+    assert resid <= 1e-12 and outer >= 2 and inner > 0
+    assert err <= 1e-9, (err, outer, inner, resid)
