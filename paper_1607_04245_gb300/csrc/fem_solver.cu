@@ -1,15 +1,16 @@
-// fem_solver.cu -- a matrix-free Jacobi-preconditioned conjugate-gradient solve with the
-// assembled Laplacian operator of Eq. 2: A v = E^T r_e(v), the element residuals of the
-// variable-coefficient Laplacian summed into the vertices through the vertex-to-cell
-// lists (fem_build_node2cell). Dirichlet vertices keep their value from the initial x.
+// fem_solver.cu -- matrix-free Jacobi-preconditioned conjugate-gradient solves with the
+// assembled operators of Eq. 2: A v = E^T r_e(v), the element residuals of the
+// variable-coefficient Laplacian or of linear elasticity summed into the vertices through
+// the vertex-to-cell lists (fem_build_node2cell). Dirichlet vertices keep their value from
+// the initial x. Also: mixed-precision iterative refinement around the FP32-mixed solve.
 //
-// Kernels here: the assembled diagonal (element diagonals A_bb = Kbar |n_b|^2 / |det J|,
-// summed per vertex), a deterministic two-level dot product, and the vector updates of
-// CG with their scalars read from device memory. The iteration loop runs on the device:
-// one CG iteration is captured once into the body of a CUDA graph WHILE node, and the
-// last kernel of the body counts the iteration and sets the loop condition (not
-// converged and fewer than max_iter iterations). The host synchronises twice per solve
-// (the initial residual norm, the final count) instead of once per iteration.
+// Kernels here: the assembled diagonals (element stiffness diagonals summed per vertex), a
+// deterministic two-level dot product, and the CG iteration in Chronopoulos and Gear's form
+// with its scalars kept in device memory. The iteration loop runs on the device: one CG
+// iteration is captured once into the body of a CUDA graph WHILE node, and the last kernel
+// of the body counts the iteration and sets the loop condition (not converged and fewer
+// than max_iter iterations). The host synchronises twice per solve (the initial residual
+// norm, the final count) instead of once per iteration.
 #include <cmath>
 #include <cstring>
 #include <mutex>
