@@ -223,3 +223,25 @@ def test_argument_errors(lap2d):
     with pytest.raises(fem.FemError):
         fem.fem_integrate_laplacian(d["coords"], d["conn"], d["u"], d["K"], c.rule.points + 1.0, c.rule.weights,
                                     prec="fp64")
+
+
+@pytest.mark.parametrize("offset", [1e3, -7.5e4])
+def test_mixed_form_far_from_origin(offset):
+    """The mesh moved far from the origin: the Jacobian columns x_j - x_0 are 6.4e4 to 4.8e6
+    times smaller than the coordinates. The mixed form differences the float64 coordinates
+    exactly (float32 hi/lo splits) and stays within its tolerance; the float32 ablation, which
+    rounds the coordinates first, loses the columns."""
+    base = workloads.laplacian_cube_case(6 * 8 ** 3)
+    mesh = workloads.Mesh(3, base.mesh.coords + offset, base.mesh.conn)
+    case = workloads.Case("laplacian", mesh, base.rule, base.u, K=base.K)
+    c, d = device_arrays(case, "mixed")
+    ref = oracle.residual_for(c)
+    r = residual(c, d, "mixed")
+    torch.cuda.synchronize()
+    assert rel_err(r, ref) <= TOL["mixed"]
+    c32, d32 = device_arrays(case, "fp32")
+    r32 = residual(c32, d32, "fp32")
+    torch.cuda.synchronize()
+    # the ablation's columns are float32 roundings of large numbers: ten times past the
+    # mixed form's tolerance already at 1e3
+    assert rel_err(r32, ref) > 10 * TOL["mixed"]
