@@ -4,7 +4,8 @@ tetrahedra in 3D (about 26 GB of cell data in the float32 forms, 43 GB in float6
 The connectivity and coefficient rows are the 1,572,864-tet workload repeated over the
 whole range (the same vertex set), so every cell's element vector must equal the one of
 its counterpart in the base workload: bit for bit on the paths that compute a cell the
-same way at any position (the staged kernel on a size divisible by 4, every float64 path),
+same way at any position (the float32 forms' pair kernel and the float64 form's staged
+kernel on a size divisible by 4, every float64 path),
 within the float32 tolerance on the ragged size, and against the oracle on a sample of
 cells spread over the whole range. One more cell is refused on the host.
 """
