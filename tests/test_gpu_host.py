@@ -36,7 +36,7 @@ def test_host_path_equals_device_path(dim, n_cells, prec, chunks):
         assert torch.equal(out, ref_dev)
     else:
         # the ragged last chunk, or (chunks = 0) the plain-load kernel, computes one cell
-        # per call of the scalar float32 routine, the staged kernel two cells per call
+        # per call of the scalar float32 routine, the device entry's pair kernel two
         assert rel_err(out, ref_dev.double().numpy()) <= 1e-6
     assert rel_err(out, oracle.residual_for(c)) <= TOL[prec]
 

@@ -71,7 +71,8 @@ def test_max_size_equals_tiled_base(base, prec):
     scale = np.abs(ref_ora).max()
     rng = np.random.default_rng(0)
     for n in (C_MAX - C_MAX % 4, C_MAX):
-        # n divisible by 4: the staged (bulk-copy) kernel; n = C_MAX (ragged): the
+        # n divisible by 4: the pair kernel (float32 forms) or the staged kernel (float64);
+        # n = C_MAX (ragged): the
         # scalar-load kernel, whose float32 cells go one per call instead of in pairs, so
         # only its float64 form is bitwise the tiled base
         conn, K = _tile(d["conn"], n), _tile(d["K"], n)
