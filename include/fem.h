@@ -308,8 +308,10 @@ fem_status fem_pcg_elasticity(int dim, int64_t n_cells, int64_t n_verts, const d
  * refinement (not in the paper): each outer step forms the true residual r = b - A x of
  * the float64 iterate with the residual kernel in residual_prec (FEM_FP64 or FEM_FP64_DF),
  * solves A d = r with fem_pcg_laplacian's Jacobi-PCG in FEM_FP32_MIXED (float32 values,
- * K rounded to float32 once, to relative residual inner_rtol or max_inner iterations) and
- * sets x += d in float64 on the free vertices. It stops when ||r|| <= rtol ||r_0|| (r_0 the
+ * K rounded to float32 once, to relative residual inner_rtol or max_inner iterations; a
+ * correction that only has to gain the last factor f < inner_rtol / 0.3 of the reduction,
+ * with 0.3 f >= 1e-6, is solved to 0.3 f instead) and sets x += d in float64 on the free
+ * vertices. It stops when ||r|| <= rtol ||r_0|| (r_0 the
  * residual of the initial x, both in float64) or after max_outer corrections.
  *   K, b, x    float64 ([n_q][C], [V] or NULL, [V]: initial guess and Dirichlet values in,
  *              solution out); the other arguments as fem_pcg_laplacian

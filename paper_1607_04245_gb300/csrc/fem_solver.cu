@@ -716,11 +716,16 @@ static fem_status refined_run(int physics, int dim, int64_t C, int64_t V, const 
         rn = std::sqrt(rr);
         if (outer == 0) rn0 = rn;
         if (rn <= rtol * rn0 || rn == 0.0 || outer >= max_outer) break;
-        // the correction in the FP32-mixed form: A d = r, d = 0 on the fixed vertices
+        // the correction in the FP32-mixed form: A d = r, d = 0 on the fixed vertices. When
+        // the reduction still needed is less than one correction at inner_rtol gives, and
+        // within float32's reach, the last correction is solved to a third of it instead, so
+        // that it ends the refinement rather than stopping just short of rtol.
+        const double need = rtol * rn0 / rn;
+        const double tol_k = (0.3 * need < inner_rtol && 0.3 * need >= 1e-6) ? 0.3 * need : inner_rtol;
         int it = 0;
         double res = 0.0;
         st = pcg_run<float>(dim, C, V, coords, conn, op32, n_q, qpts, qw, ptr, idx, fixed, w.r32, w.d32, max_inner,
-                            inner_rtol, w.inner, &it, &res, FEM_FP32_MIXED, stream, outer > 0);
+                            tol_k, w.inner, &it, &res, FEM_FP32_MIXED, stream, outer > 0);
         if (st != FEM_OK) return st;
         inner_total += it;
         refine_update_kernel<<<gV, 256, 0, stream>>>(N, V, fixed, w.d32, x);
