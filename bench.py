@@ -1161,73 +1161,82 @@ def run_ours(args):
     # --rows all | none | comma-separated row-name prefixes (e.g. "lap3d_fields8,elast3d")
     picked = None if args.rows in ("all", "none") else [x for x in args.rows.split(",") if x]
     want = lambda name: args.rows == "all" or (picked is not None and any(name.startswith(x) for x in picked))
+    def put(name, fn):
+        """Measure one optional row; a row that fails is recorded with its error and does not
+        cost the bench line."""
+        try:
+            rows[name] = fn()
+        except Exception as exc:  # noqa: BLE001 -- reported in the line and on stderr
+            print(f"bench: row {name} failed: {exc!r}", file=sys.stderr)
+            rows[name] = {"error": repr(exc)[:300]}
+
     rsteps = max(3, args.steps // 50)
+    common = (device, stream, flush, rsteps, args.warmup, peak, oracle)
     if want("fp32_ablation"):
-        rows["fp32_ablation"] = measure_residual(case, "fp32", device, stream, flush, rsteps, args.warmup, peak,
-                                                 oracle)[0]
+        put("fp32_ablation", lambda: measure_residual(case, "fp32", *common)[0])
     for prec in ("mixed", "fp64"):
         if want(f"lap3d_precomputed_geometry_{prec}"):
-            rows[f"lap3d_precomputed_geometry_{prec}"] = measure_geometry_path(case, prec, device, stream, flush, rsteps,
-                                                                              args.warmup, peak, oracle)
+            put(f"lap3d_precomputed_geometry_{prec}", lambda: measure_geometry_path(case, prec, *common))
     for prec in ("fp32", "fp64"):
         if want(f"lap3d_thread_transposition_{prec}"):
-            rows[f"lap3d_thread_transposition_{prec}"] = measure_transposed(case, prec, device, stream, flush, rsteps,
-                                                                           args.warmup, peak, oracle)
+            put(f"lap3d_thread_transposition_{prec}", lambda: measure_transposed(case, prec, *common))
     if want("lap2d_8192_fp64"):
-        rows["lap2d_8192_fp64"] = measure_residual(workloads.laplacian_square_case(), "fp64", device, stream, flush,
-                                                   rsteps, args.warmup, peak, oracle)[0]
+        put("lap2d_8192_fp64", lambda: measure_residual(workloads.laplacian_square_case(), "fp64", *common)[0])
     for dim in (2, 3):
         if not any(want(f"elast{dim}d_{prec}") for prec in ("mixed", "fp64", "fp64_df")):
             continue
         el = workloads.elasticity_case(dim)
         for prec in ("mixed", "fp64", "fp64_df"):
             if want(f"elast{dim}d_{prec}"):
-                rows[f"elast{dim}d_{prec}"] = measure_residual(el, prec, device, stream, flush, rsteps, args.warmup,
-                                                               peak, oracle)[0]
+                put(f"elast{dim}d_{prec}", lambda: measure_residual(el, prec, *common)[0])
     if any(want(f"adjoint3d_{prec}") for prec in ("mixed", "fp64", "fp64_df")):
         adj = workloads.adjoint_case(HEADLINE_CELLS)
         for prec in ("mixed", "fp64", "fp64_df"):
             if want(f"adjoint3d_{prec}"):
-                rows[f"adjoint3d_{prec}"] = measure_adjoint(adj, prec, device, stream, flush, rsteps, args.warmup, peak,
-                                                            oracle)
+                put(f"adjoint3d_{prec}", lambda: measure_adjoint(adj, prec, *common))
     for prec in ("mixed", "fp64"):
         if want(f"reaction3d_grad_a_{prec}"):
-            rows[f"reaction3d_grad_a_{prec}"] = measure_reaction(case, prec, device, stream, flush, rsteps, args.warmup,
-                                                                 peak, oracle)
+            put(f"reaction3d_grad_a_{prec}", lambda: measure_reaction(case, prec, *common))
     if want("lap3d_prepared_mixed"):
-        rows["lap3d_prepared_mixed"] = measure_prepared(case, device, stream, flush, rsteps, args.warmup, peak, oracle)
+        put("lap3d_prepared_mixed", lambda: measure_prepared(case, *common))
     for prec in ("mixed", "fp64"):
         for phys in ("laplacian", "nonlinear"):
             if want(f"pointwise_{phys}3d_{prec}"):
-                rows[f"pointwise_{phys}3d_{prec}"] = measure_pointwise(case, phys, prec, device, stream, flush, rsteps,
-                                                                       args.warmup, peak, oracle)
+                put(f"pointwise_{phys}3d_{prec}", lambda: measure_pointwise(case, phys, prec, *common))
     for prec in ("fp64", "fp64_df"):
         if want(f"pcg_lap3d_{prec}"):
-            rows[f"pcg_lap3d_{prec}"] = measure_pcg(case, device, stream, peak, prec)
+            put(f"pcg_lap3d_{prec}", lambda: measure_pcg(case, device, stream, peak, prec))
     for prec in ("fp64_df", "mixed"):
         if want(f"pcg_elast3d_{prec}"):
-            rows[f"pcg_elast3d_{prec}"] = measure_pcg_elasticity(device, stream, prec)
+            put(f"pcg_elast3d_{prec}", lambda: measure_pcg_elasticity(device, stream, prec))
     if want("pcg_elast3d_refined"):
-        rows["pcg_elast3d_refined"] = measure_pcg_elasticity(device, stream, "fp64", refined=True)
+        put("pcg_elast3d_refined", lambda: measure_pcg_elasticity(device, stream, "fp64", refined=True))
     for rprec in ("fp64", "fp64_df"):
         if want(f"pcg_refined_lap3d_{rprec}"):
-            rows[f"pcg_refined_lap3d_{rprec}"] = measure_pcg_refined(case, device, stream, rprec)
+            put(f"pcg_refined_lap3d_{rprec}", lambda: measure_pcg_refined(case, device, stream, rprec))
     for prec in ("mixed", "fp64"):
         if want(f"lap3d_fields8_{prec}"):
-            rows[f"lap3d_fields8_{prec}"] = measure_fields(case, prec, device, stream, flush, rsteps, args.warmup, peak,
-                                                           oracle)
-    if want("sweep_lap3d_mixed"):
-        sweep = {}
+            put(f"lap3d_fields8_{prec}", lambda: measure_fields(case, prec, *common))
+
+    def sweep():
+        out = {}
         for e in range(16, 24):
             sc = workloads.laplacian_cube_case(1 << e)
             r = measure_residual(sc, "mixed", device, stream, flush, max(3, rsteps // 2), args.warmup, peak)[0]
-            sweep[str(1 << e)] = {"cells_per_s": r["cells_per_s"], "alg_gbs": r["alg_gbs"],
-                                  "hbm_frac_of_measured": r["hbm_frac_of_measured"], "ms": r["ms_per_launch"]}
-        rows["sweep_lap3d_mixed"] = sweep
-    if want("serving") and args.serving_requests > 0:
-        rows["serving"] = measure_serving(device, args.serving_requests)
+            out[str(1 << e)] = {"cells_per_s": r["cells_per_s"], "alg_gbs": r["alg_gbs"],
+                                "hbm_frac_of_measured": r["hbm_frac_of_measured"], "ms": r["ms_per_launch"]}
+        return out
 
-    e2e = measure_e2e(case, "mixed", device, max(3, args.steps // 100), 3)
+    if want("sweep_lap3d_mixed"):
+        put("sweep_lap3d_mixed", sweep)
+    if want("serving") and args.serving_requests > 0:
+        put("serving", lambda: measure_serving(device, args.serving_requests))
+
+    try:
+        e2e = measure_e2e(case, "mixed", device, max(3, args.steps // 100), 3)
+    except Exception as exc:  # noqa: BLE001 -- reported in the line and on stderr
+        print(f"bench: e2e failed: {exc!r}", file=sys.stderr)
+        e2e = {"error": repr(exc)[:300]}
     # every measured launch's device-side status: a bounded wait that gave up or a mesh error
     # would make the timed work incomplete (0 = FEM_OK)
     device_status = fem.fem_device_error()
