@@ -15,6 +15,7 @@ from .binding import (  # noqa: F401
     FEM_FP64_DF,
     FEM_MAX_QPTS,
     FemError,
+    PreparedCall,
     fem_adjoint_laplacian,
     fem_build_node2cell,
     fem_check_mesh,
@@ -31,6 +32,8 @@ from .binding import (  # noqa: F401
     fem_integrate_laplacian_transposed,
     fem_integrate_pointwise,
     fem_integrate_laplacian_prepared,
+    prepared_integrate_elasticity,
+    prepared_integrate_laplacian,
     fem_prepare_vertices,
     fem_integrate_reaction_diffusion,
     fem_precompute_geometry,

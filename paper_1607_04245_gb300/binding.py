@@ -166,8 +166,26 @@ def _mesh_sizes(coords: torch.Tensor, conn: torch.Tensor):
     return int(dim), int(V), int(conn.shape[1])
 
 
-def fem_integrate_laplacian(coords, conn, u, K, qpts, qw, out=None, prec="mixed", stream=None) -> torch.Tensor:
-    """Element residuals [dim+1][C] of the variable-coefficient Laplacian."""
+class PreparedCall:
+    """One C-ABI call whose arguments were validated and marshalled once, for loops that
+    repeat it on the same buffers (Python's per-call checks cost about as much host time
+    as a small kernel takes on the device). Calling it runs the plain entry point again
+    with the same pointers, sizes and stream; the tensors and host tables it was made from
+    stay referenced for its life and must keep their storage."""
+
+    def __init__(self, name: str, args, keep):
+        self._f = getattr(lib(), name)
+        self._name = name
+        self._args = tuple(t(a) for t, a in zip(self._f.argtypes, args))  # converted once
+        self._keep = keep
+
+    def __call__(self):
+        st = self._f(*self._args)
+        if st != 0:
+            _check(self._name, st)
+
+
+def _laplacian_call(coords, conn, u, K, qpts, qw, out, prec, stream):
     p = precision(prec)
     dt = value_dtype(p)
     dim, V, C = _mesh_sizes(coords, conn)
@@ -176,12 +194,24 @@ def fem_integrate_laplacian(coords, conn, u, K, qpts, qw, out=None, prec="mixed"
     if out is None:
         out = torch.empty((dim + 1, C), dtype=dt, device=dev)
     qp, w = _HostTable(qpts, (nq, dim), "qpts"), _HostTable(qw, (nq,), "qw")
-    st = lib().fem_integrate_laplacian(
-        dim, C, V, _dev(coords, "coords", torch.float64, device=dev), _dev(conn, "conn", torch.int32, device=dev),
-        _dev(u, "u", dt, (V,), dev), _dev(K, "K", dt, (nq, C), dev), nq, qp.ptr, w.ptr,
-        _dev(out, "out", dt, (dim + 1, C), dev), p, _stream(stream))
-    _check("fem_integrate_laplacian", st)
+    args = (dim, C, V, _dev(coords, "coords", torch.float64, device=dev), _dev(conn, "conn", torch.int32, device=dev),
+            _dev(u, "u", dt, (V,), dev), _dev(K, "K", dt, (nq, C), dev), nq, qp.ptr, w.ptr,
+            _dev(out, "out", dt, (dim + 1, C), dev), p, _stream(stream))
+    return out, args, (coords, conn, u, K, out, qp, w)
+
+
+def fem_integrate_laplacian(coords, conn, u, K, qpts, qw, out=None, prec="mixed", stream=None) -> torch.Tensor:
+    """Element residuals [dim+1][C] of the variable-coefficient Laplacian."""
+    out, args, _keep = _laplacian_call(coords, conn, u, K, qpts, qw, out, prec, stream)
+    _check("fem_integrate_laplacian", lib().fem_integrate_laplacian(*args))
     return out
+
+
+def prepared_integrate_laplacian(coords, conn, u, K, qpts, qw, out, prec="mixed", stream=None) -> PreparedCall:
+    """fem_integrate_laplacian on fixed buffers as a PreparedCall: each call of the result
+    launches the residual into `out` again."""
+    _, args, keep = _laplacian_call(coords, conn, u, K, qpts, qw, out, prec, stream)
+    return PreparedCall("fem_integrate_laplacian", args, keep)
 
 
 def fem_integrate_laplacian_fields(coords, conn, u, K, qpts, qw, out=None, prec="mixed", stream=None) -> torch.Tensor:
@@ -204,8 +234,7 @@ def fem_integrate_laplacian_fields(coords, conn, u, K, qpts, qw, out=None, prec=
     return out
 
 
-def fem_integrate_elasticity(coords, conn, u, lam, mu, qpts, qw, out=None, prec="mixed", stream=None) -> torch.Tensor:
-    """Element residuals [(dim+1)*dim][C] of linear elasticity (row b*dim + k)."""
+def _elasticity_call(coords, conn, u, lam, mu, qpts, qw, out, prec, stream):
     p = precision(prec)
     dt = value_dtype(p)
     dim, V, C = _mesh_sizes(coords, conn)
@@ -214,12 +243,24 @@ def fem_integrate_elasticity(coords, conn, u, lam, mu, qpts, qw, out=None, prec=
     if out is None:
         out = torch.empty(((dim + 1) * dim, C), dtype=dt, device=dev)
     qp, w = _HostTable(qpts, (nq, dim), "qpts"), _HostTable(qw, (nq,), "qw")
-    st = lib().fem_integrate_elasticity(
-        dim, C, V, _dev(coords, "coords", torch.float64, device=dev), _dev(conn, "conn", torch.int32, device=dev),
-        _dev(u, "u", dt, (dim, V), dev), _dev(lam, "lam", dt, (nq, C), dev), _dev(mu, "mu", dt, (nq, C), dev),
-        nq, qp.ptr, w.ptr, _dev(out, "out", dt, ((dim + 1) * dim, C), dev), p, _stream(stream))
-    _check("fem_integrate_elasticity", st)
+    args = (dim, C, V, _dev(coords, "coords", torch.float64, device=dev), _dev(conn, "conn", torch.int32, device=dev),
+            _dev(u, "u", dt, (dim, V), dev), _dev(lam, "lam", dt, (nq, C), dev), _dev(mu, "mu", dt, (nq, C), dev),
+            nq, qp.ptr, w.ptr, _dev(out, "out", dt, ((dim + 1) * dim, C), dev), p, _stream(stream))
+    return out, args, (coords, conn, u, lam, mu, out, qp, w)
+
+
+def fem_integrate_elasticity(coords, conn, u, lam, mu, qpts, qw, out=None, prec="mixed", stream=None) -> torch.Tensor:
+    """Element residuals [(dim+1)*dim][C] of linear elasticity (row b*dim + k)."""
+    out, args, _keep = _elasticity_call(coords, conn, u, lam, mu, qpts, qw, out, prec, stream)
+    _check("fem_integrate_elasticity", lib().fem_integrate_elasticity(*args))
     return out
+
+
+def prepared_integrate_elasticity(coords, conn, u, lam, mu, qpts, qw, out, prec="mixed",
+                                  stream=None) -> PreparedCall:
+    """fem_integrate_elasticity on fixed buffers as a PreparedCall."""
+    _, args, keep = _elasticity_call(coords, conn, u, lam, mu, qpts, qw, out, prec, stream)
+    return PreparedCall("fem_integrate_elasticity", args, keep)
 
 
 def fem_prepare_vertices(coords, rec=None, stream=None) -> torch.Tensor:

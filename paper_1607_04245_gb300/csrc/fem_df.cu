@@ -190,6 +190,8 @@ struct DfArgs {
 
 template <int DIM>
 __global__ void __launch_bounds__(kBlock, 5) lap_df_kernel(const __grid_constant__ DfArgs a) {
+    pdl_wait();  // overlapped launch: the previous kernel's writes are visible from here
+    pdl_trigger();
     constexpr int NB = DIM + 1;
     const int64_t C = a.C;
     const double *X[DIM];
@@ -261,10 +263,10 @@ fem_status launch_lap_df(int dim, int64_t n_cells, int64_t n_verts, const double
     for (int q = 0; q < FEM_MAX_QPTS; ++q) a.wd[q] = q < n_q ? qw[q] : 0.0;
     if (dim == 2) {
         auto k = lap_df_kernel<2>;
-        k<<<grid_for(n_cells, kBlock, reinterpret_cast<const void *>(k)), kBlock, 0, stream>>>(a);
+        launch_overlapped(k, grid_for(n_cells, kBlock, reinterpret_cast<const void *>(k)), kBlock, 0, stream, a);
     } else {
         auto k = lap_df_kernel<3>;
-        k<<<grid_for(n_cells, kBlock, reinterpret_cast<const void *>(k)), kBlock, 0, stream>>>(a);
+        launch_overlapped(k, grid_for(n_cells, kBlock, reinterpret_cast<const void *>(k)), kBlock, 0, stream, a);
     }
     return check_launch("fem_integrate_laplacian (FEM_FP64_DF)");
 }
@@ -288,6 +290,8 @@ struct DfElArgs {
 
 template <int DIM>
 __global__ void __launch_bounds__(kBlock) el_df_kernel(const __grid_constant__ DfElArgs a) {
+    pdl_wait();  // overlapped launch: the previous kernel's writes are visible from here
+    pdl_trigger();
     constexpr int NB = DIM + 1;
     const int64_t C = a.C;
     const int64_t V = a.V;
@@ -378,10 +382,10 @@ fem_status launch_el_df(int dim, int64_t n_cells, int64_t n_verts, const double 
     }
     if (dim == 2) {
         auto k = el_df_kernel<2>;
-        k<<<grid_for(n_cells, kBlock, reinterpret_cast<const void *>(k)), kBlock, 0, stream>>>(a);
+        launch_overlapped(k, grid_for(n_cells, kBlock, reinterpret_cast<const void *>(k)), kBlock, 0, stream, a);
     } else {
         auto k = el_df_kernel<3>;
-        k<<<grid_for(n_cells, kBlock, reinterpret_cast<const void *>(k)), kBlock, 0, stream>>>(a);
+        launch_overlapped(k, grid_for(n_cells, kBlock, reinterpret_cast<const void *>(k)), kBlock, 0, stream, a);
     }
     return check_launch("fem_integrate_elasticity (FEM_FP64_DF)");
 }
@@ -404,6 +408,8 @@ struct DfAdjArgs {
 
 template <int DIM>
 __global__ void __launch_bounds__(kBlock) adj_df_kernel(const __grid_constant__ DfAdjArgs a) {
+    pdl_wait();  // overlapped launch: the previous kernel's writes are visible from here
+    pdl_trigger();
     constexpr int NB = DIM + 1;
     const int64_t C = a.C;
     const double *X[DIM];
@@ -479,10 +485,10 @@ fem_status launch_adj_df(int dim, int64_t n_cells, int64_t n_verts, const double
     }
     if (dim == 2) {
         auto k = adj_df_kernel<2>;
-        k<<<grid_for(n_cells, kBlock, reinterpret_cast<const void *>(k)), kBlock, 0, stream>>>(a);
+        launch_overlapped(k, grid_for(n_cells, kBlock, reinterpret_cast<const void *>(k)), kBlock, 0, stream, a);
     } else {
         auto k = adj_df_kernel<3>;
-        k<<<grid_for(n_cells, kBlock, reinterpret_cast<const void *>(k)), kBlock, 0, stream>>>(a);
+        launch_overlapped(k, grid_for(n_cells, kBlock, reinterpret_cast<const void *>(k)), kBlock, 0, stream, a);
     }
     return check_launch("fem_adjoint_laplacian (FEM_FP64_DF)");
 }

@@ -126,6 +126,8 @@ constexpr int el_min_blocks() {
 
 template <int DIM, int P, int CPT, int NQ>
 __global__ void __launch_bounds__(kBlock, el_min_blocks<DIM, P, CPT>()) el_kernel(const __grid_constant__ ElArgs a) {
+    pdl_wait();  // overlapped launch: the previous kernel's writes are visible from here
+    pdl_trigger();
     constexpr int NB = DIM + 1;
     using T = val_t<P>;
     const int64_t C = a.C;
@@ -239,13 +241,13 @@ static fem_status launch_el(const ElArgs &a, bool vec4, bool vec2, cudaStream_t 
     // the quadrature size of the workloads' rules (3 points in 2D, 4 in 3D) is compiled in
     if (vec && a.w.nq == DIM + 1) {
         auto k = el_kernel<DIM, P, CPTV, DIM + 1>;
-        k<<<grid_for((a.C + CPTV - 1) / CPTV, kBlock, reinterpret_cast<const void *>(k)), kBlock, 0, s>>>(a);
+        launch_overlapped(k, grid_for((a.C + CPTV - 1) / CPTV, kBlock, reinterpret_cast<const void *>(k)), kBlock, 0, s, a);
     } else if (vec) {
         auto k = el_kernel<DIM, P, CPTV, 0>;
-        k<<<grid_for((a.C + CPTV - 1) / CPTV, kBlock, reinterpret_cast<const void *>(k)), kBlock, 0, s>>>(a);
+        launch_overlapped(k, grid_for((a.C + CPTV - 1) / CPTV, kBlock, reinterpret_cast<const void *>(k)), kBlock, 0, s, a);
     } else {
         auto k = el_kernel<DIM, P, 1, 0>;
-        k<<<grid_for(a.C, kBlock, reinterpret_cast<const void *>(k)), kBlock, 0, s>>>(a);
+        launch_overlapped(k, grid_for(a.C, kBlock, reinterpret_cast<const void *>(k)), kBlock, 0, s, a);
     }
     return check_launch("fem_integrate_elasticity");
 }

@@ -28,6 +28,8 @@ struct GeomArgs {
 // value type (float32 storage rounds each entry once)
 template <int DIM, int P>
 __global__ void __launch_bounds__(kBlock) geometry_kernel(const __grid_constant__ GeomArgs a) {
+    pdl_wait();  // overlapped launch: the previous kernel's writes are visible from here
+    pdl_trigger();
     constexpr int NB = DIM + 1;
     using T = val_t<P>;
     const int64_t C = a.C;
@@ -80,6 +82,8 @@ __device__ __forceinline__ val_t<P> gweight(const QuadW &w, int q) {
 // fixes the quadrature size at compile time.
 template <int DIM, int P, int CPT, int NQ>
 __global__ void __launch_bounds__(kBlock) lap_geom_kernel(const __grid_constant__ LapGeomArgs a) {
+    pdl_wait();  // overlapped launch: the previous kernel's writes are visible from here
+    pdl_trigger();
     constexpr int NB = DIM + 1;
     using T = val_t<P>;
     const int64_t C = a.C;
@@ -152,13 +156,13 @@ template <int DIM, int P>
 static fem_status launch_geom_lap(const LapGeomArgs &a, bool vec, cudaStream_t s) {
     if (vec && a.w.nq == DIM + 1) {
         auto k = lap_geom_kernel<DIM, P, 4, DIM + 1>;
-        k<<<grid_for((a.C + 3) / 4, kBlock, reinterpret_cast<const void *>(k)), kBlock, 0, s>>>(a);
+        launch_overlapped(k, grid_for((a.C + 3) / 4, kBlock, reinterpret_cast<const void *>(k)), kBlock, 0, s, a);
     } else if (vec) {
         auto k = lap_geom_kernel<DIM, P, 4, 0>;
-        k<<<grid_for((a.C + 3) / 4, kBlock, reinterpret_cast<const void *>(k)), kBlock, 0, s>>>(a);
+        launch_overlapped(k, grid_for((a.C + 3) / 4, kBlock, reinterpret_cast<const void *>(k)), kBlock, 0, s, a);
     } else {
         auto k = lap_geom_kernel<DIM, P, 1, 0>;
-        k<<<grid_for(a.C, kBlock, reinterpret_cast<const void *>(k)), kBlock, 0, s>>>(a);
+        launch_overlapped(k, grid_for(a.C, kBlock, reinterpret_cast<const void *>(k)), kBlock, 0, s, a);
     }
     return check_launch("fem_integrate_laplacian_geom");
 }
@@ -186,10 +190,10 @@ extern "C" fem_status fem_precompute_geometry(int dim, int64_t n_cells, int64_t 
     const bool f64 = prec == FEM_FP64;
     if (dim == 2) {
         auto k = f64 ? geometry_kernel<2, FEM_FP64> : geometry_kernel<2, FEM_FP32>;
-        k<<<grid_for(n_cells, kBlock, reinterpret_cast<const void *>(k)), kBlock, 0, stream>>>(a);
+        launch_overlapped(k, grid_for(n_cells, kBlock, reinterpret_cast<const void *>(k)), kBlock, 0, stream, a);
     } else {
         auto k = f64 ? geometry_kernel<3, FEM_FP64> : geometry_kernel<3, FEM_FP32>;
-        k<<<grid_for(n_cells, kBlock, reinterpret_cast<const void *>(k)), kBlock, 0, stream>>>(a);
+        launch_overlapped(k, grid_for(n_cells, kBlock, reinterpret_cast<const void *>(k)), kBlock, 0, stream, a);
     }
     return check_launch("fem_precompute_geometry");
 }

@@ -62,6 +62,40 @@ __device__ __forceinline__ void record_device_error(unsigned *err, unsigned bits
     if ((*reinterpret_cast<volatile unsigned *>(err) & bits) != bits) atomicOr(err, bits);
 }
 
+// ------------------------------------------------------------------ overlapped launches
+//
+// Programmatic dependent launch (sm_90 and later): a kernel launched with programmatic
+// stream serialisation may be scheduled onto the SMs while the kernel before it on the
+// stream is still draining. pdl_wait() holds the calling thread until that kernel has
+// completed and its writes are visible, so a kernel that calls it before touching global
+// memory keeps plain stream order for its data; without the launch attribute it returns
+// at once. pdl_trigger() allows the next such kernel to be scheduled as this one's CTAs
+// exit (it changes nothing about what that kernel sees: it waits in turn).
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+
+// Launch k with programmatic stream serialisation, except while `s` is being captured
+// into a graph (there the launch is plain, so graph bodies keep full dependencies). The
+// kernel must call pdl_wait() before its first global memory access.
+template <class... KArgs, class... Args>
+cudaError_t launch_overlapped(void (*k)(KArgs...), unsigned grid, unsigned block, size_t smem, cudaStream_t s,
+                              Args... args) {
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    bool plain = cudaStreamIsCapturing(s, &cs) != cudaSuccess || cs != cudaStreamCaptureStatusNone;
+    if (plain) cudaGetLastError();  // a refused query only selects the plain launch
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    at[0].val.programmaticStreamSerializationAllowed = 1;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(grid);
+    cfg.blockDim = dim3(block);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cfg.attrs = at;
+    cfg.numAttrs = plain ? 0 : 1;
+    return cudaLaunchKernelEx(&cfg, k, args...);
+}
+
 // Clamp a vertex id into [0, n): malformed input cannot read out of bounds.
 __device__ __forceinline__ uint32_t clamp_vid(int32_t v, uint32_t n) {
     return min(static_cast<uint32_t>(v), n - 1u);

@@ -168,6 +168,8 @@ __device__ __forceinline__ void lap_cell(const double (&xs)[DIM + 1][DIM],
 // path, which reads page-locked host memory.
 template <int DIM, int P, int CPT, int NQ, bool ADJ>
 __global__ void __launch_bounds__(kBlock) lap_kernel(const __grid_constant__ LapArgs a) {
+    pdl_wait();  // overlapped launch: the previous kernel's writes are visible from here
+    pdl_trigger();
     constexpr int NB = DIM + 1;
     using T = val_t<P>;
     const int64_t C = a.C;
@@ -304,6 +306,8 @@ __device__ __noinline__ void lap_fields_fallback(const FieldsArgs &fa, int64_t c
 
 template <int DIM, int P, int CPT, int NQ>
 __global__ void __launch_bounds__(kBlock) lap_fields_kernel(const __grid_constant__ FieldsArgs fa) {
+    pdl_wait();  // overlapped launch: the previous kernel's writes are visible from here
+    pdl_trigger();
     constexpr int NB = DIM + 1;
     using T = val_t<P>;
     const LapArgs &a = fa.a;
@@ -390,10 +394,10 @@ static fem_status launch_fields(const FieldsArgs &fa, bool vec, cudaStream_t s) 
     constexpr int NQN = DIM == 3 ? 4 : 3;  // the workloads' rules
     if (vec && fa.a.w.nq == NQN) {
         auto k = lap_fields_kernel<DIM, P, CPTV, NQN>;
-        k<<<grid_for((fa.a.C + CPTV - 1) / CPTV, kBlock, reinterpret_cast<const void *>(k)), kBlock, 0, s>>>(fa);
+        launch_overlapped(k, grid_for((fa.a.C + CPTV - 1) / CPTV, kBlock, reinterpret_cast<const void *>(k)), kBlock, 0, s, fa);
     } else {
         auto k = lap_fields_kernel<DIM, P, 1, 0>;
-        k<<<grid_for(fa.a.C, kBlock, reinterpret_cast<const void *>(k)), kBlock, 0, s>>>(fa);
+        launch_overlapped(k, grid_for(fa.a.C, kBlock, reinterpret_cast<const void *>(k)), kBlock, 0, s, fa);
     }
     return check_launch("fem_integrate_laplacian_fields");
 }
@@ -510,6 +514,8 @@ constexpr int pair_min_blocks() { return ADJ ? 3 : 4; }
 template <int DIM, int P, int NQ, bool ADJ>
 __global__ void __launch_bounds__(kBlock, pair_min_blocks<ADJ>()) lap_pair_kernel(const __grid_constant__ LapArgs a) {
     static_assert(P != FEM_FP64, "float32 forms only");
+    pdl_wait();  // launched overlapped: the previous kernel's writes are visible from here
+    pdl_trigger();
     constexpr int NB = DIM + 1;
     const int64_t C = a.C;  // even
     const float *__restrict__ u = static_cast<const float *>(a.u);
@@ -576,7 +582,7 @@ __global__ void __launch_bounds__(kBlock, pair_min_blocks<ADJ>()) lap_pair_kerne
 template <int DIM, int P, int NQ, bool ADJ>
 static void launch_pair(const LapArgs &a, cudaStream_t s) {
     auto k = lap_pair_kernel<DIM, P, NQ, ADJ>;
-    k<<<resident_grid(reinterpret_cast<const void *>(k), kBlock, a.C / 2), kBlock, 0, s>>>(a);
+    launch_overlapped(k, resident_grid(reinterpret_cast<const void *>(k), kBlock, a.C / 2), kBlock, 0, s, a);
 }
 
 // ------------------------------------------------------------------ prepared vertex records
@@ -631,6 +637,8 @@ __device__ __forceinline__ void ld_record(const float *rec, uint32_t v, float (&
 // 64 registers, where the eight record values of two cells' vertices spill
 template <int DIM, int NQ>
 __global__ void __launch_bounds__(kBlock, 3) lap_rec_kernel(const __grid_constant__ LapArgs a, const float *rec) {
+    pdl_wait();  // overlapped launch: the previous kernel's writes are visible from here
+    pdl_trigger();
     constexpr int NB = DIM + 1;
     const int64_t C = a.C;  // even
     const float *__restrict__ u = static_cast<const float *>(a.u);
@@ -780,6 +788,8 @@ __device__ __forceinline__ void lap_chunk(const LapArgs &a, const double *const 
 template <int DIM, int P, int NQ, bool ADJ>
 __global__ void __launch_bounds__(kStagedThreads, FEM_STAGED_MIN_CTAS)
     lap_staged_kernel(const __grid_constant__ LapArgs a, int stages, unsigned *err) {
+    pdl_wait();  // overlapped launch: the previous kernel's writes are visible from here
+    pdl_trigger();
     constexpr int NB = DIM + 1;
     using T = val_t<P>;
     extern __shared__ __align__(128) unsigned char smem[];
@@ -826,7 +836,7 @@ static fem_status launch_staged(const LapArgs &a, uint32_t sb, cudaStream_t s) {
     int grid = 0;
     fem_status st = staged_grid(reinterpret_cast<const void *>(k), kStagedThreads, smem, (a.C + kTile - 1) / kTile, grid);
     if (st != FEM_OK) return st;
-    k<<<grid, kStagedThreads, smem, s>>>(a, stages, err);
+    launch_overlapped(k, grid, kStagedThreads, smem, s, a, stages, err);
     return FEM_OK;
 }
 
@@ -846,8 +856,8 @@ static fem_status launch_lap(const LapArgs &a, bool vec, bool pairs, cudaStream_
             int block = static_cast<int>((per + 31) / 32 * 32);
             block = block < 32 ? 32 : (block > kBlock ? kBlock : block);
             const unsigned grid = static_cast<unsigned>((a.C + block - 1) / block);
-            if (native_nq) lap_kernel<DIM, P, 1, DIM + 1, ADJ><<<grid, block, 0, s>>>(a);
-            else lap_kernel<DIM, P, 1, 0, ADJ><<<grid, block, 0, s>>>(a);
+            if (native_nq) launch_overlapped((lap_kernel<DIM, P, 1, DIM + 1, ADJ>), grid, block, 0, s, a);
+            else launch_overlapped((lap_kernel<DIM, P, 1, 0, ADJ>), grid, block, 0, s, a);
             return check_launch(ADJ ? "fem_adjoint_laplacian" : "fem_integrate_laplacian");
         }
     }
@@ -871,15 +881,15 @@ static fem_status launch_lap(const LapArgs &a, bool vec, bool pairs, cudaStream_
     if (vec && native_nq) {
         auto k = lap_kernel<DIM, P, 4, DIM + 1, ADJ>;
         int grid = grid_for((a.C + 3) / 4, kBlock, reinterpret_cast<const void *>(k));
-        k<<<grid, kBlock, 0, s>>>(a);
+        launch_overlapped(k, grid, kBlock, 0, s, a);
     } else if (vec) {
         auto k = lap_kernel<DIM, P, 4, 0, ADJ>;
         int grid = grid_for((a.C + 3) / 4, kBlock, reinterpret_cast<const void *>(k));
-        k<<<grid, kBlock, 0, s>>>(a);
+        launch_overlapped(k, grid, kBlock, 0, s, a);
     } else {
         auto k = lap_kernel<DIM, P, 1, 0, ADJ>;
         int grid = grid_for(a.C, kBlock, reinterpret_cast<const void *>(k));
-        k<<<grid, kBlock, 0, s>>>(a);
+        launch_overlapped(k, grid, kBlock, 0, s, a);
     }
     return check_launch(ADJ ? "fem_adjoint_laplacian" : "fem_integrate_laplacian");
 }
@@ -1080,10 +1090,10 @@ extern "C" fem_status fem_integrate_laplacian_prepared(int dim, int64_t n_cells,
     const bool native_nq = (dim == 3 && n_q == 4) || (dim == 2 && n_q == 3);
     if (dim == 3) {
         auto k = native_nq ? lap_rec_kernel<3, 4> : lap_rec_kernel<3, 0>;
-        k<<<resident_grid(reinterpret_cast<const void *>(k), kBlock, n_cells / 2), kBlock, 0, stream>>>(a, rec);
+        launch_overlapped(k, resident_grid(reinterpret_cast<const void *>(k), kBlock, n_cells / 2), kBlock, 0, stream, a, rec);
     } else {
         auto k = native_nq ? lap_rec_kernel<2, 3> : lap_rec_kernel<2, 0>;
-        k<<<resident_grid(reinterpret_cast<const void *>(k), kBlock, n_cells / 2), kBlock, 0, stream>>>(a, rec);
+        launch_overlapped(k, resident_grid(reinterpret_cast<const void *>(k), kBlock, n_cells / 2), kBlock, 0, stream, a, rec);
     }
     return check_launch("fem_integrate_laplacian_prepared");
 }

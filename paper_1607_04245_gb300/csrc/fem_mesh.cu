@@ -167,6 +167,8 @@ __global__ void sort_segments_kernel(const int32_t *ptr, int32_t *idx, int64_t V
 template <int NB, int NCOMP, class T>
 __global__ void gather_kernel(int64_t C, int64_t V, const T *__restrict__ elem, const int32_t *__restrict__ ptr,
                               const int32_t *__restrict__ idx, T *__restrict__ out) {
+    pdl_wait();  // overlapped launch: the previous kernel's writes are visible from here
+    pdl_trigger();
     const int64_t stride = int64_t(gridDim.x) * blockDim.x;
     auto entry = [&](int32_t t, int k) {
         const int32_t cell = t / NB, a = t - cell * NB;
@@ -212,15 +214,15 @@ static void launch_gather_t(int n_comp, int64_t C, int64_t V, const void *elem, 
     switch (n_comp) {
         case 1: {
             auto k = gather_kernel<NB, 1, T>;
-            k<<<grid_for(V, kBlock, reinterpret_cast<const void *>(k)), kBlock, 0, s>>>(C, V, el, ptr, idx, o);
+            launch_overlapped(k, grid_for(V, kBlock, reinterpret_cast<const void *>(k)), kBlock, 0, s, C, V, el, ptr, idx, o);
         } break;
         case 2: {
             auto k = gather_kernel<NB, 2, T>;
-            k<<<grid_for(V, kBlock, reinterpret_cast<const void *>(k)), kBlock, 0, s>>>(C, V, el, ptr, idx, o);
+            launch_overlapped(k, grid_for(V, kBlock, reinterpret_cast<const void *>(k)), kBlock, 0, s, C, V, el, ptr, idx, o);
         } break;
         default: {
             auto k = gather_kernel<NB, 3, T>;
-            k<<<grid_for(V, kBlock, reinterpret_cast<const void *>(k)), kBlock, 0, s>>>(C, V, el, ptr, idx, o);
+            launch_overlapped(k, grid_for(V, kBlock, reinterpret_cast<const void *>(k)), kBlock, 0, s, C, V, el, ptr, idx, o);
         } break;
     }
 }

@@ -249,6 +249,8 @@ constexpr int rd_min_blocks() {
 
 template <int DIM, int P, bool A_P1, bool REACT, bool DRIFT, int CPT, int NQ>
 __global__ void __launch_bounds__(kBlock, rd_min_blocks<DIM, P, CPT>()) rd_kernel(const __grid_constant__ RdArgs a) {
+    pdl_wait();  // overlapped launch: the previous kernel's writes are visible from here
+    pdl_trigger();
     static_assert(A_P1 || !DRIFT, "grad a vanishes inside a cell for a P0 field");
     static_assert(CPT == 1 || NQ > 0, "vector rows need a compile-time quadrature size");
     constexpr int NB = DIM + 1;
@@ -316,10 +318,10 @@ static void launch_rd_one(const RdArgs &a, bool vec4, bool vec2, cudaStream_t s)
     const bool vec = CPTV == 2 ? vec2 : vec4;
     if (P != FEM_FP64 && vec && a.w.nq == NQN) {
         auto k = rd_kernel<DIM, P, A_P1, REACT, DRIFT, CPTV, NQN>;
-        k<<<grid_for((a.C + CPTV - 1) / CPTV, kBlock, reinterpret_cast<const void *>(k)), kBlock, 0, s>>>(a);
+        launch_overlapped(k, grid_for((a.C + CPTV - 1) / CPTV, kBlock, reinterpret_cast<const void *>(k)), kBlock, 0, s, a);
     } else {
         auto k = rd_kernel<DIM, P, A_P1, REACT, DRIFT, 1, 0>;
-        k<<<grid_for(a.C, kBlock, reinterpret_cast<const void *>(k)), kBlock, 0, s>>>(a);
+        launch_overlapped(k, grid_for(a.C, kBlock, reinterpret_cast<const void *>(k)), kBlock, 0, s, a);
     }
 }
 

@@ -48,3 +48,17 @@ def test_committed_record_names_the_headline_kernel():
     assert len(rec) == 1
     kv = dict(x.split("=", 1) for x in rec[0].split()[1:])
     assert len(kv["src"]) == 16 and int(kv["bytes"]) == int(kv["read"]) + int(kv["write"])
+
+
+def test_rotating_copies_keep_each_step_out_of_the_l2():
+    """The timed steps cycle through input copies: between two uses of one copy the other
+    copies move at least 3 L2 sizes; too small a workload (over 128 copies) is timed with
+    a flush instead (None)."""
+    l2 = 126 << 20
+    for set_bytes in (83_186_972, 135 << 20, 3 << 20, 1 << 30):
+        n = bench.rotating_sets(set_bytes, l2)
+        assert n is not None and n >= 2
+        assert (n - 1) * set_bytes >= bench.ROTATE_L2_MULT * l2
+        assert n == 2 or (n - 2) * set_bytes < bench.ROTATE_L2_MULT * l2  # no more copies than needed
+    assert bench.rotating_sets(83_186_972, l2) == 6
+    assert bench.rotating_sets(600_000, l2) is None
