@@ -324,6 +324,33 @@ def timed_rotating(step_fns, steps, warmup, stream, dist=None, ws=1, sampler=Non
     return [per] * steps, t1 - t0, clocks, t_enq * 1e3 / steps
 
 
+def _nbytes(ts):
+    return sum(t.numel() * t.element_size() for t in ts if t is not None)
+
+
+def timed_copies(make_step, set_bytes, device, stream, flush, steps, warmup):
+    """Time one row. make_step(i) makes copy i of the row's device inputs and outputs
+    (i = 0: the originals) and returns (step, outputs): back to back over rotating copies
+    when rotating_sets allows (every copy's outputs must then equal copy 0's), else one
+    launch at a time after an L2 flush. Returns (per-step ms, timing note, extra fields)."""
+    import torch
+
+    n = rotating_sets(set_bytes, l2_bytes(device))
+    with torch.cuda.stream(stream):
+        if not n:
+            ms, _, _ = timed_steps(make_step(0)[0], steps, warmup, stream, flush)
+            return ms, "one launch at a time after an L2 flush, CUDA events around each launch", {}
+        made = [make_step(i) for i in range(n)]
+        ms, _, _, host = timed_rotating([m[0] for m in made], steps, warmup, stream)
+    torch.cuda.synchronize()
+    for _, outs in made[1:]:
+        if not all(torch.equal(a, b) for a, b in zip(outs, made[0][1])):
+            raise RuntimeError("an input copy gave different results")
+    note = (f"back to back over {n} resident input copies ({n * set_bytes / 1e6:.0f} MB, inputs larger than L2), "
+            "one event pair around the timed steps")
+    return ms, note, {"host_enqueue_ms_per_step": round(host, 6)}
+
+
 def measure_fp64_fma_rate(device):
     """float64 FMA instructions per second on this GPU: the library's probe kernel (every
     thread runs 8 independent chains of dependent float64 FMAs), timed with CUDA events;
@@ -481,22 +508,32 @@ def measure_geometry_path(case, prec, device, stream, flush, steps, warmup, peak
 
     import paper_1607_04245_gb300 as fem
 
-    c, d = device_case(case, prec, device)
+    c, d0 = device_case(case, prec, device)
     q = c.rule
     dt = fem.value_dtype(prec)
-    with torch.cuda.stream(stream):
-        geom = fem.fem_precompute_geometry(d["coords"], d["conn"], prec=prec, stream=stream)
+    res = {}
+
+    def make(i):
+        d = d0 if i == 0 else {k: v.clone() for k, v in d0.items()}
+        with torch.cuda.stream(stream):
+            geom = fem.fem_precompute_geometry(d["coords"], d["conn"], prec=prec, stream=stream)
         out = torch.empty((c.dim + 1, c.n_cells), dtype=dt, device=device)
-        fn = lambda: fem.fem_integrate_laplacian_geom(d["conn"], c.n_verts, d["u"], d["K"], q.points, q.weights, geom,
-                                                      out=out, prec=prec, stream=stream)
-        ms, _, _ = timed_steps(fn, steps, warmup, stream, flush)
+        if i == 0:
+            res["out"] = out
+        return fem.fem_integrate_laplacian_geom(d["conn"], c.n_verts, d["u"], d["K"], q.points, q.weights, geom,
+                                                out=out, prec=prec, stream=stream, prepare=True), (out,)
+
+    sb = _nbytes([d0["conn"], d0["u"], d0["K"]]) + (c.dim * c.dim + 1 + c.dim + 1) * c.n_cells * (
+        8 if prec == "fp64" else 4)  # the timed step's inputs, geometry and outputs
+    ms, note, extra = timed_copies(make, sb, device, stream, flush, steps, warmup)
+    out = res["out"]
     t = statistics.mean(ms) * 1e-3
     s = 8 if prec == "fp64" else 4
     nb = c.dim + 1
     nbytes = nb * 4 * c.n_cells + q.n_q * s * c.n_cells + (c.dim * c.dim + 1) * s * c.n_cells + nb * s * c.n_cells \
         + s * c.n_verts
     row = {"physics": "laplacian_precomputed_geometry", "dim": c.dim, "prec": prec, "cells": c.n_cells,
-           "ms_per_launch": round(statistics.mean(ms), 6), "cells_per_s": c.n_cells / t,
+           "ms_per_launch": round(statistics.mean(ms), 6), "timing": note, **extra, "cells_per_s": c.n_cells / t,
            "alg_bytes_per_launch": nbytes, "alg_gbs": nbytes / t / 1e9, "hbm_frac_of_measured": nbytes / t / 1e9 / peak,
            "alg_bytes_per_cell": "conn 16 + K 4s + geom 10s + out 4s + (V/C) u s (s = value bytes); geometry "
                                  "precomputed once per mesh, not timed"}
@@ -560,21 +597,33 @@ def measure_adjoint(case, prec, device, stream, flush, steps, warmup, peak, orac
 
     import paper_1607_04245_gb300 as fem
 
-    c, d = device_case(case, prec, device)
+    c, d0 = device_case(case, prec, device)
     q = c.rule
-    with torch.cuda.stream(stream):
-        ptr, idx = fem.fem_build_node2cell(d["conn"], c.n_verts, stream=stream)
-        dt = fem.value_dtype(prec)
+    dt = fem.value_dtype(prec)
+    res = {}
+
+    def make(i):
+        d = d0 if i == 0 else {k: v.clone() for k, v in d0.items()}
+        with torch.cuda.stream(stream):
+            ptr, idx = fem.fem_build_node2cell(d["conn"], c.n_verts, stream=stream)
         dK = torch.empty((q.n_q, c.n_cells), dtype=dt, device=device)
         du = torch.empty(c.n_verts, dtype=dt, device=device)
         scratch = torch.empty((c.dim + 1, c.n_cells), dtype=dt, device=device)
-        fn = lambda: fem.fem_adjoint_laplacian(d["coords"], d["conn"], d["u"], d["K"], q.points, q.weights, d["adj"],
-                                               ptr, idx, dK=dK, du=du, scratch=scratch, prec=prec, stream=stream)
-        ms, _, _ = timed_steps(fn, steps, warmup, stream, flush)
+        if i == 0:
+            res["dK"], res["du"] = dK, du
+        return fem.fem_adjoint_laplacian(d["coords"], d["conn"], d["u"], d["K"], q.points, q.weights, d["adj"], ptr,
+                                         idx, dK=dK, du=du, scratch=scratch, prec=prec, stream=stream,
+                                         prepare=True), (dK, du)
+
+    sz = 8 if prec in ("fp64", "fp64_df") else 4
+    sb = _nbytes(d0.values()) + (q.n_q + c.dim + 1) * c.n_cells * sz + c.n_verts * sz \
+        + 4 * ((c.dim + 1) * c.n_cells + c.n_verts + 1)  # inputs, dK, scratch, du, vertex-to-cell lists
+    ms, note, extra = timed_copies(make, sb, device, stream, flush, steps, warmup)
+    dK, du = res["dK"], res["du"]
     t = statistics.mean(ms) * 1e-3
     nbytes = adjoint_bytes(c.dim, prec, c.n_cells, c.n_verts, q.n_q)
     row = {"physics": "laplacian_adjoint", "dim": c.dim, "prec": prec, "cells": c.n_cells,
-           "ms_per_step": round(statistics.mean(ms), 6), "cells_per_s": c.n_cells / t,
+           "ms_per_step": round(statistics.mean(ms), 6), "timing": note, **extra, "cells_per_s": c.n_cells / t,
            "alg_bytes_per_step": nbytes, "alg_gbs": nbytes / t / 1e9, "hbm_frac_of_measured": nbytes / t / 1e9 / peak,
            "kernels_per_step": 2}
     if oracle_mod is not None:
@@ -605,17 +654,28 @@ def measure_reaction(case, prec, device, stream, flush, steps, warmup, peak, ora
     a_d = torch.from_numpy(a_np).to(device=device, dtype=dt)
     c_d = torch.from_numpy(np.ascontiguousarray(c_np)).to(device=device, dtype=dt)
     q = c.rule
-    out = torch.empty((c.dim + 1, c.n_cells), dtype=dt, device=device)
-    fn = lambda: fem.fem_integrate_reaction_diffusion(d["coords"], d["conn"], d["u"], a_d, q.points, q.weights,
-                                                      c=c_d, a_space=1, drift=drift, out=out, prec=prec, stream=stream)
-    with torch.cuda.stream(stream):
-        ms, _, _ = timed_steps(fn, steps, warmup, stream, flush)
+    d0 = dict(d, a=a_d, c=c_d)
+    res = {}
+
+    def make(i):
+        dd = d0 if i == 0 else {k: v.clone() for k, v in d0.items()}
+        out = torch.empty((c.dim + 1, c.n_cells), dtype=dt, device=device)
+        if i == 0:
+            res["out"] = out
+        return fem.fem_integrate_reaction_diffusion(dd["coords"], dd["conn"], dd["u"], dd["a"], q.points, q.weights,
+                                                    c=dd["c"], a_space=1, drift=drift, out=out, prec=prec,
+                                                    stream=stream, prepare=True), (out,)
+
+    sb = _nbytes(d0.values()) + (c.dim + 1) * c.n_cells * (8 if prec == "fp64" else 4)
+    ms, note, extra = timed_copies(make, sb, device, stream, flush, steps, warmup)
+    out = res["out"]
     t = statistics.mean(ms) * 1e-3
     s = 8 if prec == "fp64" else 4
     nb = c.dim + 1
     nbytes = nb * 4 * c.n_cells + q.n_q * s * c.n_cells + nb * s * c.n_cells + (c.dim * 8 + 2 * s) * c.n_verts
     row = {"physics": "reaction_diffusion_p1_grad_a", "dim": c.dim, "prec": prec, "cells": c.n_cells,
-           "drift": drift, "ms_per_launch": round(statistics.mean(ms), 6), "cells_per_s": c.n_cells / t,
+           "drift": drift, "ms_per_launch": round(statistics.mean(ms), 6), "timing": note, **extra,
+           "cells_per_s": c.n_cells / t,
            "alg_bytes_per_launch": nbytes, "alg_gbs": nbytes / t / 1e9, "hbm_frac_of_measured": nbytes / t / 1e9 / peak,
            "alg_bytes_per_cell": "conn 4(d+1) + c n_q s + out (d+1) s + (V/C)(coords 8d + u s + a s)"}
     if oracle_mod is not None:
@@ -645,16 +705,25 @@ def measure_prepared(case, device, stream, flush, steps, warmup, peak, oracle_mo
         rec = fem.fem_prepare_vertices(d["coords"], stream=stream)
         ms_prep, _, _ = timed_steps(lambda: fem.fem_prepare_vertices(d["coords"], rec=rec, stream=stream), steps,
                                     warmup, stream, flush)
+    res = {}
+
+    def make(i):
+        dd = dict(d, rec=rec) if i == 0 else {k: v.clone() for k, v in dict(d, rec=rec).items()}
         out = torch.empty((c.dim + 1, c.n_cells), dtype=torch.float32, device=device)
-        fn = lambda: fem.fem_integrate_laplacian_prepared(d["coords"], rec, d["conn"], d["u"], d["K"], q.points,
-                                                          q.weights, out=out, stream=stream)
-        ms, _, _ = timed_steps(fn, steps, warmup, stream, flush)
+        if i == 0:
+            res["out"] = out
+        return fem.fem_integrate_laplacian_prepared(dd["coords"], dd["rec"], dd["conn"], dd["u"], dd["K"], q.points,
+                                                    q.weights, out=out, stream=stream, prepare=True), (out,)
+
+    sb = _nbytes(list(d.values()) + [rec]) + (c.dim + 1) * c.n_cells * 4
+    ms, note, extra = timed_copies(make, sb, device, stream, flush, steps, warmup)
+    out = res["out"]
     t = statistics.mean(ms) * 1e-3
     C, V, nb = c.n_cells, c.n_verts, c.dim + 1
     R = 8 if c.dim == 3 else 4
     nbytes = nb * 4 * C + q.n_q * 4 * C + nb * 4 * C + (R * 4 + 4) * V
     row = {"physics": "laplacian_prepared_vertex_records", "dim": c.dim, "prec": "mixed", "cells": C,
-           "ms_per_launch": round(statistics.mean(ms), 6), "ms_median": round(statistics.median(ms), 6),
+           "ms_per_launch": round(statistics.mean(ms), 6), "timing": note, **extra,
            "cells_per_s": C / t, "alg_bytes_per_launch": nbytes, "alg_gbs": nbytes / t / 1e9,
            "hbm_frac_of_measured": nbytes / t / 1e9 / peak,
            "prepare_ms_per_mesh": round(statistics.mean(ms_prep), 6),
@@ -694,18 +763,25 @@ def measure_pointwise(case, physics, prec, device, stream, flush, steps, warmup,
                                 coef[:, :, :0].contiguous(), q.points, q.weights, f1=POINTWISE_SRC[physics],
                                 prec=prec)
     compile_s = time.perf_counter() - t0
-    fn = lambda: fem.fem_integrate_pointwise(d["coords"], d["conn"], d["u"], coef, q.points, q.weights,
-                                             f1=POINTWISE_SRC[physics], out=out, prec=prec, stream=stream)
-    with torch.cuda.stream(stream):
-        ms, _, _ = timed_steps(fn, steps, warmup, stream, flush)
+    d0 = dict(d, coef=coef) if coef is not None else dict(d)
+    d0.pop("K", None)
+
+    def make(i):
+        dd = d0 if i == 0 else {k: v.clone() for k, v in d0.items()}
+        o = out if i == 0 else torch.empty_like(out)
+        return fem.fem_integrate_pointwise(dd["coords"], dd["conn"], dd["u"], dd.get("coef"), q.points, q.weights,
+                                           f1=POINTWISE_SRC[physics], out=o, prec=prec, stream=stream,
+                                           prepare=True), (o,)
+
+    ms, note, extra = timed_copies(make, _nbytes(d0.values()) + _nbytes([out]), device, stream, flush, steps, warmup)
     t = statistics.mean(ms) * 1e-3
     s = 8 if prec == "fp64" else 4
     nb, C, V = c.dim + 1, c.n_cells, c.n_verts
     ncoef = 1 if coef is not None else 0
     nbytes = nb * 4 * C + ncoef * q.n_q * s * C + nb * s * C + (c.dim * 8 + s) * V
     row = {"physics": f"pointwise_{physics}", "dim": c.dim, "prec": prec, "cells": C,
-           "ms_per_launch": round(statistics.mean(ms), 6), "cells_per_s": C / t, "alg_bytes_per_launch": nbytes,
-           "alg_gbs": nbytes / t / 1e9, "hbm_frac_of_measured": nbytes / t / 1e9 / peak,
+           "ms_per_launch": round(statistics.mean(ms), 6), "timing": note, **extra, "cells_per_s": C / t,
+           "alg_bytes_per_launch": nbytes, "alg_gbs": nbytes / t / 1e9, "hbm_frac_of_measured": nbytes / t / 1e9 / peak,
            "compile_s": round(compile_s, 3),
            "alg_bytes_per_cell": "conn 4(d+1) + coef n_coef n_q s + out (d+1) s + (V/C)(coords 8d + u s)",
            "kernel": "fem_pointwise_kernel (NVRTC, one cell per thread, per-point evaluation of Eq. 2)"}
@@ -879,16 +955,23 @@ def measure_fields(case, prec, device, stream, flush, steps, warmup, peak, oracl
     U_d = torch.from_numpy(U).to(device=device, dtype=dt)
     q = c.rule
     out = torch.empty((n_fields, c.dim + 1, c.n_cells), dtype=dt, device=device)
-    fn = lambda: fem.fem_integrate_laplacian_fields(d["coords"], d["conn"], U_d, d["K"], q.points, q.weights, out=out,
-                                                    prec=prec, stream=stream)
-    with torch.cuda.stream(stream):
-        ms, _, _ = timed_steps(fn, steps, warmup, stream, flush)
+    d0 = dict(d, U=U_d)
+    d0.pop("u", None)
+
+    def make(i):
+        dd = d0 if i == 0 else {k: v.clone() for k, v in d0.items()}
+        o = out if i == 0 else torch.empty_like(out)
+        return fem.fem_integrate_laplacian_fields(dd["coords"], dd["conn"], dd["U"], dd["K"], q.points, q.weights,
+                                                  out=o, prec=prec, stream=stream, prepare=True), (o,)
+
+    ms, note, extra = timed_copies(make, _nbytes(d0.values()) + _nbytes([out]), device, stream, flush, steps, warmup)
     t = statistics.mean(ms) * 1e-3
     sz = 8 if prec == "fp64" else 4
     C, V, nb = c.n_cells, c.n_verts, c.dim + 1
     nbytes = nb * 4 * C + q.n_q * sz * C + c.dim * 8 * V + n_fields * (sz * V + nb * sz * C)
     row = {"physics": "laplacian_fields", "dim": c.dim, "prec": prec, "cells": C, "fields": n_fields,
-           "ms_per_launch": round(statistics.mean(ms), 6), "field_cells_per_s": n_fields * C / t,
+           "ms_per_launch": round(statistics.mean(ms), 6), "timing": note, **extra,
+           "field_cells_per_s": n_fields * C / t,
            "alg_bytes_per_launch": nbytes, "alg_gbs": nbytes / t / 1e9, "hbm_frac_of_measured": nbytes / t / 1e9 / peak,
            "alg_bytes_per_cell": "conn 4(d+1) + K n_q s + (V/C) coords 8d + F ((V/C) u s + out (d+1) s)"}
     if oracle_mod is not None:

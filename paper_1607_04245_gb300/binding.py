@@ -171,7 +171,11 @@ class PreparedCall:
     repeat it on the same buffers (Python's per-call checks cost about as much host time
     as a small kernel takes on the device). Calling it runs the plain entry point again
     with the same pointers, sizes and stream; the tensors and host tables it was made from
-    stay referenced for its life and must keep their storage."""
+    stay referenced for its life and must keep their storage. prepared_integrate_laplacian
+    and prepared_integrate_elasticity make one; so do fem_integrate_laplacian_fields,
+    fem_integrate_laplacian_prepared, fem_integrate_pointwise,
+    fem_integrate_reaction_diffusion, fem_integrate_laplacian_geom and
+    fem_adjoint_laplacian when given prepare=True (they then run nothing)."""
 
     def __init__(self, name: str, args, keep):
         self._f = getattr(lib(), name)
@@ -183,6 +187,15 @@ class PreparedCall:
         st = self._f(*self._args)
         if st != 0:
             _check(self._name, st)
+
+
+def _run(name: str, args, keep, prepare: bool):
+    """Call entry point `name` with marshalled `args`, or return that call as a
+    PreparedCall (prepare=True) without running it."""
+    if prepare:
+        return PreparedCall(name, args, keep)
+    _check(name, getattr(lib(), name)(*args))
+    return None
 
 
 def _laplacian_call(coords, conn, u, K, qpts, qw, out, prec, stream):
@@ -214,7 +227,7 @@ def prepared_integrate_laplacian(coords, conn, u, K, qpts, qw, out, prec="mixed"
     return PreparedCall("fem_integrate_laplacian", args, keep)
 
 
-def fem_integrate_laplacian_fields(coords, conn, u, K, qpts, qw, out=None, prec="mixed", stream=None) -> torch.Tensor:
+def fem_integrate_laplacian_fields(coords, conn, u, K, qpts, qw, out=None, prec="mixed", stream=None, prepare=False):
     """Element residuals [F][dim+1][C] of the variable-coefficient Laplacian for F nodal
     fields u [F][V] on one mesh (geometry computed once per cell)."""
     p = precision(prec)
@@ -226,11 +239,13 @@ def fem_integrate_laplacian_fields(coords, conn, u, K, qpts, qw, out=None, prec=
     if out is None:
         out = torch.empty((nf, dim + 1, C), dtype=dt, device=dev)
     qp, w = _HostTable(qpts, (nq, dim), "qpts"), _HostTable(qw, (nq,), "qw")
-    st = lib().fem_integrate_laplacian_fields(
+    args = (
         dim, C, V, _dev(coords, "coords", torch.float64, device=dev), _dev(conn, "conn", torch.int32, device=dev), nf,
         _dev(u, "u", dt, (nf, V), dev), _dev(K, "K", dt, (nq, C), dev), nq, qp.ptr, w.ptr,
         _dev(out, "out", dt, (nf, dim + 1, C), dev), p, _stream(stream))
-    _check("fem_integrate_laplacian_fields", st)
+    pc = _run("fem_integrate_laplacian_fields", args, (coords, conn, u, K, out, qp, w), prepare)
+    if prepare:
+        return pc
     return out
 
 
@@ -278,7 +293,7 @@ def fem_prepare_vertices(coords, rec=None, stream=None) -> torch.Tensor:
     return rec
 
 
-def fem_integrate_laplacian_prepared(coords, rec, conn, u, K, qpts, qw, out=None, stream=None) -> torch.Tensor:
+def fem_integrate_laplacian_prepared(coords, rec, conn, u, K, qpts, qw, out=None, stream=None, prepare=False):
     """fem_integrate_laplacian (FP32-mixed) from the prepared vertex records: bitwise the same
     element vectors [dim+1][C]."""
     dim, V, C = _mesh_sizes(coords, conn)
@@ -288,17 +303,19 @@ def fem_integrate_laplacian_prepared(coords, rec, conn, u, K, qpts, qw, out=None
     if out is None:
         out = torch.empty((dim + 1, C), dtype=torch.float32, device=dev)
     qp, w = _HostTable(qpts, (nq, dim), "qpts"), _HostTable(qw, (nq,), "qw")
-    st = lib().fem_integrate_laplacian_prepared(
+    args = (
         dim, C, V, _dev(coords, "coords", torch.float64, device=dev), _dev(rec, "rec", torch.float32, (V, R), dev),
         _dev(conn, "conn", torch.int32, device=dev), _dev(u, "u", torch.float32, (V,), dev),
         _dev(K, "K", torch.float32, (nq, C), dev), nq, qp.ptr, w.ptr,
         _dev(out, "out", torch.float32, (dim + 1, C), dev), _stream(stream))
-    _check("fem_integrate_laplacian_prepared", st)
+    pc = _run("fem_integrate_laplacian_prepared", args, (coords, rec, conn, u, K, out, qp, w), prepare)
+    if prepare:
+        return pc
     return out
 
 
 def fem_integrate_pointwise(coords, conn, u, coef, qpts, qw, f1=None, f0=None, out=None, prec="mixed",
-                            stream=None) -> torch.Tensor:
+                            stream=None, prepare=False):
     """Element vectors [(dim+1)*n_comp][C] of Eq. 2 for pointwise functions given as CUDA
     source text: f1 and f0 are function bodies (see fem_integrate_pointwise in
     include/fem.h for the names in scope), compiled at run time and cached. u is [V] or
@@ -314,18 +331,20 @@ def fem_integrate_pointwise(coords, conn, u, coef, qpts, qw, f1=None, f0=None, o
         out = torch.empty(((dim + 1) * n_comp, C), dtype=dt, device=dev)
     qp, w = _HostTable(qpts, (nq, dim), "qpts"), _HostTable(qw, (nq,), "qw")
     enc = lambda t: None if t is None else t.encode()
-    st = lib().fem_integrate_pointwise(
+    args = (
         enc(f0), enc(f1), dim, n_comp, n_coef, C, V, _dev(coords, "coords", torch.float64, device=dev),
         _dev(conn, "conn", torch.int32, device=dev),
         _dev(u, "u", dt, (V,) if u.dim() == 1 else (n_comp, V), dev),
         None if coef is None else _dev(coef, "coef", dt, (n_coef, nq, C), dev), nq, qp.ptr, w.ptr,
         _dev(out, "out", dt, ((dim + 1) * n_comp, C), dev), p, _stream(stream))
-    _check("fem_integrate_pointwise", st)
+    pc = _run("fem_integrate_pointwise", args, (coords, conn, u, coef, out, qp, w), prepare)
+    if prepare:
+        return pc
     return out
 
 
 def fem_integrate_reaction_diffusion(coords, conn, u, a, qpts, qw, c=None, a_space=1, drift=0.0, out=None,
-                                     prec="mixed", stream=None) -> torch.Tensor:
+                                     prec="mixed", stream=None, prepare=False):
     """Element vectors [dim+1][C] of f1 = a grad u, f0 = c u + drift grad a . grad u (Eqs. 2
     and 8): a is P1 nodal ([V], a_space=1) or P0 ([C], a_space=0, grad a = 0); c is
     [n_q][C] or None."""
@@ -338,12 +357,14 @@ def fem_integrate_reaction_diffusion(coords, conn, u, a, qpts, qw, c=None, a_spa
         raise ValueError("qpts is required")
     out = torch.empty((dim + 1, C), dtype=dt, device=dev) if out is None else out
     qp, w = _HostTable(qpts, (nq, dim), "qpts"), _HostTable(qw, (nq,), "qw")
-    st = lib().fem_integrate_reaction_diffusion(
+    args = (
         dim, C, V, _dev(coords, "coords", torch.float64, device=dev), _dev(conn, "conn", torch.int32, device=dev),
         _dev(u, "u", dt, (V,), dev), _dev(a, "a", dt, (V,) if a_space == 1 else (C,), dev), int(a_space),
         None if c is None else _dev(c, "c", dt, (nq, C), dev), float(drift), nq, qp.ptr, w.ptr,
         _dev(out, "out", dt, (dim + 1, C), dev), p, _stream(stream))
-    _check("fem_integrate_reaction_diffusion", st)
+    pc = _run("fem_integrate_reaction_diffusion", args, (coords, conn, u, a, c, out, qp, w), prepare)
+    if prepare:
+        return pc
     return out
 
 
@@ -538,7 +559,7 @@ def fem_precompute_geometry(coords, conn, geom=None, prec="mixed", stream=None) 
 
 
 def fem_integrate_laplacian_geom(conn, n_verts: int, u, K, qpts, qw, geom, out=None, prec="mixed",
-                                 stream=None) -> torch.Tensor:
+                                 stream=None, prepare=False):
     """Laplacian element residuals [dim+1][C] from the precomputed geometry."""
     p = precision(prec)
     dt = value_dtype(p)
@@ -547,11 +568,13 @@ def fem_integrate_laplacian_geom(conn, n_verts: int, u, K, qpts, qw, geom, out=N
     dev = conn.device
     out = torch.empty((dim + 1, C), dtype=dt, device=dev) if out is None else out
     qp, w = _HostTable(qpts, (nq, dim), "qpts"), _HostTable(qw, (nq,), "qw")
-    st = lib().fem_integrate_laplacian_geom(
+    args = (
         dim, C, int(n_verts), _dev(conn, "conn", torch.int32, device=dev), _dev(u, "u", dt, (n_verts,), dev),
         _dev(K, "K", dt, (nq, C), dev), nq, qp.ptr, w.ptr, _dev(geom, "geom", dt, (dim * dim + 1, C), dev),
         _dev(out, "out", dt, (dim + 1, C), dev), p, _stream(stream))
-    _check("fem_integrate_laplacian_geom", st)
+    pc = _run("fem_integrate_laplacian_geom", args, (conn, u, K, geom, out, qp, w), prepare)
+    if prepare:
+        return pc
     return out
 
 
@@ -577,7 +600,7 @@ def fem_build_node2cell(conn, n_verts: int, node_ptr=None, node_idx=None, work=N
 
 
 def fem_adjoint_laplacian(coords, conn, u, K, qpts, qw, lam_adj, node_ptr, node_idx, dK=None, du=None,
-                          scratch=None, prec="mixed", stream=None) -> Tuple[torch.Tensor, torch.Tensor]:
+                          scratch=None, prec="mixed", stream=None, prepare=False):
     """Gradient of J = sum lambda . r: returns (dK [n_q][C], du [V])."""
     p = precision(prec)
     dt = value_dtype(p)
@@ -588,14 +611,16 @@ def fem_adjoint_laplacian(coords, conn, u, K, qpts, qw, lam_adj, node_ptr, node_
     du = torch.empty(V, dtype=dt, device=dev) if du is None else du
     scratch = torch.empty((dim + 1, C), dtype=dt, device=dev) if scratch is None else scratch
     qp, w = _HostTable(qpts, (nq, dim), "qpts"), _HostTable(qw, (nq,), "qw")
-    st = lib().fem_adjoint_laplacian(
+    args = (
         dim, C, V, _dev(coords, "coords", torch.float64, device=dev), _dev(conn, "conn", torch.int32, device=dev),
         _dev(u, "u", dt, (V,), dev), _dev(K, "K", dt, (nq, C), dev), nq, qp.ptr, w.ptr,
         _dev(lam_adj, "lambda", dt, (dim + 1, C), dev), _dev(dK, "dK", dt, (nq, C), dev),
         _dev(du, "du", dt, (V,), dev), _dev(node_ptr, "node_ptr", torch.int32, (V + 1,), dev),
         _dev(node_idx, "node_idx", torch.int32, ((dim + 1) * C,), dev),
         _dev(scratch, "scratch", dt, (dim + 1, C), dev), p, _stream(stream))
-    _check("fem_adjoint_laplacian", st)
+    pc = _run("fem_adjoint_laplacian", args, (coords, conn, u, K, lam_adj, node_ptr, node_idx, dK, du, scratch, qp, w), prepare)
+    if prepare:
+        return pc
     return dK, du
 
 

@@ -107,3 +107,50 @@ def test_prepared_call_validates_once_at_preparation():
     bad_out = torch.empty((3, case.n_cells), dtype=torch.float32, device="cuda")  # dim+1 = 4 rows needed
     with pytest.raises(ValueError):
         fem.prepared_integrate_laplacian(coords, conn, u, K, q.points, q.weights, bad_out)
+
+
+def test_prepare_option_launches_the_plain_call():
+    """prepare=True returns the call as a PreparedCall; running it gives bitwise what the
+    plain call gives (adjoint, reaction-diffusion, precomputed geometry, prepared records,
+    several fields, run-time compiled physics)."""
+    case = workloads.adjoint_case(24576).rounded_to_f32()
+    f32 = torch.float32
+    coords, conn = to_dev(case.mesh.coords, torch.float64), to_dev(case.mesh.conn, torch.int32)
+    u, K, q, V, C = to_dev(case.u, f32), to_dev(case.K, f32), case.rule, case.n_verts, case.n_cells
+    lam = to_dev(case.adj, f32)
+    ptr, idx = fem.fem_build_node2cell(conn, V)
+    a = torch.linspace(0.5, 2.0, V, device="cuda", dtype=f32)
+    cr = torch.linspace(0.25, 1.0, q.n_q * C, device="cuda", dtype=f32).reshape(q.n_q, C)
+    geom = fem.fem_precompute_geometry(coords, conn)
+    rec = fem.fem_prepare_vertices(coords)
+    U = torch.stack([u, -u, 2 * u])
+    calls = {
+        "adjoint": (lambda **k: fem.fem_adjoint_laplacian(coords, conn, u, K, q.points, q.weights, lam, ptr, idx, **k),
+                    lambda: dict(dK=torch.empty((q.n_q, C), dtype=f32, device="cuda"),
+                                 du=torch.empty(V, dtype=f32, device="cuda"))),
+        "reaction": (lambda **k: fem.fem_integrate_reaction_diffusion(coords, conn, u, a, q.points, q.weights, c=cr,
+                                                                      a_space=1, drift=1.0, **k),
+                     lambda: dict(out=torch.empty((4, C), dtype=f32, device="cuda"))),
+        "geom": (lambda **k: fem.fem_integrate_laplacian_geom(conn, V, u, K, q.points, q.weights, geom, **k),
+                 lambda: dict(out=torch.empty((4, C), dtype=f32, device="cuda"))),
+        "prepared": (lambda **k: fem.fem_integrate_laplacian_prepared(coords, rec, conn, u, K, q.points, q.weights,
+                                                                      **k),
+                     lambda: dict(out=torch.empty((4, C), dtype=f32, device="cuda"))),
+        "fields": (lambda **k: fem.fem_integrate_laplacian_fields(coords, conn, U, K, q.points, q.weights, **k),
+                   lambda: dict(out=torch.empty((3, 4, C), dtype=f32, device="cuda"))),
+        "pointwise": (lambda **k: fem.fem_integrate_pointwise(coords, conn, u, K[None].contiguous(), q.points,
+                                                              q.weights, f1="for (int i = 0; i < DIM; ++i) "
+                                                              "f1[i] = a[0] * grad_u[i];", **k),
+                      lambda: dict(out=torch.empty((4, C), dtype=f32, device="cuda"))),
+    }
+    for name, (call, outs) in calls.items():
+        o1, o2 = outs(), outs()
+        call(**o1)
+        pc = call(prepare=True, **o2)
+        assert isinstance(pc, fem.PreparedCall), name
+        torch.cuda.synchronize()
+        pc()
+        pc()
+        torch.cuda.synchronize()
+        for k in o1:
+            assert torch.equal(o1[k], o2[k]), (name, k)
