@@ -141,9 +141,10 @@ __global__ void __launch_bounds__(256) dot_final_kernel(const double *partial, d
 }
 
 // scalars[] layout: 0 gamma = r.u, 1 delta = w.u, 2 alpha, 3 beta, 4 rr = r.r,
-// 5 (rtol ||r_0||)^2, 6 iterations done, 7 the 32-bit block counter of the reduction (last_block)
+// 5 (rtol ||r_0||)^2, 6 iterations done, 7 the 32-bit block counter of the reduction
+// (last_block), 8 alpha and beta rounded to float32 once (read by the float32 update)
 enum { S_GAMMA = 0, S_DELTA = 1, S_ALPHA = 2, S_BETA = 3, S_RR = 4, S_TOL2 = 5, S_ITER = 6, S_TICKETS = 7,
-       S_COUNT = 8 };
+       S_AB32 = 8, S_COUNT = 9 };
 
 __device__ __forceinline__ unsigned *tickets(double *sc) { return reinterpret_cast<unsigned *>(sc + S_TICKETS); }
 
@@ -206,12 +207,66 @@ __device__ __forceinline__ double dot_term(T a, T b) {
     else return a * b;
 }
 
+// Inner products of float32 vectors without float64 arithmetic (the float64 pipe of this
+// part issues 2 operations per clock per SM, against 128 float32): a double-float sum
+// hi + lo, each product split exactly by TwoProduct and added by TwoSum (Knuth; the
+// product of two float32 values is exact in the pair), the low parts summed in float32.
+struct PairSum {
+    float hi = 0.0f, lo = 0.0f;
+    __device__ __forceinline__ void add_prod(float a, float b) {
+        float p, e, s, t;
+        two_prod(a, b, p, e);
+        two_sum(hi, p, s, t);
+        hi = s;
+        lo += t + e;
+    }
+    __device__ __forceinline__ void merge(float h, float l) {
+        float s, t;
+        two_sum(hi, h, s, t);
+        hi = s;
+        lo += t + l;
+    }
+    __device__ __forceinline__ double value() const { return static_cast<double>(hi) + static_cast<double>(lo); }
+};
+
+// Warp tree of PairSums: lane 0 ends with the warp's total (fixed order: lane i takes lane
+// i + o at o = 16, 8, 4, 2, 1).
+__device__ __forceinline__ void warp_merge(PairSum &a) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        const float h = __shfl_down_sync(0xffffffffu, a.hi, o), l = __shfl_down_sync(0xffffffffu, a.lo, o);
+        a.merge(h, l);
+    }
+}
+
+// The total of one PairSum per thread of a 256-thread block, in thread 0: warp trees, then
+// the eight warp totals in a ninth (sh: 8 float2 of shared memory, free again on return).
+__device__ __forceinline__ PairSum block_merge256(PairSum a, float2 *sh) {
+    warp_merge(a);
+    const int lane = threadIdx.x & 31;
+    if (lane == 0) sh[threadIdx.x >> 5] = make_float2(a.hi, a.lo);
+    __syncthreads();
+    PairSum b;
+    if (threadIdx.x < 32) {
+        if (lane < 8) b.hi = sh[lane].x, b.lo = sh[lane].y;
+        warp_merge(b);
+    }
+    __syncthreads();
+    return b;
+}
+
 // p = u + beta p, s = w + beta s, x += alpha p, r -= alpha s, u = r / D (in the vectors'
 // own type). On fixed vertices r, u, w and so p and s stay 0, and x keeps its value.
 template <class T>
 __global__ void cg_update_kernel(int64_t N, const double *sc, const T *w, const T *D, T *x, T *r, T *u, T *p,
                                  T *sv) {
-    const T alpha = static_cast<T>(sc[S_ALPHA]), beta = static_cast<T>(sc[S_BETA]);
+    T alpha, beta;
+    if constexpr (std::is_same<T, float>::value) {
+        const float2 ab = *reinterpret_cast<const float2 *>(sc + S_AB32);  // no per-thread float64 conversion
+        alpha = ab.x, beta = ab.y;
+    } else {
+        alpha = sc[S_ALPHA], beta = sc[S_BETA];
+    }
     const int64_t stride = int64_t(gridDim.x) * blockDim.x;
     for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < N; i += stride) {
         const T pi = u[i] + beta * p[i];
@@ -237,13 +292,16 @@ __global__ void __launch_bounds__(256) cg_apply_dots_kernel(int64_t C, int64_t V
                                                             const int32_t *__restrict__ idx, const uint8_t *fixed,
                                                             const T *r, const T *u, T *w, double *partial, double *sc,
                                                             int max_iter, cudaGraphConditionalHandle loop) {
+    constexpr bool F32 = std::is_same<T, float>::value;
     __shared__ double sh[256];
+    __shared__ float2 sh2[8];
     // list entry t = NB cell + a: element row (a, component k)
     auto entry = [&](int32_t t, int k) {
         const int32_t cell = t / NB, a = t - cell * NB;
         return __ldg(elem + int64_t(a * NCOMP + k) * C + cell);
     };
-    double ru = 0.0, wu = 0.0, rr = 0.0;
+    double ru = 0.0, wu = 0.0, rr = 0.0;  // float64 vectors
+    PairSum pru, pwu, prr;                 // float32 vectors
     for (int64_t n = int64_t(blockIdx.x) * 256 + threadIdx.x; n < V; n += int64_t(kDotBlocks) * 256) {
         const int32_t b = ptr[n], e = ptr[n + 1];
         NodeSum<T> acc[NCOMP];
@@ -274,28 +332,56 @@ __global__ void __launch_bounds__(256) cg_apply_dots_kernel(int64_t C, int64_t V
             const T wn = fx ? T(0) : acc[k].value();
             w[i] = wn;
             const T rn = r[i], un = u[i];
-            ru += dot_term(rn, un);
-            wu += dot_term(wn, un);
-            rr += dot_term(rn, rn);
+            if constexpr (F32) {
+                pru.add_prod(rn, un);
+                pwu.add_prod(wn, un);
+                prr.add_prod(rn, rn);
+            } else {
+                ru += dot_term(rn, un);
+                wu += dot_term(wn, un);
+                rr += dot_term(rn, rn);
+            }
         }
     }
-    double t = block_sum256(ru, sh);
-    if (threadIdx.x == 0) partial[blockIdx.x] = t;
-    __syncthreads();
-    t = block_sum256(wu, sh);
-    if (threadIdx.x == 0) partial[kDotBlocks + blockIdx.x] = t;
-    __syncthreads();
-    t = block_sum256(rr, sh);
-    if (threadIdx.x == 0) partial[2 * kDotBlocks + blockIdx.x] = t;
-    if (!last_block(tickets(sc))) return;
-    double a0 = 0.0, a1 = 0.0, a2 = 0.0;
-    for (int i = threadIdx.x; i < kDotBlocks; i += 256)
-        a0 += __ldcg(partial + i), a1 += __ldcg(partial + kDotBlocks + i), a2 += __ldcg(partial + 2 * kDotBlocks + i);
-    const double gamma = block_sum256(a0, sh);
-    __syncthreads();
-    const double delta = block_sum256(a1, sh);
-    __syncthreads();
-    const double rrs = block_sum256(a2, sh);
+    double gamma = 0.0, delta = 0.0, rrs = 0.0;  // the totals, in thread 0 of the last block
+    if constexpr (F32) {
+        // block partials as (hi, lo) pairs in place of the float64 partials
+        float2 *pp = reinterpret_cast<float2 *>(partial);
+        PairSum t = block_merge256(pru, sh2);
+        if (threadIdx.x == 0) pp[blockIdx.x] = make_float2(t.hi, t.lo);
+        t = block_merge256(pwu, sh2);
+        if (threadIdx.x == 0) pp[kDotBlocks + blockIdx.x] = make_float2(t.hi, t.lo);
+        t = block_merge256(prr, sh2);
+        if (threadIdx.x == 0) pp[2 * kDotBlocks + blockIdx.x] = make_float2(t.hi, t.lo);
+        if (!last_block(tickets(sc))) return;
+        PairSum a0, a1, a2;
+        for (int i = threadIdx.x; i < kDotBlocks; i += 256) {
+            const float2 v0 = __ldcg(pp + i), v1 = __ldcg(pp + kDotBlocks + i), v2 = __ldcg(pp + 2 * kDotBlocks + i);
+            a0.merge(v0.x, v0.y), a1.merge(v1.x, v1.y), a2.merge(v2.x, v2.y);
+        }
+        gamma = block_merge256(a0, sh2).value();
+        delta = block_merge256(a1, sh2).value();
+        rrs = block_merge256(a2, sh2).value();
+    } else {
+        double t = block_sum256(ru, sh);
+        if (threadIdx.x == 0) partial[blockIdx.x] = t;
+        __syncthreads();
+        t = block_sum256(wu, sh);
+        if (threadIdx.x == 0) partial[kDotBlocks + blockIdx.x] = t;
+        __syncthreads();
+        t = block_sum256(rr, sh);
+        if (threadIdx.x == 0) partial[2 * kDotBlocks + blockIdx.x] = t;
+        if (!last_block(tickets(sc))) return;
+        double a0 = 0.0, a1 = 0.0, a2 = 0.0;
+        for (int i = threadIdx.x; i < kDotBlocks; i += 256)
+            a0 += __ldcg(partial + i), a1 += __ldcg(partial + kDotBlocks + i),
+                a2 += __ldcg(partial + 2 * kDotBlocks + i);
+        gamma = block_sum256(a0, sh);
+        __syncthreads();
+        delta = block_sum256(a1, sh);
+        __syncthreads();
+        rrs = block_sum256(a2, sh);
+    }
     if (threadIdx.x == 0) {
         if constexpr (INIT) {
             sc[S_ALPHA] = delta != 0.0 ? gamma / delta : 0.0;
@@ -311,6 +397,8 @@ __global__ void __launch_bounds__(256) cg_apply_dots_kernel(int64_t C, int64_t V
             const bool more = it < static_cast<double>(max_iter) && rrs > sc[S_TOL2] && rrs > 0.0;
             cudaGraphSetConditional(loop, more ? 1u : 0u);
         }
+        *reinterpret_cast<float2 *>(sc + S_AB32) =
+            make_float2(static_cast<float>(sc[S_ALPHA]), static_cast<float>(sc[S_BETA]));
         sc[S_GAMMA] = gamma;
         sc[S_DELTA] = delta;
         sc[S_RR] = rrs;
