@@ -187,14 +187,15 @@ __device__ __forceinline__ bool last_block(unsigned *ticket) {
 // The vectors hold n_comp components per vertex, component-major ([n_comp][V]): entry i
 // belongs to vertex i mod V, whose Dirichlet flag covers all its components.
 
-// r = b - Ax on the free vertices (0 on fixed ones), u = r / D, p = s = 0
+// r = b - Ax on the free vertices (0 on fixed ones), u = D^-1 r, p = s = 0 (Dinv: the
+// reciprocal of the Jacobi diagonal, formed once per solve by diag_fix_kernel)
 template <class T>
-__global__ void cg_init_kernel(int64_t N, int64_t V, const T *b, const T *Ax, const T *D, const uint8_t *fixed,
+__global__ void cg_init_kernel(int64_t N, int64_t V, const T *b, const T *Ax, const T *Dinv, const uint8_t *fixed,
                                T *r, T *u, T *p, T *sv) {
     const int64_t stride = int64_t(gridDim.x) * blockDim.x;
     for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < N; i += stride) {
         const T ri = fixed[i % V] ? T(0) : (b ? b[i] : T(0)) - Ax[i];
-        r[i] = ri, u[i] = ri / D[i], p[i] = T(0), sv[i] = T(0);
+        r[i] = ri, u[i] = ri * Dinv[i], p[i] = T(0), sv[i] = T(0);
     }
 }
 
@@ -255,10 +256,10 @@ __device__ __forceinline__ PairSum block_merge256(PairSum a, float2 *sh) {
     return b;
 }
 
-// p = u + beta p, s = w + beta s, x += alpha p, r -= alpha s, u = r / D (in the vectors'
+// p = u + beta p, s = w + beta s, x += alpha p, r -= alpha s, u = D^-1 r (in the vectors'
 // own type). On fixed vertices r, u, w and so p and s stay 0, and x keeps its value.
 template <class T>
-__global__ void cg_update_kernel(int64_t N, const double *sc, const T *w, const T *D, T *x, T *r, T *u, T *p,
+__global__ void cg_update_kernel(int64_t N, const double *sc, const T *w, const T *Dinv, T *x, T *r, T *u, T *p,
                                  T *sv) {
     T alpha, beta;
     if constexpr (std::is_same<T, float>::value) {
@@ -276,7 +277,7 @@ __global__ void cg_update_kernel(int64_t N, const double *sc, const T *w, const 
         x[i] = x[i] + alpha * pi;
         const T ri = r[i] - alpha * si;
         r[i] = ri;
-        u[i] = ri / D[i];
+        u[i] = ri * Dinv[i];
     }
 }
 
@@ -426,18 +427,19 @@ static cudaStream_t capture_stream() {
     return per_dev[dev];
 }
 
-// fixed vertices get D = 1 (their rows are the identity)
+// fixed vertices get D = 1 (their rows are the identity); then D is replaced by its
+// reciprocal, so that every application of the preconditioner is one multiply
 template <class T>
 __global__ void diag_fix_kernel(int64_t N, int64_t V, const uint8_t *fixed, T *D) {
     const int64_t stride = int64_t(gridDim.x) * blockDim.x;
     for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < N; i += stride)
-        if (fixed[i % V] || !(D[i] > T(0))) D[i] = T(1);
+        D[i] = (fixed[i % V] || !(D[i] > T(0))) ? T(1) : T(1) / D[i];
 }
 
 static size_t align256(size_t n) { return (n + 255) & ~size_t(255); }
 
 struct Workspace {
-    void *elem, *D, *r, *z, *p, *q, *sv;  // z holds u = D^-1 r, q holds w = A u, sv holds s = A p
+    void *elem, *D, *r, *z, *p, *q, *sv;  // D holds D^-1, z holds u = D^-1 r, q holds w = A u, sv s = A p
     double *partial, *scalars;
 };
 
@@ -473,8 +475,8 @@ static fem_status pcg_run(int dim, int64_t C, int64_t V, const double *coords, c
                           double rtol, const Workspace &w, int *iters_out, double *resid_out, fem_precision prec,
                           cudaStream_t s, bool diag_ready = false) {
     // the residual runs in `prec`; every other kernel sees the value type (FEM_FP64_DF
-    // values are float64). diag_ready: w.D already holds this operator's diagonal (a
-    // repeated solve with the same workspace).
+    // values are float64). diag_ready: w.D already holds the reciprocal of this operator's
+    // diagonal (a repeated solve with the same workspace).
     const fem_precision vprec = prec == FEM_FP64_DF ? FEM_FP64 : prec;
     T *X = static_cast<T *>(x);
     T *D = static_cast<T *>(w.D), *r = static_cast<T *>(w.r), *z = static_cast<T *>(w.z);
