@@ -22,6 +22,12 @@
  *    synchronises the stream: work is enqueued on `stream` (0 = the legacy default
  *    stream) and the call returns after the launch. The one exception is
  *    fem_pcg_laplacian, which waits for its result and runs its loop as a CUDA graph.
+ *  - Outside stream capture the integration, adjoint, geometry and assembly kernels are
+ *    launched with programmatic stream serialisation (programmatic dependent launch):
+ *    a kernel may be scheduled onto the GPU while the kernel before it on `stream`
+ *    drains, and waits, before touching memory, until that kernel has completed and its
+ *    writes are visible. Stream order for data is unchanged; only the launch gap goes.
+ *    Under capture the launches are plain.
  *  - Layouts are structure-of-arrays with the cell (or vertex) index fastest:
  *        coords [dim][n_verts]        always float64
  *        conn   [dim+1][n_cells]      int32 vertex ids in [0, n_verts)
