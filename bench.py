@@ -292,8 +292,8 @@ def rotating_sets(set_bytes, l2):
 def timed_rotating(step_fns, steps, warmup, stream, dist=None, ws=1, sampler=None):
     """Device time (ms) of `steps` steps run back to back between one pair of CUDA events,
     step i on input copy i mod len(step_fns); warm-up as in timed_steps. Returns the mean
-    per step of each of ~10 contiguous chunks of the steps, one entry per step (so that sum()
-    is the timed region and the median is over chunks), the wall time, the clock record and
+    per step of each of up to 5 contiguous chunks of the steps, one entry per step (so that
+    sum() is the timed region and the median is over chunks), the wall time, the clock record and
     the host's enqueue time per step (well below the device time per step: the device never
     waits for the host)."""
     import torch
@@ -308,9 +308,10 @@ def timed_rotating(step_fns, steps, warmup, stream, dist=None, ws=1, sampler=Non
         if i % 16 == 0:
             torch.cuda.synchronize()
     torch.cuda.synchronize()
-    # events at the bounds of ~10 contiguous chunks of steps: their sum is the timed region,
-    # their per-step means give a median
-    chunk = max(1, steps // 10)
+    # events at the bounds of up to 5 contiguous chunks of at least 50 steps: their sum is
+    # the timed region, their per-step means give a median. (An event between two steps
+    # costs the second one its overlapped start, so chunks are few and long.)
+    chunk = max(50, -(-steps // 5))
     bounds = list(range(0, steps, chunk)) + [steps]
     evs = [torch.cuda.Event(enable_timing=True) for _ in bounds]
     barrier(dist, ws)
