@@ -109,6 +109,10 @@ __device__ __forceinline__ void split64(double x, float &hi, float &lo_u) {
 #endif
 
 extern "C" __global__ void __launch_bounds__(256) fem_pointwise_kernel(const PwArgs a) {
+    // launched overlapped with the kernel before it on the stream (outside graph capture):
+    // its writes are visible from here on
+    asm volatile("griddepcontrol.wait;" ::: "memory");
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
     const i64 C = a.C;
     const T *u = (const T *)a.u;
     const T *coef = (const T *)a.coef;
@@ -119,7 +123,7 @@ extern "C" __global__ void __launch_bounds__(256) fem_pointwise_kernel(const PwA
     for (i64 e = (i64)blockIdx.x * blockDim.x + threadIdx.x; e < C; e += (i64)gridDim.x * blockDim.x) {
         u32 v[NB];
         for (int b = 0; b < NB; ++b) {
-            const int id = a.conn[b * C + e];
+            const int id = __ldcs(a.conn + b * C + e);
             vmax = max(vmax, (u32)id);
             v[b] = min((u32)id, a.V - 1u);
         }
@@ -220,7 +224,7 @@ extern "C" __global__ void __launch_bounds__(256) fem_pointwise_kernel(const PwA
                 for (int j = 0; j < FEM_DIM; ++j) s += ph[j + 1] * ec[j][i];
                 xq[i] = s;
             }
-            for (int c = 0; c < FEM_NCOEF; ++c) aq[c] = coef[((i64)c * FEM_NQ + q) * C + e];
+            for (int c = 0; c < FEM_NCOEF; ++c) aq[c] = __ldcs(coef + ((i64)c * FEM_NQ + q) * C + e);
             const T wq = (T)FEM_W(q);
 #if FEM_HAS_F0
             T f0[FEM_NCOMP];
@@ -241,7 +245,7 @@ extern "C" __global__ void __launch_bounds__(256) fem_pointwise_kernel(const PwA
             for (int k = 0; k < FEM_NCOMP; ++k) {
                 T s = F0[b][k];
                 for (int i = 0; i < FEM_DIM; ++i) s += G[b][i] * F1[k * FEM_DIM + i];
-                out[(i64)(b * FEM_NCOMP + k) * C + e] = adet * s;
+                __stcs(out + (i64)(b * FEM_NCOMP + k) * C + e, adet * s);
             }
     }
     if (vmax >= a.V || bad) record_err(a.err);
@@ -471,8 +475,21 @@ extern "C" fem_status fem_integrate_pointwise(const char *f0_src, const char *f1
     const int64_t need = (n_cells + 255) / 256, cap = int64_t(m.grid_per_sm) * sm_count();
     const unsigned grid = static_cast<unsigned>(need < cap ? need : cap);
     void *params[] = {&a};
-    cudaError_t e = cudaLaunchKernel(reinterpret_cast<const void *>(m.kernel), dim3(grid), dim3(256), params, 0,
-                                     stream);
+    // overlapped with the previous kernel's tail, as the built-in kernels are (the kernel
+    // waits for it first), except while the stream is being captured
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    const bool refused = cudaStreamIsCapturing(stream, &cs) != cudaSuccess;
+    if (refused) cudaGetLastError();
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    at[0].val.programmaticStreamSerializationAllowed = 1;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(grid);
+    cfg.blockDim = dim3(256);
+    cfg.stream = stream;
+    cfg.attrs = at;
+    cfg.numAttrs = (refused || cs != cudaStreamCaptureStatusNone) ? 0 : 1;
+    cudaError_t e = cudaLaunchKernelExC(&cfg, reinterpret_cast<const void *>(m.kernel), params);
     if (e != cudaSuccess) return fail(FEM_ERR_CUDA, "fem_integrate_pointwise launch: %s", cudaGetErrorString(e));
     return FEM_OK;
 }

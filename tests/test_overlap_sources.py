@@ -28,9 +28,9 @@ def _kernel_bodies(srcs):
             name = m.group(1)
             brace = text.index("{", m.end())
             first = text[brace + 1:brace + 600].strip()
-            # compile-time checks come first and touch no memory
-            while first.startswith("static_assert("):
-                first = first[first.index(";") + 1:].strip()
+            # compile-time checks and comments come first and touch no memory
+            while first.startswith(("static_assert(", "//")):
+                first = first[first.index(";" if first.startswith("static") else "\n") + 1:].strip()
             bodies.setdefault(name, []).append(first)
     return bodies
 
@@ -75,3 +75,10 @@ def test_kernels_that_trigger_also_wait():
         for first in firsts:
             if "pdl_trigger()" in first[:200]:
                 assert first.startswith("pdl_wait();"), name
+
+
+def test_run_time_compiled_kernel_waits_first():
+    """The kernel that fem_integrate_pointwise generates (launched overlapped too) opens
+    with the same wait, written as inline PTX in its source text."""
+    firsts = _kernel_bodies(_sources())["fem_pointwise_kernel"]
+    assert firsts and all(f.startswith('asm volatile("griddepcontrol.wait;"') for f in firsts)
