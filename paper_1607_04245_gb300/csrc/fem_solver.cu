@@ -148,15 +148,21 @@ enum { S_GAMMA = 0, S_DELTA = 1, S_ALPHA = 2, S_BETA = 3, S_RR = 4, S_TOL2 = 5, 
 
 __device__ __forceinline__ unsigned *tickets(double *sc) { return reinterpret_cast<unsigned *>(sc + S_TICKETS); }
 
-// Block-level sum of one double per thread (256 threads); thread 0 gets the total.
-__device__ __forceinline__ double block_sum256(double v, double *sh) {
-    sh[threadIdx.x] = v;
+// Block-level sums of three doubles per thread (256 threads; sh: 3 x 256 doubles): a
+// shared-memory tree, one barrier per level for the three; every thread gets the totals.
+__device__ __forceinline__ void block_sum256x3(double (&v)[3], double *sh) {
+#pragma unroll
+    for (int m = 0; m < 3; ++m) sh[m * 256 + threadIdx.x] = v[m];
     __syncthreads();
     for (int o = 128; o > 0; o >>= 1) {
-        if (threadIdx.x < o) sh[threadIdx.x] += sh[threadIdx.x + o];
+        if (threadIdx.x < o)
+#pragma unroll
+            for (int m = 0; m < 3; ++m) sh[m * 256 + threadIdx.x] += sh[m * 256 + threadIdx.x + o];
         __syncthreads();
     }
-    return sh[0];
+#pragma unroll
+    for (int m = 0; m < 3; ++m) v[m] = sh[m * 256];
+    __syncthreads();
 }
 
 // True in the block that finishes last: each block's thread 0 publishes the block's partial
@@ -240,20 +246,27 @@ __device__ __forceinline__ void warp_merge(PairSum &a) {
     }
 }
 
-// The total of one PairSum per thread of a 256-thread block, in thread 0: warp trees, then
-// the eight warp totals in a ninth (sh: 8 float2 of shared memory, free again on return).
-__device__ __forceinline__ PairSum block_merge256(PairSum a, float2 *sh) {
-    warp_merge(a);
+// The totals of three PairSums per thread of a 256-thread block, in thread 0: warp trees,
+// then the eight warp totals of each in a ninth (sh: 3 x 8 float2 of shared memory, free
+// again on return; one barrier pair for the three).
+__device__ __forceinline__ void block_merge256x3(PairSum (&a)[3], float2 *sh) {
     const int lane = threadIdx.x & 31;
-    if (lane == 0) sh[threadIdx.x >> 5] = make_float2(a.hi, a.lo);
-    __syncthreads();
-    PairSum b;
-    if (threadIdx.x < 32) {
-        if (lane < 8) b.hi = sh[lane].x, b.lo = sh[lane].y;
-        warp_merge(b);
+#pragma unroll
+    for (int m = 0; m < 3; ++m) {
+        warp_merge(a[m]);
+        if (lane == 0) sh[m * 8 + (threadIdx.x >> 5)] = make_float2(a[m].hi, a[m].lo);
     }
     __syncthreads();
-    return b;
+    if (threadIdx.x < 32) {
+#pragma unroll
+        for (int m = 0; m < 3; ++m) {
+            PairSum b;
+            if (lane < 8) b.hi = sh[m * 8 + lane].x, b.lo = sh[m * 8 + lane].y;
+            warp_merge(b);
+            a[m] = b;
+        }
+    }
+    __syncthreads();
 }
 
 // p = u + beta p, s = w + beta s, x += alpha p, r -= alpha s, u = D^-1 r (in the vectors'
@@ -294,15 +307,15 @@ __global__ void __launch_bounds__(256) cg_apply_dots_kernel(int64_t C, int64_t V
                                                             const T *r, const T *u, T *w, double *partial, double *sc,
                                                             int max_iter, cudaGraphConditionalHandle loop) {
     constexpr bool F32 = std::is_same<T, float>::value;
-    __shared__ double sh[256];
-    __shared__ float2 sh2[8];
+    __shared__ double sh[F32 ? 1 : 3 * 256];
+    __shared__ float2 sh2[3 * 8];
     // list entry t = NB cell + a: element row (a, component k)
     auto entry = [&](int32_t t, int k) {
         const int32_t cell = t / NB, a = t - cell * NB;
         return __ldg(elem + int64_t(a * NCOMP + k) * C + cell);
     };
     double ru = 0.0, wu = 0.0, rr = 0.0;  // float64 vectors
-    PairSum pru, pwu, prr;                 // float32 vectors
+    PairSum pd[3];                         // float32 vectors: r.u, w.u, r.r
     for (int64_t n = int64_t(blockIdx.x) * 256 + threadIdx.x; n < V; n += int64_t(kDotBlocks) * 256) {
         const int32_t b = ptr[n], e = ptr[n + 1];
         NodeSum<T> acc[NCOMP];
@@ -334,9 +347,9 @@ __global__ void __launch_bounds__(256) cg_apply_dots_kernel(int64_t C, int64_t V
             w[i] = wn;
             const T rn = r[i], un = u[i];
             if constexpr (F32) {
-                pru.add_prod(rn, un);
-                pwu.add_prod(wn, un);
-                prr.add_prod(rn, rn);
+                pd[0].add_prod(rn, un);
+                pd[1].add_prod(wn, un);
+                pd[2].add_prod(rn, rn);
             } else {
                 ru += dot_term(rn, un);
                 wu += dot_term(wn, un);
@@ -348,40 +361,31 @@ __global__ void __launch_bounds__(256) cg_apply_dots_kernel(int64_t C, int64_t V
     if constexpr (F32) {
         // block partials as (hi, lo) pairs in place of the float64 partials
         float2 *pp = reinterpret_cast<float2 *>(partial);
-        PairSum t = block_merge256(pru, sh2);
-        if (threadIdx.x == 0) pp[blockIdx.x] = make_float2(t.hi, t.lo);
-        t = block_merge256(pwu, sh2);
-        if (threadIdx.x == 0) pp[kDotBlocks + blockIdx.x] = make_float2(t.hi, t.lo);
-        t = block_merge256(prr, sh2);
-        if (threadIdx.x == 0) pp[2 * kDotBlocks + blockIdx.x] = make_float2(t.hi, t.lo);
+        block_merge256x3(pd, sh2);
+        if (threadIdx.x == 0)
+            for (int m = 0; m < 3; ++m) pp[m * kDotBlocks + blockIdx.x] = make_float2(pd[m].hi, pd[m].lo);
         if (!last_block(tickets(sc))) return;
-        PairSum a0, a1, a2;
-        for (int i = threadIdx.x; i < kDotBlocks; i += 256) {
-            const float2 v0 = __ldcg(pp + i), v1 = __ldcg(pp + kDotBlocks + i), v2 = __ldcg(pp + 2 * kDotBlocks + i);
-            a0.merge(v0.x, v0.y), a1.merge(v1.x, v1.y), a2.merge(v2.x, v2.y);
-        }
-        gamma = block_merge256(a0, sh2).value();
-        delta = block_merge256(a1, sh2).value();
-        rrs = block_merge256(a2, sh2).value();
-    } else {
-        double t = block_sum256(ru, sh);
-        if (threadIdx.x == 0) partial[blockIdx.x] = t;
-        __syncthreads();
-        t = block_sum256(wu, sh);
-        if (threadIdx.x == 0) partial[kDotBlocks + blockIdx.x] = t;
-        __syncthreads();
-        t = block_sum256(rr, sh);
-        if (threadIdx.x == 0) partial[2 * kDotBlocks + blockIdx.x] = t;
-        if (!last_block(tickets(sc))) return;
-        double a0 = 0.0, a1 = 0.0, a2 = 0.0;
+        PairSum at[3];
         for (int i = threadIdx.x; i < kDotBlocks; i += 256)
-            a0 += __ldcg(partial + i), a1 += __ldcg(partial + kDotBlocks + i),
-                a2 += __ldcg(partial + 2 * kDotBlocks + i);
-        gamma = block_sum256(a0, sh);
-        __syncthreads();
-        delta = block_sum256(a1, sh);
-        __syncthreads();
-        rrs = block_sum256(a2, sh);
+#pragma unroll
+            for (int m = 0; m < 3; ++m) {
+                const float2 v = __ldcg(pp + m * kDotBlocks + i);
+                at[m].merge(v.x, v.y);
+            }
+        block_merge256x3(at, sh2);
+        gamma = at[0].value(), delta = at[1].value(), rrs = at[2].value();
+    } else {
+        double t[3] = {ru, wu, rr};
+        block_sum256x3(t, sh);
+        if (threadIdx.x == 0)
+            for (int m = 0; m < 3; ++m) partial[m * kDotBlocks + blockIdx.x] = t[m];
+        if (!last_block(tickets(sc))) return;
+        double at[3] = {0.0, 0.0, 0.0};
+        for (int i = threadIdx.x; i < kDotBlocks; i += 256)
+#pragma unroll
+            for (int m = 0; m < 3; ++m) at[m] += __ldcg(partial + m * kDotBlocks + i);
+        block_sum256x3(at, sh);
+        gamma = at[0], delta = at[1], rrs = at[2];
     }
     if (threadIdx.x == 0) {
         if constexpr (INIT) {
