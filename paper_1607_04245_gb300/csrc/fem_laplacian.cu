@@ -497,8 +497,8 @@ __device__ __forceinline__ void lap_pair(const double *const (&X)[DIM], const ui
 // The float32 forms' kernel for rows that are 8-byte aligned (an even cell count): each
 // thread owns two consecutive cells at a time and computes them as f32x2 pairs
 // (lap_pair), reading every cell-indexed row with 8-byte loads and writing 8-byte
-// streaming stores, grid-stride over the cell pairs with one wave of resident CTAs (4 of
-// 256 threads per SM at 64 registers for the residual). A badly shaped cell of the mixed form is
+// streaming stores, grid-stride over the cell pairs with one wave of resident CTAs (3 of
+// 256 threads per SM at up to 80 registers). A badly shaped cell of the mixed form is
 // recomputed in float64 out of line (lap_fallback_store) after its pair's stores.
 //
 // Measured on the 1,572,864-tet workload (L2 flushed, CUDA events): 25.9 us against
@@ -507,9 +507,12 @@ __device__ __forceinline__ void lap_pair(const double *const (&X)[DIM], const ui
 // at this size; at 2^23 cells the two are within 1 %. Both are bound by the latency of
 // the 16 vertex gathers per cell and by the integer float64 -> float32 splits (ALU pipe
 // half busy), not by DRAM (30 % of peak over the launch).
-// (the adjoint's element part holds lambda and h_lambda too: 3 CTAs, 80 registers, no spills)
+// Residual and adjoint alike run 3 CTAs per SM at up to 80 registers: with launches that
+// overlap the previous kernel's tail and steps back to back, the residual took 23.2 us
+// against 23.5 us at 4 CTAs (64 registers) on the 1,572,864-tet workload, and 106.5
+// against 108.8 us on 2^23 cells; 2 CTAs (118 registers) took 27.2 us.
 template <bool ADJ>
-constexpr int pair_min_blocks() { return ADJ ? 3 : 4; }
+constexpr int pair_min_blocks() { return 3; }
 
 template <int DIM, int P, int NQ, bool ADJ>
 __global__ void __launch_bounds__(kBlock, pair_min_blocks<ADJ>()) lap_pair_kernel(const __grid_constant__ LapArgs a) {
