@@ -507,15 +507,16 @@ __device__ __forceinline__ void lap_pair(const double *const (&X)[DIM], const ui
 // at this size; at 2^23 cells the two are within 1 %. Both are bound by the latency of
 // the 16 vertex gathers per cell and by the integer float64 -> float32 splits (ALU pipe
 // half busy), not by DRAM (30 % of peak over the launch).
-// Residual and adjoint alike run 3 CTAs per SM at up to 80 registers: with launches that
-// overlap the previous kernel's tail and steps back to back, the residual took 23.2 us
-// against 23.5 us at 4 CTAs (64 registers) on the 1,572,864-tet workload, and 106.5
-// against 108.8 us on 2^23 cells; 2 CTAs (118 registers) took 27.2 us.
-template <bool ADJ>
-constexpr int pair_min_blocks() { return 3; }
+// The mixed form and the adjoint run 3 CTAs per SM at up to 80 registers: with launches
+// that overlap the previous kernel's tail and steps back to back, the mixed residual took
+// 23.2 us against 23.5 us at 4 CTAs (64 registers) on the 1,572,864-tet workload, and 106.5
+// against 108.8 us on 2^23 cells; 2 CTAs (118 registers) took 27.2 us. The float32
+// ablation, without the coordinate splits, keeps 4 (3 took 25.3 against 23.7 us).
+template <int P, bool ADJ>
+constexpr int pair_min_blocks() { return (P == FEM_FP32 && !ADJ) ? 4 : 3; }
 
 template <int DIM, int P, int NQ, bool ADJ>
-__global__ void __launch_bounds__(kBlock, pair_min_blocks<ADJ>()) lap_pair_kernel(const __grid_constant__ LapArgs a) {
+__global__ void __launch_bounds__(kBlock, pair_min_blocks<P, ADJ>()) lap_pair_kernel(const __grid_constant__ LapArgs a) {
     static_assert(P != FEM_FP64, "float32 forms only");
     pdl_wait();  // launched overlapped: the previous kernel's writes are visible from here
     pdl_trigger();
