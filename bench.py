@@ -1298,7 +1298,7 @@ def run_ours(args):
     ms_per_step = t_max / args.steps * 1e3
     value = weak_scaling_value(ws, case.n_cells, args.steps, t_max)
 
-    fp64_steps = max(3, args.steps // 20)
+    fp64_steps = max(20, args.steps // 20)  # at least 20 back-to-back steps per row
     row64, _, _, _ = measure_residual(case, "fp64", device, stream, flush, fp64_steps, args.warmup, peak,
                                       oracle if rank == 0 else None)
 
@@ -1357,7 +1357,7 @@ def run_ours(args):
             print(f"bench: row {name} failed: {exc!r}", file=sys.stderr)
             rows[name] = {"error": repr(exc)[:300]}
 
-    rsteps = max(3, args.steps // 50)
+    rsteps = max(20, args.steps // 50)
     common = (device, stream, flush, rsteps, args.warmup, peak, oracle)
     if want("fp32_ablation"):
         put("fp32_ablation", lambda: measure_residual(case, "fp32", *common)[0])
@@ -1409,7 +1409,7 @@ def run_ours(args):
         out = {}
         for e in range(16, 24):
             sc = workloads.laplacian_cube_case(1 << e)
-            r = measure_residual(sc, "mixed", device, stream, flush, max(3, rsteps // 2), args.warmup, peak)[0]
+            r = measure_residual(sc, "mixed", device, stream, flush, max(20, rsteps // 2), args.warmup, peak)[0]
             out[str(1 << e)] = {"cells_per_s": r["cells_per_s"], "alg_gbs": r["alg_gbs"],
                                 "hbm_frac_of_measured": r["hbm_frac_of_measured"], "ms": r["ms_per_launch"]}
         return out

@@ -155,8 +155,9 @@ __global__ void __launch_bounds__(kBlock) lap_geom_kernel(const __grid_constant_
 template <int DIM, int P>
 static fem_status launch_geom_lap(const LapGeomArgs &a, bool vec, cudaStream_t s) {
     if (vec && a.w.nq == DIM + 1) {
+        // one wave of resident CTAs (24.5 against 24.7 us per step with up to 8 waves)
         auto k = lap_geom_kernel<DIM, P, 4, DIM + 1>;
-        launch_overlapped(k, grid_for((a.C + 3) / 4, kBlock, reinterpret_cast<const void *>(k)), kBlock, 0, s, a);
+        launch_overlapped(k, resident_grid(reinterpret_cast<const void *>(k), kBlock, (a.C + 3) / 4), kBlock, 0, s, a);
     } else if (vec) {
         auto k = lap_geom_kernel<DIM, P, 4, 0>;
         launch_overlapped(k, grid_for((a.C + 3) / 4, kBlock, reinterpret_cast<const void *>(k)), kBlock, 0, s, a);

@@ -393,8 +393,11 @@ static fem_status launch_fields(const FieldsArgs &fa, bool vec, cudaStream_t s) 
     constexpr int CPTV = P == FEM_FP64 ? 2 : 4;
     constexpr int NQN = DIM == 3 ? 4 : 3;  // the workloads' rules
     if (vec && fa.a.w.nq == NQN) {
+        // float32 forms: one wave of resident CTAs (8 fields: 69.5 -> 68.0 us per step)
         auto k = lap_fields_kernel<DIM, P, CPTV, NQN>;
-        launch_overlapped(k, grid_for((fa.a.C + CPTV - 1) / CPTV, kBlock, reinterpret_cast<const void *>(k)), kBlock, 0, s, fa);
+        const int64_t n = (fa.a.C + CPTV - 1) / CPTV;
+        const void *kp = reinterpret_cast<const void *>(k);
+        launch_overlapped(k, P == FEM_FP64 ? grid_for(n, kBlock, kp) : resident_grid(kp, kBlock, n), kBlock, 0, s, fa);
     } else {
         auto k = lap_fields_kernel<DIM, P, 1, 0>;
         launch_overlapped(k, grid_for(fa.a.C, kBlock, reinterpret_cast<const void *>(k)), kBlock, 0, s, fa);
