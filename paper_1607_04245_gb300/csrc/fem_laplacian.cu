@@ -514,7 +514,7 @@ __device__ __forceinline__ void lap_pair(const double *const (&X)[DIM], const ui
 // that overlap the previous kernel's tail and steps back to back, the mixed residual took
 // 23.2 us against 23.5 us at 4 CTAs (64 registers) on the 1,572,864-tet workload, and 106.5
 // against 108.8 us on 2^23 cells; 2 CTAs (118 registers) took 27.2 us. The float32
-// ablation, without the coordinate splits, keeps 4 (3 took 25.3 against 23.7 us).
+// ablation, without the coordinate splits, keeps 4 (3 took 23.1 against 21.9 us).
 template <int P, bool ADJ>
 constexpr int pair_min_blocks() { return (P == FEM_FP32 && !ADJ) ? 4 : 3; }
 
