@@ -154,3 +154,40 @@ def test_prepare_option_launches_the_plain_call():
         torch.cuda.synchronize()
         for k in o1:
             assert torch.equal(o1[k], o2[k]), (name, k)
+
+
+def test_run_time_compiled_kernel_in_an_unsynchronised_chain():
+    """The kernel fem_integrate_pointwise generates also waits for the kernel before it: a
+    chain of its residuals and assemblies with no synchronisation equals the synchronised
+    chain bitwise."""
+    case = workloads.laplacian_cube_case(196608).rounded_to_f32()
+    f32 = torch.float32
+    coords, conn = to_dev(case.mesh.coords, torch.float64), to_dev(case.mesh.conn, torch.int32)
+    V, q = case.n_verts, case.rule
+    K = to_dev(case.K, f32)[None].contiguous()
+    ptr, idx = fem.fem_build_node2cell(conn, V)
+    f1 = "for (int i = 0; i < DIM; ++i) f1[i] = a[0] * grad_u[i];"
+
+    def chain(sync):
+        u = to_dev(case.u, f32).reshape(1, V)
+        fields = [u]
+        elem = torch.empty((4, case.n_cells), dtype=f32, device="cuda")
+        torch.cuda.synchronize()
+        for _ in range(STEPS):
+            fem.fem_integrate_pointwise(coords, conn, fields[-1][0], K, q.points, q.weights, f1=f1, out=elem,
+                                        prec="mixed")
+            if sync:
+                torch.cuda.synchronize()
+            nxt = torch.empty((1, V), dtype=f32, device="cuda")
+            fem.fem_gather_nodes(elem, ptr, idx, V, 3, out=nxt, prec="mixed")
+            if sync:
+                torch.cuda.synchronize()
+            fields.append(nxt)
+        torch.cuda.synchronize()
+        return fields
+
+    a, b = chain(False), chain(True)
+    assert fem.fem_device_error() == 0
+    for i, (x, y) in enumerate(zip(a, b)):
+        assert torch.equal(x, y), i
+    assert not torch.equal(a[-1], a[-2])
