@@ -191,3 +191,50 @@ def test_run_time_compiled_kernel_in_an_unsynchronised_chain():
     for i, (x, y) in enumerate(zip(a, b)):
         assert torch.equal(x, y), i
     assert not torch.equal(a[-1], a[-2])
+
+
+@pytest.mark.parametrize("kind", ("geom", "reaction", "prepared"))
+def test_other_overlapped_kernels_in_an_unsynchronised_chain(kind):
+    """The precomputed-geometry, reaction-diffusion and prepared-record kernels in a
+    dependent chain with the gather kernel, unsynchronised against synchronised."""
+    case = workloads.laplacian_cube_case(196608).rounded_to_f32()
+    f32 = torch.float32
+    coords, conn = to_dev(case.mesh.coords, torch.float64), to_dev(case.mesh.conn, torch.int32)
+    V, C, q = case.n_verts, case.n_cells, case.rule
+    K = to_dev(case.K, f32)
+    ptr, idx = fem.fem_build_node2cell(conn, V)
+    geom = fem.fem_precompute_geometry(coords, conn)
+    rec = fem.fem_prepare_vertices(coords)
+    a = torch.linspace(0.5, 2.0, V, device="cuda", dtype=f32)
+    cr = torch.linspace(0.25, 1.0, q.n_q * C, device="cuda", dtype=f32).reshape(q.n_q, C)
+
+    def step(v, out):
+        if kind == "geom":
+            fem.fem_integrate_laplacian_geom(conn, V, v, K, q.points, q.weights, geom, out=out)
+        elif kind == "reaction":
+            fem.fem_integrate_reaction_diffusion(coords, conn, v, a, q.points, q.weights, c=cr, a_space=1,
+                                                 drift=1.0, out=out)
+        else:
+            fem.fem_integrate_laplacian_prepared(coords, rec, conn, v, K, q.points, q.weights, out=out)
+
+    def chain(sync):
+        fields = [to_dev(case.u, f32).reshape(1, V)]
+        elem = torch.empty((4, C), dtype=f32, device="cuda")
+        torch.cuda.synchronize()
+        for _ in range(STEPS):
+            step(fields[-1][0], elem)
+            if sync:
+                torch.cuda.synchronize()
+            nxt = torch.empty((1, V), dtype=f32, device="cuda")
+            fem.fem_gather_nodes(elem, ptr, idx, V, 3, out=nxt, prec="mixed")
+            if sync:
+                torch.cuda.synchronize()
+            fields.append(nxt)
+        torch.cuda.synchronize()
+        return fields
+
+    x, y = chain(False), chain(True)
+    assert fem.fem_device_error() == 0
+    for i, (p, r) in enumerate(zip(x, y)):
+        assert torch.equal(p, r), (kind, i)
+    assert not torch.equal(x[-1], x[-2])
