@@ -1420,7 +1420,7 @@ def run_ours(args):
         put("serving", lambda: measure_serving(device, args.serving_requests))
 
     try:
-        e2e = measure_e2e(case, "mixed", device, max(3, args.steps // 100), 3)
+        e2e = measure_e2e(case, "mixed", device, max(20, args.steps // 100), 3)
     except Exception as exc:  # noqa: BLE001 -- reported in the line and on stderr
         print(f"bench: e2e failed: {exc!r}", file=sys.stderr)
         e2e = {"error": repr(exc)[:300]}
