@@ -327,3 +327,18 @@ def test_pcg_elasticity_validation(lib):
     # three components per vertex: the vectors are three times the Laplacian solve's
     assert lib.fem_pcg_elasticity_work_bytes(3, 1000, 300, 0) > lib.fem_pcg_work_bytes(3, 1000, 300, 0)
     assert lib.fem_pcg_elasticity_work_bytes(4, 1000, 300, 0) == -1
+
+
+def test_prepared_call_repeats_the_c_call_and_reports_its_status(lib):
+    """A PreparedCall converts its arguments to ctypes values once and makes the same C
+    call each time it is called; a failing status raises FemError every time (here the
+    host-side check of dim, before any device work)."""
+    from paper_1607_04245_gb300 import binding
+
+    args = (4, 10, 10, None, None, None, None, 4, None, None, None, binding.FEM_FP32_MIXED, None)
+    pc = binding.PreparedCall("fem_integrate_laplacian", args, keep=())
+    assert all(isinstance(x, ctypes._SimpleCData) for x in pc._args)
+    for _ in range(2):
+        with pytest.raises(binding.FemError) as e:
+            pc()
+        assert e.value.status == -1 and "dim" in str(e.value)
